@@ -1,0 +1,289 @@
+#!/usr/bin/env python
+"""Throughput of the hard-sphere lattice Boltzmann step on one GB300.
+
+Workload: a 512 x 512 x 192 slit, sigma = 12, eta = 0.25, tau = 0.7,
+F_e = 5e-7 (bounce-back walls in z, periodic x, y), FP32 compute, populations
+stored as FP32 deviations (``--storage f16`` for FP16 deviations). One step =
+moments -> ball average + g2 -> shell force + BGK collision + streaming.
+The populations (3.8 GB FP32) exceed the 129 MB L2, so no flush is needed.
+
+Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+on the host cores on a bounded sample of the same workload instead.
+Multi-GPU (torchrun): independent replicas, one slit per GPU (the slit does
+not shard in this build), max time over ranks, weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS incl. Enskog force, % HBM roofline; time-to-steady-state warm vs cold"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([s.strip() for s in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if len(s) > 3 + k and s[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def bytes_alg(storage: int):
+    """Algorithmic bytes per node per step: populations in and out once
+    (2 x 19 x s_pop) plus the nonlocal fields written once and read once
+    (n,u out 16, n in 4, g2 out 4, n,u,g2 in 20 = 44)."""
+    s = 2 if storage == 1 else 4
+    return 2 * 19 * s + 44
+
+
+def bytes_fcs(storage: int):
+    """Algorithmic bytes per node of the fused force + collide + stream kernel:
+    19 populations read and written, {dn,u} (16 B) and dG (4 B) read once."""
+    s = 2 if storage == 1 else 4
+    return 2 * 19 * s + 20
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def cpu_sample(steps_hint: float = 15.0):
+    """Time the FP64 oracle on a bounded sample of the workload (all host cores)."""
+    import oracle
+    from paper_0712_2247_gb300.inputs import C2
+
+    W = C2
+    nx = ny = 64
+    o = oracle.Oracle(nx, ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, seed=W.seed)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter()
+    per = t1 - t0
+    k = max(1, min(20, int(steps_hint / max(per, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    nodes = nx * ny * W.nz
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": nodes * k / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {nx}x{ny}x{W.nz} slit of the same sigma/eta/tau/F_e, "
+                      f"{k} steps after 1 untimed, {dt:.1f} s"}, dt, k, nodes
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    steps, warm = args.steps, args.warmup
+    import oracle
+    from paper_0712_2247_gb300.inputs import C2
+
+    W = C2
+    nx = ny = 32
+    o = oracle.Oracle(nx, ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, seed=W.seed)
+    o.step(warm)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    nodes = nx * ny * W.nz
+    v = nodes * steps / dt / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
+            "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "slit 512x512x192 sigma=12 eta=0.25 tau=0.7 F_e=5e-7 "
+                                   "(oracle sample 32x32x192 per step)", "storage": "f64"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{nx}x{ny}x{W.nz} slit per step, {steps} steps"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    from paper_0712_2247_gb300 import build, lbif
+    from paper_0712_2247_gb300.inputs import c2
+
+    build.build()
+    storage = 1 if args.storage == "f16" else 0
+    W = c2(args.eta, storage)
+    stream = torch.cuda.current_stream()
+    g = lbif.Slit(W.nx, W.ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, storage=storage,
+                  seed=W.seed + rank, stream=stream.cuda_stream)
+    N = W.nodes
+    # warm-up
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        kms, nl = g.step_profiled(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.barrier()
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    mlups = world * N / (ms_per_step * 1e-3) / 1e6
+    status = g.status()
+
+    # dominant kernel roofline (force + collide + stream), live CUDA-event timing
+    peak, peak_kind = _peaks()
+    dom = max(kms, key=lambda k: kms[k])
+    launches = sum(nl.values())
+    fcs_ms = kms["force_collide_stream"] / max(nl["force_collide_stream"], 1)
+    dom_bytes = {"force_collide_stream": bytes_fcs(storage) * N,
+                 "moments": (19 * (2 if storage else 4) + 20) * N,
+                 "ball_g2": 8 * N, "tail": 16 * N}[dom]
+    dom_ms = kms[dom] / max(nl[dom], 1)
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+    step_gbs = bytes_alg(storage) * N / (ms_per_step * 1e-3) / 1e9
+
+    # end to end through the C ABI with host buffers: per iteration upload the
+    # density field from pinned host memory, run S steps, read the profiles back
+    S = 10
+    rho_h = torch.empty(W.nz * W.ny * W.nx, dtype=torch.float32, pin_memory=True)
+    rho_h.fill_(float(g.n0))
+    rho_np = rho_h.numpy().reshape(W.nz, W.ny, W.nx)
+    iters = max(1, args.steps // S)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        g.set_fields(rho_np)
+        g.step(S)
+        g.profiles(allow_diverged=True)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * N * S * iters / e2e_s / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": 4 * N / S, "d2h_bytes_per_step": 5 * 8 * W.nz / S,
+           "note": f"per iteration: {4 * N} B density upload (pinned), {S} steps, FP64 profile readback"}
+    g.close()
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu, _, _, _ = cpu_sample(args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"slit {W.nx}x{W.ny}x{W.nz} sigma={W.sigma} eta={W.eta} tau={W.tau} "
+                               f"F_e={W.body[0]} bounce-back z, periodic x,y, seeded 1e-3 noise",
+                   "storage": args.storage, "nodes": N, "parallelism": f"replicas x{world}",
+                   "l2": "populations (>= 1.9 GB) exceed L2; no flush",
+                   "bytes_alg_per_node": bytes_alg(storage),
+                   "step_gbs_alg": step_gbs, "step_roofline_frac": step_gbs / peak,
+                   "kernel_ms_per_step": {k: v / max(nl[k], 1) for k, v in kms.items() if nl[k]},
+                   "status": status},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind + " hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "bytes_alg_per_launch": dom_bytes},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
+    ap.add_argument("--eta", type=float, default=0.25)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

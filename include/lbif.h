@@ -1,0 +1,147 @@
+/*
+ * lbif — lattice Boltzmann for inhomogeneous hard-sphere fluids, one GB300.
+ *
+ * C ABI of the per-time-step hot path of Melchionna & Marconi, "Lattice
+ * Boltzmann method for inhomogeneous fluids" (EPL 2008). Every entry point
+ * takes plain pointers and sizes; no C++ or torch type crosses it.
+ *
+ * Conventions shared by all calls
+ *   - Grid: nx * ny * nz nodes, node index idx = (z * ny + y) * nx + x
+ *     (x fastest). x and y are periodic; z is periodic or bounded by two
+ *     half-way bounce-back walls at z = -1/2 and z = nz - 1/2 (all nz nodes
+ *     are fluid). Lattice units: spacing 1, time step 1, m = 1,
+ *     k_B T = v_T^2 = c_s^2 = 1/3.
+ *   - sigma (hard-sphere diameter) is an even integer number of lattice
+ *     spacings (Sec. Methods: "sigma an even multiple of the lattice
+ *     spacing"); odd or non-integer sigma returns LBIF_ERR_UNSUPPORTED.
+ *   - Ownership: a handle owns every device buffer it allocates; callers own
+ *     all buffers they pass in. Nothing returned aliases caller memory.
+ *   - Errors: every call returns 0 (LBIF_OK) or a negative LBIF_ERR_* code
+ *     and never aborts; lbif_last_error() gives a message. A divergence
+ *     (non-finite or non-positive density, coarse packing fraction >= 1)
+ *     is recorded in a device status word and reported as LBIF_ERR_DIVERGED
+ *     by the next synchronising call; it is sticky until destroy.
+ *   - Streams: work is enqueued on the stream given at creation (NULL = the
+ *     legacy default stream). lbif_step is asynchronous; calls that return
+ *     host data synchronise that stream.
+ *   - Determinism: no atomics on data paths; the same inputs give
+ *     bit-identical outputs.
+ */
+#ifndef LBIF_H
+#define LBIF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBIF_OK               0
+#define LBIF_ERR_ARG         -1  /* invalid argument */
+#define LBIF_ERR_NOMEM       -2  /* device or host allocation failed */
+#define LBIF_ERR_CUDA        -3  /* a CUDA runtime call failed */
+#define LBIF_ERR_DIVERGED    -4  /* the state became non-physical (sticky) */
+#define LBIF_ERR_TIMEOUT     -5  /* a bounded device wait ran out */
+#define LBIF_ERR_UNSUPPORTED -6  /* parameters outside what the method defines */
+#define LBIF_ERR_IO          -7  /* checkpoint file error */
+
+typedef struct lbif_ctx* lbif_handle; /* opaque, library-owned */
+
+typedef struct { int32_t nx, ny, nz; } lbif_grid;
+
+typedef enum { LBIF_WALL_BOUNCEBACK = 0, LBIF_PERIODIC = 1 } lbif_zbc;
+typedef struct { int32_t z; /* lbif_zbc */ } lbif_walls;
+
+/* Forces entering the collisional source (Eq. brey; C1 of Eq. LBHS). */
+typedef struct {
+    double  body[3];   /* F_e per particle (Eq. uno); force density n F_e   */
+    int32_t hs;        /* 1: hard-sphere shell force of Eq. LBHS           */
+    int32_t coupling;  /* 1: density-current term of Eq. LBHS              */
+    int32_t regularize;/* 1: (1 - exp(-|r - r_w|/sigma)) on that term      */
+    int32_t g2_form;   /* 0: g2 as printed in Sec. Methods; 1: Carnahan-Starling */
+    int32_t tail;      /* 1: Lennard-Jones mean-field attractive tail       */
+    double  eps;       /* tail well depth (k_B T = 1/3 units)               */
+    double  rcut;      /* tail cut-off in units of sigma                    */
+} lbif_force;
+
+#define LBIF_STORE_F32 0 /* populations stored as FP32 h_i = f_i/(w_i n0) - 1 */
+#define LBIF_STORE_F16 1 /* same deviations stored as FP16 (round to nearest)  */
+
+typedef struct {
+    int32_t  storage;  /* LBIF_STORE_F32 or LBIF_STORE_F16                     */
+    uint64_t seed;     /* initial density noise: n = n0 (1 + noise (2U - 1)),  */
+    double   noise;    /*   U from SplitMix64(seed ^ node index)                */
+    void*    stream;   /* cudaStream_t to enqueue on; NULL = default stream    */
+} lbif_opts;
+
+/* Create a slit (or periodic box) of packing fraction eta = pi sigma^3 n0/6
+ * with BGK relaxation time tau (> 1/2) and initialise the populations to the
+ * rest equilibrium of the seeded noisy density (Sec. Methods, local
+ * equilibrium; Sec. Methods, slit with bounce-back walls). f may be NULL
+ * (ideal fluid, no force); o may be NULL (FP32, seed 0, noise 1e-3, default
+ * stream). On success *out receives the handle. */
+int lbif_create(lbif_handle* out, lbif_grid g, double sigma, double eta, double tau,
+                lbif_walls w, const lbif_force* f, const lbif_opts* o);
+
+/* Advance nsteps forward-Euler LB updates (Sec. Methods, update of f_i):
+ * moments n, u = j/n; coarse-grained density and g2 field; the shell force
+ * of Eq. LBHS (plus body force and tail); BGK collision with source
+ * w_i c_i.F/c_s^2; streaming with bounce-back. Asynchronous. */
+int lbif_step(lbif_handle h, int64_t nsteps);
+
+/* Same as lbif_step, and also times every kernel class with CUDA events
+ * recorded on the handle's stream between launches: kernel_ms[k] receives
+ * the total milliseconds of class k over the nsteps (k = 0 moments, 1 ball +
+ * g2, 2 tail, 3 force + collide + stream; classes not launched get 0) and
+ * launches[k] the number of launches. nk = length of both arrays (>= 4).
+ * Synchronises at the end. Diagnostics for the benchmark. */
+int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches,
+                       int32_t nk);
+
+/* Density n (nx*ny*nz floats), velocity u (3 planes of nx*ny*nz floats,
+ * SoA: u_x then u_y then u_z) and local pressure p = k_B T n + the static
+ * collisional part (k_B T sigma^3/6) 4 pi sum_q W_q g2_q n n_q (bulk limit:
+ * Sec. Theory, p_bulk) of the current populations. Any pointer may be NULL.
+ * on_device = 1: pointers are device memory; 0: host memory. Synchronises. */
+int lbif_moments(lbif_handle h, float* rho, float* u, float* pressure, int32_t on_device);
+
+/* Total force density F / n0 (3 SoA planes) of the current state, as used by
+ * the next step (body + hard sphere + tail). Diagnostics; synchronises. */
+int lbif_forces(lbif_handle h, float* F, int32_t on_device);
+
+/* Re-initialise the populations to f_eq(n, u) of given fields (same layout
+ * as lbif_moments; u may be NULL = 0) and reset the step counter. */
+int lbif_set_fields(lbif_handle h, const float* rho, const float* u, int32_t on_device);
+
+/* FP64 x,y-averaged profiles n(z), u_x(z) (nz doubles each; either may be
+ * NULL), total mass and momentum (out4 = {M, Jx, Jy, Jz}; may be NULL), from
+ * a deterministic FP64 reduction on the device. Synchronises. */
+int lbif_profiles(lbif_handle h, double* n_z, double* ux_z, double* out4);
+
+/* Steady-state residual over the steps since the previous call:
+ *   R = max over {n(z), u_x(z)} of ||p(t) - p(t0)||_2 / ((t - t0) ||p(t)||_2),
+ * FP64; R = +inf on the first call. mass/mom may be NULL. Synchronises. */
+int lbif_residual(lbif_handle h, double* r, double* mass, double mom[3]);
+
+/* Steps taken since creation (or the last lbif_set_fields). */
+int lbif_time(lbif_handle h, int64_t* t);
+
+/* Device status word (0 = healthy; bit 0 divergence). Synchronises. */
+int lbif_status(lbif_handle h, int32_t* status);
+
+/* Checkpoint: write / read the populations (storage tag, grid, step count)
+ * to / from a host file. lbif_load requires a handle of the same grid,
+ * sigma and storage. */
+int lbif_save(lbif_handle h, const char* path);
+int lbif_load(lbif_handle h, const char* path);
+
+int lbif_destroy(lbif_handle h);
+
+/* Message of the last error of a handle; NULL handle = last global error
+ * (e.g. of a failed lbif_create). Never NULL. */
+const char* lbif_last_error(lbif_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBIF_H */

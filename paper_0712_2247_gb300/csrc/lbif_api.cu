@@ -1,0 +1,665 @@
+// Host side of the C ABI declared in include/lbif.h: argument checks, the
+// quadrature / ball / tail tables (built in FP64, rounded once to FP32),
+// device allocation and the per-step launch sequence.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "lbif_internal.h"
+
+using namespace lbif;
+
+struct lbif_ctx {
+    Params P;
+    cudaStream_t stream = nullptr;
+    void* pop[2] = {nullptr, nullptr};
+    int cur = 0;
+    float4* M = nullptr;
+    float* dn = nullptr;
+    float* dG = nullptr;
+    float4* Ft = nullptr;
+    int* tail_off = nullptr;
+    float4* tail_K = nullptr;
+    int tail_pairs = 0;
+    int* status_d = nullptr;
+    double* prof_d = nullptr;
+    float* scratch = nullptr;  // 3 N floats, for host-side outputs
+    int64_t t = 0;
+    // residual bookkeeping
+    std::vector<double> last_n, last_ux;
+    int64_t last_t = -1;
+    int sticky = 0;
+    std::string err;
+};
+
+static thread_local std::string g_err = "no error";
+
+static int fail(lbif_ctx* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    g_err = msg;
+    return code;
+}
+
+#define CK(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), LBIF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static size_t pop_bytes(const Params& P) { return (P.storage == LBIF_STORE_F16 ? 2 : 4); }
+
+static void free_ctx(lbif_ctx* h)
+{
+    if (!h) return;
+    void* bufs[] = {h->pop[0], h->pop[1], h->M,        h->dn,     h->dG,      h->Ft,
+                    h->tail_off, h->tail_K, h->status_d, h->prof_d, h->scratch};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete h;
+}
+
+// --------------------------------------------------------------------------
+// tables
+// --------------------------------------------------------------------------
+static int padded_offset(const Geom& g, int dx, int dy, int dz)
+{
+    return (dz * g.py + dy) * g.px + dx;
+}
+
+// Linear interpolation stencil of the point s (lattice units) relative to a
+// node: the corners of the axes with a fractional part, with their weights.
+static int interp_stencil(const Geom& g, const double s[3], int off[4], float w[4])
+{
+    int b[3];
+    double t[3];
+    int frac_axes[3], nf = 0;
+    for (int a = 0; a < 3; ++a) {
+        double r = nearbyint(s[a]);
+        if (fabs(s[a] - r) < 1e-12) {
+            b[a] = (int)r;
+            t[a] = 0.0;
+        } else {
+            b[a] = (int)floor(s[a]);
+            t[a] = s[a] - b[a];
+            frac_axes[nf++] = a;
+        }
+    }
+    if (nf > 2) return -1;
+    int n = 1 << nf;
+    for (int c = 0; c < n; ++c) {
+        int d[3] = {b[0], b[1], b[2]};
+        double wt = 1.0;
+        for (int k = 0; k < nf; ++k) {
+            int a = frac_axes[k];
+            int bit = (c >> k) & 1;
+            d[a] += bit;
+            wt *= bit ? t[a] : 1.0 - t[a];
+        }
+        off[c] = padded_offset(g, d[0], d[1], d[2]);
+        w[c] = (float)wt;
+    }
+    return n;
+}
+
+// 18-point sphere rule (6 axis points, weight 1/30; 12 face diagonals,
+// weight 1/15), ordered in antipodal pairs; the second of a pair mirrors the
+// first's stencil so a uniform field cancels exactly.
+static int build_shell(Params& P)
+{
+    const Geom& g = P.g;
+    double dirs[9][3];
+    double wts[9];
+    int k = 0;
+    for (int a = 0; a < 3; ++a) {
+        dirs[k][0] = dirs[k][1] = dirs[k][2] = 0.0;
+        dirs[k][a] = 1.0;
+        wts[k++] = 1.0 / 30.0;
+    }
+    const double h = 1.0 / sqrt(2.0);
+    for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b)
+            for (int sb = 1; sb >= -1; sb -= 2) {
+                dirs[k][0] = dirs[k][1] = dirs[k][2] = 0.0;
+                dirs[k][a] = h;
+                dirs[k][b] = sb * h;
+                wts[k++] = 1.0 / 15.0;
+            }
+    for (int j = 0; j < 9; ++j) {
+        ShellPoint& sp = P.sp[2 * j];
+        ShellPoint& sm = P.sp[2 * j + 1];
+        double s[3], m[3];
+        for (int a = 0; a < 3; ++a) {
+            s[a] = P.sigma * dirs[j][a];
+            m[a] = 0.5 * P.sigma * dirs[j][a];
+            sp.dir[a] = (float)dirs[j][a];
+            sm.dir[a] = -(float)dirs[j][a];
+        }
+        sp.w = sm.w = (float)wts[j];
+        sp.nnb = interp_stencil(g, s, sp.nb_off, sp.nb_w);
+        sp.nmd = interp_stencil(g, m, sp.md_off, sp.md_w);
+        if (sp.nnb < 0 || sp.nmd < 0) return -1;
+        sm.nnb = sp.nnb;
+        sm.nmd = sp.nmd;
+        for (int c = 0; c < 4; ++c) {
+            sm.nb_off[c] = -sp.nb_off[c];
+            sm.nb_w[c] = sp.nb_w[c];
+            sm.md_off[c] = -sp.md_off[c];
+            sm.md_w[c] = sp.md_w[c];
+        }
+    }
+    return 0;
+}
+
+// ball |d|^2 <= (sigma/2)^2 as x-row segments
+static int build_ball(Params& P)
+{
+    int r = P.sigma / 2, n = 0, count = 0;
+    for (int dz = -r; dz <= r; ++dz)
+        for (int dy = -r; dy <= r; ++dy) {
+            int rem = r * r - dy * dy - dz * dz;
+            if (rem < 0) continue;
+            int w = 0;
+            while ((w + 1) * (w + 1) <= rem) ++w;
+            if (n >= MAX_SEG) return -1;
+            P.seg_off[n] = padded_offset(P.g, -w, dy, dz);
+            P.seg_len[n] = 2 * w + 1;
+            count += 2 * w + 1;
+            ++n;
+        }
+    P.nseg = n;
+    P.ball_inv = (float)(1.0 / count);
+    return 0;
+}
+
+static double g2_host(double e, int form)
+{
+    double d = (1 - e) * (1 - e) * (1 - e);
+    return form == 1 ? (1 - 0.5 * e) / d : (1 - 0.5 * e + 0.25 * e * e) / d;
+}
+
+// --------------------------------------------------------------------------
+// create / destroy
+// --------------------------------------------------------------------------
+extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double eta, double tau,
+                           lbif_walls w, const lbif_force* f, const lbif_opts* o)
+{
+    if (!out) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: out is NULL");
+    *out = nullptr;
+    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1)
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: grid extents must be >= 1");
+    if (!(sigma >= 2.0) || sigma != floor(sigma) || ((int)sigma) % 2 != 0 || sigma > MAX_SIGMA)
+        return fail(nullptr, LBIF_ERR_UNSUPPORTED,
+                    "lbif_create: sigma must be an even integer in [2, 24] lattice spacings");
+    if (!(eta > 0.0 && eta < 1.0)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: eta must be in (0,1)");
+    if (!(tau > 0.5)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: tau must be > 1/2");
+    if (w.z != LBIF_WALL_BOUNCEBACK && w.z != LBIF_PERIODIC)
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: walls.z must be BOUNCEBACK or PERIODIC");
+    lbif_force fz;
+    memset(&fz, 0, sizeof(fz));
+    const lbif_force& F = f ? *f : fz;
+    lbif_opts oz;
+    memset(&oz, 0, sizeof(oz));
+    oz.noise = 1e-3;
+    const lbif_opts& O = o ? *o : oz;
+    if (O.storage != LBIF_STORE_F32 && O.storage != LBIF_STORE_F16)
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: storage must be 0 (FP32) or 1 (FP16)");
+    if (!(O.noise >= 0.0 && O.noise < 1.0)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: noise must be in [0,1)");
+    if (F.tail && !(F.rcut >= 1.0 && F.rcut <= 4.0 && F.eps >= 0.0))
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: tail needs rcut in [1,4] and eps >= 0");
+    if ((F.g2_form != 0 && F.g2_form != 1))
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: g2_form must be 0 or 1");
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(F.body[a])) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: body force not finite");
+
+    lbif_ctx* h = new lbif_ctx();
+    memset(&h->P, 0, sizeof(Params));
+    Params& P = h->P;
+    int s = (int)sigma;
+    Geom& g = P.g;
+    g.nx = gr.nx;
+    g.ny = gr.ny;
+    g.nz = gr.nz;
+    g.zper = (w.z == LBIF_PERIODIC);
+    g.hw = s;
+    if (F.tail) g.hw = std::max(g.hw, (int)ceil(F.rcut * s));
+    g.px = g.nx + 2 * g.hw;
+    g.py = g.ny + 2 * g.hw;
+    g.pz = g.nz + 2 * g.hw;
+    g.N = (long long)g.nx * g.ny * g.nz;
+    g.Npad = (g.N + 63) / 64 * 64;
+    g.P = (long long)g.px * g.py * g.pz;
+    if (g.P >= (1LL << 31)) {
+        delete h;
+        return fail(nullptr, LBIF_ERR_UNSUPPORTED, "lbif_create: padded grid exceeds 2^31 nodes");
+    }
+    const double kT = 1.0 / 3.0;
+    double n0 = 6.0 * eta / (M_PI * sigma * sigma * sigma);
+    P.sigma = s;
+    P.inv_tau = (float)(1.0 / tau);
+    P.rho0 = (float)n0;
+    P.eta0 = (float)eta;
+    P.G0 = (float)g2_host(eta, F.g2_form);
+    P.hs_pref = (float)(-kT * sigma * sigma * 4.0 * M_PI * n0);
+    P.p_pref = (float)(kT * sigma * sigma * sigma / 6.0 * 4.0 * M_PI * n0 * n0);
+    P.kappa = (float)(2.0 / (sqrt(kT) * sqrt(M_PI)));
+    P.inv_sigma = (float)(1.0 / sigma);
+    for (int a = 0; a < 3; ++a) P.body[a] = (float)F.body[a];
+    P.hs = F.hs ? 1 : 0;
+    P.coupling = F.coupling ? 1 : 0;
+    P.regularize = F.regularize ? 1 : 0;
+    P.g2form = F.g2_form;
+    P.tail = F.tail ? 1 : 0;
+    P.storage = O.storage;
+    if (build_ball(P) || build_shell(P)) {
+        delete h;
+        return fail(nullptr, LBIF_ERR_UNSUPPORTED, "lbif_create: quadrature tables do not fit");
+    }
+    h->stream = (cudaStream_t)O.stream;
+
+    // tail taps: one representative of each +-d pair with sigma <= |d| <= rcut sigma
+    std::vector<int> toff;
+    std::vector<float4> tK;
+    if (P.tail) {
+        double rmax = F.rcut * sigma;
+        int R = (int)ceil(rmax);
+        double s6 = pow(sigma, 6.0), s12 = s6 * s6;
+        for (int dz = 0; dz <= R; ++dz)
+            for (int dy = (dz == 0 ? 0 : -R); dy <= R; ++dy)
+                for (int dx = ((dz == 0 && dy == 0) ? 1 : -R); dx <= R; ++dx) {
+                    double r2 = (double)dx * dx + (double)dy * dy + (double)dz * dz;
+                    if (r2 < sigma * sigma || r2 > rmax * rmax) continue;
+                    double r = sqrt(r2);
+                    double dphi = 4.0 * F.eps * (-12.0 * s12 / pow(r, 13.0) + 6.0 * s6 / pow(r, 7.0));
+                    toff.push_back(padded_offset(g, dx, dy, dz));
+                    tK.push_back(make_float4((float)(dphi * dx / r), (float)(dphi * dy / r),
+                                             (float)(dphi * dz / r), 0.f));
+                }
+        h->tail_pairs = (int)toff.size();
+    }
+
+    size_t pb = pop_bytes(P) * (size_t)Q * (size_t)g.Npad;
+#define ALLOC(ptr, bytes)                                                                   \
+    do {                                                                                    \
+        if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                           \
+            cudaGetLastError();                                                             \
+            free_ctx(h);                                                                    \
+            return fail(nullptr, LBIF_ERR_NOMEM, "lbif_create: device allocation failed");  \
+        }                                                                                   \
+    } while (0)
+    ALLOC(h->pop[0], pb);
+    ALLOC(h->pop[1], pb);
+    ALLOC(h->M, sizeof(float4) * (size_t)g.P);
+    ALLOC(h->dn, sizeof(float) * (size_t)g.P);
+    ALLOC(h->dG, sizeof(float) * (size_t)g.P);
+    ALLOC(h->status_d, sizeof(int));
+    ALLOC(h->prof_d, sizeof(double) * 5 * (size_t)g.nz);
+    if (P.tail) {
+        ALLOC(h->Ft, sizeof(float4) * (size_t)g.N);
+        ALLOC(h->tail_off, sizeof(int) * toff.size());
+        ALLOC(h->tail_K, sizeof(float4) * tK.size());
+    }
+#undef ALLOC
+    lbif_ctx* hc = h;
+    CK(hc, cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
+    CK(hc, cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
+    CK(hc, cudaMemsetAsync(h->M, 0, sizeof(float4) * (size_t)g.P, h->stream));
+    CK(hc, cudaMemsetAsync(h->dn, 0, sizeof(float) * (size_t)g.P, h->stream));
+    CK(hc, cudaMemsetAsync(h->dG, 0, sizeof(float) * (size_t)g.P, h->stream));
+    CK(hc, cudaMemsetAsync(h->status_d, 0, sizeof(int), h->stream));
+    if (P.tail) {
+        CK(hc, cudaMemcpyAsync(h->tail_off, toff.data(), sizeof(int) * toff.size(),
+                               cudaMemcpyHostToDevice, h->stream));
+        CK(hc, cudaMemcpyAsync(h->tail_K, tK.data(), sizeof(float4) * tK.size(),
+                               cudaMemcpyHostToDevice, h->stream));
+    }
+    CK(hc, launch_fill_outside(P, h->M, h->dn, h->dG, h->stream));
+    CK(hc, launch_init_noise(P, h->pop[0], O.seed, O.noise, 0, h->stream));
+    CK(hc, cudaStreamSynchronize(h->stream));
+    *out = h;
+    return LBIF_OK;
+}
+
+extern "C" int lbif_destroy(lbif_handle h)
+{
+    if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_destroy: NULL handle");
+    cudaStreamSynchronize(h->stream);
+    free_ctx(h);
+    return LBIF_OK;
+}
+
+extern "C" const char* lbif_last_error(lbif_handle h)
+{
+    if (h) return h->err.empty() ? "no error" : h->err.c_str();
+    return g_err.c_str();
+}
+
+// --------------------------------------------------------------------------
+// stepping
+// --------------------------------------------------------------------------
+static int refresh_fields(lbif_ctx* h, bool want_G)
+{
+    const Params& P = h->P;
+    CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn, h->status_d, h->stream));
+    if (want_G) CK(h, launch_ball(P, h->dn, h->dG, h->status_d, h->stream));
+    if (P.tail) CK(h, launch_tail(P, h->dn, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
+    return LBIF_OK;
+}
+
+extern "C" int lbif_step(lbif_handle h, int64_t nsteps)
+{
+    if (!h || nsteps < 0) return fail(h, LBIF_ERR_ARG, "lbif_step: bad arguments");
+    const Params& P = h->P;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int rc = refresh_fields(h, P.hs != 0);
+        if (rc) return rc;
+        CK(h, launch_fcs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dG, h->Ft, h->stream));
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    return LBIF_OK;
+}
+
+extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_ms,
+                                  int64_t* launches, int32_t nk)
+{
+    if (!h || nsteps < 0 || !kernel_ms || !launches || nk < 4)
+        return fail(h, LBIF_ERR_ARG, "lbif_step_profiled: bad arguments");
+    const Params& P = h->P;
+    for (int k = 0; k < nk; ++k) {
+        kernel_ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    // one event before the first launch, then one after every launch
+    int per = 2 + (P.hs ? 1 : 0) + (P.tail ? 1 : 0);
+    std::vector<cudaEvent_t> ev((size_t)nsteps * per + 1);
+    std::vector<int> cls((size_t)nsteps * per);
+    for (auto& e : ev) CK(h, cudaEventCreate(&e));
+    size_t j = 0;
+    CK(h, cudaEventRecord(ev[0], h->stream));
+    for (int64_t s = 0; s < nsteps; ++s) {
+        CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn, h->status_d, h->stream));
+        cls[j] = 0;
+        CK(h, cudaEventRecord(ev[++j], h->stream));
+        if (P.hs) {
+            CK(h, launch_ball(P, h->dn, h->dG, h->status_d, h->stream));
+            cls[j] = 1;
+            CK(h, cudaEventRecord(ev[++j], h->stream));
+        }
+        if (P.tail) {
+            CK(h, launch_tail(P, h->dn, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
+            cls[j] = 2;
+            CK(h, cudaEventRecord(ev[++j], h->stream));
+        }
+        CK(h, launch_fcs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dG, h->Ft, h->stream));
+        cls[j] = 3;
+        CK(h, cudaEventRecord(ev[++j], h->stream));
+        h->cur ^= 1;
+        h->t += 1;
+    }
+    CK(h, cudaEventSynchronize(ev[j]));
+    for (size_t k = 0; k < j; ++k) {
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, ev[k], ev[k + 1]));
+        kernel_ms[cls[k]] += ms;
+        launches[cls[k]] += 1;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return LBIF_OK;
+}
+
+static int check_status(lbif_ctx* h)
+{
+    int st = 0;
+    CK(h, cudaMemcpyAsync(&st, h->status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (st) h->sticky |= st;
+    if (h->sticky)
+        return fail(h, LBIF_ERR_DIVERGED,
+                    (h->sticky & 2) ? "state diverged: coarse-grained packing fraction reached 1"
+                                    : "state diverged: non-finite or non-positive density");
+    return LBIF_OK;
+}
+
+static int ensure_scratch(lbif_ctx* h)
+{
+    if (h->scratch) return LBIF_OK;
+    if (cudaMalloc((void**)&h->scratch, sizeof(float) * 3 * (size_t)h->P.g.N) != cudaSuccess) {
+        cudaGetLastError();
+        h->scratch = nullptr;
+        return fail(h, LBIF_ERR_NOMEM, "scratch allocation failed");
+    }
+    return LBIF_OK;
+}
+
+extern "C" int lbif_moments(lbif_handle h, float* rho, float* u, float* pressure, int32_t on_device)
+{
+    if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_moments: NULL handle");
+    const Params& P = h->P;
+    int rc = refresh_fields(h, pressure && P.hs);
+    if (rc) return rc;
+    size_t N = (size_t)P.g.N;
+    if (on_device) {
+        CK(h, launch_moments_out(P, h->M, h->dG, rho, u, pressure, h->stream));
+    } else {
+        if ((rc = ensure_scratch(h))) return rc;
+        float* d = h->scratch;
+        if (rho) {
+            CK(h, launch_moments_out(P, h->M, h->dG, d, nullptr, nullptr, h->stream));
+            CK(h, cudaMemcpyAsync(rho, d, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+        if (pressure) {
+            CK(h, launch_moments_out(P, h->M, h->dG, nullptr, nullptr, d, h->stream));
+            CK(h, cudaMemcpyAsync(pressure, d, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+        }
+        if (u) {
+            CK(h, launch_moments_out(P, h->M, h->dG, nullptr, d, nullptr, h->stream));
+            CK(h, cudaMemcpyAsync(u, d, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
+        }
+    }
+    return check_status(h);
+}
+
+extern "C" int lbif_forces(lbif_handle h, float* F, int32_t on_device)
+{
+    if (!h || !F) return fail(h, LBIF_ERR_ARG, "lbif_forces: bad arguments");
+    const Params& P = h->P;
+    int rc = refresh_fields(h, P.hs != 0);
+    if (rc) return rc;
+    if (on_device) {
+        CK(h, launch_force_out(P, h->M, h->dG, h->Ft, F, h->stream));
+    } else {
+        if ((rc = ensure_scratch(h))) return rc;
+        CK(h, launch_force_out(P, h->M, h->dG, h->Ft, h->scratch, h->stream));
+        CK(h, cudaMemcpyAsync(F, h->scratch, sizeof(float) * 3 * (size_t)P.g.N,
+                              cudaMemcpyDeviceToHost, h->stream));
+    }
+    return check_status(h);
+}
+
+extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, int32_t on_device)
+{
+    if (!h || !rho) return fail(h, LBIF_ERR_ARG, "lbif_set_fields: bad arguments");
+    const Params& P = h->P;
+    size_t N = (size_t)P.g.N;
+    const float* drho = rho;
+    const float* du = u;
+    if (!on_device) {
+        int rc = ensure_scratch(h);
+        if (rc) return rc;
+        // rho in plane 0; u needs 3 planes, so set it up in two passes when present
+        float* d = h->scratch;
+        if (u) {
+            float* tmp = nullptr;
+            if (cudaMalloc((void**)&tmp, sizeof(float) * N) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, LBIF_ERR_NOMEM, "lbif_set_fields: allocation failed");
+            }
+            cudaError_t e1 = cudaMemcpyAsync(tmp, rho, sizeof(float) * N, cudaMemcpyHostToDevice, h->stream);
+            cudaError_t e2 = cudaMemcpyAsync(d, u, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->stream);
+            cudaError_t e3 = launch_init_fields(P, h->pop[h->cur], tmp, d, h->stream);
+            cudaError_t e4 = cudaStreamSynchronize(h->stream);
+            cudaFree(tmp);
+            if (e1 || e2 || e3 || e4) return fail(h, LBIF_ERR_CUDA, "lbif_set_fields: copy/launch failed");
+            h->t = 0;
+            h->last_t = -1;
+            return LBIF_OK;
+        }
+        CK(h, cudaMemcpyAsync(d, rho, sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
+        drho = d;
+        du = nullptr;
+    }
+    CK(h, launch_init_fields(P, h->pop[h->cur], drho, du, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->t = 0;
+    h->last_t = -1;
+    return LBIF_OK;
+}
+
+extern "C" int lbif_profiles(lbif_handle h, double* n_z, double* ux_z, double* out4)
+{
+    if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_profiles: NULL handle");
+    const Params& P = h->P;
+    int nz = P.g.nz;
+    CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn, h->status_d, h->stream));
+    CK(h, launch_profiles(P, h->M, h->prof_d, h->stream));
+    std::vector<double> prof((size_t)nz * 5);
+    CK(h, cudaMemcpyAsync(prof.data(), h->prof_d, sizeof(double) * prof.size(),
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    double A = (double)P.g.nx * P.g.ny;
+    double n0 = (double)P.rho0;
+    double tot[4] = {0, 0, 0, 0};
+    for (int z = 0; z < nz; ++z) {
+        const double* r = &prof[(size_t)z * 5];
+        if (n_z) n_z[z] = n0 * (1.0 + r[0] / A);
+        if (ux_z) ux_z[z] = r[1] / A;
+        tot[0] += A + r[0];
+        tot[1] += r[2];
+        tot[2] += r[3];
+        tot[3] += r[4];
+    }
+    if (out4)
+        for (int k = 0; k < 4; ++k) out4[k] = n0 * tot[k];
+    return check_status(h);
+}
+
+extern "C" int lbif_residual(lbif_handle h, double* r, double* mass, double mom[3])
+{
+    if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_residual: NULL handle");
+    int nz = h->P.g.nz;
+    std::vector<double> n(nz), ux(nz);
+    double tot[4];
+    int rc = lbif_profiles(h, n.data(), ux.data(), tot);
+    double R = INFINITY;
+    if (h->last_t >= 0 && h->t > h->last_t) {
+        double K = (double)(h->t - h->last_t);
+        double worst = 0.0;
+        const std::vector<double>* cur[2] = {&n, &ux};
+        const std::vector<double>* old[2] = {&h->last_n, &h->last_ux};
+        for (int k = 0; k < 2; ++k) {
+            double dd = 0.0, pp = 0.0;
+            for (int z = 0; z < nz; ++z) {
+                double d = (*cur[k])[z] - (*old[k])[z];
+                dd += d * d;
+                pp += (*cur[k])[z] * (*cur[k])[z];
+            }
+            double v = pp > 0 ? sqrt(dd) / (K * sqrt(pp)) : (dd > 0 ? INFINITY : 0.0);
+            worst = fmax(worst, v);
+        }
+        R = worst;
+    }
+    h->last_n = n;
+    h->last_ux = ux;
+    h->last_t = h->t;
+    if (r) *r = R;
+    if (mass) *mass = tot[0];
+    if (mom) {
+        mom[0] = tot[1];
+        mom[1] = tot[2];
+        mom[2] = tot[3];
+    }
+    return rc;
+}
+
+extern "C" int lbif_time(lbif_handle h, int64_t* t)
+{
+    if (!h || !t) return fail(h, LBIF_ERR_ARG, "lbif_time: bad arguments");
+    *t = h->t;
+    return LBIF_OK;
+}
+
+extern "C" int lbif_status(lbif_handle h, int32_t* status)
+{
+    if (!h || !status) return fail(h, LBIF_ERR_ARG, "lbif_status: bad arguments");
+    int rc = check_status(h);
+    *status = h->sticky;
+    return rc == LBIF_ERR_DIVERGED ? LBIF_OK : rc;
+}
+
+// --------------------------------------------------------------------------
+// checkpoint
+// --------------------------------------------------------------------------
+struct CkptHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, sigma, storage;
+    int64_t t;
+};
+
+extern "C" int lbif_save(lbif_handle h, const char* path)
+{
+    if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_save: bad arguments");
+    const Params& P = h->P;
+    size_t es = pop_bytes(P);
+    size_t plane = es * (size_t)P.g.N;
+    std::vector<char> buf(plane * Q);
+    for (int i = 0; i < Q; ++i)
+        CK(h, cudaMemcpyAsync(buf.data() + plane * i, (char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i,
+                              plane, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    FILE* fp = fopen(path, "wb");
+    if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_save: cannot open ") + path);
+    CkptHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "LBIFCKP1", 8);
+    hd.version = 1;
+    hd.nx = P.g.nx;
+    hd.ny = P.g.ny;
+    hd.nz = P.g.nz;
+    hd.sigma = P.sigma;
+    hd.storage = P.storage;
+    hd.t = h->t;
+    bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    ok = (fclose(fp) == 0) && ok;
+    return ok ? LBIF_OK : fail(h, LBIF_ERR_IO, "lbif_save: write failed");
+}
+
+extern "C" int lbif_load(lbif_handle h, const char* path)
+{
+    if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_load: bad arguments");
+    const Params& P = h->P;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_load: cannot open ") + path);
+    CkptHeader hd;
+    size_t es = pop_bytes(P);
+    size_t plane = es * (size_t)P.g.N;
+    std::vector<char> buf(plane * Q);
+    bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "LBIFCKP1", 8) == 0 &&
+              hd.nx == P.g.nx && hd.ny == P.g.ny && hd.nz == P.g.nz && hd.sigma == P.sigma &&
+              hd.storage == P.storage && fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    fclose(fp);
+    if (!ok) return fail(h, LBIF_ERR_IO, "lbif_load: file does not match this handle");
+    for (int i = 0; i < Q; ++i)
+        CK(h, cudaMemcpyAsync((char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i, buf.data() + plane * i,
+                              plane, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->t = hd.t;
+    h->last_t = -1;
+    return LBIF_OK;
+}

@@ -1,0 +1,229 @@
+"""Thin ctypes binding of the C ABI in ``include/lbif.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``liblbif.so``. There is no CPU fallback; loading fails loudly when the library
+is missing or when no CUDA device is present at call time.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbif.so")
+
+LBIF_OK = 0
+ERRORS = {
+    -1: "LBIF_ERR_ARG", -2: "LBIF_ERR_NOMEM", -3: "LBIF_ERR_CUDA", -4: "LBIF_ERR_DIVERGED",
+    -5: "LBIF_ERR_TIMEOUT", -6: "LBIF_ERR_UNSUPPORTED", -7: "LBIF_ERR_IO",
+}
+STORE_F32, STORE_F16 = 0, 1
+
+# every function the header declares, with (restype, argtypes)
+_vp, _i32, _i64, _f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_pd = ctypes.POINTER(ctypes.c_double)
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Walls(ctypes.Structure):
+    _fields_ = [("z", ctypes.c_int32)]
+
+
+class Force(ctypes.Structure):
+    _fields_ = [("body", ctypes.c_double * 3), ("hs", ctypes.c_int32), ("coupling", ctypes.c_int32),
+                ("regularize", ctypes.c_int32), ("g2_form", ctypes.c_int32), ("tail", ctypes.c_int32),
+                ("eps", ctypes.c_double), ("rcut", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("seed", ctypes.c_uint64), ("noise", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+SIGNATURES = {
+    "lbif_create": (_i32, [ctypes.POINTER(_vp), Grid, _f64, _f64, _f64, Walls,
+                           ctypes.POINTER(Force), ctypes.POINTER(Opts)]),
+    "lbif_step": (_i32, [_vp, _i64]),
+    "lbif_step_profiled": (_i32, [_vp, _i64, _pd, ctypes.POINTER(_i64), _i32]),
+    "lbif_moments": (_i32, [_vp, _vp, _vp, _vp, _i32]),
+    "lbif_forces": (_i32, [_vp, _vp, _i32]),
+    "lbif_set_fields": (_i32, [_vp, _vp, _vp, _i32]),
+    "lbif_profiles": (_i32, [_vp, _pd, _pd, _pd]),
+    "lbif_residual": (_i32, [_vp, _pd, _pd, _pd]),
+    "lbif_time": (_i32, [_vp, ctypes.POINTER(_i64)]),
+    "lbif_status": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "lbif_save": (_i32, [_vp, ctypes.c_char_p]),
+    "lbif_load": (_i32, [_vp, ctypes.c_char_p]),
+    "lbif_destroy": (_i32, [_vp]),
+    "lbif_last_error": (ctypes.c_char_p, [_vp]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load ``liblbif.so`` (built by ``paper_0712_2247_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"lbif: CUDA library {path} is missing; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class LbifError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(a) -> Optional[int]:
+    """Device pointer of a torch tensor or host pointer of a numpy array (float32, contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float32 and a.flags.c_contiguous, "need contiguous float32"
+        return a.ctypes.data
+    assert a.is_contiguous() and str(a.dtype) == "torch.float32", "need contiguous float32"
+    return a.data_ptr()
+
+
+def _on_device(*arrays) -> int:
+    for a in arrays:
+        if a is not None:
+            return 0 if isinstance(a, np.ndarray) else int(a.is_cuda)
+    return 0
+
+
+class Slit:
+    """One slit (or periodic box) advanced on the GPU through the C ABI.
+
+    Arrays are (nz, ny, nx) with x fastest; host arrays are numpy float32, device
+    arrays are contiguous torch float32 CUDA tensors.
+    """
+
+    def __init__(self, nx: int, ny: int, nz: int, sigma: float, eta: float, tau: float, *,
+                 periodic_z: bool = False, body: Sequence[float] = (0.0, 0.0, 0.0), hs: bool = True,
+                 coupling: bool = True, regularize: bool = True, g2_form: int = 0,
+                 tail: bool = False, eps: float = 1.0, rcut: float = 2.5, storage: int = STORE_F32,
+                 seed: int = 0, noise: float = 1e-3, stream: Optional[int] = None):
+        self._lib = load_library()
+        f = Force((ctypes.c_double * 3)(*[float(b) for b in body]), int(hs), int(coupling),
+                  int(regularize), int(g2_form), int(tail), float(eps), float(rcut))
+        o = Opts(int(storage), int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), stream)
+        h = _vp()
+        rc = self._lib.lbif_create(ctypes.byref(h), Grid(nx, ny, nz), float(sigma), float(eta),
+                                   float(tau), Walls(1 if periodic_z else 0), ctypes.byref(f),
+                                   ctypes.byref(o))
+        if rc != LBIF_OK:
+            raise LbifError(rc, self._lib.lbif_last_error(None).decode())
+        self._h = h
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        self.sigma, self.eta, self.tau = sigma, eta, tau
+        self.n0 = 6.0 * eta / (np.pi * sigma ** 3)
+
+    # -- plumbing ---------------------------------------------------------
+    def _check(self, rc: int, allow_diverged: bool = False):
+        if rc != LBIF_OK and not (allow_diverged and rc == -4):
+            raise LbifError(rc, self._lib.lbif_last_error(self._h).decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbif_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- calls ------------------------------------------------------------
+    def step(self, nsteps: int = 1):
+        self._check(self._lib.lbif_step(self._h, int(nsteps)))
+
+    KERNEL_CLASSES = ("moments", "ball_g2", "tail", "force_collide_stream")
+
+    def step_profiled(self, nsteps: int):
+        """Advance nsteps and return ({class: total ms}, {class: launches})."""
+        ms = (ctypes.c_double * 4)()
+        nl = (ctypes.c_int64 * 4)()
+        self._check(self._lib.lbif_step_profiled(self._h, int(nsteps), ms, nl, 4))
+        return (dict(zip(self.KERNEL_CLASSES, ms[:])), dict(zip(self.KERNEL_CLASSES, nl[:])))
+
+    def moments(self, rho=None, u=None, pressure=None, allow_diverged=False):
+        """Fill caller-owned buffers; with no buffers, return numpy (rho, u) arrays."""
+        if rho is None and u is None and pressure is None:
+            rho = np.empty(self.shape, np.float32)
+            u = np.empty((3,) + self.shape, np.float32)
+            self._check(self._lib.lbif_moments(self._h, _ptr(rho), _ptr(u), None, 0), allow_diverged)
+            return rho, u
+        self._check(self._lib.lbif_moments(self._h, _ptr(rho), _ptr(u), _ptr(pressure),
+                                           _on_device(rho, u, pressure)), allow_diverged)
+        return rho, u, pressure
+
+    def pressure(self) -> np.ndarray:
+        p = np.empty(self.shape, np.float32)
+        self._check(self._lib.lbif_moments(self._h, None, None, _ptr(p), 0))
+        return p
+
+    def forces(self, out=None) -> np.ndarray:
+        """Total force density divided by n0, shape (3, nz, ny, nx)."""
+        F = np.empty((3,) + self.shape, np.float32) if out is None else out
+        self._check(self._lib.lbif_forces(self._h, _ptr(F), _on_device(F)))
+        return F
+
+    def set_fields(self, rho, u=None):
+        self._check(self._lib.lbif_set_fields(self._h, _ptr(rho), _ptr(u), _on_device(rho, u)))
+
+    def profiles(self, allow_diverged=False):
+        nz = self.shape[0]
+        n = np.empty(nz)
+        ux = np.empty(nz)
+        tot = np.empty(4)
+        pd = lambda a: a.ctypes.data_as(_pd)
+        self._check(self._lib.lbif_profiles(self._h, pd(n), pd(ux), pd(tot)), allow_diverged)
+        return n, ux, tot
+
+    def residual(self):
+        r, m = ctypes.c_double(), ctypes.c_double()
+        mom = (ctypes.c_double * 3)()
+        self._check(self._lib.lbif_residual(self._h, ctypes.byref(r), ctypes.byref(m), mom))
+        return r.value, m.value, np.array(mom[:])
+
+    @property
+    def t(self) -> int:
+        v = ctypes.c_int64()
+        self._check(self._lib.lbif_time(self._h, ctypes.byref(v)))
+        return v.value
+
+    def status(self) -> int:
+        v = ctypes.c_int32()
+        self._check(self._lib.lbif_status(self._h, ctypes.byref(v)))
+        return v.value
+
+    def save(self, path: str):
+        self._check(self._lib.lbif_save(self._h, path.encode()))
+
+    def load(self, path: str):
+        self._check(self._lib.lbif_load(self._h, path.encode()))
