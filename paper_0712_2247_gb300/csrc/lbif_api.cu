@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -16,9 +17,10 @@ struct lbif_ctx {
     Params P;
     cudaStream_t stream = nullptr;
     void* pop[2] = {nullptr, nullptr};
-    int cur = 0;
+    int cur = 0;                      // populations of the current step
+    float* dn[2] = {nullptr, nullptr};
+    int dcur = 0;                     // dn[dcur] = reference of pop[cur]
     float4* M = nullptr;
-    float* dn = nullptr;
     float* dG = nullptr;
     float4* Ft = nullptr;
     int* tail_off = nullptr;
@@ -26,9 +28,9 @@ struct lbif_ctx {
     int tail_pairs = 0;
     int* status_d = nullptr;
     double* prof_d = nullptr;
-    float* scratch = nullptr;  // 3 N floats, for host-side outputs
+    float* scratch = nullptr;         // 3 N floats, for host-side outputs
     int64_t t = 0;
-    // residual bookkeeping
+    int64_t fields_t = -1, G_t = -1, tail_t = -1;  // step the cached fields belong to
     std::vector<double> last_n, last_ux;
     int64_t last_t = -1;
     int sticky = 0;
@@ -56,12 +58,14 @@ static size_t pop_bytes(const Params& P) { return (P.storage == LBIF_STORE_F16 ?
 static void free_ctx(lbif_ctx* h)
 {
     if (!h) return;
-    void* bufs[] = {h->pop[0], h->pop[1], h->M,        h->dn,     h->dG,      h->Ft,
-                    h->tail_off, h->tail_K, h->status_d, h->prof_d, h->scratch};
+    void* bufs[] = {h->pop[0], h->pop[1], h->dn[0],  h->dn[1],    h->M,      h->dG,
+                    h->Ft,     h->tail_off, h->tail_K, h->status_d, h->prof_d, h->scratch};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete h;
 }
+
+static void invalidate(lbif_ctx* h) { h->fields_t = h->G_t = h->tail_t = -1; }
 
 // --------------------------------------------------------------------------
 // tables
@@ -72,7 +76,7 @@ static int padded_offset(const Geom& g, int dx, int dy, int dz)
 }
 
 // Linear interpolation stencil of the point s (lattice units) relative to a
-// node: the corners of the axes with a fractional part, with their weights.
+// node: the corners along the axes with a fractional part, with weights.
 static int interp_stencil(const Geom& g, const double s[3], int off[4], float w[4])
 {
     int b[3];
@@ -106,74 +110,46 @@ static int interp_stencil(const Geom& g, const double s[3], int off[4], float w[
     return n;
 }
 
-// 18-point sphere rule (6 axis points, weight 1/30; 12 face diagonals,
-// weight 1/15), ordered in antipodal pairs; the second of a pair mirrors the
-// first's stencil so a uniform field cancels exactly.
+// 18-point sphere rule: 6 axis points (weight 1/30) and the 12 face
+// diagonals (weight 1/15) as antipodal pairs (layout in lbif_internal.h)
 static int build_shell(Params& P)
 {
     const Geom& g = P.g;
-    double dirs[9][3];
-    double wts[9];
-    int k = 0;
+    const double sig = P.sigma;
     for (int a = 0; a < 3; ++a) {
-        dirs[k][0] = dirs[k][1] = dirs[k][2] = 0.0;
-        dirs[k][a] = 1.0;
-        wts[k++] = 1.0 / 30.0;
+        int e[3] = {0, 0, 0};
+        e[a] = 1;
+        P.sh.ax_nb[a] = padded_offset(g, P.sigma * e[0], P.sigma * e[1], P.sigma * e[2]);
+        int hh = P.sigma / 2;
+        P.sh.ax_md[a] = padded_offset(g, hh * e[0], hh * e[1], hh * e[2]);
     }
-    const double h = 1.0 / sqrt(2.0);
-    for (int a = 0; a < 3; ++a)
-        for (int b = a + 1; b < 3; ++b)
-            for (int sb = 1; sb >= -1; sb -= 2) {
-                dirs[k][0] = dirs[k][1] = dirs[k][2] = 0.0;
-                dirs[k][a] = h;
-                dirs[k][b] = sb * h;
-                wts[k++] = 1.0 / 15.0;
+    const double r2 = 1.0 / sqrt(2.0);
+    const int planes[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int pl = 0; pl < 3; ++pl)
+        for (int sb = 0; sb < 2; ++sb) {
+            int j = 2 * pl + sb;
+            double d[3] = {0, 0, 0};
+            d[planes[pl][0]] = r2;
+            d[planes[pl][1]] = sb ? -r2 : r2;
+            double s[3], m[3];
+            for (int a = 0; a < 3; ++a) {
+                s[a] = sig * d[a];
+                m[a] = 0.5 * sig * d[a];
             }
-    for (int j = 0; j < 9; ++j) {
-        ShellPoint& sp = P.sp[2 * j];
-        ShellPoint& sm = P.sp[2 * j + 1];
-        double s[3], m[3];
-        for (int a = 0; a < 3; ++a) {
-            s[a] = P.sigma * dirs[j][a];
-            m[a] = 0.5 * P.sigma * dirs[j][a];
-            sp.dir[a] = (float)dirs[j][a];
-            sm.dir[a] = -(float)dirs[j][a];
+            if (interp_stencil(g, s, P.sh.dg_nb_off[j], P.sh.dg_nb_w[j]) != 4) return -1;
+            if (interp_stencil(g, m, P.sh.dg_md_off[j], P.sh.dg_md_w[j]) != 4) return -1;
         }
-        sp.w = sm.w = (float)wts[j];
-        sp.nnb = interp_stencil(g, s, sp.nb_off, sp.nb_w);
-        sp.nmd = interp_stencil(g, m, sp.md_off, sp.md_w);
-        if (sp.nnb < 0 || sp.nmd < 0) return -1;
-        sm.nnb = sp.nnb;
-        sm.nmd = sp.nmd;
-        for (int c = 0; c < 4; ++c) {
-            sm.nb_off[c] = -sp.nb_off[c];
-            sm.nb_w[c] = sp.nb_w[c];
-            sm.md_off[c] = -sp.md_off[c];
-            sm.md_w[c] = sp.md_w[c];
-        }
-    }
     return 0;
 }
 
-// ball |d|^2 <= (sigma/2)^2 as x-row segments
-static int build_ball(Params& P)
+static int ball_count(int sigma)
 {
-    int r = P.sigma / 2, n = 0, count = 0;
+    int r = sigma / 2, c = 0;
     for (int dz = -r; dz <= r; ++dz)
-        for (int dy = -r; dy <= r; ++dy) {
-            int rem = r * r - dy * dy - dz * dz;
-            if (rem < 0) continue;
-            int w = 0;
-            while ((w + 1) * (w + 1) <= rem) ++w;
-            if (n >= MAX_SEG) return -1;
-            P.seg_off[n] = padded_offset(P.g, -w, dy, dz);
-            P.seg_len[n] = 2 * w + 1;
-            count += 2 * w + 1;
-            ++n;
-        }
-    P.nseg = n;
-    P.ball_inv = (float)(1.0 / count);
-    return 0;
+        for (int dy = -r; dy <= r; ++dy)
+            for (int dx = -r; dx <= r; ++dx)
+                if (dx * dx + dy * dy + dz * dz <= r * r) ++c;
+    return c;
 }
 
 static double g2_host(double e, int form)
@@ -248,6 +224,7 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     P.p_pref = (float)(kT * sigma * sigma * sigma / 6.0 * 4.0 * M_PI * n0 * n0);
     P.kappa = (float)(2.0 / (sqrt(kT) * sqrt(M_PI)));
     P.inv_sigma = (float)(1.0 / sigma);
+    P.ball_inv = (float)(1.0 / ball_count(s));
     for (int a = 0; a < 3; ++a) P.body[a] = (float)F.body[a];
     P.hs = F.hs ? 1 : 0;
     P.coupling = F.coupling ? 1 : 0;
@@ -255,7 +232,13 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     P.g2form = F.g2_form;
     P.tail = F.tail ? 1 : 0;
     P.storage = O.storage;
-    if (build_ball(P) || build_shell(P)) {
+    {
+        const int cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+        const int cy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+        const int cz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+        for (int i = 0; i < Q; ++i) P.nbr[i] = padded_offset(g, cx[i], cy[i], cz[i]);
+    }
+    if (build_shell(P)) {
         delete h;
         return fail(nullptr, LBIF_ERR_UNSUPPORTED, "lbif_create: quadrature tables do not fit");
     }
@@ -293,8 +276,9 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     } while (0)
     ALLOC(h->pop[0], pb);
     ALLOC(h->pop[1], pb);
+    ALLOC(h->dn[0], sizeof(float) * (size_t)g.P);
+    ALLOC(h->dn[1], sizeof(float) * (size_t)g.P);
     ALLOC(h->M, sizeof(float4) * (size_t)g.P);
-    ALLOC(h->dn, sizeof(float) * (size_t)g.P);
     ALLOC(h->dG, sizeof(float) * (size_t)g.P);
     ALLOC(h->status_d, sizeof(int));
     ALLOC(h->prof_d, sizeof(double) * 5 * (size_t)g.nz);
@@ -305,21 +289,32 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     }
 #undef ALLOC
     lbif_ctx* hc = h;
-    CK(hc, cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
-    CK(hc, cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
-    CK(hc, cudaMemsetAsync(h->M, 0, sizeof(float4) * (size_t)g.P, h->stream));
-    CK(hc, cudaMemsetAsync(h->dn, 0, sizeof(float) * (size_t)g.P, h->stream));
-    CK(hc, cudaMemsetAsync(h->dG, 0, sizeof(float) * (size_t)g.P, h->stream));
-    CK(hc, cudaMemsetAsync(h->status_d, 0, sizeof(int), h->stream));
+#define CKC(call)                                                                           \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            std::string m_ = std::string(#call) + ": " + cudaGetErrorString(e_);            \
+            free_ctx(hc);                                                                   \
+            return fail(nullptr, LBIF_ERR_CUDA, m_);                                        \
+        }                                                                                   \
+    } while (0)
+    CKC(cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
+    CKC(cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
+    CKC(cudaMemsetAsync(h->dn[0], 0, sizeof(float) * (size_t)g.P, h->stream));
+    CKC(cudaMemsetAsync(h->dn[1], 0, sizeof(float) * (size_t)g.P, h->stream));
+    CKC(cudaMemsetAsync(h->M, 0, sizeof(float4) * (size_t)g.P, h->stream));
+    CKC(cudaMemsetAsync(h->dG, 0, sizeof(float) * (size_t)g.P, h->stream));
+    CKC(cudaMemsetAsync(h->status_d, 0, sizeof(int), h->stream));
     if (P.tail) {
-        CK(hc, cudaMemcpyAsync(h->tail_off, toff.data(), sizeof(int) * toff.size(),
-                               cudaMemcpyHostToDevice, h->stream));
-        CK(hc, cudaMemcpyAsync(h->tail_K, tK.data(), sizeof(float4) * tK.size(),
-                               cudaMemcpyHostToDevice, h->stream));
+        CKC(cudaMemcpyAsync(h->tail_off, toff.data(), sizeof(int) * toff.size(),
+                            cudaMemcpyHostToDevice, h->stream));
+        CKC(cudaMemcpyAsync(h->tail_K, tK.data(), sizeof(float4) * tK.size(),
+                            cudaMemcpyHostToDevice, h->stream));
     }
-    CK(hc, launch_fill_outside(P, h->M, h->dn, h->dG, h->stream));
-    CK(hc, launch_init_noise(P, h->pop[0], O.seed, O.noise, 0, h->stream));
-    CK(hc, cudaStreamSynchronize(h->stream));
+    CKC(launch_fill_outside(P, h->M, h->dn[0], h->dn[1], h->dG, h->stream));
+    CKC(launch_init_noise(P, h->pop[0], h->dn[0], O.seed, O.noise, 0, h->stream));
+    CKC(cudaStreamSynchronize(h->stream));
+#undef CKC
     *out = h;
     return LBIF_OK;
 }
@@ -341,25 +336,46 @@ extern "C" const char* lbif_last_error(lbif_handle h)
 // --------------------------------------------------------------------------
 // stepping
 // --------------------------------------------------------------------------
+// Moments (and, when asked, the g2 field and the tail force) of the current
+// populations; cached per step so that output calls between steps do not
+// redo them. The new dn goes to dn[dcur^1]; the reference dn[dcur] is kept.
 static int refresh_fields(lbif_ctx* h, bool want_G)
 {
     const Params& P = h->P;
-    CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn, h->status_d, h->stream));
-    if (want_G) CK(h, launch_ball(P, h->dn, h->dG, h->status_d, h->stream));
-    if (P.tail) CK(h, launch_tail(P, h->dn, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
+    float* dnew = h->dn[h->dcur ^ 1];
+    if (h->fields_t != h->t) {
+        CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn[h->dcur], dnew, h->status_d, h->stream));
+        h->fields_t = h->t;
+    }
+    if (want_G && h->G_t != h->t) {
+        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->stream));
+        h->G_t = h->t;
+    }
+    if (P.tail && h->tail_t != h->t) {
+        CK(h, launch_tail(P, dnew, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
+        h->tail_t = h->t;
+    }
+    return LBIF_OK;
+}
+
+static int advance(lbif_ctx* h)
+{
+    const Params& P = h->P;
+    CK(h, launch_fcs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dn[h->dcur ^ 1], h->dG, h->Ft,
+                     h->stream));
+    h->cur ^= 1;
+    h->dcur ^= 1;
+    h->t += 1;
     return LBIF_OK;
 }
 
 extern "C" int lbif_step(lbif_handle h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return fail(h, LBIF_ERR_ARG, "lbif_step: bad arguments");
-    const Params& P = h->P;
     for (int64_t k = 0; k < nsteps; ++k) {
-        int rc = refresh_fields(h, P.hs != 0);
+        int rc = refresh_fields(h, h->P.hs != 0);
         if (rc) return rc;
-        CK(h, launch_fcs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dG, h->Ft, h->stream));
-        h->cur ^= 1;
-        h->t += 1;
+        if ((rc = advance(h))) return rc;
     }
     return LBIF_OK;
 }
@@ -374,7 +390,6 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
         kernel_ms[k] = 0.0;
         launches[k] = 0;
     }
-    // one event before the first launch, then one after every launch
     int per = 2 + (P.hs ? 1 : 0) + (P.tail ? 1 : 0);
     std::vector<cudaEvent_t> ev((size_t)nsteps * per + 1);
     std::vector<int> cls((size_t)nsteps * per);
@@ -382,25 +397,26 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
     size_t j = 0;
     CK(h, cudaEventRecord(ev[0], h->stream));
     for (int64_t s = 0; s < nsteps; ++s) {
-        CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn, h->status_d, h->stream));
+        float* dnew = h->dn[h->dcur ^ 1];
+        CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn[h->dcur], dnew, h->status_d, h->stream));
         cls[j] = 0;
         CK(h, cudaEventRecord(ev[++j], h->stream));
         if (P.hs) {
-            CK(h, launch_ball(P, h->dn, h->dG, h->status_d, h->stream));
+            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->stream));
             cls[j] = 1;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
         if (P.tail) {
-            CK(h, launch_tail(P, h->dn, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
+            CK(h, launch_tail(P, dnew, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
             cls[j] = 2;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
-        CK(h, launch_fcs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dG, h->Ft, h->stream));
+        int rc = advance(h);
+        if (rc) return rc;
         cls[j] = 3;
         CK(h, cudaEventRecord(ev[++j], h->stream));
-        h->cur ^= 1;
-        h->t += 1;
     }
+    invalidate(h);
     CK(h, cudaEventSynchronize(ev[j]));
     for (size_t k = 0; k < j; ++k) {
         float ms = 0.f;
@@ -490,35 +506,26 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
     size_t N = (size_t)P.g.N;
     const float* drho = rho;
     const float* du = u;
+    float* tmp = nullptr;
     if (!on_device) {
         int rc = ensure_scratch(h);
         if (rc) return rc;
-        // rho in plane 0; u needs 3 planes, so set it up in two passes when present
-        float* d = h->scratch;
-        if (u) {
-            float* tmp = nullptr;
-            if (cudaMalloc((void**)&tmp, sizeof(float) * N) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(h, LBIF_ERR_NOMEM, "lbif_set_fields: allocation failed");
-            }
-            cudaError_t e1 = cudaMemcpyAsync(tmp, rho, sizeof(float) * N, cudaMemcpyHostToDevice, h->stream);
-            cudaError_t e2 = cudaMemcpyAsync(d, u, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->stream);
-            cudaError_t e3 = launch_init_fields(P, h->pop[h->cur], tmp, d, h->stream);
-            cudaError_t e4 = cudaStreamSynchronize(h->stream);
-            cudaFree(tmp);
-            if (e1 || e2 || e3 || e4) return fail(h, LBIF_ERR_CUDA, "lbif_set_fields: copy/launch failed");
-            h->t = 0;
-            h->last_t = -1;
-            return LBIF_OK;
-        }
+        // rho goes to the (not yet used) second population buffer, u to the scratch
+        float* d = (float*)h->pop[h->cur ^ 1];
         CK(h, cudaMemcpyAsync(d, rho, sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
         drho = d;
-        du = nullptr;
+        if (u) {
+            CK(h, cudaMemcpyAsync(h->scratch, u, sizeof(float) * 3 * N, cudaMemcpyHostToDevice,
+                                  h->stream));
+            du = h->scratch;
+        }
     }
-    CK(h, launch_init_fields(P, h->pop[h->cur], drho, du, h->stream));
+    (void)tmp;
+    CK(h, launch_init_fields(P, h->pop[h->cur], h->dn[h->dcur], drho, du, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->t = 0;
     h->last_t = -1;
+    invalidate(h);
     return LBIF_OK;
 }
 
@@ -527,7 +534,8 @@ extern "C" int lbif_profiles(lbif_handle h, double* n_z, double* ux_z, double* o
     if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_profiles: NULL handle");
     const Params& P = h->P;
     int nz = P.g.nz;
-    CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn, h->status_d, h->stream));
+    int rc = refresh_fields(h, false);
+    if (rc) return rc;
     CK(h, launch_profiles(P, h->M, h->prof_d, h->stream));
     std::vector<double> prof((size_t)nz * 5);
     CK(h, cudaMemcpyAsync(prof.data(), h->prof_d, sizeof(double) * prof.size(),
@@ -604,7 +612,7 @@ extern "C" int lbif_status(lbif_handle h, int32_t* status)
 }
 
 // --------------------------------------------------------------------------
-// checkpoint
+// checkpoint: populations and their reference density field
 // --------------------------------------------------------------------------
 struct CkptHeader {
     char magic[8];
@@ -616,26 +624,33 @@ extern "C" int lbif_save(lbif_handle h, const char* path)
 {
     if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_save: bad arguments");
     const Params& P = h->P;
+    int rc = ensure_scratch(h);
+    if (rc) return rc;
     size_t es = pop_bytes(P);
-    size_t plane = es * (size_t)P.g.N;
+    size_t N = (size_t)P.g.N;
+    size_t plane = es * N;
     std::vector<char> buf(plane * Q);
+    std::vector<float> ref(N);
     for (int i = 0; i < Q; ++i)
         CK(h, cudaMemcpyAsync(buf.data() + plane * i, (char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i,
                               plane, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, launch_read_ref(P, h->dn[h->dcur], h->scratch, h->stream));
+    CK(h, cudaMemcpyAsync(ref.data(), h->scratch, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     FILE* fp = fopen(path, "wb");
     if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_save: cannot open ") + path);
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, "LBIFCKP1", 8);
-    hd.version = 1;
+    memcpy(hd.magic, "LBIFCKP2", 8);
+    hd.version = 2;
     hd.nx = P.g.nx;
     hd.ny = P.g.ny;
     hd.nz = P.g.nz;
     hd.sigma = P.sigma;
     hd.storage = P.storage;
     hd.t = h->t;
-    bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(buf.data(), 1, buf.size(), fp) == buf.size() &&
+              fwrite(ref.data(), sizeof(float), N, fp) == N;
     ok = (fclose(fp) == 0) && ok;
     return ok ? LBIF_OK : fail(h, LBIF_ERR_IO, "lbif_save: write failed");
 }
@@ -644,22 +659,30 @@ extern "C" int lbif_load(lbif_handle h, const char* path)
 {
     if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_load: bad arguments");
     const Params& P = h->P;
+    int rc = ensure_scratch(h);
+    if (rc) return rc;
     FILE* fp = fopen(path, "rb");
     if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_load: cannot open ") + path);
     CkptHeader hd;
     size_t es = pop_bytes(P);
-    size_t plane = es * (size_t)P.g.N;
+    size_t N = (size_t)P.g.N;
+    size_t plane = es * N;
     std::vector<char> buf(plane * Q);
-    bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "LBIFCKP1", 8) == 0 &&
+    std::vector<float> ref(N);
+    bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "LBIFCKP2", 8) == 0 &&
               hd.nx == P.g.nx && hd.ny == P.g.ny && hd.nz == P.g.nz && hd.sigma == P.sigma &&
-              hd.storage == P.storage && fread(buf.data(), 1, buf.size(), fp) == buf.size();
+              hd.storage == P.storage && fread(buf.data(), 1, buf.size(), fp) == buf.size() &&
+              fread(ref.data(), sizeof(float), N, fp) == N;
     fclose(fp);
     if (!ok) return fail(h, LBIF_ERR_IO, "lbif_load: file does not match this handle");
     for (int i = 0; i < Q; ++i)
         CK(h, cudaMemcpyAsync((char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i, buf.data() + plane * i,
                               plane, cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaMemcpyAsync(h->scratch, ref.data(), sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_write_ref(P, h->scratch, h->dn[h->dcur], h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->t = hd.t;
     h->last_t = -1;
+    invalidate(h);
     return LBIF_OK;
 }

