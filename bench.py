@@ -178,6 +178,9 @@ def run_ours(args, world, rank, local):
     build.build()
     storage = 1 if args.storage == "f16" else 0
     W = c2(args.eta, storage)
+    if args.grid:
+        nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
+        W = W.with_(nx=nx, ny=ny, nz=nz)
     stream = torch.cuda.current_stream()
     g = lbif.Slit(W.nx, W.ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, storage=storage,
                   seed=W.seed + rank, stream=stream.cuda_stream)
@@ -276,6 +279,8 @@ def main():
     ap.add_argument("--eta", type=float, default=0.25)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", default=None,
+                    help="override the slit extents NXxNYxNZ (profiling captures on a smaller case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -75,47 +75,13 @@ static int padded_offset(const Geom& g, int dx, int dy, int dz)
     return (dz * g.py + dy) * g.px + dx;
 }
 
-// Linear interpolation stencil of the point s (lattice units) relative to a
-// node: the corners along the axes with a fractional part, with weights.
-static int interp_stencil(const Geom& g, const double s[3], int off[4], float w[4])
-{
-    int b[3];
-    double t[3];
-    int frac_axes[3], nf = 0;
-    for (int a = 0; a < 3; ++a) {
-        double r = nearbyint(s[a]);
-        if (fabs(s[a] - r) < 1e-12) {
-            b[a] = (int)r;
-            t[a] = 0.0;
-        } else {
-            b[a] = (int)floor(s[a]);
-            t[a] = s[a] - b[a];
-            frac_axes[nf++] = a;
-        }
-    }
-    if (nf > 2) return -1;
-    int n = 1 << nf;
-    for (int c = 0; c < n; ++c) {
-        int d[3] = {b[0], b[1], b[2]};
-        double wt = 1.0;
-        for (int k = 0; k < nf; ++k) {
-            int a = frac_axes[k];
-            int bit = (c >> k) & 1;
-            d[a] += bit;
-            wt *= bit ? t[a] : 1.0 - t[a];
-        }
-        off[c] = padded_offset(g, d[0], d[1], d[2]);
-        w[c] = (float)wt;
-    }
-    return n;
-}
-
 // 18-point sphere rule: 6 axis points (weight 1/30) and the 12 face
-// diagonals (weight 1/15) as antipodal pairs (layout in lbif_internal.h)
+// diagonals (weight 1/15), layout in lbif_internal.h. The off-lattice
+// points sit at sigma/sqrt2 (neighbour) and sigma/(2 sqrt2) (midpoint) along
+// two axes; linear interpolation between floor and floor + 1 on each.
 static int build_shell(Params& P)
 {
     const Geom& g = P.g;
-    const double sig = P.sigma;
     for (int a = 0; a < 3; ++a) {
         int e[3] = {0, 0, 0};
         e[a] = 1;
@@ -123,22 +89,31 @@ static int build_shell(Params& P)
         int hh = P.sigma / 2;
         P.sh.ax_md[a] = padded_offset(g, hh * e[0], hh * e[1], hh * e[2]);
     }
-    const double r2 = 1.0 / sqrt(2.0);
+    const int stride[3] = {1, g.px, g.px * g.py};
     const int planes[3][2] = {{0, 1}, {0, 2}, {1, 2}};
-    for (int pl = 0; pl < 3; ++pl)
-        for (int sb = 0; sb < 2; ++sb) {
-            int j = 2 * pl + sb;
-            double d[3] = {0, 0, 0};
-            d[planes[pl][0]] = r2;
-            d[planes[pl][1]] = sb ? -r2 : r2;
-            double s[3], m[3];
-            for (int a = 0; a < 3; ++a) {
-                s[a] = sig * d[a];
-                m[a] = 0.5 * sig * d[a];
+    const double A = P.sigma / sqrt(2.0);
+    for (int pl = 0; pl < 3; ++pl) {
+        int sa = stride[planes[pl][0]], sb = stride[planes[pl][1]];
+        for (int which = 0; which < 2; ++which) {
+            double s = which ? 0.5 * A : A;
+            int lo = (int)floor(s);
+            double t = s - lo;
+            if (t <= 1e-12 || t >= 1.0 - 1e-12) return -1;  // irrational for every even sigma
+            for (int k = 0; k < 4; ++k) {
+                int ka = k & 1, kb = k >> 1;
+                float w = (float)((ka ? t : 1.0 - t) * (kb ? t : 1.0 - t));
+                if (which) {
+                    P.sh.md_a[pl][k] = (lo + ka) * sa;
+                    P.sh.md_b[pl][k] = (lo + kb) * sb;
+                    P.sh.md_w[pl][k] = w;
+                } else {
+                    P.sh.nb_a[pl][k] = (lo + ka) * sa;
+                    P.sh.nb_b[pl][k] = (lo + kb) * sb;
+                    P.sh.nb_w[pl][k] = w;
+                }
             }
-            if (interp_stencil(g, s, P.sh.dg_nb_off[j], P.sh.dg_nb_w[j]) != 4) return -1;
-            if (interp_stencil(g, m, P.sh.dg_md_off[j], P.sh.dg_md_w[j]) != 4) return -1;
         }
+    }
     return 0;
 }
 

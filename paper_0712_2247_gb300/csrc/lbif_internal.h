@@ -38,19 +38,21 @@ struct Geom {
     long long P;     // px*py*pz
 };
 
-// 18-point sphere rule as antipodal pairs, stencils as padded-grid offsets.
+// 18-point sphere rule, stencils as padded-grid offsets.
 //   axis pair a (a = x, y, z): neighbour at +-sigma e_a, midpoint at +-sigma/2 e_a
-//   diagonal pair j = 2*plane + (second sign < 0), planes (x,y), (x,z), (y,z):
-//     the "+" member sits at sigma (e_a + s e_b)/sqrt2 and interpolates its
-//     neighbour and midpoint from 4 corners; the antipode uses the negated
-//     offsets with the same weights.
+//   face-diagonal quartet of plane (a, b) = (x,y), (x,z), (y,z): the four
+//     points sigma (sa e_a + sb e_b)/sqrt2, sa, sb = +-1. Each interpolates its
+//     neighbour (and midpoint) from the corners (sa (lo + ka), sb (lo + kb)),
+//     ka, kb in {0, 1}, with the weights w[k], k = ka + 2 kb, shared by all
+//     four members in the same order, so mirror images sum bit-identically.
+//     nb_a[k] = (lo + ka) * stride_a, nb_b[k] = (lo + kb) * stride_b.
 struct Shell {
     int ax_nb[3];
     int ax_md[3];
-    int dg_nb_off[6][4];
-    float dg_nb_w[6][4];
-    int dg_md_off[6][4];
-    float dg_md_w[6][4];
+    int nb_a[3][4], nb_b[3][4];
+    float nb_w[3][4];
+    int md_a[3][4], md_b[3][4];
+    float md_w[3][4];
 };
 
 struct Params {

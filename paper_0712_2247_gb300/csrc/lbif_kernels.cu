@@ -57,6 +57,45 @@ __device__ __forceinline__ void for_images(const Geom& g, int x, int y, int z, F
                 fn(((zi + g.hw) * g.py + (yi + g.hw)) * g.px + (xi + g.hw));
 }
 
+// Block -> node mapping of the stencil kernels: a CTA is a 32 x 8 (x, y) tile
+// of one z plane; CTAs are ordered tile-in-group fastest, then z, then group,
+// where a group is up to 4 x 16 tiles (128 x 128 nodes). The CTAs resident at
+// any moment then cover a compact 128 x 128 x ~20 block, whose +-sigma
+// stencil footprint stays in L2 instead of spanning 2 sigma + 1 full planes.
+constexpr int TILE_X = 32, TILE_Y = 8;
+
+struct TileMap {
+    int tiles_x, tiles_y, gtx, gty, ngx;
+};
+
+__device__ __forceinline__ bool tile_node(const Geom& g, const TileMap& tm, int& x, int& y, int& z)
+{
+    const int per = tm.gtx * tm.gty;
+    const int b = blockIdx.x;
+    const int tig = b % per;
+    const int rest = b / per;
+    z = rest % g.nz;
+    const int grp = rest / g.nz;
+    const int tile_x = (grp % tm.ngx) * tm.gtx + tig % tm.gtx;
+    const int tile_y = (grp / tm.ngx) * tm.gty + tig / tm.gtx;
+    x = tile_x * TILE_X + (threadIdx.x % TILE_X);
+    y = tile_y * TILE_Y + (threadIdx.x / TILE_X);
+    return tile_x < tm.tiles_x && tile_y < tm.tiles_y && x < g.nx && y < g.ny;
+}
+
+static inline TileMap make_tilemap(const Geom& g, unsigned& blocks)
+{
+    TileMap tm;
+    tm.tiles_x = (g.nx + TILE_X - 1) / TILE_X;
+    tm.tiles_y = (g.ny + TILE_Y - 1) / TILE_Y;
+    tm.gtx = tm.tiles_x < 4 ? tm.tiles_x : 4;
+    tm.gty = tm.tiles_y < 16 ? tm.tiles_y : 16;
+    tm.ngx = (tm.tiles_x + tm.gtx - 1) / tm.gtx;
+    int ngy = (tm.tiles_y + tm.gty - 1) / tm.gty;
+    blocks = (unsigned)tm.gtx * tm.gty * g.nz * tm.ngx * ngy;
+    return tm;
+}
+
 template <typename T>
 __device__ __forceinline__ void load_pops(const Params& P, const T* __restrict__ pop, long long idx,
                                           float h[Q])
@@ -322,12 +361,10 @@ __device__ __forceinline__ float ucomp(const float4& v)
     return A == 0 ? v.y : (A == 1 ? v.z : v.w);
 }
 
-// T_q = A_q - (G0 + A_q) lk s_q.(u_q - u),  A_q = G_q n_q / n0 - G0
-__device__ __forceinline__ float shell_term(float dq, float gq, float su, float G0, float lk)
-{
-    float Aq = G0 * dq + gq * (1.f + dq);
-    return Aq - (G0 + Aq) * lk * su;
-}
+// For one quadrature point: A = G_q n_q / n0 - G0 = G0 dq + gq (1 + dq) and the
+// coupling products (G0 + A) lk s_q.(u_q - u) split by axis, so that
+// T_q = A - Pa - Pb.
+__device__ __forceinline__ float shell_A(float dq, float gq, float G0) { return G0 * dq + gq * (1.f + dq); }
 
 template <int A>
 __device__ __forceinline__ void axis_pair(const Params& P, const float4* __restrict__ M,
@@ -338,42 +375,59 @@ __device__ __forceinline__ void axis_pair(const Params& P, const float4* __restr
     float4 vp = __ldg(M + p + o), vm = __ldg(M + p - o);
     float gp = __ldg(dG + p + om), gm = __ldg(dG + p - om);
     float u0 = ucomp<A>(m0);
-    float tp = shell_term(vp.x, gp, ucomp<A>(vp) - u0, P.G0, lk);
-    float tm = shell_term(vm.x, gm, u0 - ucomp<A>(vm), P.G0, lk);
+    float Ap = shell_A(vp.x, gp, P.G0), Am = shell_A(vm.x, gm, P.G0);
+    float tp = Ap - (P.G0 + Ap) * lk * (ucomp<A>(vp) - u0);
+    float tm = Am - (P.G0 + Am) * lk * (u0 - ucomp<A>(vm));
     f[A] += (1.f / 30.f) * (tp - tm);
 }
 
-template <int PL, int SB>
-__device__ __forceinline__ void diag_pair(const Params& P, const float4* __restrict__ M,
-                                          const float* __restrict__ dG, int p, const float4& m0,
-                                          float lk, float f[3])
+// The four points sigma (sa e_a + sb e_b)/sqrt2 of one coordinate plane.
+// The a-component pairs members with equal b-offset and the b-component
+// members with equal a-offset, so that terms which cancel in a field uniform
+// along a (or b) cancel exactly before rounding meets the small remainder.
+template <int PL>
+__device__ __forceinline__ void diag_quartet(const Params& P, const float4* __restrict__ M,
+                                             const float* __restrict__ dG, int p,
+                                             const float4& m0, float lk, float f[3])
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
-    constexpr int j = 2 * PL + SB;
-    constexpr float s = SB ? -1.f : 1.f;
     constexpr float h = 0.70710678118654752f;
-    float dqp = 0.f, uap = 0.f, ubp = 0.f, dqm = 0.f, uam = 0.f, ubm = 0.f, gp = 0.f, gm = 0.f;
+    // member order: (+,+), (-,+), (+,-), (-,-)
+    float dq[4] = {0.f, 0.f, 0.f, 0.f}, ua[4] = {0.f, 0.f, 0.f, 0.f}, ub[4] = {0.f, 0.f, 0.f, 0.f};
+    float gq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const int o = P.sh.dg_nb_off[j][c], om = P.sh.dg_md_off[j][c];
-        const float w = P.sh.dg_nb_w[j][c], wm = P.sh.dg_md_w[j][c];
-        float4 vp = __ldg(M + p + o), vm = __ldg(M + p - o);
-        dqp += w * vp.x;
-        uap += w * ucomp<a>(vp);
-        ubp += w * ucomp<b>(vp);
-        dqm += w * vm.x;
-        uam += w * ucomp<a>(vm);
-        ubm += w * ucomp<b>(vm);
-        gp += wm * __ldg(dG + p + om);
-        gm += wm * __ldg(dG + p - om);
+    for (int k = 0; k < 4; ++k) {
+        const int oa = P.sh.nb_a[PL][k], ob = P.sh.nb_b[PL][k];
+        const int ma = P.sh.md_a[PL][k], mb = P.sh.md_b[PL][k];
+        const float w = P.sh.nb_w[PL][k], wm = P.sh.md_w[PL][k];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1;
+            float4 v = __ldg(M + p + sa * oa + sb * ob);
+            dq[m] += w * v.x;
+            ua[m] += w * ucomp<a>(v);
+            ub[m] += w * ucomp<b>(v);
+            gq[m] += wm * __ldg(dG + p + sa * ma + sb * mb);
+        }
     }
-    float ua0 = ucomp<a>(m0), ub0 = ucomp<b>(m0);
-    float sup = h * ((uap - ua0) + s * (ubp - ub0));
-    float sum = -h * ((uam - ua0) + s * (ubm - ub0));
-    float d = (1.f / 15.f) * (shell_term(dqp, gp, sup, P.G0, lk) - shell_term(dqm, gm, sum, P.G0, lk));
-    f[a] += h * d;
-    f[b] += s * h * d;
+    const float ua0 = ucomp<a>(m0), ub0 = ucomp<b>(m0);
+    float Aq[4], Pa[4], Pb[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float sa = (m & 1) ? -1.f : 1.f, sb = (m & 2) ? -1.f : 1.f;
+        Aq[m] = shell_A(dq[m], gq[m], P.G0);
+        float c = (P.G0 + Aq[m]) * lk * h;
+        Pa[m] = c * (sa * (ua[m] - ua0));
+        Pb[m] = c * (sb * (ub[m] - ub0));
+    }
+    // T = A - Pa - Pb; a-component sum sa T, b-component sum sb T
+    float da = ((Aq[0] - Aq[1]) - (Pa[0] - Pa[1]) - (Pb[0] - Pb[1])) +
+               ((Aq[2] - Aq[3]) - (Pa[2] - Pa[3]) - (Pb[2] - Pb[3]));
+    float db = ((Aq[0] - Aq[2]) - (Pa[0] - Pa[2]) - (Pb[0] - Pb[2])) +
+               ((Aq[1] - Aq[3]) - (Pa[1] - Pa[3]) - (Pb[1] - Pb[3]));
+    f[a] += (h / 15.f) * da;
+    f[b] += (h / 15.f) * db;
 }
 
 // total force F / n0 at a node (body + hard sphere + tail)
@@ -400,12 +454,9 @@ __device__ __forceinline__ void node_force(const Params& P, const float4* __rest
         axis_pair<0>(P, M, dG, p, m0, lk, f);
         axis_pair<1>(P, M, dG, p, m0, lk, f);
         axis_pair<2>(P, M, dG, p, m0, lk, f);
-        diag_pair<0, 0>(P, M, dG, p, m0, lk, f);
-        diag_pair<0, 1>(P, M, dG, p, m0, lk, f);
-        diag_pair<1, 0>(P, M, dG, p, m0, lk, f);
-        diag_pair<1, 1>(P, M, dG, p, m0, lk, f);
-        diag_pair<2, 0>(P, M, dG, p, m0, lk, f);
-        diag_pair<2, 1>(P, M, dG, p, m0, lk, f);
+        diag_quartet<0>(P, M, dG, p, m0, lk, f);
+        diag_quartet<1>(P, M, dG, p, m0, lk, f);
+        diag_quartet<2>(P, M, dG, p, m0, lk, f);
         float pre = P.hs_pref * opd;
         fx += pre * f[0];
         fy += pre * f[1];
@@ -452,17 +503,16 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
 // the value relative to the target's current density.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256, 2) k_fcs(Params P, const T* __restrict__ pin,
+__global__ void __launch_bounds__(256, 2) k_fcs(Params P, TileMap tm, const T* __restrict__ pin,
                                                 T* __restrict__ pout, const float4* __restrict__ M,
                                                 const float* __restrict__ dn,
                                                 const float* __restrict__ dG,
                                                 const float4* __restrict__ Ft)
 {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= P.g.N) return;
     const Geom& g = P.g;
     int x, y, z;
-    decompose(g, idx, x, y, z);
+    if (!tile_node(g, tm, x, y, z)) return;
+    const long long idx = ((long long)z * g.ny + y) * g.nx + x;
     int p = pidx(g, x, y, z);
     float4 m0 = __ldg(M + p);
     float fx, fy, fz;
@@ -498,13 +548,13 @@ __global__ void __launch_bounds__(256, 2) k_fcs(Params P, const T* __restrict__ 
 // ---------------------------------------------------------------------------
 // outputs
 // ---------------------------------------------------------------------------
-__global__ void k_force_out(Params P, const float4* __restrict__ M, const float* __restrict__ dG,
-                            const float4* __restrict__ Ft, float* __restrict__ F)
+__global__ void k_force_out(Params P, TileMap tm, const float4* __restrict__ M,
+                            const float* __restrict__ dG, const float4* __restrict__ Ft,
+                            float* __restrict__ F)
 {
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= P.g.N) return;
     int x, y, z;
-    decompose(P.g, idx, x, y, z);
+    if (!tile_node(P.g, tm, x, y, z)) return;
+    const long long idx = ((long long)z * P.g.ny + y) * P.g.nx + x;
     int p = pidx(P.g, x, y, z);
     float4 m = M[p];
     float fx, fy, fz;
@@ -522,16 +572,17 @@ __device__ __forceinline__ float shell_A_sum(const Params& P, const float4* M, c
         for (int sg = -1; sg <= 1; sg += 2) {
             float dq = __ldg(&M[p + sg * P.sh.ax_nb[a]].x);
             float gq = __ldg(dG + p + sg * P.sh.ax_md[a]);
-            s += (1.f / 30.f) * (P.G0 * dq + gq * (1.f + dq));
+            s += (1.f / 30.f) * shell_A(dq, gq, P.G0);
         }
-    for (int j = 0; j < 6; ++j)
-        for (int sg = -1; sg <= 1; sg += 2) {
+    for (int pl = 0; pl < 3; ++pl)
+        for (int m = 0; m < 4; ++m) {
+            const int sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1;
             float dq = 0.f, gq = 0.f;
-            for (int c = 0; c < 4; ++c) {
-                dq += P.sh.dg_nb_w[j][c] * __ldg(&M[p + sg * P.sh.dg_nb_off[j][c]].x);
-                gq += P.sh.dg_md_w[j][c] * __ldg(dG + p + sg * P.sh.dg_md_off[j][c]);
+            for (int k = 0; k < 4; ++k) {
+                dq += P.sh.nb_w[pl][k] * __ldg(&M[p + sa * P.sh.nb_a[pl][k] + sb * P.sh.nb_b[pl][k]].x);
+                gq += P.sh.md_w[pl][k] * __ldg(dG + p + sa * P.sh.md_a[pl][k] + sb * P.sh.md_b[pl][k]);
             }
-            s += (1.f / 15.f) * (P.G0 * dq + gq * (1.f + dq));
+            s += (1.f / 15.f) * shell_A(dq, gq, P.G0);
         }
     return s;
 }
@@ -700,19 +751,21 @@ cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const 
 cudaError_t launch_fcs(const Params& P, const void* pin, void* pout, const float4* M,
                        const float* dn, const float* dG, const float4* Ft, cudaStream_t s)
 {
+    unsigned blocks;
+    TileMap tm = make_tilemap(P.g, blocks);
     if (P.storage == LBIF_STORE_F16)
-        k_fcs<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pin, (__half*)pout, M,
-                                                           dn, dG, Ft);
+        k_fcs<__half><<<blocks, 256, 0, s>>>(P, tm, (const __half*)pin, (__half*)pout, M, dn, dG, Ft);
     else
-        k_fcs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, M, dn,
-                                                          dG, Ft);
+        k_fcs<float><<<blocks, 256, 0, s>>>(P, tm, (const float*)pin, (float*)pout, M, dn, dG, Ft);
     return cudaGetLastError();
 }
 
 cudaError_t launch_force_out(const Params& P, const float4* M, const float* dG, const float4* Ft,
                              float* F, cudaStream_t s)
 {
-    k_force_out<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, M, dG, Ft, F);
+    unsigned blocks;
+    TileMap tm = make_tilemap(P.g, blocks);
+    k_force_out<<<blocks, 256, 0, s>>>(P, tm, M, dG, Ft, F);
     return cudaGetLastError();
 }
 
