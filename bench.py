@@ -95,11 +95,17 @@ def bytes_alg(storage: int):
     return 2 * 19 * s + 44
 
 
-def bytes_fcs(storage: int):
-    """Algorithmic bytes per node of the fused force + collide + stream kernel:
-    19 populations read and written, {dn,u} (16 B) and dG (4 B) read once."""
+def kernel_bytes(storage: int):
+    """Algorithmic bytes per node moved by each kernel class (each array element
+    read or written once; stencil neighbours come from cache):
+      moments         19 populations in, reference dn in, {dn,u} + dn out
+      ball_g2         dn in, dG out
+      tail            dn in, F_tail out
+      force           {dn,u} + dG in, F out
+      collide_stream  19 populations in and out, {dn,u}, F and neighbour dn in"""
     s = 2 if storage == 1 else 4
-    return 2 * 19 * s + 20
+    return {"moments": 19 * s + 4 + 20, "ball_g2": 8, "tail": 20, "force": 36,
+            "collide_stream": 2 * 19 * s + 36}
 
 
 def dist_setup(args):
@@ -208,17 +214,17 @@ def run_ours(args, world, rank, local):
     mlups = world * N / (ms_per_step * 1e-3) / 1e6
     status = g.status()
 
-    # dominant kernel roofline (force + collide + stream), live CUDA-event timing
+    # dominant kernel roofline, live CUDA-event timing of each launch class
     peak, peak_kind = _peaks()
     dom = max(kms, key=lambda k: kms[k])
     launches = sum(nl.values())
-    fcs_ms = kms["force_collide_stream"] / max(nl["force_collide_stream"], 1)
-    dom_bytes = {"force_collide_stream": bytes_fcs(storage) * N,
-                 "moments": (19 * (2 if storage else 4) + 20) * N,
-                 "ball_g2": 8 * N, "tail": 16 * N}[dom]
+    kb = kernel_bytes(storage)
+    dom_bytes = kb[dom] * N
     dom_ms = kms[dom] / max(nl[dom], 1)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     step_gbs = bytes_alg(storage) * N / (ms_per_step * 1e-3) / 1e9
+    per_kernel = {k: {"ms": kms[k] / nl[k], "gbs_alg": kb[k] * N / (kms[k] / nl[k] * 1e-3) / 1e9}
+                  for k in kms if nl[k]}
 
     # end to end through the C ABI with host buffers: per iteration upload the
     # density field from pinned host memory, run S steps, read the profiles back
@@ -255,7 +261,7 @@ def run_ours(args, world, rank, local):
                    "l2": "populations (>= 1.9 GB) exceed L2; no flush",
                    "bytes_alg_per_node": bytes_alg(storage),
                    "step_gbs_alg": step_gbs, "step_roofline_frac": step_gbs / peak,
-                   "kernel_ms_per_step": {k: v / max(nl[k], 1) for k, v in kms.items() if nl[k]},
+                   "kernels": per_kernel,
                    "status": status},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind + " hbm_gbs", "unit": "GB/s", "frac": achieved / peak,

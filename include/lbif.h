@@ -92,8 +92,8 @@ int lbif_step(lbif_handle h, int64_t nsteps);
 /* Same as lbif_step, and also times every kernel class with CUDA events
  * recorded on the handle's stream between launches: kernel_ms[k] receives
  * the total milliseconds of class k over the nsteps (k = 0 moments, 1 ball +
- * g2, 2 tail, 3 force + collide + stream; classes not launched get 0) and
- * launches[k] the number of launches. nk = length of both arrays (>= 4).
+ * g2, 2 tail, 3 force, 4 collide + stream; classes not launched get 0) and
+ * launches[k] the number of launches. nk = length of both arrays (>= 5).
  * Synchronises at the end. Diagnostics for the benchmark. */
 int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches,
                        int32_t nk);

@@ -23,6 +23,7 @@ struct lbif_ctx {
     float4* M = nullptr;
     float* dG = nullptr;
     float4* Ft = nullptr;
+    float4* F = nullptr;              // F / n0 per node (force kernel -> collision kernel)
     int* tail_off = nullptr;
     float4* tail_K = nullptr;
     int tail_pairs = 0;
@@ -58,8 +59,8 @@ static size_t pop_bytes(const Params& P) { return (P.storage == LBIF_STORE_F16 ?
 static void free_ctx(lbif_ctx* h)
 {
     if (!h) return;
-    void* bufs[] = {h->pop[0], h->pop[1], h->dn[0],  h->dn[1],    h->M,      h->dG,
-                    h->Ft,     h->tail_off, h->tail_K, h->status_d, h->prof_d, h->scratch};
+    void* bufs[] = {h->pop[0], h->pop[1], h->dn[0],    h->dn[1], h->M,        h->dG,     h->Ft,
+                    h->F,      h->tail_off, h->tail_K, h->status_d, h->prof_d, h->scratch};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete h;
@@ -254,6 +255,7 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     ALLOC(h->dn[0], sizeof(float) * (size_t)g.P);
     ALLOC(h->dn[1], sizeof(float) * (size_t)g.P);
     ALLOC(h->M, sizeof(float4) * (size_t)g.P);
+    ALLOC(h->F, sizeof(float4) * (size_t)g.N);
     ALLOC(h->dG, sizeof(float) * (size_t)g.P);
     ALLOC(h->status_d, sizeof(int));
     ALLOC(h->prof_d, sizeof(double) * 5 * (size_t)g.nz);
@@ -336,8 +338,8 @@ static int refresh_fields(lbif_ctx* h, bool want_G)
 static int advance(lbif_ctx* h)
 {
     const Params& P = h->P;
-    CK(h, launch_fcs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dn[h->dcur ^ 1], h->dG, h->Ft,
-                     h->stream));
+    CK(h, launch_force(P, h->M, h->dG, h->Ft, h->F, h->stream));
+    CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dn[h->dcur ^ 1], h->F, h->stream));
     h->cur ^= 1;
     h->dcur ^= 1;
     h->t += 1;
@@ -358,14 +360,14 @@ extern "C" int lbif_step(lbif_handle h, int64_t nsteps)
 extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_ms,
                                   int64_t* launches, int32_t nk)
 {
-    if (!h || nsteps < 0 || !kernel_ms || !launches || nk < 4)
+    if (!h || nsteps < 0 || !kernel_ms || !launches || nk < 5)
         return fail(h, LBIF_ERR_ARG, "lbif_step_profiled: bad arguments");
     const Params& P = h->P;
     for (int k = 0; k < nk; ++k) {
         kernel_ms[k] = 0.0;
         launches[k] = 0;
     }
-    int per = 2 + (P.hs ? 1 : 0) + (P.tail ? 1 : 0);
+    int per = 3 + (P.hs ? 1 : 0) + (P.tail ? 1 : 0);
     std::vector<cudaEvent_t> ev((size_t)nsteps * per + 1);
     std::vector<int> cls((size_t)nsteps * per);
     for (auto& e : ev) CK(h, cudaEventCreate(&e));
@@ -386,10 +388,15 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
             cls[j] = 2;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
-        int rc = advance(h);
-        if (rc) return rc;
+        CK(h, launch_force(P, h->M, h->dG, h->Ft, h->F, h->stream));
         cls[j] = 3;
         CK(h, cudaEventRecord(ev[++j], h->stream));
+        CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, dnew, h->F, h->stream));
+        cls[j] = 4;
+        CK(h, cudaEventRecord(ev[++j], h->stream));
+        h->cur ^= 1;
+        h->dcur ^= 1;
+        h->t += 1;
     }
     invalidate(h);
     CK(h, cudaEventSynchronize(ev[j]));

@@ -87,8 +87,10 @@ cudaError_t launch_moments(const Params& P, const void* pop, float4* M, float* d
 cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s);
 cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const float4* K,
                         int npairs, float4* Ft, cudaStream_t s);
-cudaError_t launch_fcs(const Params& P, const void* pin, void* pout, const float4* M,
-                       const float* dn, const float* dG, const float4* Ft, cudaStream_t s);
+cudaError_t launch_force(const Params& P, const float4* M, const float* dG, const float4* Ft,
+                         float4* F, cudaStream_t s);
+cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const float4* M, const float* dn,
+                      const float4* F, cudaStream_t s);
 cudaError_t launch_force_out(const Params& P, const float4* M, const float* dG, const float4* Ft,
                              float* F, cudaStream_t s);
 cudaError_t launch_moments_out(const Params& P, const float4* M, const float* dG, float* rho,

@@ -496,30 +496,48 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
 }
 
 // ---------------------------------------------------------------------------
-// steps 5-6: BGK collision with the first-order source and push streaming
-// with half-way bounce-back (Sec. Methods: forward-Euler update, local
-// equilibrium; bounce-back walls). Works on k_i = h_i - dn (the populations
-// relative to the node's own current density) and stores, at the target,
-// the value relative to the target's current density.
+// step 5: total force F / n0 per node (body + hard sphere + tail), one thread
+// per node over 32 x 8 tiles; stored as float4 for the collision kernel.
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256, 2) k_fcs(Params P, TileMap tm, const T* __restrict__ pin,
-                                                T* __restrict__ pout, const float4* __restrict__ M,
-                                                const float* __restrict__ dn,
-                                                const float* __restrict__ dG,
-                                                const float4* __restrict__ Ft)
+__global__ void __launch_bounds__(256, 3) k_force(Params P, TileMap tm, const float4* __restrict__ M,
+                                                  const float* __restrict__ dG,
+                                                  const float4* __restrict__ Ft,
+                                                  float4* __restrict__ F)
 {
     const Geom& g = P.g;
     int x, y, z;
     if (!tile_node(g, tm, x, y, z)) return;
     const long long idx = ((long long)z * g.ny + y) * g.nx + x;
-    int p = pidx(g, x, y, z);
+    const int p = pidx(g, x, y, z);
     float4 m0 = __ldg(M + p);
     float fx, fy, fz;
     node_force(P, M, dG, Ft, idx, z, p, m0, fx, fy, fz);
+    F[idx] = make_float4(fx, fy, fz, 0.f);
+}
+
+// ---------------------------------------------------------------------------
+// step 6: BGK collision with the first-order source and push streaming with
+// half-way bounce-back (Sec. Methods: forward-Euler update, local equilibrium;
+// bounce-back walls). Works on k_i = h_i - dn (populations relative to the
+// node's own current density) and stores, at the target, the value relative
+// to the target's current density.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_cs(Params P, const T* __restrict__ pin, T* __restrict__ pout,
+                                            const float4* __restrict__ M,
+                                            const float* __restrict__ dn,
+                                            const float4* __restrict__ F)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
+    const Geom& g = P.g;
+    int x, y, z;
+    decompose(g, idx, x, y, z);
+    const int p = pidx(g, x, y, z);
     float gi[Q];
     load_pops(P, pin, idx, gi);
-
+    const float4 m0 = __ldg(M + p);
+    const float4 f = __ldg(F + idx);
     float S, jx, jy, jz;
     sums_of(gi, S, jx, jy, jz);
     const float d0 = m0.x, ux = m0.y, uy = m0.z, uz = m0.w;
@@ -529,7 +547,7 @@ __global__ void __launch_bounds__(256, 2) k_fcs(Params P, TileMap tm, const T* _
     for (int i = 0; i < Q; ++i) {
         float k = gi[i] - S;
         float e = eq_excess(i, opd, ux, uy, uz, uu);
-        float ks = k - (k - e) * P.inv_tau + 3.f * (kCx[i] * fx + kCy[i] * fy + kCz[i] * fz);
+        float ks = k - (k - e) * P.inv_tau + 3.f * (kCx[i] * f.x + kCy[i] * f.y + kCz[i] * f.z);
         int tx = x + kCx[i], ty = y + kCy[i], tz = z + kCz[i];
         tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
         ty = ty < 0 ? ty + g.ny : (ty >= g.ny ? ty - g.ny : ty);
@@ -748,15 +766,22 @@ cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_fcs(const Params& P, const void* pin, void* pout, const float4* M,
-                       const float* dn, const float* dG, const float4* Ft, cudaStream_t s)
+cudaError_t launch_force(const Params& P, const float4* M, const float* dG, const float4* Ft,
+                         float4* F, cudaStream_t s)
 {
     unsigned blocks;
     TileMap tm = make_tilemap(P.g, blocks);
+    k_force<<<blocks, 256, 0, s>>>(P, tm, M, dG, Ft, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const float4* M, const float* dn,
+                      const float4* F, cudaStream_t s)
+{
     if (P.storage == LBIF_STORE_F16)
-        k_fcs<__half><<<blocks, 256, 0, s>>>(P, tm, (const __half*)pin, (__half*)pout, M, dn, dG, Ft);
+        k_cs<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pin, (__half*)pout, M, dn, F);
     else
-        k_fcs<float><<<blocks, 256, 0, s>>>(P, tm, (const float*)pin, (float*)pout, M, dn, dG, Ft);
+        k_cs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, M, dn, F);
     return cudaGetLastError();
 }
 

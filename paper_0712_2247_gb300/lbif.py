@@ -162,13 +162,13 @@ class Slit:
     def step(self, nsteps: int = 1):
         self._check(self._lib.lbif_step(self._h, int(nsteps)))
 
-    KERNEL_CLASSES = ("moments", "ball_g2", "tail", "force_collide_stream")
+    KERNEL_CLASSES = ("moments", "ball_g2", "tail", "force", "collide_stream")
 
     def step_profiled(self, nsteps: int):
         """Advance nsteps and return ({class: total ms}, {class: launches})."""
-        ms = (ctypes.c_double * 4)()
-        nl = (ctypes.c_int64 * 4)()
-        self._check(self._lib.lbif_step_profiled(self._h, int(nsteps), ms, nl, 4))
+        ms = (ctypes.c_double * 5)()
+        nl = (ctypes.c_int64 * 5)()
+        self._check(self._lib.lbif_step_profiled(self._h, int(nsteps), ms, nl, 5))
         return (dict(zip(self.KERNEL_CLASSES, ms[:])), dict(zip(self.KERNEL_CLASSES, nl[:])))
 
     def moments(self, rho=None, u=None, pressure=None, allow_diverged=False):
