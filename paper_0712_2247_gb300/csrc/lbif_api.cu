@@ -20,7 +20,9 @@ struct lbif_ctx {
     int cur = 0;                      // populations of the current step
     float* dn[2] = {nullptr, nullptr};
     int dcur = 0;                     // dn[dcur] = reference of pop[cur]
-    float4* M = nullptr;
+    float* ux = nullptr;
+    float* uy = nullptr;
+    float* uz = nullptr;
     float* dG = nullptr;
     float4* Ft = nullptr;
     float4* F = nullptr;              // F / n0 per node (force kernel -> collision kernel)
@@ -56,14 +58,43 @@ static int fail(lbif_ctx* h, int code, const std::string& msg)
 
 static size_t pop_bytes(const Params& P) { return (P.storage == LBIF_STORE_F16 ? 2 : 4); }
 
+// padded fields carry PAD_SLACK floats before their first element
+static float* padded_alloc(size_t P)
+{
+    float* raw = nullptr;
+    if (cudaMalloc((void**)&raw, sizeof(float) * (P + 2 * PAD_SLACK)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return raw + PAD_SLACK;
+}
+
+static void padded_free(float* p)
+{
+    if (p) cudaFree(p - PAD_SLACK);
+}
+
 static void free_ctx(lbif_ctx* h)
 {
     if (!h) return;
-    void* bufs[] = {h->pop[0], h->pop[1], h->dn[0],    h->dn[1], h->M,        h->dG,     h->Ft,
-                    h->F,      h->tail_off, h->tail_K, h->status_d, h->prof_d, h->scratch};
+    void* bufs[] = {h->pop[0], h->pop[1], h->Ft,     h->F,      h->tail_off,
+                    h->tail_K, h->status_d, h->prof_d, h->scratch};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    float* pads[] = {h->dn[0], h->dn[1], h->ux, h->uy, h->uz, h->dG};
+    for (float* q : pads) padded_free(q);
     delete h;
+}
+
+static Fields fields_of(const lbif_ctx* h)
+{
+    Fields f;
+    f.dn = h->dn[h->dcur ^ 1];
+    f.ux = h->ux;
+    f.uy = h->uy;
+    f.uz = h->uz;
+    f.dG = h->dG;
+    return f;
 }
 
 static void invalidate(lbif_ctx* h) { h->fields_t = h->G_t = h->tail_t = -1; }
@@ -179,7 +210,8 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     g.zper = (w.z == LBIF_PERIODIC);
     g.hw = s;
     if (F.tail) g.hw = std::max(g.hw, (int)ceil(F.rcut * s));
-    g.px = g.nx + 2 * g.hw;
+    g.hw = (g.hw + 3) / 4 * 4;                   // rows 16-byte aligned
+    g.px = (g.nx + 2 * g.hw + 8 + 3) / 4 * 4;    // + slack columns for float4 windows
     g.py = g.ny + 2 * g.hw;
     g.pz = g.nz + 2 * g.hw;
     g.N = (long long)g.nx * g.ny * g.nz;
@@ -212,7 +244,10 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
         const int cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
         const int cy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
         const int cz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-        for (int i = 0; i < Q; ++i) P.nbr[i] = padded_offset(g, cx[i], cy[i], cz[i]);
+        for (int i = 0; i < Q; ++i) {
+            P.nbr[i] = padded_offset(g, cx[i], cy[i], cz[i]);
+            P.soff[i] = cx[i] + (long long)cy[i] * g.nx + (long long)cz[i] * g.nx * g.ny;
+        }
     }
     if (build_shell(P)) {
         delete h;
@@ -252,17 +287,23 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     } while (0)
     ALLOC(h->pop[0], pb);
     ALLOC(h->pop[1], pb);
-    ALLOC(h->dn[0], sizeof(float) * (size_t)g.P);
-    ALLOC(h->dn[1], sizeof(float) * (size_t)g.P);
-    ALLOC(h->M, sizeof(float4) * (size_t)g.P);
     ALLOC(h->F, sizeof(float4) * (size_t)g.N);
-    ALLOC(h->dG, sizeof(float) * (size_t)g.P);
     ALLOC(h->status_d, sizeof(int));
     ALLOC(h->prof_d, sizeof(double) * 5 * (size_t)g.nz);
     if (P.tail) {
         ALLOC(h->Ft, sizeof(float4) * (size_t)g.N);
         ALLOC(h->tail_off, sizeof(int) * toff.size());
         ALLOC(h->tail_K, sizeof(float4) * tK.size());
+    }
+    {
+        float** pads[] = {&h->dn[0], &h->dn[1], &h->ux, &h->uy, &h->uz, &h->dG};
+        for (float** q : pads) {
+            *q = padded_alloc((size_t)g.P);
+            if (!*q) {
+                free_ctx(h);
+                return fail(nullptr, LBIF_ERR_NOMEM, "lbif_create: device allocation failed");
+            }
+        }
     }
 #undef ALLOC
     lbif_ctx* hc = h;
@@ -277,10 +318,13 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     } while (0)
     CKC(cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
     CKC(cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
-    CKC(cudaMemsetAsync(h->dn[0], 0, sizeof(float) * (size_t)g.P, h->stream));
-    CKC(cudaMemsetAsync(h->dn[1], 0, sizeof(float) * (size_t)g.P, h->stream));
-    CKC(cudaMemsetAsync(h->M, 0, sizeof(float4) * (size_t)g.P, h->stream));
-    CKC(cudaMemsetAsync(h->dG, 0, sizeof(float) * (size_t)g.P, h->stream));
+    {
+        float* pads[] = {h->dn[0], h->dn[1], h->ux, h->uy, h->uz, h->dG};
+        const float outside[] = {-1.f, -1.f, 0.f, 0.f, 0.f, 0.f};
+        for (float* q : pads)
+            CKC(cudaMemsetAsync(q - PAD_SLACK, 0, sizeof(float) * ((size_t)g.P + 2 * PAD_SLACK), h->stream));
+        CKC(launch_fill_outside(P, pads, outside, 6, h->stream));
+    }
     CKC(cudaMemsetAsync(h->status_d, 0, sizeof(int), h->stream));
     if (P.tail) {
         CKC(cudaMemcpyAsync(h->tail_off, toff.data(), sizeof(int) * toff.size(),
@@ -288,7 +332,6 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
         CKC(cudaMemcpyAsync(h->tail_K, tK.data(), sizeof(float4) * tK.size(),
                             cudaMemcpyHostToDevice, h->stream));
     }
-    CKC(launch_fill_outside(P, h->M, h->dn[0], h->dn[1], h->dG, h->stream));
     CKC(launch_init_noise(P, h->pop[0], h->dn[0], O.seed, O.noise, 0, h->stream));
     CKC(cudaStreamSynchronize(h->stream));
 #undef CKC
@@ -321,7 +364,8 @@ static int refresh_fields(lbif_ctx* h, bool want_G)
     const Params& P = h->P;
     float* dnew = h->dn[h->dcur ^ 1];
     if (h->fields_t != h->t) {
-        CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn[h->dcur], dnew, h->status_d, h->stream));
+        CK(h, launch_moments(P, h->pop[h->cur], h->dn[h->dcur], dnew, h->ux, h->uy, h->uz,
+                             h->status_d, h->stream));
         h->fields_t = h->t;
     }
     if (want_G && h->G_t != h->t) {
@@ -338,8 +382,9 @@ static int refresh_fields(lbif_ctx* h, bool want_G)
 static int advance(lbif_ctx* h)
 {
     const Params& P = h->P;
-    CK(h, launch_force(P, h->M, h->dG, h->Ft, h->F, h->stream));
-    CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, h->dn[h->dcur ^ 1], h->F, h->stream));
+    const Fields f = fields_of(h);
+    CK(h, launch_force(P, f, h->Ft, h->F, h->stream));
+    CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], f, h->F, h->stream));
     h->cur ^= 1;
     h->dcur ^= 1;
     h->t += 1;
@@ -375,7 +420,9 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
     CK(h, cudaEventRecord(ev[0], h->stream));
     for (int64_t s = 0; s < nsteps; ++s) {
         float* dnew = h->dn[h->dcur ^ 1];
-        CK(h, launch_moments(P, h->pop[h->cur], h->M, h->dn[h->dcur], dnew, h->status_d, h->stream));
+        const Fields f = fields_of(h);
+        CK(h, launch_moments(P, h->pop[h->cur], h->dn[h->dcur], dnew, h->ux, h->uy, h->uz,
+                             h->status_d, h->stream));
         cls[j] = 0;
         CK(h, cudaEventRecord(ev[++j], h->stream));
         if (P.hs) {
@@ -388,10 +435,10 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
             cls[j] = 2;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
-        CK(h, launch_force(P, h->M, h->dG, h->Ft, h->F, h->stream));
+        CK(h, launch_force(P, f, h->Ft, h->F, h->stream));
         cls[j] = 3;
         CK(h, cudaEventRecord(ev[++j], h->stream));
-        CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], h->M, dnew, h->F, h->stream));
+        CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], f, h->F, h->stream));
         cls[j] = 4;
         CK(h, cudaEventRecord(ev[++j], h->stream));
         h->cur ^= 1;
@@ -442,22 +489,22 @@ extern "C" int lbif_moments(lbif_handle h, float* rho, float* u, float* pressure
     if (rc) return rc;
     size_t N = (size_t)P.g.N;
     if (on_device) {
-        CK(h, launch_moments_out(P, h->M, h->dG, rho, u, pressure, h->stream));
+        CK(h, launch_moments_out(P, fields_of(h), rho, u, pressure, h->stream));
     } else {
         if ((rc = ensure_scratch(h))) return rc;
         float* d = h->scratch;
         if (rho) {
-            CK(h, launch_moments_out(P, h->M, h->dG, d, nullptr, nullptr, h->stream));
+            CK(h, launch_moments_out(P, fields_of(h), d, nullptr, nullptr, h->stream));
             CK(h, cudaMemcpyAsync(rho, d, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
         }
         if (pressure) {
-            CK(h, launch_moments_out(P, h->M, h->dG, nullptr, nullptr, d, h->stream));
+            CK(h, launch_moments_out(P, fields_of(h), nullptr, nullptr, d, h->stream));
             CK(h, cudaMemcpyAsync(pressure, d, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
             CK(h, cudaStreamSynchronize(h->stream));
         }
         if (u) {
-            CK(h, launch_moments_out(P, h->M, h->dG, nullptr, d, nullptr, h->stream));
+            CK(h, launch_moments_out(P, fields_of(h), nullptr, d, nullptr, h->stream));
             CK(h, cudaMemcpyAsync(u, d, sizeof(float) * 3 * N, cudaMemcpyDeviceToHost, h->stream));
         }
     }
@@ -470,11 +517,13 @@ extern "C" int lbif_forces(lbif_handle h, float* F, int32_t on_device)
     const Params& P = h->P;
     int rc = refresh_fields(h, P.hs != 0);
     if (rc) return rc;
+    // the same force kernel as the time step, then a layout change to SoA
+    CK(h, launch_force(P, fields_of(h), h->Ft, h->F, h->stream));
     if (on_device) {
-        CK(h, launch_force_out(P, h->M, h->dG, h->Ft, F, h->stream));
+        CK(h, launch_force_soa(P, h->F, F, h->stream));
     } else {
         if ((rc = ensure_scratch(h))) return rc;
-        CK(h, launch_force_out(P, h->M, h->dG, h->Ft, h->scratch, h->stream));
+        CK(h, launch_force_soa(P, h->F, h->scratch, h->stream));
         CK(h, cudaMemcpyAsync(F, h->scratch, sizeof(float) * 3 * (size_t)P.g.N,
                               cudaMemcpyDeviceToHost, h->stream));
     }
@@ -488,7 +537,6 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
     size_t N = (size_t)P.g.N;
     const float* drho = rho;
     const float* du = u;
-    float* tmp = nullptr;
     if (!on_device) {
         int rc = ensure_scratch(h);
         if (rc) return rc;
@@ -502,7 +550,6 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
             du = h->scratch;
         }
     }
-    (void)tmp;
     CK(h, launch_init_fields(P, h->pop[h->cur], h->dn[h->dcur], drho, du, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     h->t = 0;
@@ -518,7 +565,7 @@ extern "C" int lbif_profiles(lbif_handle h, double* n_z, double* ux_z, double* o
     int nz = P.g.nz;
     int rc = refresh_fields(h, false);
     if (rc) return rc;
-    CK(h, launch_profiles(P, h->M, h->prof_d, h->stream));
+    CK(h, launch_profiles(P, fields_of(h), h->prof_d, h->stream));
     std::vector<double> prof((size_t)nz * 5);
     CK(h, cudaMemcpyAsync(prof.data(), h->prof_d, sizeof(double) * prof.size(),
                           cudaMemcpyDeviceToHost, h->stream));

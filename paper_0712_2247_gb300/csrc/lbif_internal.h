@@ -5,17 +5,21 @@
 //           idx = (z*ny + y)*nx + x, two buffers, push streaming. A population
 //           is stored as g_i = f_i/(w_i n0) - 1 - R(r): its relative deviation
 //           from the rest weights w_i n0, minus the node's reference density
-//           deviation R(r), so that stored values are O(u) even where the
+//           deviation R(r), so that stored values stay small even where the
 //           density is far from n0 (next to the walls).
 //   dn[2]   float on a padded grid (halo hw on every side), double-buffered:
 //           dn[cur] holds R = dn(r, t-1), the reference of the stored
 //           populations; the moments kernel writes dn(r, t) = R + sum_i w_i g_i
 //           into dn[cur^1], which becomes the reference after the step.
-//   M       float4 {dn, ux, uy, uz} on the padded grid (u = j/n).
+//   ux, uy, uz  float velocity u = j/n on the padded grid.
 //   dG      float  g2(etabar) - g2(eta0) on the padded grid.
+//   F       float4 F/n0 per node (force kernel -> collision kernel).
 //   The x/y halo holds periodic images written by the producing kernel; the
 //   z halo holds images (periodic z) or the constant outside-the-fluid values
-//   dn = -1, u = 0, dG = 0 (slit), so stencils need no bounds tests.
+//   dn = -1, u = 0, dG = 0 (slit), so stencils need no bounds tests. Padded
+//   rows are 16-byte aligned (hw and px multiples of 4) so four consecutive x
+//   nodes are one float4; every padded array has 64 floats of slack on both
+//   sides for the vector windows of the stencils.
 #pragma once
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -27,11 +31,12 @@ namespace lbif {
 
 constexpr int Q = 19;
 constexpr int MAX_SIGMA = 24;
+constexpr int PAD_SLACK = 64;  // floats before and after every padded array
 
 struct Geom {
     int nx, ny, nz;
-    int hw;          // halo width of the padded fields
-    int px, py, pz;  // padded extents
+    int hw;          // halo width of the padded fields (multiple of 4)
+    int px, py, pz;  // padded extents (px multiple of 4)
     int zper;
     long long N;     // nx*ny*nz
     long long Npad;  // population plane stride (N rounded up to 64)
@@ -69,32 +74,42 @@ struct Params {
     float body[3];
     int sigma;
     int hs, coupling, regularize, g2form, tail, storage;
-    int nbr[Q];      // padded offsets of the 19 lattice neighbours
+    int nbr[Q];         // padded offsets of the 19 lattice neighbours
+    long long soff[Q];  // node-index offsets of the 19 neighbours (no wrap)
     Shell sh;
 };
 
+// moment fields of the current step (padded)
+struct Fields {
+    const float* dn;
+    const float* ux;
+    const float* uy;
+    const float* uz;
+    const float* dG;
+};
+
 // ---- launchers (lbif_kernels.cu) -------------------------------------------
-cudaError_t launch_fill_outside(const Params& P, float4* M, float* dnA, float* dnB, float* dG,
-                                cudaStream_t s);
+cudaError_t launch_fill_outside(const Params& P, float* const* planes, const float* values,
+                                int nplanes, cudaStream_t s);
 cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t seed, double amp,
                               long long offset, cudaStream_t s);
 cudaError_t launch_init_fields(const Params& P, void* pop, float* dn, const float* rho,
                                const float* u, cudaStream_t s);
 cudaError_t launch_write_ref(const Params& P, const float* ref, float* dn, cudaStream_t s);
 cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaStream_t s);
-cudaError_t launch_moments(const Params& P, const void* pop, float4* M, float* dref, float* dnew,
-                           int* status, cudaStream_t s);
+cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, float* dnew,
+                           float* ux, float* uy, float* uz, int* status, cudaStream_t s);
 cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s);
 cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const float4* K,
                         int npairs, float4* Ft, cudaStream_t s);
-cudaError_t launch_force(const Params& P, const float4* M, const float* dG, const float4* Ft,
-                         float4* F, cudaStream_t s);
-cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const float4* M, const float* dn,
+cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F,
+                         cudaStream_t s);
+cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields& f,
                       const float4* F, cudaStream_t s);
-cudaError_t launch_force_out(const Params& P, const float4* M, const float* dG, const float4* Ft,
-                             float* F, cudaStream_t s);
-cudaError_t launch_moments_out(const Params& P, const float4* M, const float* dG, float* rho,
-                               float* u, float* p, cudaStream_t s);
-cudaError_t launch_profiles(const Params& P, const float4* M, double* prof, cudaStream_t s);
+cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s);
+cudaError_t launch_moments_out(const Params& P, const Fields& f, float* rho, float* u, float* p,
+                               cudaStream_t s);
+cudaError_t launch_profiles(const Params& P, const Fields& f, double* prof, cudaStream_t s);
+bool force_vectorised(int sigma);
 
 }  // namespace lbif

@@ -3,28 +3,42 @@
 // Arithmetic is FP32 on small quantities only. Populations are stored
 // relative to the node's reference density (see lbif_internal.h), every
 // field entering the nonlocal force is a deviation from the uniform state
-// (dn = n/n0 - 1, dG = g2 - g2(eta0)), and antipodal quadrature points are
+// (dn = n/n0 - 1, dG = g2 - g2(eta0)), and mirror-image quadrature points are
 // combined before they are summed, so a uniform state gives an exactly zero
 // force. FP64 appears only in the profile / mass reductions.
 #include "lbif_internal.h"
 
 namespace lbif {
 
-// D3Q19, antipodes in consecutive pairs (1,2), (3,4), ..., (17,18).
-__constant__ int kCx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-__constant__ int kCy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-__constant__ int kCz[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-__constant__ float kW[Q] = {1.f / 3.f,  1.f / 18.f, 1.f / 18.f, 1.f / 18.f, 1.f / 18.f,
-                            1.f / 18.f, 1.f / 18.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f,
-                            1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f,
-                            1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
-
-__device__ __forceinline__ int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+// D3Q19, antipodes in consecutive pairs (1,2), (3,4), ..., (17,18). The
+// components are returned by switches so that, inside unrolled loops, every
+// product with a lattice velocity folds to an add, a subtract or nothing.
+__device__ __forceinline__ constexpr int kCx(int i)
+{
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+         : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__device__ __forceinline__ constexpr int kCy(int i)
+{
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+         : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__device__ __forceinline__ constexpr int kCz(int i)
+{
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+         : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
+__device__ __forceinline__ constexpr float kW(int i)
+{
+    return i == 0 ? 1.f / 3.f : (i <= 6 ? 1.f / 18.f : 1.f / 36.f);
+}
+__device__ __forceinline__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
 __device__ __forceinline__ float ldp(const float* p) { return __ldg(p); }
 __device__ __forceinline__ float ldp(const __half* p) { return __half2float(__ldg(p)); }
 __device__ __forceinline__ void stp(float* p, float v) { *p = v; }
 __device__ __forceinline__ void stp(__half* p, float v) { *p = __float2half_rn(v); }
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 __device__ __forceinline__ int pidx(const Geom& g, int x, int y, int z)
 {
@@ -57,18 +71,17 @@ __device__ __forceinline__ void for_images(const Geom& g, int x, int y, int z, F
                 fn(((zi + g.hw) * g.py + (yi + g.hw)) * g.px + (xi + g.hw));
 }
 
-// Block -> node mapping of the stencil kernels: a CTA is a 32 x 8 (x, y) tile
-// of one z plane; CTAs are ordered tile-in-group fastest, then z, then group,
-// where a group is up to 4 x 16 tiles (128 x 128 nodes). The CTAs resident at
-// any moment then cover a compact 128 x 128 x ~20 block, whose +-sigma
-// stencil footprint stays in L2 instead of spanning 2 sigma + 1 full planes.
-constexpr int TILE_X = 32, TILE_Y = 8;
-
+// Block -> node mapping of the stencil kernels: a CTA covers a TX x 8 (x, y)
+// tile of one z plane; CTAs are ordered tile-in-group fastest, then z, then
+// group, where a group spans about 128 x 128 nodes. The CTAs resident at any
+// moment then cover a compact 128 x 128 x ~20 block whose +-sigma stencil
+// footprint stays in L2 instead of spanning 2 sigma + 1 full planes.
 struct TileMap {
-    int tiles_x, tiles_y, gtx, gty, ngx;
+    int tx, tiles_x, tiles_y, gtx, gty, ngx;
 };
 
-__device__ __forceinline__ bool tile_node(const Geom& g, const TileMap& tm, int& x, int& y, int& z)
+__device__ __forceinline__ bool tile_origin(const Geom& g, const TileMap& tm, int& tile_x,
+                                            int& tile_y, int& z)
 {
     const int per = tm.gtx * tm.gty;
     const int b = blockIdx.x;
@@ -76,19 +89,19 @@ __device__ __forceinline__ bool tile_node(const Geom& g, const TileMap& tm, int&
     const int rest = b / per;
     z = rest % g.nz;
     const int grp = rest / g.nz;
-    const int tile_x = (grp % tm.ngx) * tm.gtx + tig % tm.gtx;
-    const int tile_y = (grp / tm.ngx) * tm.gty + tig / tm.gtx;
-    x = tile_x * TILE_X + (threadIdx.x % TILE_X);
-    y = tile_y * TILE_Y + (threadIdx.x / TILE_X);
-    return tile_x < tm.tiles_x && tile_y < tm.tiles_y && x < g.nx && y < g.ny;
+    tile_x = (grp % tm.ngx) * tm.gtx + tig % tm.gtx;
+    tile_y = (grp / tm.ngx) * tm.gty + tig / tm.gtx;
+    return tile_x < tm.tiles_x && tile_y < tm.tiles_y;
 }
 
-static inline TileMap make_tilemap(const Geom& g, unsigned& blocks)
+static inline TileMap make_tilemap(const Geom& g, int tx, unsigned& blocks)
 {
     TileMap tm;
-    tm.tiles_x = (g.nx + TILE_X - 1) / TILE_X;
-    tm.tiles_y = (g.ny + TILE_Y - 1) / TILE_Y;
-    tm.gtx = tm.tiles_x < 4 ? tm.tiles_x : 4;
+    tm.tx = tx;
+    tm.tiles_x = (g.nx + tx - 1) / tx;
+    tm.tiles_y = (g.ny + 7) / 8;
+    int want_x = (128 + tx - 1) / tx;
+    tm.gtx = tm.tiles_x < want_x ? tm.tiles_x : want_x;
     tm.gty = tm.tiles_y < 16 ? tm.tiles_y : 16;
     tm.ngx = (tm.tiles_x + tm.gtx - 1) / tm.gtx;
     int ngy = (tm.tiles_y + tm.gty - 1) / tm.gty;
@@ -110,11 +123,11 @@ __device__ __forceinline__ void sums_of(const float g[Q], float& S, float& jx, f
     float s = 0.f, ax = 0.f, ay = 0.f, az = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        float wg = kW[i] * g[i];
+        float wg = kW(i) * g[i];
         s += wg;
-        ax += kCx[i] * wg;
-        ay += kCy[i] * wg;
-        az += kCz[i] * wg;
+        ax += kCx(i) * wg;
+        ay += kCy(i) * wg;
+        az += kCz(i) * wg;
     }
     S = s;
     jx = ax;
@@ -125,14 +138,20 @@ __device__ __forceinline__ void sums_of(const float g[Q], float& S, float& jx, f
 // e_i = h_i^eq - dn = (1 + dn)(3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
 __device__ __forceinline__ float eq_excess(int i, float opd, float ux, float uy, float uz, float uu)
 {
-    float cu = kCx[i] * ux + kCy[i] * uy + kCz[i] * uz;
+    float cu = kCx(i) * ux + kCy(i) * uy + kCz(i) * uz;
     return opd * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
 }
 
 // ---------------------------------------------------------------------------
 // initialisation and reference-field plumbing
 // ---------------------------------------------------------------------------
-__global__ void k_fill_outside(Params P, float4* M, float* dnA, float* dnB, float* dG)
+struct OutsidePlanes {
+    float* p[8];
+    float v[8];
+    int n;
+};
+
+__global__ void k_fill_outside(Params P, OutsidePlanes op)
 {
     // constant values beyond the walls: n = 0 (dn = -1), u = 0, g2 unused (0)
     const Geom& g = P.g;
@@ -144,10 +163,7 @@ __global__ void k_fill_outside(Params P, float4* M, float* dnA, float* dnB, floa
     long long rem = k - zl * plane;
     int zp = (int)(zl < g.hw ? zl : zl + g.nz);
     long long p = (long long)zp * plane + rem;
-    M[p] = make_float4(-1.f, 0.f, 0.f, 0.f);
-    dnA[p] = -1.f;
-    dnB[p] = -1.f;
-    dG[p] = 0.f;
+    for (int j = 0; j < op.n; ++j) op.p[j][p] = op.v[j];
 }
 
 __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
@@ -216,12 +232,12 @@ __global__ void k_read_ref(Params P, const float* dn, float* ref)
 
 // ---------------------------------------------------------------------------
 // step 1: moments (Sec. Theory: n = int f, n u = int v f)
-//   reads the reference R = dn(t-1) from dref, writes dn(t) to dnew and M
+//   reads the reference R = dn(t-1) from dref, writes dn(t) and u
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments(Params P, const T* __restrict__ pop,
-                                                 float4* __restrict__ M, float* dref, float* dnew,
-                                                 int* status)
+                                                 const float* dref, float* dnew, float* oux,
+                                                 float* ouy, float* ouz, int* status)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -236,10 +252,11 @@ __global__ void __launch_bounds__(256) k_moments(Params P, const T* __restrict__
     float inv = 1.f / (1.f + dn);
     float ux = jx * inv, uy = jy * inv, uz = jz * inv;
     if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
-    float4 m = make_float4(dn, ux, uy, uz);
     for_images(P.g, x, y, z, [&](int p) {
-        M[p] = m;
         dnew[p] = dn;
+        oux[p] = ux;
+        ouy[p] = uy;
+        ouz[p] = uz;
     });
 }
 
@@ -353,47 +370,46 @@ __global__ void __launch_bounds__(256) k_ball(Params P, const float* __restrict_
 }
 
 // ---------------------------------------------------------------------------
-// step 3: hard-sphere shell force, Eq. LBHS at constant T, 18-point rule
+// step 3: hard-sphere shell force, Eq. LBHS at constant T, 18-point rule.
+//   T_q = A_q - (G0 + A_q) lk s_q.(u_q - u),  A_q = G_q n_q / n0 - G0
+//       = G0 dq + gq (1 + dq);  the coupling product is split by axis,
+//   T_q = A_q - Pa_q - Pb_q, so that parts that cancel between mirror points
+//   cancel exactly before they meet the small remainder.
 // ---------------------------------------------------------------------------
-template <int A>
-__device__ __forceinline__ float ucomp(const float4& v)
-{
-    return A == 0 ? v.y : (A == 1 ? v.z : v.w);
-}
-
-// For one quadrature point: A = G_q n_q / n0 - G0 = G0 dq + gq (1 + dq) and the
-// coupling products (G0 + A) lk s_q.(u_q - u) split by axis, so that
-// T_q = A - Pa - Pb.
 __device__ __forceinline__ float shell_A(float dq, float gq, float G0) { return G0 * dq + gq * (1.f + dq); }
 
 template <int A>
-__device__ __forceinline__ void axis_pair(const Params& P, const float4* __restrict__ M,
-                                          const float* __restrict__ dG, int p, const float4& m0,
+__device__ __forceinline__ const float* ufield(const Fields& f)
+{
+    return A == 0 ? f.ux : (A == 1 ? f.uy : f.uz);
+}
+
+// generic path: one node per thread, scalar loads (any even sigma)
+template <int A>
+__device__ __forceinline__ void axis_pair(const Params& P, const Fields& fl, int p, const float u0[3],
                                           float lk, float f[3])
 {
     const int o = P.sh.ax_nb[A], om = P.sh.ax_md[A];
-    float4 vp = __ldg(M + p + o), vm = __ldg(M + p - o);
-    float gp = __ldg(dG + p + om), gm = __ldg(dG + p - om);
-    float u0 = ucomp<A>(m0);
-    float Ap = shell_A(vp.x, gp, P.G0), Am = shell_A(vm.x, gm, P.G0);
-    float tp = Ap - (P.G0 + Ap) * lk * (ucomp<A>(vp) - u0);
-    float tm = Am - (P.G0 + Am) * lk * (u0 - ucomp<A>(vm));
+    const float* uf = ufield<A>(fl);
+    float dp = __ldg(fl.dn + p + o), dm = __ldg(fl.dn + p - o);
+    float up = __ldg(uf + p + o), um = __ldg(uf + p - o);
+    float gp = __ldg(fl.dG + p + om), gm = __ldg(fl.dG + p - om);
+    float Ap = shell_A(dp, gp, P.G0), Am = shell_A(dm, gm, P.G0);
+    float tp = Ap - (P.G0 + Ap) * lk * (up - u0[A]);
+    float tm = Am - (P.G0 + Am) * lk * (u0[A] - um);
     f[A] += (1.f / 30.f) * (tp - tm);
 }
 
-// The four points sigma (sa e_a + sb e_b)/sqrt2 of one coordinate plane.
-// The a-component pairs members with equal b-offset and the b-component
-// members with equal a-offset, so that terms which cancel in a field uniform
-// along a (or b) cancel exactly before rounding meets the small remainder.
 template <int PL>
-__device__ __forceinline__ void diag_quartet(const Params& P, const float4* __restrict__ M,
-                                             const float* __restrict__ dG, int p,
-                                             const float4& m0, float lk, float f[3])
+__device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, int p,
+                                             const float u0[3], float lk, float f[3])
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
     constexpr float h = 0.70710678118654752f;
-    // member order: (+,+), (-,+), (+,-), (-,-)
+    const float* fa = a == 0 ? fl.ux : fl.uy;
+    const float* fb = b == 1 ? fl.uy : fl.uz;
+    // member m: sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1
     float dq[4] = {0.f, 0.f, 0.f, 0.f}, ua[4] = {0.f, 0.f, 0.f, 0.f}, ub[4] = {0.f, 0.f, 0.f, 0.f};
     float gq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -404,24 +420,23 @@ __device__ __forceinline__ void diag_quartet(const Params& P, const float4* __re
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const int sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1;
-            float4 v = __ldg(M + p + sa * oa + sb * ob);
-            dq[m] += w * v.x;
-            ua[m] += w * ucomp<a>(v);
-            ub[m] += w * ucomp<b>(v);
-            gq[m] += wm * __ldg(dG + p + sa * ma + sb * mb);
+            const int o = p + sa * oa + sb * ob;
+            dq[m] = fmaf(w, __ldg(fl.dn + o), dq[m]);
+            ua[m] = fmaf(w, __ldg(fa + o), ua[m]);
+            ub[m] = fmaf(w, __ldg(fb + o), ub[m]);
+            gq[m] = fmaf(wm, __ldg(fl.dG + p + sa * ma + sb * mb), gq[m]);
         }
     }
-    const float ua0 = ucomp<a>(m0), ub0 = ucomp<b>(m0);
     float Aq[4], Pa[4], Pb[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const float sa = (m & 1) ? -1.f : 1.f, sb = (m & 2) ? -1.f : 1.f;
         Aq[m] = shell_A(dq[m], gq[m], P.G0);
         float c = (P.G0 + Aq[m]) * lk * h;
-        Pa[m] = c * (sa * (ua[m] - ua0));
-        Pb[m] = c * (sb * (ub[m] - ub0));
+        Pa[m] = c * (sa * (ua[m] - u0[a]));
+        Pb[m] = c * (sb * (ub[m] - u0[b]));
     }
-    // T = A - Pa - Pb; a-component sum sa T, b-component sum sb T
+    // a-component sums sa T over members paired by equal b offset, b-component sb T
     float da = ((Aq[0] - Aq[1]) - (Pa[0] - Pa[1]) - (Pb[0] - Pb[1])) +
                ((Aq[2] - Aq[3]) - (Pa[2] - Pa[3]) - (Pb[2] - Pb[3]));
     float db = ((Aq[0] - Aq[2]) - (Pa[0] - Pa[2]) - (Pb[0] - Pb[2])) +
@@ -430,33 +445,37 @@ __device__ __forceinline__ void diag_quartet(const Params& P, const float4* __re
     f[b] += (h / 15.f) * db;
 }
 
-// total force F / n0 at a node (body + hard sphere + tail)
-__device__ __forceinline__ void node_force(const Params& P, const float4* __restrict__ M,
-                                           const float* __restrict__ dG,
-                                           const float4* __restrict__ Ft, long long idx, int z,
-                                           int p, const float4& m0, float& fx, float& fy, float& fz)
+__device__ __forceinline__ float coupling_factor(const Params& P, int z)
 {
-    float opd = 1.f + m0.x;
+    if (!P.coupling) return 0.f;
+    float lam = 1.f;
+    if (P.regularize && !P.g.zper) {
+        float dw = fminf(z + 0.5f, P.g.nz - 0.5f - z);
+        lam = 1.f - expf(-dw * P.inv_sigma);
+    }
+    return lam * P.kappa;
+}
+
+// total force F / n0 at a node (body + hard sphere + tail)
+__device__ __forceinline__ void node_force(const Params& P, const Fields& fl,
+                                           const float4* __restrict__ Ft, long long idx, int z,
+                                           int p, float& fx, float& fy, float& fz)
+{
+    const float d0 = __ldg(fl.dn + p);
+    const float u0[3] = {__ldg(fl.ux + p), __ldg(fl.uy + p), __ldg(fl.uz + p)};
+    float opd = 1.f + d0;
     fx = opd * P.body[0];
     fy = opd * P.body[1];
     fz = opd * P.body[2];
     if (P.hs) {
-        float lk = 0.f;
-        if (P.coupling) {
-            float lam = 1.f;
-            if (P.regularize && !P.g.zper) {
-                float dw = fminf(z + 0.5f, P.g.nz - 0.5f - z);
-                lam = 1.f - expf(-dw * P.inv_sigma);
-            }
-            lk = lam * P.kappa;
-        }
+        const float lk = coupling_factor(P, z);
         float f[3] = {0.f, 0.f, 0.f};
-        axis_pair<0>(P, M, dG, p, m0, lk, f);
-        axis_pair<1>(P, M, dG, p, m0, lk, f);
-        axis_pair<2>(P, M, dG, p, m0, lk, f);
-        diag_quartet<0>(P, M, dG, p, m0, lk, f);
-        diag_quartet<1>(P, M, dG, p, m0, lk, f);
-        diag_quartet<2>(P, M, dG, p, m0, lk, f);
+        axis_pair<0>(P, fl, p, u0, lk, f);
+        axis_pair<1>(P, fl, p, u0, lk, f);
+        axis_pair<2>(P, fl, p, u0, lk, f);
+        diag_quartet<0>(P, fl, p, u0, lk, f);
+        diag_quartet<1>(P, fl, p, u0, lk, f);
+        diag_quartet<2>(P, fl, p, u0, lk, f);
         float pre = P.hs_pref * opd;
         fx += pre * f[0];
         fy += pre * f[1];
@@ -469,6 +488,280 @@ __device__ __forceinline__ void node_force(const Params& P, const float4* __rest
         fz += t.z;
     }
 }
+
+__global__ void __launch_bounds__(256) k_force(Params P, TileMap tm, Fields fl,
+                                               const float4* __restrict__ Ft, float4* __restrict__ F)
+{
+    const Geom& g = P.g;
+    int tx, ty, z;
+    if (!tile_origin(g, tm, tx, ty, z)) return;
+    const int x = tx * tm.tx + threadIdx.x % 32, y = ty * 8 + threadIdx.x / 32;
+    if (x >= g.nx || y >= g.ny) return;
+    const long long idx = ((long long)z * g.ny + y) * g.nx + x;
+    float fx, fy, fz;
+    node_force(P, fl, Ft, idx, z, pidx(g, x, y, z), fx, fy, fz);
+    F[idx] = make_float4(fx, fy, fz, 0.f);
+}
+
+// ---- vectorised path: four consecutive x nodes per thread, float4 loads ----
+// (sigma a template parameter, so the x offsets and the window alignments are
+// compile-time constants; the y / z strides are runtime)
+typedef float v4[4];
+
+__host__ __device__ constexpr int floor4(int d) { return d >= 0 ? (d / 4) * 4 : -(((-d) + 3) / 4) * 4; }
+
+__device__ __forceinline__ void set4(v4 r, float4 a)
+{
+    r[0] = a.x;
+    r[1] = a.y;
+    r[2] = a.z;
+    r[3] = a.w;
+}
+
+// values at x offsets D..D+3 of a float4-aligned base
+template <int D>
+__device__ __forceinline__ void win(const float* __restrict__ f, int b, v4 r)
+{
+    constexpr int B4 = floor4(D), RR = D - B4;
+    if constexpr (RR == 0) {
+        set4(r, ld4(f + b + B4));
+    } else {
+        const float4 A = ld4(f + b + B4), C = ld4(f + b + B4 + 4);
+        const float t[8] = {A.x, A.y, A.z, A.w, C.x, C.y, C.z, C.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) r[j] = t[RR + j];
+    }
+}
+
+// windows at x offsets D and D + 1 (the two corners along x), sharing loads
+template <int D>
+__device__ __forceinline__ void win2(const float* __restrict__ f, int b, v4 w0, v4 w1)
+{
+    constexpr int RR = D - floor4(D);
+    if constexpr (RR == 0) {
+        const float4 A = ld4(f + b + D);
+        const float s = __ldg(f + b + D + 4);
+        set4(w0, A);
+        w1[0] = A.y;
+        w1[1] = A.z;
+        w1[2] = A.w;
+        w1[3] = s;
+    } else if constexpr (RR == 3) {
+        const float4 C = ld4(f + b + D + 1);
+        const float s = __ldg(f + b + D);
+        w0[0] = s;
+        w0[1] = C.x;
+        w0[2] = C.y;
+        w0[3] = C.z;
+        set4(w1, C);
+    } else {
+        const float4 A = ld4(f + b + D - RR), C = ld4(f + b + D - RR + 4);
+        const float t[8] = {A.x, A.y, A.z, A.w, C.x, C.y, C.z, C.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            w0[j] = t[RR + j];
+            w1[j] = t[RR + 1 + j];
+        }
+    }
+}
+
+// x offsets of the two corners of a member with x sign SA: SA > 0: (LO, LO+1),
+// SA < 0: (-LO, -LO-1); returns the windows in corner order (ka = 0, 1)
+template <int LO, int SA>
+__device__ __forceinline__ void corners_x(const float* __restrict__ f, int b, v4 c0, v4 c1)
+{
+    if constexpr (SA > 0)
+        win2<LO>(f, b, c0, c1);
+    else
+        win2<-LO - 1>(f, b, c1, c0);
+}
+
+template <int SIG, int PL, int M>
+__device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int pb, v4 dq, v4 ua,
+                                         v4 ub, v4 gq)
+{
+    // PL 0: plane (x, y); PL 1: plane (x, z); a = x
+    constexpr int LO = cisqrt(SIG * SIG / 2), LOM = cisqrt((SIG / 2) * (SIG / 2) / 2);
+    constexpr int SA = (M & 1) ? -1 : 1, SB = (M & 2) ? -1 : 1;
+    const int sbs = PL == 0 ? P.g.px : P.g.px * P.g.py;
+    const float* fb = PL == 0 ? fl.uy : fl.uz;
+#pragma unroll
+    for (int kb = 0; kb < 2; ++kb) {
+        const int row = pb + SB * (LO + kb) * sbs;
+        const float w0 = P.sh.nb_w[PL][2 * kb], w1 = P.sh.nb_w[PL][2 * kb + 1];
+        v4 c0, c1;
+        corners_x<LO, SA>(fl.dn, row, c0, c1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) dq[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], dq[j]));
+        corners_x<LO, SA>(fl.ux, row, c0, c1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ua[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], ua[j]));
+        corners_x<LO, SA>(fb, row, c0, c1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) ub[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], ub[j]));
+        const int mrow = pb + SB * (LOM + kb) * sbs;
+        const float v0 = P.sh.md_w[PL][2 * kb], v1 = P.sh.md_w[PL][2 * kb + 1];
+        corners_x<LOM, SA>(fl.dG, mrow, c0, c1);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) gq[j] = fmaf(v1, c1[j], fmaf(v0, c0[j], gq[j]));
+    }
+}
+
+template <int SIG, int M>
+__device__ __forceinline__ void member_yz(const Params& P, const Fields& fl, int pb, v4 dq, v4 ua,
+                                          v4 ub, v4 gq)
+{
+    // plane (y, z): no x offset, every corner is an aligned float4
+    constexpr int LO = cisqrt(SIG * SIG / 2), LOM = cisqrt((SIG / 2) * (SIG / 2) / 2);
+    constexpr int SA = (M & 1) ? -1 : 1, SB = (M & 2) ? -1 : 1;
+    const int sy = P.g.px, sz = P.g.px * P.g.py;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int ka = k & 1, kb = k >> 1;
+        const int o = pb + SA * (LO + ka) * sy + SB * (LO + kb) * sz;
+        const int om = pb + SA * (LOM + ka) * sy + SB * (LOM + kb) * sz;
+        const float w = P.sh.nb_w[2][k], wm = P.sh.md_w[2][k];
+        v4 d, a, b, gg;
+        set4(d, ld4(fl.dn + o));
+        set4(a, ld4(fl.uy + o));
+        set4(b, ld4(fl.uz + o));
+        set4(gg, ld4(fl.dG + om));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            dq[j] = fmaf(w, d[j], dq[j]);
+            ua[j] = fmaf(w, a[j], ua[j]);
+            ub[j] = fmaf(w, b[j], ub[j]);
+            gq[j] = fmaf(wm, gg[j], gq[j]);
+        }
+    }
+}
+
+template <int SIG, int PL, int M>
+__device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, int pb,
+                                             const v4 ua0, const v4 ub0, float lk, v4 Aq, v4 Pa,
+                                             v4 Pb)
+{
+    constexpr float h = 0.70710678118654752f;
+    constexpr float sa = (M & 1) ? -1.f : 1.f, sb = (M & 2) ? -1.f : 1.f;
+    v4 dq, ua, ub, gq;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dq[j] = ua[j] = ub[j] = gq[j] = 0.f;
+    if constexpr (PL == 2)
+        member_yz<SIG, M>(P, fl, pb, dq, ua, ub, gq);
+    else
+        member_x<SIG, PL, M>(P, fl, pb, dq, ua, ub, gq);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Aq[j] = shell_A(dq[j], gq[j], P.G0);
+        float c = (P.G0 + Aq[j]) * lk * h;
+        Pa[j] = c * (sa * (ua[j] - ua0[j]));
+        Pb[j] = c * (sb * (ub[j] - ub0[j]));
+    }
+}
+
+template <int SIG, int PL>
+__device__ __forceinline__ void quartet4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
+                                         float lk, v4 f[3])
+{
+    constexpr int a = PL == 2 ? 1 : 0;
+    constexpr int b = PL == 0 ? 1 : 2;
+    constexpr float c = 0.70710678118654752f / 15.f;
+    v4 A0, P0a, P0b, A1, P1a, P1b, A2, P2a, P2b, A3, P3a, P3b;
+    member_terms<SIG, PL, 0>(P, fl, pb, u0[a], u0[b], lk, A0, P0a, P0b);
+    member_terms<SIG, PL, 1>(P, fl, pb, u0[a], u0[b], lk, A1, P1a, P1b);
+    member_terms<SIG, PL, 2>(P, fl, pb, u0[a], u0[b], lk, A2, P2a, P2b);
+    member_terms<SIG, PL, 3>(P, fl, pb, u0[a], u0[b], lk, A3, P3a, P3b);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float da = ((A0[j] - A1[j]) - (P0a[j] - P1a[j]) - (P0b[j] - P1b[j])) +
+                   ((A2[j] - A3[j]) - (P2a[j] - P3a[j]) - (P2b[j] - P3b[j]));
+        float db = ((A0[j] - A2[j]) - (P0a[j] - P2a[j]) - (P0b[j] - P2b[j])) +
+                   ((A1[j] - A3[j]) - (P1a[j] - P3a[j]) - (P1b[j] - P3b[j]));
+        f[a][j] += c * da;
+        f[b][j] += c * db;
+    }
+}
+
+template <int SIG, int A>
+__device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
+                                      float lk, v4 f[3])
+{
+    const float* uf = ufield<A>(fl);
+    v4 dp, dm, up, um, gp, gm;
+    if constexpr (A == 0) {
+        win<SIG>(fl.dn, pb, dp);
+        win<-SIG>(fl.dn, pb, dm);
+        win<SIG>(uf, pb, up);
+        win<-SIG>(uf, pb, um);
+        win<SIG / 2>(fl.dG, pb, gp);
+        win<-SIG / 2>(fl.dG, pb, gm);
+    } else {
+        const int st = A == 1 ? P.g.px : P.g.px * P.g.py;
+        set4(dp, ld4(fl.dn + pb + SIG * st));
+        set4(dm, ld4(fl.dn + pb - SIG * st));
+        set4(up, ld4(uf + pb + SIG * st));
+        set4(um, ld4(uf + pb - SIG * st));
+        set4(gp, ld4(fl.dG + pb + (SIG / 2) * st));
+        set4(gm, ld4(fl.dG + pb - (SIG / 2) * st));
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float Ap = shell_A(dp[j], gp[j], P.G0), Am = shell_A(dm[j], gm[j], P.G0);
+        float tp = Ap - (P.G0 + Ap) * lk * (up[j] - u0[A][j]);
+        float tm = Am - (P.G0 + Am) * lk * (u0[A][j] - um[j]);
+        f[A][j] += (1.f / 30.f) * (tp - tm);
+    }
+}
+
+template <int SIG>
+__global__ void __launch_bounds__(256) k_force4(Params P, TileMap tm, Fields fl,
+                                                const float4* __restrict__ Ft, float4* __restrict__ F)
+{
+    const Geom& g = P.g;
+    int tx, ty, z;
+    if (!tile_origin(g, tm, tx, ty, z)) return;
+    const int x = tx * 128 + 4 * (threadIdx.x % 32), y = ty * 8 + threadIdx.x / 32;
+    if (x >= g.nx || y >= g.ny) return;
+    const int pb = pidx(g, x, y, z);  // 16-byte aligned: x, hw, px multiples of 4
+    v4 d0, u0[3];
+    set4(d0, ld4(fl.dn + pb));
+    set4(u0[0], ld4(fl.ux + pb));
+    set4(u0[1], ld4(fl.uy + pb));
+    set4(u0[2], ld4(fl.uz + pb));
+    v4 f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) f[a][j] = 0.f;
+    if (P.hs) {
+        const float lk = coupling_factor(P, z);
+        axis4<SIG, 0>(P, fl, pb, u0, lk, f);
+        axis4<SIG, 1>(P, fl, pb, u0, lk, f);
+        axis4<SIG, 2>(P, fl, pb, u0, lk, f);
+        quartet4<SIG, 0>(P, fl, pb, u0, lk, f);
+        quartet4<SIG, 1>(P, fl, pb, u0, lk, f);
+        quartet4<SIG, 2>(P, fl, pb, u0, lk, f);
+    }
+    const long long idx0 = ((long long)z * g.ny + y) * g.nx + x;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (x + j >= g.nx) break;
+        const float opd = 1.f + d0[j];
+        const float pre = P.hs_pref * opd;
+        float fx = opd * P.body[0] + pre * f[0][j];
+        float fy = opd * P.body[1] + pre * f[1][j];
+        float fz = opd * P.body[2] + pre * f[2][j];
+        if (P.tail) {
+            float4 t = Ft[idx0 + j];
+            fx += t.x;
+            fy += t.y;
+            fz += t.z;
+        }
+        F[idx0 + j] = make_float4(fx, fy, fz, 0.f);
+    }
+}
+
+bool force_vectorised(int sigma) { return sigma == 4 || sigma == 8 || sigma == 12; }
 
 // ---------------------------------------------------------------------------
 // step 4: mean-field attractive tail, F/n0 = n0 (1 + dn) sum_d dn(r+d) phi'(|d|) d/|d|
@@ -496,37 +789,15 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
 }
 
 // ---------------------------------------------------------------------------
-// step 5: total force F / n0 per node (body + hard sphere + tail), one thread
-// per node over 32 x 8 tiles; stored as float4 for the collision kernel.
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256, 3) k_force(Params P, TileMap tm, const float4* __restrict__ M,
-                                                  const float* __restrict__ dG,
-                                                  const float4* __restrict__ Ft,
-                                                  float4* __restrict__ F)
-{
-    const Geom& g = P.g;
-    int x, y, z;
-    if (!tile_node(g, tm, x, y, z)) return;
-    const long long idx = ((long long)z * g.ny + y) * g.nx + x;
-    const int p = pidx(g, x, y, z);
-    float4 m0 = __ldg(M + p);
-    float fx, fy, fz;
-    node_force(P, M, dG, Ft, idx, z, p, m0, fx, fy, fz);
-    F[idx] = make_float4(fx, fy, fz, 0.f);
-}
-
-// ---------------------------------------------------------------------------
-// step 6: BGK collision with the first-order source and push streaming with
-// half-way bounce-back (Sec. Methods: forward-Euler update, local equilibrium;
-// bounce-back walls). Works on k_i = h_i - dn (populations relative to the
-// node's own current density) and stores, at the target, the value relative
-// to the target's current density.
+// steps 5-6: BGK collision with the first-order source and push streaming
+// with half-way bounce-back (Sec. Methods: forward-Euler update, local
+// equilibrium; bounce-back walls). Works on k_i = h_i - dn (populations
+// relative to the node's own current density) and stores, at the target,
+// the value relative to the target's current density.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(256) k_cs(Params P, const T* __restrict__ pin, T* __restrict__ pout,
-                                            const float4* __restrict__ M,
-                                            const float* __restrict__ dn,
-                                            const float4* __restrict__ F)
+                                            Fields fl, const float4* __restrict__ F)
 {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -536,19 +807,32 @@ __global__ void __launch_bounds__(256) k_cs(Params P, const T* __restrict__ pin,
     const int p = pidx(g, x, y, z);
     float gi[Q];
     load_pops(P, pin, idx, gi);
-    const float4 m0 = __ldg(M + p);
+    const float d0 = __ldg(fl.dn + p), ux = __ldg(fl.ux + p), uy = __ldg(fl.uy + p),
+                uz = __ldg(fl.uz + p);
     const float4 f = __ldg(F + idx);
     float S, jx, jy, jz;
     sums_of(gi, S, jx, jy, jz);
-    const float d0 = m0.x, ux = m0.y, uy = m0.z, uz = m0.w;
     const float opd = 1.f + d0;
     const float uu = ux * ux + uy * uy + uz * uz;
+    const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
+    if (interior) {
+        // no wrap, no wall: target = idx + constant offset
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            float k = gi[i] - S;
+            float e = eq_excess(i, opd, ux, uy, uz, uu);
+            float ks = k - (k - e) * P.inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
+            float dt = i == 0 ? d0 : __ldg(fl.dn + p + P.nbr[i]);
+            stp(pout + (long long)i * g.Npad + (idx + P.soff[i]), ks + (d0 - dt));
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         float k = gi[i] - S;
         float e = eq_excess(i, opd, ux, uy, uz, uu);
-        float ks = k - (k - e) * P.inv_tau + 3.f * (kCx[i] * f.x + kCy[i] * f.y + kCz[i] * f.z);
-        int tx = x + kCx[i], ty = y + kCy[i], tz = z + kCz[i];
+        float ks = k - (k - e) * P.inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
+        int tx = x + kCx(i), ty = y + kCy(i), tz = z + kCz(i);
         tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
         ty = ty < 0 ? ty + g.ny : (ty >= g.ny ? ty - g.ny : ty);
         if (g.zper) {
@@ -557,7 +841,7 @@ __global__ void __launch_bounds__(256) k_cs(Params P, const T* __restrict__ pin,
             stp(pout + (long long)opp_of(i) * g.Npad + idx, ks);
             continue;
         }
-        float dt = i == 0 ? d0 : __ldg(dn + p + P.nbr[i]);
+        float dt = i == 0 ? d0 : __ldg(fl.dn + p + P.nbr[i]);
         long long t = ((long long)tz * g.ny + ty) * g.nx + tx;
         stp(pout + (long long)i * g.Npad + t, ks + (d0 - dt));
     }
@@ -566,30 +850,24 @@ __global__ void __launch_bounds__(256) k_cs(Params P, const T* __restrict__ pin,
 // ---------------------------------------------------------------------------
 // outputs
 // ---------------------------------------------------------------------------
-__global__ void k_force_out(Params P, TileMap tm, const float4* __restrict__ M,
-                            const float* __restrict__ dG, const float4* __restrict__ Ft,
-                            float* __restrict__ F)
+__global__ void k_force_soa(Params P, const float4* __restrict__ F, float* __restrict__ out)
 {
-    int x, y, z;
-    if (!tile_node(P.g, tm, x, y, z)) return;
-    const long long idx = ((long long)z * P.g.ny + y) * P.g.nx + x;
-    int p = pidx(P.g, x, y, z);
-    float4 m = M[p];
-    float fx, fy, fz;
-    node_force(P, M, dG, Ft, idx, z, p, m, fx, fy, fz);
-    F[idx] = fx;
-    F[P.g.N + idx] = fy;
-    F[2 * P.g.N + idx] = fz;
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
+    float4 v = F[idx];
+    out[idx] = v.x;
+    out[P.g.N + idx] = v.y;
+    out[2 * P.g.N + idx] = v.z;
 }
 
 // sum over the 18 points of W_q A_q (A_q = G_q n_q / n0 - G0)
-__device__ __forceinline__ float shell_A_sum(const Params& P, const float4* M, const float* dG, int p)
+__device__ __forceinline__ float shell_A_sum(const Params& P, const Fields& fl, int p)
 {
     float s = 0.f;
     for (int a = 0; a < 3; ++a)
         for (int sg = -1; sg <= 1; sg += 2) {
-            float dq = __ldg(&M[p + sg * P.sh.ax_nb[a]].x);
-            float gq = __ldg(dG + p + sg * P.sh.ax_md[a]);
+            float dq = __ldg(fl.dn + p + sg * P.sh.ax_nb[a]);
+            float gq = __ldg(fl.dG + p + sg * P.sh.ax_md[a]);
             s += (1.f / 30.f) * shell_A(dq, gq, P.G0);
         }
     for (int pl = 0; pl < 3; ++pl)
@@ -597,8 +875,8 @@ __device__ __forceinline__ float shell_A_sum(const Params& P, const float4* M, c
             const int sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1;
             float dq = 0.f, gq = 0.f;
             for (int k = 0; k < 4; ++k) {
-                dq += P.sh.nb_w[pl][k] * __ldg(&M[p + sa * P.sh.nb_a[pl][k] + sb * P.sh.nb_b[pl][k]].x);
-                gq += P.sh.md_w[pl][k] * __ldg(dG + p + sa * P.sh.md_a[pl][k] + sb * P.sh.md_b[pl][k]);
+                dq += P.sh.nb_w[pl][k] * __ldg(fl.dn + p + sa * P.sh.nb_a[pl][k] + sb * P.sh.nb_b[pl][k]);
+                gq += P.sh.md_w[pl][k] * __ldg(fl.dG + p + sa * P.sh.md_a[pl][k] + sb * P.sh.md_b[pl][k]);
             }
             s += (1.f / 15.f) * shell_A(dq, gq, P.G0);
         }
@@ -606,31 +884,30 @@ __device__ __forceinline__ float shell_A_sum(const Params& P, const float4* M, c
 }
 
 // rho, u and p = kT n + (kT sigma^3/6) 4 pi n0^2 (1 + dn) sum_q W_q (G0 + A_q)
-__global__ void k_moments_out(Params P, const float4* __restrict__ M, const float* __restrict__ dG,
-                              float* rho, float* u, float* pr)
+__global__ void k_moments_out(Params P, Fields fl, float* rho, float* u, float* pr)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
     int x, y, z;
     decompose(P.g, idx, x, y, z);
     int p = pidx(P.g, x, y, z);
-    float4 m = M[p];
-    if (rho) rho[idx] = P.rho0 * (1.f + m.x);
+    const float d = fl.dn[p];
+    if (rho) rho[idx] = P.rho0 * (1.f + d);
     if (u) {
-        u[idx] = m.y;
-        u[P.g.N + idx] = m.z;
-        u[2 * P.g.N + idx] = m.w;
+        u[idx] = fl.ux[p];
+        u[P.g.N + idx] = fl.uy[p];
+        u[2 * P.g.N + idx] = fl.uz[p];
     }
     if (pr) {
         float s = 0.f;
-        if (P.hs) s = (P.G0 + shell_A_sum(P, M, dG, p)) * P.p_pref * (1.f + m.x);
-        pr[idx] = (1.f / 3.f) * P.rho0 * (1.f + m.x) + s;
+        if (P.hs) s = (P.G0 + shell_A_sum(P, fl, p)) * P.p_pref * (1.f + d);
+        pr[idx] = (1.f / 3.f) * P.rho0 * (1.f + d) + s;
     }
 }
 
 // per z plane: sum dn, sum ux, sum (1+dn) u  (FP64, fixed-order tree)
 constexpr int PROF_K = 5;
-__global__ void k_profiles(Params P, const float4* __restrict__ M, double* prof)
+__global__ void k_profiles(Params P, Fields fl, double* prof)
 {
     __shared__ double sh[PROF_K][256];
     const Geom& g = P.g;
@@ -639,13 +916,14 @@ __global__ void k_profiles(Params P, const float4* __restrict__ M, double* prof)
     int A = g.nx * g.ny;
     for (int k = threadIdx.x; k < A; k += blockDim.x) {
         int y = k / g.nx, x = k - y * g.nx;
-        float4 m = M[pidx(g, x, y, z)];
-        double opd = 1.0 + (double)m.x;
-        a[0] += (double)m.x;
-        a[1] += (double)m.y;
-        a[2] += opd * m.y;
-        a[3] += opd * m.z;
-        a[4] += opd * m.w;
+        int p = pidx(g, x, y, z);
+        double d = (double)fl.dn[p], vx = fl.ux[p], vy = fl.uy[p], vz = fl.uz[p];
+        double opd = 1.0 + d;
+        a[0] += d;
+        a[1] += vx;
+        a[2] += opd * vx;
+        a[3] += opd * vy;
+        a[4] += opd * vz;
     }
     for (int j = 0; j < PROF_K; ++j) sh[j][threadIdx.x] = a[j];
     __syncthreads();
@@ -662,12 +940,19 @@ __global__ void k_profiles(Params P, const float4* __restrict__ M, double* prof)
 // ---------------------------------------------------------------------------
 static inline unsigned nblocks(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-cudaError_t launch_fill_outside(const Params& P, float4* M, float* dnA, float* dnB, float* dG,
-                                cudaStream_t s)
+cudaError_t launch_fill_outside(const Params& P, float* const* planes, const float* values,
+                                int nplanes, cudaStream_t s)
 {
     long long total = (long long)P.g.px * P.g.py * 2 * P.g.hw;
     if (P.g.zper || total == 0) return cudaSuccess;
-    k_fill_outside<<<nblocks(total, 256), 256, 0, s>>>(P, M, dnA, dnB, dG);
+    if (nplanes > 8) return cudaErrorInvalidValue;
+    OutsidePlanes op;
+    op.n = nplanes;
+    for (int j = 0; j < nplanes; ++j) {
+        op.p[j] = planes[j];
+        op.v[j] = values[j];
+    }
+    k_fill_outside<<<nblocks(total, 256), 256, 0, s>>>(P, op);
     return cudaGetLastError();
 }
 
@@ -703,15 +988,15 @@ cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(const Params& P, const void* pop, float4* M, float* dref, float* dnew,
-                           int* status, cudaStream_t s)
+cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, float* dnew,
+                           float* ux, float* uy, float* uz, int* status, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_moments<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pop, M, dref, dnew,
-                                                               status);
+        k_moments<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pop, dref, dnew, ux,
+                                                               uy, uz, status);
     else
-        k_moments<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pop, M, dref, dnew,
-                                                              status);
+        k_moments<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pop, dref, dnew, ux,
+                                                              uy, uz, status);
     return cudaGetLastError();
 }
 
@@ -766,44 +1051,49 @@ cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(const Params& P, const float4* M, const float* dG, const float4* Ft,
-                         float4* F, cudaStream_t s)
+cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F, cudaStream_t s)
 {
     unsigned blocks;
-    TileMap tm = make_tilemap(P.g, blocks);
-    k_force<<<blocks, 256, 0, s>>>(P, tm, M, dG, Ft, F);
+    if (force_vectorised(P.sigma)) {
+        TileMap tm = make_tilemap(P.g, 128, blocks);
+        switch (P.sigma) {
+        case 4: k_force4<4><<<blocks, 256, 0, s>>>(P, tm, f, Ft, F); break;
+        case 8: k_force4<8><<<blocks, 256, 0, s>>>(P, tm, f, Ft, F); break;
+        default: k_force4<12><<<blocks, 256, 0, s>>>(P, tm, f, Ft, F); break;
+        }
+    } else {
+        TileMap tm = make_tilemap(P.g, 32, blocks);
+        k_force<<<blocks, 256, 0, s>>>(P, tm, f, Ft, F);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const float4* M, const float* dn,
+cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields& f,
                       const float4* F, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_cs<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pin, (__half*)pout, M, dn, F);
+        k_cs<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pin, (__half*)pout, f, F);
     else
-        k_cs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, M, dn, F);
+        k_cs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, f, F);
     return cudaGetLastError();
 }
 
-cudaError_t launch_force_out(const Params& P, const float4* M, const float* dG, const float4* Ft,
-                             float* F, cudaStream_t s)
+cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s)
 {
-    unsigned blocks;
-    TileMap tm = make_tilemap(P.g, blocks);
-    k_force_out<<<blocks, 256, 0, s>>>(P, tm, M, dG, Ft, F);
+    k_force_soa<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, F, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments_out(const Params& P, const float4* M, const float* dG, float* rho,
-                               float* u, float* p, cudaStream_t s)
+cudaError_t launch_moments_out(const Params& P, const Fields& f, float* rho, float* u, float* p,
+                               cudaStream_t s)
 {
-    k_moments_out<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, M, dG, rho, u, p);
+    k_moments_out<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, f, rho, u, p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_profiles(const Params& P, const float4* M, double* prof, cudaStream_t s)
+cudaError_t launch_profiles(const Params& P, const Fields& f, double* prof, cudaStream_t s)
 {
-    k_profiles<<<P.g.nz, 256, 0, s>>>(P, M, prof);
+    k_profiles<<<P.g.nz, 256, 0, s>>>(P, f, prof);
     return cudaGetLastError();
 }
 
