@@ -77,7 +77,7 @@ __device__ __forceinline__ void for_images(const Geom& g, int x, int y, int z, F
 // moment then cover a compact 128 x 128 x ~20 block whose +-sigma stencil
 // footprint stays in L2 instead of spanning 2 sigma + 1 full planes.
 struct TileMap {
-    int tx, tiles_x, tiles_y, gtx, gty, ngx;
+    int tx, ty, tiles_x, tiles_y, gtx, gty, ngx;
 };
 
 __device__ __forceinline__ bool tile_origin(const Geom& g, const TileMap& tm, int& tile_x,
@@ -94,15 +94,16 @@ __device__ __forceinline__ bool tile_origin(const Geom& g, const TileMap& tm, in
     return tile_x < tm.tiles_x && tile_y < tm.tiles_y;
 }
 
-static inline TileMap make_tilemap(const Geom& g, int tx, unsigned& blocks)
+static inline TileMap make_tilemap(const Geom& g, int tx, int ty, unsigned& blocks)
 {
     TileMap tm;
     tm.tx = tx;
+    tm.ty = ty;
     tm.tiles_x = (g.nx + tx - 1) / tx;
-    tm.tiles_y = (g.ny + 7) / 8;
-    int want_x = (128 + tx - 1) / tx;
+    tm.tiles_y = (g.ny + ty - 1) / ty;
+    int want_x = (128 + tx - 1) / tx, want_y = (128 + ty - 1) / ty;
     tm.gtx = tm.tiles_x < want_x ? tm.tiles_x : want_x;
-    tm.gty = tm.tiles_y < 16 ? tm.tiles_y : 16;
+    tm.gty = tm.tiles_y < want_y ? tm.tiles_y : want_y;
     tm.ngx = (tm.tiles_x + tm.gtx - 1) / tm.gtx;
     int ngy = (tm.tiles_y + tm.gty - 1) / tm.gty;
     blocks = (unsigned)tm.gtx * tm.gty * g.nz * tm.ngx * ngy;
@@ -292,7 +293,7 @@ __host__ __device__ constexpr int cisqrt(int n)
     return w;
 }
 
-constexpr int BALL_TX = 32, BALL_TY = 8;
+constexpr int BALL_TX = 32, BALL_TY = 32, BALL_THREADS = 1024;
 
 template <int R>
 constexpr int ball_smem_floats()
@@ -300,12 +301,12 @@ constexpr int ball_smem_floats()
     return (BALL_TY + 2 * R) * (BALL_TX + 2 * R) + (R + 1) * (BALL_TY + 2 * R) * BALL_TX;
 }
 
-// One CTA = a 32 x 8 column of nodes marching up a z chunk. Per input plane:
+// One CTA = a 32 x 32 column of nodes marching up a z chunk. Per input plane:
 // stage the plane (+R halo) in shared memory, build x-row sums of every
 // half-width 0..R, add the disc sums D_k (disc of radius^2 R^2 - k^2) into a
 // register ring of the 2R+1 output planes it touches, emit the completed one.
 template <int R>
-__global__ void __launch_bounds__(256) k_ball(Params P, const float* __restrict__ dn,
+__global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __restrict__ dn,
                                               float* __restrict__ dG, int* status, int zchunk)
 {
     constexpr int TX = BALL_TX, TY = BALL_TY;
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(256) k_force(Params P, TileMap tm, Fields fl,
     const Geom& g = P.g;
     int tx, ty, z;
     if (!tile_origin(g, tm, tx, ty, z)) return;
-    const int x = tx * tm.tx + threadIdx.x % 32, y = ty * 8 + threadIdx.x / 32;
+    const int x = tx * tm.tx + threadIdx.x % 32, y = ty * tm.ty + threadIdx.x / 32;
     if (x >= g.nx || y >= g.ny) return;
     const long long idx = ((long long)z * g.ny + y) * g.nx + x;
     float fx, fy, fz;
@@ -714,13 +715,13 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
 }
 
 template <int SIG>
-__global__ void __launch_bounds__(256) k_force4(Params P, TileMap tm, Fields fl,
+__global__ void __launch_bounds__(128) k_force4(Params P, TileMap tm, Fields fl,
                                                 const float4* __restrict__ Ft, float4* __restrict__ F)
 {
     const Geom& g = P.g;
     int tx, ty, z;
     if (!tile_origin(g, tm, tx, ty, z)) return;
-    const int x = tx * 128 + 4 * (threadIdx.x % 32), y = ty * 8 + threadIdx.x / 32;
+    const int x = tx * 128 + 4 * (threadIdx.x % 32), y = ty * tm.ty + threadIdx.x / 32;
     if (x >= g.nx || y >= g.ny) return;
     const int pb = pidx(g, x, y, z);  // 16-byte aligned: x, hw, px multiples of 4
     v4 d0, u0[3];
@@ -796,8 +797,8 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
 // the value relative to the target's current density.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256) k_cs(Params P, const T* __restrict__ pin, T* __restrict__ pout,
-                                            Fields fl, const float4* __restrict__ F)
+__global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ pin, T* __restrict__ pout,
+                                               Fields fl, const float4* __restrict__ F)
 {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -816,14 +817,20 @@ __global__ void __launch_bounds__(256) k_cs(Params P, const T* __restrict__ pin,
     const float uu = ux * ux + uy * uy + uz * uz;
     const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
     if (interior) {
-        // no wrap, no wall: target = idx + constant offset
+        // no wrap, no wall: target = idx + constant offset. The neighbour
+        // densities are fetched together first so their latencies overlap.
+        float dd[Q];
+        dd[0] = 0.f;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) dd[i] = __ldg(fl.dn + p + P.nbr[i]);
+#pragma unroll
+        for (int i = 1; i < Q; ++i) dd[i] = d0 - dd[i];
 #pragma unroll
         for (int i = 0; i < Q; ++i) {
             float k = gi[i] - S;
             float e = eq_excess(i, opd, ux, uy, uz, uu);
             float ks = k - (k - e) * P.inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
-            float dt = i == 0 ? d0 : __ldg(fl.dn + p + P.nbr[i]);
-            stp(pout + (long long)i * g.Npad + (idx + P.soff[i]), ks + (d0 - dt));
+            stp(pout + (long long)i * g.Npad + (idx + P.soff[i]), ks + dd[i]);
         }
         return;
     }
@@ -1013,7 +1020,7 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
         configured = true;
     }
     int gx = (g.nx + BALL_TX - 1) / BALL_TX, gy = (g.ny + BALL_TY - 1) / BALL_TY;
-    int want = 1216;  // ~8 CTAs per SM on 152 SMs
+    int want = 608;  // ~4 waves of one 1024-thread CTA per SM on 152 SMs
     int nchunk = (want + gx * gy - 1) / (gx * gy);
     int maxchunk = g.nz / (2 * R) > 1 ? g.nz / (2 * R) : 1;
     if (nchunk > maxchunk) nchunk = maxchunk;
@@ -1021,7 +1028,7 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
     int zchunk = (g.nz + nchunk - 1) / nchunk;
     nchunk = (g.nz + zchunk - 1) / zchunk;
     dim3 grid(gx, gy, nchunk);
-    k_ball<R><<<grid, 256, smem, s>>>(P, dn, dG, status, zchunk);
+    k_ball<R><<<grid, BALL_THREADS, smem, s>>>(P, dn, dG, status, zchunk);
     return cudaGetLastError();
 }
 
@@ -1055,14 +1062,14 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
 {
     unsigned blocks;
     if (force_vectorised(P.sigma)) {
-        TileMap tm = make_tilemap(P.g, 128, blocks);
+        TileMap tm = make_tilemap(P.g, 128, 4, blocks);
         switch (P.sigma) {
-        case 4: k_force4<4><<<blocks, 256, 0, s>>>(P, tm, f, Ft, F); break;
-        case 8: k_force4<8><<<blocks, 256, 0, s>>>(P, tm, f, Ft, F); break;
-        default: k_force4<12><<<blocks, 256, 0, s>>>(P, tm, f, Ft, F); break;
+        case 4: k_force4<4><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
+        case 8: k_force4<8><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
+        default: k_force4<12><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
         }
     } else {
-        TileMap tm = make_tilemap(P.g, 32, blocks);
+        TileMap tm = make_tilemap(P.g, 32, 8, blocks);
         k_force<<<blocks, 256, 0, s>>>(P, tm, f, Ft, F);
     }
     return cudaGetLastError();
