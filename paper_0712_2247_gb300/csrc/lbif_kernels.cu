@@ -71,7 +71,7 @@ __device__ __forceinline__ void for_images(const Geom& g, int x, int y, int z, F
                 fn(((zi + g.hw) * g.py + (yi + g.hw)) * g.px + (xi + g.hw));
 }
 
-// Block -> node mapping of the stencil kernels: a CTA covers a TX x 8 (x, y)
+// Block -> node mapping of the stencil kernels: a CTA covers a TX x TY (x, y)
 // tile of one z plane; CTAs are ordered tile-in-group fastest, then z, then
 // group, where a group spans about 128 x 128 nodes. The CTAs resident at any
 // moment then cover a compact 128 x 128 x ~20 block whose +-sigma stencil
@@ -293,7 +293,7 @@ __host__ __device__ constexpr int cisqrt(int n)
     return w;
 }
 
-constexpr int BALL_TX = 32, BALL_TY = 32, BALL_THREADS = 1024;
+constexpr int BALL_TX = 32, BALL_TY = 8, BALL_THREADS = 256;
 
 template <int R>
 constexpr int ball_smem_floats()
@@ -301,7 +301,7 @@ constexpr int ball_smem_floats()
     return (BALL_TY + 2 * R) * (BALL_TX + 2 * R) + (R + 1) * (BALL_TY + 2 * R) * BALL_TX;
 }
 
-// One CTA = a 32 x 32 column of nodes marching up a z chunk. Per input plane:
+// One CTA = a 32 x 8 column of nodes marching up a z chunk. Per input plane:
 // stage the plane (+R halo) in shared memory, build x-row sums of every
 // half-width 0..R, add the disc sums D_k (disc of radius^2 R^2 - k^2) into a
 // register ring of the 2R+1 output planes it touches, emit the completed one.
@@ -1020,7 +1020,7 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
         configured = true;
     }
     int gx = (g.nx + BALL_TX - 1) / BALL_TX, gy = (g.ny + BALL_TY - 1) / BALL_TY;
-    int want = 608;  // ~4 waves of one 1024-thread CTA per SM on 152 SMs
+    int want = 1216;  // ~8 CTAs per SM on 152 SMs
     int nchunk = (want + gx * gy - 1) / (gx * gy);
     int maxchunk = g.nz / (2 * R) > 1 ? g.nz / (2 * R) : 1;
     if (nchunk > maxchunk) nchunk = maxchunk;
