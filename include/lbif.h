@@ -135,6 +135,50 @@ int lbif_status(lbif_handle h, int32_t* status);
 int lbif_save(lbif_handle h, const char* path);
 int lbif_load(lbif_handle h, const char* path);
 
+/* ---- ensemble of slits ---------------------------------------------------
+ * Many independent slits of one sigma and lateral size nx x ny, each with its
+ * own width H[s] (nodes along z), packing fraction eta[s], body force F[s]
+ * (per particle, along x) and relaxation time tau[s], advanced together: they
+ * are stacked along z with hw >= sigma planes of "outside" (n = 0) between
+ * them, so every stencil of the step (ball, shell, streaming, bounce-back)
+ * sees only its own slit, and one launch per kernel covers all of them.
+ * f gives the force model (its body[] is ignored); o as for lbif_create, but
+ * with o->stream NULL the handle creates and owns a non-blocking stream
+ * (needed for graph capture). lbif_step / lbif_moments / lbif_profiles /
+ * lbif_save / lbif_load work on the stacked grid (gap planes read as 0). */
+int lbif_batch_create(lbif_handle* out, int32_t nslits, const int32_t* H, const double* eta,
+                      const double* F, const double* tau, double sigma, int32_t nx, int32_t ny,
+                      const lbif_force* f, const lbif_opts* o);
+
+/* Number of slits, first plane of each slit in the stacked grid (zlo[nslits],
+ * may be NULL) and the number of fluid nodes. */
+int lbif_batch_info(lbif_handle h, int32_t* nslits, int32_t* zlo, int64_t* nodes);
+
+/* Re-initialise every slit to the local equilibrium of x,y-uniform profiles:
+ * n_z[s*hmax + j], ux_z[s*hmax + j] (host arrays; ux_z may be NULL = 0) for
+ * the j-th plane of slit s, j < H[s] (entries j >= H[s] are ignored). Resets
+ * the step counter. Used to seed slits from a predicted steady state. */
+int lbif_batch_seed(lbif_handle h, const float* n_z, const float* ux_z, int32_t hmax);
+
+/* Advance all slits, check_every steps per CUDA-graph replay (rounded up to
+ * even), until every slit's residual (lbif_residual's definition over its own
+ * x,y-averaged profiles, with t - t0 = check_every) is below tol, or
+ * max_steps. Converged slits are frozen (their kernels exit at once) while the
+ * others continue. steps_taken[s] (may be NULL) = steps at which slit s met
+ * tol, -1 if it did not within max_steps, -2 if it diverged. */
+int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int32_t check_every,
+                   int64_t* steps_taken);
+
+/* FP64 x,y-averaged profiles of every slit, n_z / ux_z[s*hmax + j] (host
+ * arrays, either may be NULL; zero beyond H[s]). Synchronises. */
+int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax);
+
+/* Time the candidate launch shapes of the ball and force kernels on this
+ * handle's current state (trials launches each) and keep the fastest. The
+ * state is unchanged. Chosen values (may be NULL): ball CTA target, force
+ * tile-group edge in nodes. */
+int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group);
+
 int lbif_destroy(lbif_handle h);
 
 /* Message of the last error of a handle; NULL handle = last global error

@@ -1,6 +1,8 @@
 // Host side of the C ABI declared in include/lbif.h: argument checks, the
-// quadrature / ball / tail tables (built in FP64, rounded once to FP32),
-// device allocation and the per-step launch sequence.
+// quadrature / tail tables (built in FP64, rounded once to FP32), the slit
+// tables, device allocation, the per-step launch sequence, the ensemble
+// driver (CUDA graph of K steps, per-slit FP64 residual, freezing) and its
+// launch-shape autotuner.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -13,9 +15,15 @@
 
 using namespace lbif;
 
+struct SlitDesc {
+    int zlo, zhi;
+    double eta, tau, body[3];
+};
+
 struct lbif_ctx {
     Params P;
     cudaStream_t stream = nullptr;
+    bool own_stream = false;
     void* pop[2] = {nullptr, nullptr};
     int cur = 0;                      // populations of the current step
     float* dn[2] = {nullptr, nullptr};
@@ -32,6 +40,16 @@ struct lbif_ctx {
     int* status_d = nullptr;
     double* prof_d = nullptr;
     float* scratch = nullptr;         // 3 N floats, for host-side outputs
+    SlitParam* d_sl = nullptr;
+    int* d_zslit = nullptr;
+    int* d_done = nullptr;
+    std::vector<SlitParam> sl;
+    std::vector<int> zslit;
+    std::vector<int> done;
+    bool batch = false;
+    int ball_want = 0, force_group = 0;  // launch shapes (0 = defaults; set by the autotuner)
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
     int64_t t = 0;
     int64_t fields_t = -1, G_t = -1, tail_t = -1;  // step the cached fields belong to
     std::vector<double> last_n, last_ux;
@@ -77,12 +95,14 @@ static void padded_free(float* p)
 static void free_ctx(lbif_ctx* h)
 {
     if (!h) return;
-    void* bufs[] = {h->pop[0], h->pop[1], h->Ft,     h->F,      h->tail_off,
-                    h->tail_K, h->status_d, h->prof_d, h->scratch};
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    void* bufs[] = {h->pop[0], h->pop[1], h->Ft,    h->F,       h->tail_off, h->tail_K, h->status_d,
+                    h->prof_d, h->scratch, h->d_sl, h->d_zslit, h->d_done};
     for (void* b : bufs)
         if (b) cudaFree(b);
     float* pads[] = {h->dn[0], h->dn[1], h->ux, h->uy, h->uz, h->dG};
     for (float* q : pads) padded_free(q);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
 
@@ -165,51 +185,58 @@ static double g2_host(double e, int form)
     return form == 1 ? (1 - 0.5 * e) / d : (1 - 0.5 * e + 0.25 * e * e) / d;
 }
 
+static SlitParam slit_param(const SlitDesc& d, double sigma, int g2form)
+{
+    const double kT = 1.0 / 3.0;
+    double n0 = 6.0 * d.eta / (M_PI * sigma * sigma * sigma);
+    SlitParam s;
+    memset(&s, 0, sizeof(s));
+    s.rho0 = (float)n0;
+    s.eta0 = (float)d.eta;
+    s.G0 = (float)g2_host(d.eta, g2form);
+    s.inv_tau = (float)(1.0 / d.tau);
+    s.hs_pref = (float)(-kT * sigma * sigma * 4.0 * M_PI * n0);
+    s.p_pref = (float)(kT * sigma * sigma * sigma / 6.0 * 4.0 * M_PI * n0 * n0);
+    for (int a = 0; a < 3; ++a) s.body[a] = (float)d.body[a];
+    s.zlo = d.zlo;
+    s.zhi = d.zhi;
+    return s;
+}
+
 // --------------------------------------------------------------------------
 // create / destroy
 // --------------------------------------------------------------------------
-extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double eta, double tau,
-                           lbif_walls w, const lbif_force* f, const lbif_opts* o)
+static int check_common(double sigma, const lbif_force& F, const lbif_opts& O, const char* who)
 {
-    if (!out) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: out is NULL");
-    *out = nullptr;
-    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1)
-        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: grid extents must be >= 1");
+    std::string w(who);
     if (!(sigma >= 2.0) || sigma != floor(sigma) || ((int)sigma) % 2 != 0 || sigma > MAX_SIGMA)
         return fail(nullptr, LBIF_ERR_UNSUPPORTED,
-                    "lbif_create: sigma must be an even integer in [2, 24] lattice spacings");
-    if (!(eta > 0.0 && eta < 1.0)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: eta must be in (0,1)");
-    if (!(tau > 0.5)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: tau must be > 1/2");
-    if (w.z != LBIF_WALL_BOUNCEBACK && w.z != LBIF_PERIODIC)
-        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: walls.z must be BOUNCEBACK or PERIODIC");
-    lbif_force fz;
-    memset(&fz, 0, sizeof(fz));
-    const lbif_force& F = f ? *f : fz;
-    lbif_opts oz;
-    memset(&oz, 0, sizeof(oz));
-    oz.noise = 1e-3;
-    const lbif_opts& O = o ? *o : oz;
+                    w + ": sigma must be an even integer in [2, 24] lattice spacings");
     if (O.storage != LBIF_STORE_F32 && O.storage != LBIF_STORE_F16)
-        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: storage must be 0 (FP32) or 1 (FP16)");
-    if (!(O.noise >= 0.0 && O.noise < 1.0)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: noise must be in [0,1)");
+        return fail(nullptr, LBIF_ERR_ARG, w + ": storage must be 0 (FP32) or 1 (FP16)");
+    if (!(O.noise >= 0.0 && O.noise < 1.0)) return fail(nullptr, LBIF_ERR_ARG, w + ": noise must be in [0,1)");
     if (F.tail && !(F.rcut >= 1.0 && F.rcut <= 4.0 && F.eps >= 0.0))
-        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: tail needs rcut in [1,4] and eps >= 0");
-    if ((F.g2_form != 0 && F.g2_form != 1))
-        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: g2_form must be 0 or 1");
+        return fail(nullptr, LBIF_ERR_ARG, w + ": tail needs rcut in [1,4] and eps >= 0");
+    if ((F.g2_form != 0 && F.g2_form != 1)) return fail(nullptr, LBIF_ERR_ARG, w + ": g2_form must be 0 or 1");
     for (int a = 0; a < 3; ++a)
-        if (!isfinite(F.body[a])) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: body force not finite");
+        if (!isfinite(F.body[a])) return fail(nullptr, LBIF_ERR_ARG, w + ": body force not finite");
+    return LBIF_OK;
+}
 
+static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int zper,
+                       const lbif_force& F, const lbif_opts& O, const std::vector<SlitDesc>& slits,
+                       const std::vector<int>& zslit, bool batch)
+{
     lbif_ctx* h = new lbif_ctx();
     memset(&h->P, 0, sizeof(Params));
     Params& P = h->P;
-    int s = (int)sigma;
     Geom& g = P.g;
-    g.nx = gr.nx;
-    g.ny = gr.ny;
-    g.nz = gr.nz;
-    g.zper = (w.z == LBIF_PERIODIC);
-    g.hw = s;
-    if (F.tail) g.hw = std::max(g.hw, (int)ceil(F.rcut * s));
+    g.nx = nx;
+    g.ny = ny;
+    g.nz = nz;
+    g.zper = zper;
+    g.hw = sigma;
+    if (F.tail) g.hw = std::max(g.hw, (int)ceil(F.rcut * sigma));
     g.hw = (g.hw + 3) / 4 * 4;                   // rows 16-byte aligned
     g.px = (g.nx + 2 * g.hw + 8 + 3) / 4 * 4;    // + slack columns for float4 windows
     g.py = g.ny + 2 * g.hw;
@@ -219,27 +246,20 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     g.P = (long long)g.px * g.py * g.pz;
     if (g.P >= (1LL << 31)) {
         delete h;
-        return fail(nullptr, LBIF_ERR_UNSUPPORTED, "lbif_create: padded grid exceeds 2^31 nodes");
+        return fail(nullptr, LBIF_ERR_UNSUPPORTED, "create: padded grid exceeds 2^31 nodes");
     }
     const double kT = 1.0 / 3.0;
-    double n0 = 6.0 * eta / (M_PI * sigma * sigma * sigma);
-    P.sigma = s;
-    P.inv_tau = (float)(1.0 / tau);
-    P.rho0 = (float)n0;
-    P.eta0 = (float)eta;
-    P.G0 = (float)g2_host(eta, F.g2_form);
-    P.hs_pref = (float)(-kT * sigma * sigma * 4.0 * M_PI * n0);
-    P.p_pref = (float)(kT * sigma * sigma * sigma / 6.0 * 4.0 * M_PI * n0 * n0);
+    P.sigma = sigma;
     P.kappa = (float)(2.0 / (sqrt(kT) * sqrt(M_PI)));
     P.inv_sigma = (float)(1.0 / sigma);
-    P.ball_inv = (float)(1.0 / ball_count(s));
-    for (int a = 0; a < 3; ++a) P.body[a] = (float)F.body[a];
+    P.ball_inv = (float)(1.0 / ball_count(sigma));
     P.hs = F.hs ? 1 : 0;
     P.coupling = F.coupling ? 1 : 0;
     P.regularize = F.regularize ? 1 : 0;
     P.g2form = F.g2_form;
     P.tail = F.tail ? 1 : 0;
     P.storage = O.storage;
+    P.nslits = (int)slits.size();
     {
         const int cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
         const int cy[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
@@ -251,9 +271,23 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     }
     if (build_shell(P)) {
         delete h;
-        return fail(nullptr, LBIF_ERR_UNSUPPORTED, "lbif_create: quadrature tables do not fit");
+        return fail(nullptr, LBIF_ERR_UNSUPPORTED, "create: quadrature tables do not fit");
     }
-    h->stream = (cudaStream_t)O.stream;
+    h->batch = batch;
+    for (const SlitDesc& d : slits) h->sl.push_back(slit_param(d, sigma, F.g2_form));
+    h->zslit = zslit;
+    h->done.assign(slits.size(), 0);
+    if (O.stream) {
+        h->stream = (cudaStream_t)O.stream;
+    } else if (batch) {
+        // graph capture needs a stream other than the legacy default one
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return fail(nullptr, LBIF_ERR_CUDA, "create: stream creation failed");
+        }
+        h->own_stream = true;
+    }
 
     // tail taps: one representative of each +-d pair with sigma <= |d| <= rcut sigma
     std::vector<int> toff;
@@ -261,12 +295,12 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     if (P.tail) {
         double rmax = F.rcut * sigma;
         int R = (int)ceil(rmax);
-        double s6 = pow(sigma, 6.0), s12 = s6 * s6;
+        double s6 = pow((double)sigma, 6.0), s12 = s6 * s6;
         for (int dz = 0; dz <= R; ++dz)
             for (int dy = (dz == 0 ? 0 : -R); dy <= R; ++dy)
                 for (int dx = ((dz == 0 && dy == 0) ? 1 : -R); dx <= R; ++dx) {
                     double r2 = (double)dx * dx + (double)dy * dy + (double)dz * dz;
-                    if (r2 < sigma * sigma || r2 > rmax * rmax) continue;
+                    if (r2 < (double)sigma * sigma || r2 > rmax * rmax) continue;
                     double r = sqrt(r2);
                     double dphi = 4.0 * F.eps * (-12.0 * s12 / pow(r, 13.0) + 6.0 * s6 / pow(r, 7.0));
                     toff.push_back(padded_offset(g, dx, dy, dz));
@@ -282,7 +316,7 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
         if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                           \
             cudaGetLastError();                                                             \
             free_ctx(h);                                                                    \
-            return fail(nullptr, LBIF_ERR_NOMEM, "lbif_create: device allocation failed");  \
+            return fail(nullptr, LBIF_ERR_NOMEM, "create: device allocation failed");       \
         }                                                                                   \
     } while (0)
     ALLOC(h->pop[0], pb);
@@ -290,22 +324,28 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
     ALLOC(h->F, sizeof(float4) * (size_t)g.N);
     ALLOC(h->status_d, sizeof(int));
     ALLOC(h->prof_d, sizeof(double) * 5 * (size_t)g.nz);
+    ALLOC(h->d_sl, sizeof(SlitParam) * h->sl.size());
+    ALLOC(h->d_zslit, sizeof(int) * (size_t)g.nz);
+    ALLOC(h->d_done, sizeof(int) * h->sl.size());
     if (P.tail) {
         ALLOC(h->Ft, sizeof(float4) * (size_t)g.N);
         ALLOC(h->tail_off, sizeof(int) * toff.size());
         ALLOC(h->tail_K, sizeof(float4) * tK.size());
     }
+#undef ALLOC
     {
         float** pads[] = {&h->dn[0], &h->dn[1], &h->ux, &h->uy, &h->uz, &h->dG};
         for (float** q : pads) {
             *q = padded_alloc((size_t)g.P);
             if (!*q) {
                 free_ctx(h);
-                return fail(nullptr, LBIF_ERR_NOMEM, "lbif_create: device allocation failed");
+                return fail(nullptr, LBIF_ERR_NOMEM, "create: device allocation failed");
             }
         }
     }
-#undef ALLOC
+    P.sl = h->d_sl;
+    P.zslit = h->d_zslit;
+    P.done = h->d_done;
     lbif_ctx* hc = h;
 #define CKC(call)                                                                           \
     do {                                                                                    \
@@ -316,6 +356,11 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
             return fail(nullptr, LBIF_ERR_CUDA, m_);                                        \
         }                                                                                   \
     } while (0)
+    CKC(cudaMemcpyAsync(h->d_sl, h->sl.data(), sizeof(SlitParam) * h->sl.size(), cudaMemcpyHostToDevice,
+                        h->stream));
+    CKC(cudaMemcpyAsync(h->d_zslit, h->zslit.data(), sizeof(int) * h->zslit.size(),
+                        cudaMemcpyHostToDevice, h->stream));
+    CKC(cudaMemsetAsync(h->d_done, 0, sizeof(int) * h->sl.size(), h->stream));
     CKC(cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
     CKC(cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
     {
@@ -324,6 +369,19 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
         for (float* q : pads)
             CKC(cudaMemsetAsync(q - PAD_SLACK, 0, sizeof(float) * ((size_t)g.P + 2 * PAD_SLACK), h->stream));
         CKC(launch_fill_outside(P, pads, outside, 6, h->stream));
+        if (batch) {
+            // gap planes between stacked slits hold the outside values too
+            for (int z = 0; z < g.nz; ++z) {
+                if (zslit[z] >= 0) continue;
+                size_t plane = (size_t)g.px * g.py, off = (size_t)(z + g.hw) * plane;
+                std::vector<float> minus1(plane, -1.f);
+                CKC(cudaMemcpyAsync(h->dn[0] + off, minus1.data(), sizeof(float) * plane,
+                                    cudaMemcpyHostToDevice, h->stream));
+                CKC(cudaMemcpyAsync(h->dn[1] + off, minus1.data(), sizeof(float) * plane,
+                                    cudaMemcpyHostToDevice, h->stream));
+                CKC(cudaStreamSynchronize(h->stream));
+            }
+        }
     }
     CKC(cudaMemsetAsync(h->status_d, 0, sizeof(int), h->stream));
     if (P.tail) {
@@ -337,6 +395,75 @@ extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double 
 #undef CKC
     *out = h;
     return LBIF_OK;
+}
+
+extern "C" int lbif_create(lbif_handle* out, lbif_grid gr, double sigma, double eta, double tau,
+                           lbif_walls w, const lbif_force* f, const lbif_opts* o)
+{
+    if (!out) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: out is NULL");
+    *out = nullptr;
+    if (gr.nx < 1 || gr.ny < 1 || gr.nz < 1)
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: grid extents must be >= 1");
+    if (!(eta > 0.0 && eta < 1.0)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: eta must be in (0,1)");
+    if (!(tau > 0.5)) return fail(nullptr, LBIF_ERR_ARG, "lbif_create: tau must be > 1/2");
+    if (w.z != LBIF_WALL_BOUNCEBACK && w.z != LBIF_PERIODIC)
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_create: walls.z must be BOUNCEBACK or PERIODIC");
+    lbif_force fz;
+    memset(&fz, 0, sizeof(fz));
+    const lbif_force& F = f ? *f : fz;
+    lbif_opts oz;
+    memset(&oz, 0, sizeof(oz));
+    oz.noise = 1e-3;
+    const lbif_opts& O = o ? *o : oz;
+    int rc = check_common(sigma, F, O, "lbif_create");
+    if (rc) return rc;
+    SlitDesc d;
+    d.zlo = 0;
+    d.zhi = gr.nz - 1;
+    d.eta = eta;
+    d.tau = tau;
+    for (int a = 0; a < 3; ++a) d.body[a] = F.body[a];
+    std::vector<int> zs(gr.nz, 0);
+    return create_impl(out, gr.nx, gr.ny, gr.nz, (int)sigma, w.z == LBIF_PERIODIC, F, O, {d}, zs, false);
+}
+
+extern "C" int lbif_batch_create(lbif_handle* out, int32_t nslits, const int32_t* H, const double* eta,
+                                 const double* Fx, const double* tau, double sigma, int32_t nx,
+                                 int32_t ny, const lbif_force* f, const lbif_opts* o)
+{
+    if (!out) return fail(nullptr, LBIF_ERR_ARG, "lbif_batch_create: out is NULL");
+    *out = nullptr;
+    if (nslits < 1 || !H || !eta || !Fx || !tau || nx < 1 || ny < 1)
+        return fail(nullptr, LBIF_ERR_ARG, "lbif_batch_create: bad arguments");
+    lbif_force fz;
+    memset(&fz, 0, sizeof(fz));
+    const lbif_force& F = f ? *f : fz;
+    lbif_opts oz;
+    memset(&oz, 0, sizeof(oz));
+    oz.noise = 1e-3;
+    const lbif_opts& O = o ? *o : oz;
+    int rc = check_common(sigma, F, O, "lbif_batch_create");
+    if (rc) return rc;
+    int hw = (int)sigma;
+    if (F.tail) hw = std::max(hw, (int)ceil(F.rcut * sigma));
+    hw = (hw + 3) / 4 * 4;
+    std::vector<SlitDesc> slits;
+    std::vector<int> zs;
+    for (int s = 0; s < nslits; ++s) {
+        if (H[s] < 1 || !(eta[s] > 0.0 && eta[s] < 1.0) || !(tau[s] > 0.5) || !isfinite(Fx[s]))
+            return fail(nullptr, LBIF_ERR_ARG, "lbif_batch_create: bad slit parameters");
+        if (s > 0) zs.insert(zs.end(), hw, -1);  // gap of outside planes
+        SlitDesc d;
+        d.zlo = (int)zs.size();
+        d.zhi = d.zlo + H[s] - 1;
+        d.eta = eta[s];
+        d.tau = tau[s];
+        d.body[0] = Fx[s];
+        d.body[1] = d.body[2] = 0.0;
+        slits.push_back(d);
+        zs.insert(zs.end(), H[s], s);
+    }
+    return create_impl(out, nx, ny, (int)zs.size(), (int)sigma, 0, F, O, slits, zs, true);
 }
 
 extern "C" int lbif_destroy(lbif_handle h)
@@ -359,22 +486,22 @@ extern "C" const char* lbif_last_error(lbif_handle h)
 // Moments (and, when asked, the g2 field and the tail force) of the current
 // populations; cached per step so that output calls between steps do not
 // redo them. The new dn goes to dn[dcur^1]; the reference dn[dcur] is kept.
-static int refresh_fields(lbif_ctx* h, bool want_G)
+static int refresh_fields(lbif_ctx* h, bool want_G, int skip_done)
 {
     const Params& P = h->P;
     float* dnew = h->dn[h->dcur ^ 1];
     if (h->fields_t != h->t) {
         CK(h, launch_moments(P, h->pop[h->cur], h->dn[h->dcur], dnew, h->ux, h->uy, h->uz,
-                             h->status_d, h->stream));
-        h->fields_t = h->t;
+                             h->status_d, skip_done, h->stream));
+        h->fields_t = skip_done ? -1 : h->t;
     }
     if (want_G && h->G_t != h->t) {
-        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->stream));
-        h->G_t = h->t;
+        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, skip_done, h->stream));
+        h->G_t = skip_done ? -1 : h->t;
     }
     if (P.tail && h->tail_t != h->t) {
         CK(h, launch_tail(P, dnew, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
-        h->tail_t = h->t;
+        h->tail_t = skip_done ? -1 : h->t;
     }
     return LBIF_OK;
 }
@@ -383,7 +510,7 @@ static int advance(lbif_ctx* h)
 {
     const Params& P = h->P;
     const Fields f = fields_of(h);
-    CK(h, launch_force(P, f, h->Ft, h->F, h->stream));
+    CK(h, launch_force(P, f, h->Ft, h->F, h->force_group, h->stream));
     CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], f, h->F, h->stream));
     h->cur ^= 1;
     h->dcur ^= 1;
@@ -391,13 +518,20 @@ static int advance(lbif_ctx* h)
     return LBIF_OK;
 }
 
+// one full step of the active slits (frozen slits skipped)
+static int one_step(lbif_ctx* h)
+{
+    int rc = refresh_fields(h, h->P.hs != 0, 1);
+    if (rc) return rc;
+    return advance(h);
+}
+
 extern "C" int lbif_step(lbif_handle h, int64_t nsteps)
 {
     if (!h || nsteps < 0) return fail(h, LBIF_ERR_ARG, "lbif_step: bad arguments");
     for (int64_t k = 0; k < nsteps; ++k) {
-        int rc = refresh_fields(h, h->P.hs != 0);
+        int rc = one_step(h);
         if (rc) return rc;
-        if ((rc = advance(h))) return rc;
     }
     return LBIF_OK;
 }
@@ -422,11 +556,11 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
         float* dnew = h->dn[h->dcur ^ 1];
         const Fields f = fields_of(h);
         CK(h, launch_moments(P, h->pop[h->cur], h->dn[h->dcur], dnew, h->ux, h->uy, h->uz,
-                             h->status_d, h->stream));
+                             h->status_d, 1, h->stream));
         cls[j] = 0;
         CK(h, cudaEventRecord(ev[++j], h->stream));
         if (P.hs) {
-            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->stream));
+            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, 1, h->stream));
             cls[j] = 1;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
@@ -435,7 +569,7 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
             cls[j] = 2;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
-        CK(h, launch_force(P, f, h->Ft, h->F, h->stream));
+        CK(h, launch_force(P, f, h->Ft, h->F, h->force_group, h->stream));
         cls[j] = 3;
         CK(h, cudaEventRecord(ev[++j], h->stream));
         CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], f, h->F, h->stream));
@@ -485,7 +619,7 @@ extern "C" int lbif_moments(lbif_handle h, float* rho, float* u, float* pressure
 {
     if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_moments: NULL handle");
     const Params& P = h->P;
-    int rc = refresh_fields(h, pressure && P.hs);
+    int rc = refresh_fields(h, pressure && P.hs, 0);
     if (rc) return rc;
     size_t N = (size_t)P.g.N;
     if (on_device) {
@@ -515,10 +649,10 @@ extern "C" int lbif_forces(lbif_handle h, float* F, int32_t on_device)
 {
     if (!h || !F) return fail(h, LBIF_ERR_ARG, "lbif_forces: bad arguments");
     const Params& P = h->P;
-    int rc = refresh_fields(h, P.hs != 0);
+    int rc = refresh_fields(h, P.hs != 0, 0);
     if (rc) return rc;
     // the same force kernel as the time step, then a layout change to SoA
-    CK(h, launch_force(P, fields_of(h), h->Ft, h->F, h->stream));
+    CK(h, launch_force(P, fields_of(h), h->Ft, h->F, h->force_group, h->stream));
     if (on_device) {
         CK(h, launch_force_soa(P, h->F, F, h->stream));
     } else {
@@ -528,6 +662,13 @@ extern "C" int lbif_forces(lbif_handle h, float* F, int32_t on_device)
                               cudaMemcpyDeviceToHost, h->stream));
     }
     return check_status(h);
+}
+
+static void reset_time(lbif_ctx* h)
+{
+    h->t = 0;
+    h->last_t = -1;
+    invalidate(h);
 }
 
 extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, int32_t on_device)
@@ -552,9 +693,21 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
     }
     CK(h, launch_init_fields(P, h->pop[h->cur], h->dn[h->dcur], drho, du, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
-    h->t = 0;
-    h->last_t = -1;
-    invalidate(h);
+    reset_time(h);
+    return LBIF_OK;
+}
+
+// FP64 per-plane sums of the current state (all slits, frozen ones included)
+static int plane_sums(lbif_ctx* h, std::vector<double>& prof)
+{
+    const Params& P = h->P;
+    int rc = refresh_fields(h, false, 0);
+    if (rc) return rc;
+    CK(h, launch_profiles(P, fields_of(h), h->prof_d, h->stream));
+    prof.resize((size_t)P.g.nz * 5);
+    CK(h, cudaMemcpyAsync(prof.data(), h->prof_d, sizeof(double) * prof.size(),
+                          cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
     return LBIF_OK;
 }
 
@@ -562,29 +715,47 @@ extern "C" int lbif_profiles(lbif_handle h, double* n_z, double* ux_z, double* o
 {
     if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_profiles: NULL handle");
     const Params& P = h->P;
-    int nz = P.g.nz;
-    int rc = refresh_fields(h, false);
+    std::vector<double> prof;
+    int rc = plane_sums(h, prof);
     if (rc) return rc;
-    CK(h, launch_profiles(P, fields_of(h), h->prof_d, h->stream));
-    std::vector<double> prof((size_t)nz * 5);
-    CK(h, cudaMemcpyAsync(prof.data(), h->prof_d, sizeof(double) * prof.size(),
-                          cudaMemcpyDeviceToHost, h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
     double A = (double)P.g.nx * P.g.ny;
-    double n0 = (double)P.rho0;
     double tot[4] = {0, 0, 0, 0};
-    for (int z = 0; z < nz; ++z) {
+    for (int z = 0; z < P.g.nz; ++z) {
         const double* r = &prof[(size_t)z * 5];
-        if (n_z) n_z[z] = n0 * (1.0 + r[0] / A);
-        if (ux_z) ux_z[z] = r[1] / A;
-        tot[0] += A + r[0];
-        tot[1] += r[2];
-        tot[2] += r[3];
-        tot[3] += r[4];
+        int s = h->zslit[z];
+        double n0 = s >= 0 ? (double)h->sl[s].rho0 : 0.0;
+        if (n_z) n_z[z] = s >= 0 ? n0 * (1.0 + r[0] / A) : 0.0;
+        if (ux_z) ux_z[z] = s >= 0 ? r[1] / A : 0.0;
+        if (s < 0) continue;
+        tot[0] += n0 * (A + r[0]);
+        tot[1] += n0 * r[2];
+        tot[2] += n0 * r[3];
+        tot[3] += n0 * r[4];
     }
     if (out4)
-        for (int k = 0; k < 4; ++k) out4[k] = n0 * tot[k];
+        for (int k = 0; k < 4; ++k) out4[k] = tot[k];
     return check_status(h);
+}
+
+// ||p - q||_2 / (K ||p||_2), max over the two profiles
+static double profile_residual(const double* n, const double* n_old, const double* u,
+                               const double* u_old, int len, double K)
+{
+    double worst = 0.0;
+    const double* cur[2] = {n, u};
+    const double* old[2] = {n_old, u_old};
+    for (int k = 0; k < 2; ++k) {
+        double dd = 0.0, pp = 0.0;
+        for (int z = 0; z < len; ++z) {
+            double d = cur[k][z] - old[k][z];
+            dd += d * d;
+            pp += cur[k][z] * cur[k][z];
+        }
+        double v = pp > 0 ? sqrt(dd) / (K * sqrt(pp)) : (dd > 0 ? INFINITY : 0.0);
+        if (!(v == v)) v = INFINITY;
+        worst = fmax(worst, v);
+    }
+    return worst;
 }
 
 extern "C" int lbif_residual(lbif_handle h, double* r, double* mass, double mom[3])
@@ -595,23 +766,9 @@ extern "C" int lbif_residual(lbif_handle h, double* r, double* mass, double mom[
     double tot[4];
     int rc = lbif_profiles(h, n.data(), ux.data(), tot);
     double R = INFINITY;
-    if (h->last_t >= 0 && h->t > h->last_t) {
-        double K = (double)(h->t - h->last_t);
-        double worst = 0.0;
-        const std::vector<double>* cur[2] = {&n, &ux};
-        const std::vector<double>* old[2] = {&h->last_n, &h->last_ux};
-        for (int k = 0; k < 2; ++k) {
-            double dd = 0.0, pp = 0.0;
-            for (int z = 0; z < nz; ++z) {
-                double d = (*cur[k])[z] - (*old[k])[z];
-                dd += d * d;
-                pp += (*cur[k])[z] * (*cur[k])[z];
-            }
-            double v = pp > 0 ? sqrt(dd) / (K * sqrt(pp)) : (dd > 0 ? INFINITY : 0.0);
-            worst = fmax(worst, v);
-        }
-        R = worst;
-    }
+    if (h->last_t >= 0 && h->t > h->last_t)
+        R = profile_residual(n.data(), h->last_n.data(), ux.data(), h->last_ux.data(), nz,
+                             (double)(h->t - h->last_t));
     h->last_n = n;
     h->last_ux = ux;
     h->last_t = h->t;
@@ -638,6 +795,241 @@ extern "C" int lbif_status(lbif_handle h, int32_t* status)
     int rc = check_status(h);
     *status = h->sticky;
     return rc == LBIF_ERR_DIVERGED ? LBIF_OK : rc;
+}
+
+// --------------------------------------------------------------------------
+// ensemble
+// --------------------------------------------------------------------------
+extern "C" int lbif_batch_info(lbif_handle h, int32_t* nslits, int32_t* zlo, int64_t* nodes)
+{
+    if (!h) return fail(nullptr, LBIF_ERR_ARG, "lbif_batch_info: NULL handle");
+    if (nslits) *nslits = (int32_t)h->sl.size();
+    if (zlo)
+        for (size_t s = 0; s < h->sl.size(); ++s) zlo[s] = h->sl[s].zlo;
+    if (nodes) {
+        int64_t c = 0;
+        for (const SlitParam& s : h->sl) c += (int64_t)(s.zhi - s.zlo + 1) * h->P.g.nx * h->P.g.ny;
+        *nodes = c;
+    }
+    return LBIF_OK;
+}
+
+static int upload_done(lbif_ctx* h)
+{
+    CK(h, cudaMemcpyAsync(h->d_done, h->done.data(), sizeof(int) * h->done.size(),
+                          cudaMemcpyHostToDevice, h->stream));
+    return LBIF_OK;
+}
+
+extern "C" int lbif_batch_seed(lbif_handle h, const float* n_z, const float* ux_z, int32_t hmax)
+{
+    if (!h || !n_z || hmax < 1) return fail(h, LBIF_ERR_ARG, "lbif_batch_seed: bad arguments");
+    for (const SlitParam& s : h->sl)
+        if (s.zhi - s.zlo + 1 > hmax) return fail(h, LBIF_ERR_ARG, "lbif_batch_seed: hmax below a slit width");
+    size_t cnt = h->sl.size() * (size_t)hmax;
+    float* d = nullptr;
+    int rc = ensure_scratch(h);
+    if (rc) return rc;
+    if ((size_t)3 * h->P.g.N < 2 * cnt) return fail(h, LBIF_ERR_ARG, "lbif_batch_seed: profiles too large");
+    d = h->scratch;
+    CK(h, cudaMemcpyAsync(d, n_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream));
+    if (ux_z) CK(h, cudaMemcpyAsync(d + cnt, ux_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_init_profiles(h->P, h->pop[h->cur], h->dn[h->dcur], d, ux_z ? d + cnt : nullptr, hmax,
+                               h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    std::fill(h->done.begin(), h->done.end(), 0);
+    if ((rc = upload_done(h))) return rc;
+    reset_time(h);
+    return LBIF_OK;
+}
+
+extern "C" int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax)
+{
+    if (!h || hmax < 1) return fail(h, LBIF_ERR_ARG, "lbif_batch_profiles: bad arguments");
+    std::vector<double> prof;
+    int rc = plane_sums(h, prof);
+    if (rc) return rc;
+    double A = (double)h->P.g.nx * h->P.g.ny;
+    for (size_t s = 0; s < h->sl.size(); ++s) {
+        const SlitParam& S = h->sl[s];
+        for (int j = 0; j < hmax; ++j) {
+            int z = S.zlo + j;
+            bool in = z <= S.zhi;
+            if (n_z) n_z[s * hmax + j] = in ? S.rho0 * (1.0 + prof[(size_t)z * 5] / A) : 0.0;
+            if (ux_z) ux_z[s * hmax + j] = in ? prof[(size_t)z * 5 + 1] / A : 0.0;
+        }
+    }
+    return check_status(h);
+}
+
+// capture `steps` (even) steps of the active slits into a CUDA graph
+static int build_graph(lbif_ctx* h, int steps)
+{
+    if (h->graph && h->graph_steps == steps) return LBIF_OK;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    int rc = one_step(h);  // eager step: first-use kernel attributes are set outside capture
+    if (rc) return rc;
+    rc = one_step(h);
+    if (rc) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int64_t t0 = h->t;
+    for (int k = 0; k < steps && rc == LBIF_OK; ++k) rc = one_step(h);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->t = t0;  // the capture only recorded the launches
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(h, LBIF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, LBIF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    h->graph_steps = steps;
+    invalidate(h);
+    return LBIF_OK;
+}
+
+// Advance the active slits by `steps` steps through the graph (steps even).
+static int run_graph(lbif_ctx* h, int steps)
+{
+    int rc = build_graph(h, steps);
+    if (rc) return rc;
+    CK(h, cudaGraphLaunch(h->graph, h->stream));
+    h->t += steps;
+    invalidate(h);
+    return LBIF_OK;
+}
+
+extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int32_t check_every,
+                              int64_t* steps_taken)
+{
+    if (!h || !(tol > 0) || max_steps < 0 || check_every < 2)
+        return fail(h, LBIF_ERR_ARG, "lbif_batch_run: bad arguments");
+    const int K = (check_every + 1) / 2 * 2;
+    const size_t S = h->sl.size();
+    const double A = (double)h->P.g.nx * h->P.g.ny;
+    std::fill(h->done.begin(), h->done.end(), 0);
+    int rc = upload_done(h);
+    if (rc) return rc;
+    std::vector<int64_t> taken(S, -1);
+    std::vector<std::vector<double>> pn(S), pu(S);  // previous profiles
+    int64_t t0 = h->t;
+    size_t active = S;
+    std::vector<double> prof;
+    while (active > 0 && h->t - t0 < max_steps) {
+        if ((rc = run_graph(h, K))) return rc;
+        if ((rc = plane_sums(h, prof))) return rc;
+        for (size_t s = 0; s < S; ++s) {
+            if (h->done[s]) continue;
+            const SlitParam& P = h->sl[s];
+            int len = P.zhi - P.zlo + 1;
+            std::vector<double> n(len), u(len);
+            bool bad = false;
+            for (int j = 0; j < len; ++j) {
+                const double* r = &prof[(size_t)(P.zlo + j) * 5];
+                n[j] = P.rho0 * (1.0 + r[0] / A);
+                u[j] = r[1] / A;
+                bad |= !(n[j] > 0.0) || !isfinite(u[j]);
+            }
+            if (bad) {
+                h->done[s] = 1;  // diverged: frozen, reported as -2
+                taken[s] = -2;
+                --active;
+                continue;
+            }
+            if (!pn[s].empty()) {
+                double R = profile_residual(n.data(), pn[s].data(), u.data(), pu[s].data(), len, (double)K);
+                if (R < tol) {
+                    h->done[s] = 1;
+                    taken[s] = h->t - t0;
+                    --active;
+                }
+            }
+            pn[s].swap(n);
+            pu[s].swap(u);
+        }
+        if ((rc = upload_done(h))) return rc;
+    }
+    if (steps_taken)
+        for (size_t s = 0; s < S; ++s) steps_taken[s] = taken[s];
+    // unfreeze: later calls step every slit again
+    std::fill(h->done.begin(), h->done.end(), 0);
+    if ((rc = upload_done(h))) return rc;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBIF_OK;
+}
+
+// Time each candidate launch shape on the handle's own state and keep the
+// fastest: the ball kernel's CTA target (z-chunking) and the force kernel's
+// tile-group edge. The state is saved and restored around the trials.
+extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group)
+{
+    if (!h || trials < 1) return fail(h, LBIF_ERR_ARG, "lbif_autotune: bad arguments");
+    const Params& P = h->P;
+    int rc = refresh_fields(h, P.hs != 0, 0);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    const int balls[] = {304, 608, 1216, 2432, 4864};
+    const int groups[] = {64, 128, 256, 1 << 20};
+    float best = 1e30f;
+    int best_ball = 0, best_group = 0;
+    float* dnew = h->dn[h->dcur ^ 1];
+    // the ball kernel writes dG only; the force kernel writes F only: both
+    // are pure functions of the current fields, so trials change no state
+    for (int b : balls) {
+        float tot = 0.f;
+        for (int k = 0; k < trials + 1; ++k) {
+            CK(h, cudaEventRecord(e0, h->stream));
+            CK(h, launch_ball(P, dnew, h->dG, h->status_d, b, 0, h->stream));
+            CK(h, cudaEventRecord(e1, h->stream));
+            CK(h, cudaEventSynchronize(e1));
+            float ms;
+            CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (k) tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            best_ball = b;
+        }
+    }
+    best = 1e30f;
+    for (int gsz : groups) {
+        float tot = 0.f;
+        for (int k = 0; k < trials + 1; ++k) {
+            CK(h, cudaEventRecord(e0, h->stream));
+            CK(h, launch_force(P, fields_of(h), h->Ft, h->F, gsz, h->stream));
+            CK(h, cudaEventRecord(e1, h->stream));
+            CK(h, cudaEventSynchronize(e1));
+            float ms;
+            CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (k) tot += ms;
+        }
+        if (tot < best) {
+            best = tot;
+            best_group = gsz;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->ball_want = best_ball;
+    h->force_group = best_group;
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    if (ball_want) *ball_want = best_ball;
+    if (force_group) *force_group = best_group;
+    return check_status(h);
 }
 
 // --------------------------------------------------------------------------
@@ -710,8 +1102,7 @@ extern "C" int lbif_load(lbif_handle h, const char* path)
     CK(h, cudaMemcpyAsync(h->scratch, ref.data(), sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
     CK(h, launch_write_ref(P, h->scratch, h->dn[h->dcur], h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    reset_time(h);
     h->t = hd.t;
-    h->last_t = -1;
-    invalidate(h);
     return LBIF_OK;
 }

@@ -60,22 +60,34 @@ struct Shell {
     float md_w[3][4];
 };
 
-struct Params {
-    Geom g;
-    float inv_tau;
-    float rho0;      // n0
+// Per-slit parameters. A handle holds one slit (z planes 0..nz-1) or an
+// ensemble of slits stacked along z with hw planes of "outside" between them;
+// zslit[z] gives the slit of a plane (-1 for a gap plane).
+struct SlitParam {
+    float rho0;      // n0 of the slit
     float eta0;
     float G0;        // g2(eta0)
+    float inv_tau;
     float hs_pref;   // -kT sigma^2 4 pi n0
     float p_pref;    // kT sigma^3/6 4 pi n0^2
+    float body[3];   // F_e per particle
+    int zlo, zhi;    // first and last fluid plane
+    int pad;
+};
+
+struct Params {
+    Geom g;
     float kappa;     // 2/(v_T sqrt(pi))
     float inv_sigma;
     float ball_inv;  // 1 / ball node count
-    float body[3];
     int sigma;
     int hs, coupling, regularize, g2form, tail, storage;
-    int nbr[Q];         // padded offsets of the 19 lattice neighbours
-    long long soff[Q];  // node-index offsets of the 19 neighbours (no wrap)
+    int nslits;
+    const SlitParam* sl;  // device table, nslits entries
+    const int* zslit;     // device table, nz entries
+    const int* done;      // device flags, nslits entries (1 = frozen)
+    int nbr[Q];           // padded offsets of the 19 lattice neighbours
+    long long soff[Q];    // node-index offsets of the 19 neighbours (no wrap)
     Shell sh;
 };
 
@@ -93,16 +105,22 @@ cudaError_t launch_fill_outside(const Params& P, float* const* planes, const flo
                                 int nplanes, cudaStream_t s);
 cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t seed, double amp,
                               long long offset, cudaStream_t s);
+cudaError_t launch_init_profiles(const Params& P, void* pop, float* dn, const float* n_z,
+                                 const float* ux_z, int hmax, cudaStream_t s);
 cudaError_t launch_init_fields(const Params& P, void* pop, float* dn, const float* rho,
                                const float* u, cudaStream_t s);
 cudaError_t launch_write_ref(const Params& P, const float* ref, float* dn, cudaStream_t s);
 cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaStream_t s);
 cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, float* dnew,
-                           float* ux, float* uy, float* uz, int* status, cudaStream_t s);
-cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s);
+                           float* ux, float* uy, float* uz, int* status, int skip_done,
+                           cudaStream_t s);
+// want: CTAs to aim for when splitting z into chunks (<= 0: default)
+cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, int want,
+                        int skip_done, cudaStream_t s);
 cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const float4* K,
                         int npairs, float4* Ft, cudaStream_t s);
-cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F,
+// group: edge (nodes) of the x-y block the resident CTAs sweep together (<= 0: default)
+cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F, int group,
                          cudaStream_t s);
 cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields& f,
                       const float4* F, cudaStream_t s);

@@ -94,14 +94,14 @@ __device__ __forceinline__ bool tile_origin(const Geom& g, const TileMap& tm, in
     return tile_x < tm.tiles_x && tile_y < tm.tiles_y;
 }
 
-static inline TileMap make_tilemap(const Geom& g, int tx, int ty, unsigned& blocks)
+static inline TileMap make_tilemap(const Geom& g, int tx, int ty, int group, unsigned& blocks)
 {
     TileMap tm;
     tm.tx = tx;
     tm.ty = ty;
     tm.tiles_x = (g.nx + tx - 1) / tx;
     tm.tiles_y = (g.ny + ty - 1) / ty;
-    int want_x = (128 + tx - 1) / tx, want_y = (128 + ty - 1) / ty;
+    int want_x = (group + tx - 1) / tx, want_y = (group + ty - 1) / ty;
     tm.gtx = tm.tiles_x < want_x ? tm.tiles_x : want_x;
     tm.gty = tm.tiles_y < want_y ? tm.tiles_y : want_y;
     tm.ngx = (tm.tiles_x + tm.gtx - 1) / tm.gtx;
@@ -109,6 +109,10 @@ static inline TileMap make_tilemap(const Geom& g, int tx, int ty, unsigned& bloc
     blocks = (unsigned)tm.gtx * tm.gty * g.nz * tm.ngx * ngy;
     return tm;
 }
+
+// slit of plane z (-1 for a gap plane between stacked slits)
+__device__ __forceinline__ int slit_of(const Params& P, int z) { return __ldg(P.zslit + z); }
+__device__ __forceinline__ bool frozen(const Params& P, int s) { return __ldg(P.done + s) != 0; }
 
 template <typename T>
 __device__ __forceinline__ void load_pops(const Params& P, const T* __restrict__ pop, long long idx,
@@ -180,14 +184,15 @@ __global__ void k_init_noise(Params P, T* pop, float* dn, uint64_t seed, double 
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    if (slit_of(P, z) < 0) return;
     uint64_t r = splitmix64(seed ^ (uint64_t)(offset + idx));
     double U = (double)(r >> 11) * (1.0 / 9007199254740992.0);
     // f_i = w_i n0 (1 + xi): reference xi, all stored deviations 0
     float xi = (float)(amp * (2.0 * U - 1.0));
 #pragma unroll
     for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
-    int x, y, z;
-    decompose(P.g, idx, x, y, z);
     for_images(P.g, x, y, z, [&](int p) { dn[p] = xi; });
 }
 
@@ -196,7 +201,11 @@ __global__ void k_init_fields(Params P, T* pop, float* dn, const float* rho, con
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
-    float d = rho[idx] / P.rho0 - 1.f;
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    const int s = slit_of(P, z);
+    if (s < 0) return;
+    float d = rho[idx] / P.sl[s].rho0 - 1.f;
     float ux = 0.f, uy = 0.f, uz = 0.f;
     if (u) {
         ux = u[idx];
@@ -207,8 +216,27 @@ __global__ void k_init_fields(Params P, T* pop, float* dn, const float* rho, con
     float opd = 1.f + d;
 #pragma unroll
     for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, eq_excess(i, opd, ux, uy, uz, uu));
+    for_images(P.g, x, y, z, [&](int p) { dn[p] = d; });
+}
+
+// x,y-uniform fields from per-slit profiles n(z), u_x(z) (row s of n_z, ux_z
+// holds slit s, entry j its plane zlo + j)
+template <typename T>
+__global__ void k_init_profiles(Params P, T* pop, float* dn, const float* n_z, const float* ux_z,
+                                int hmax)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
     int x, y, z;
     decompose(P.g, idx, x, y, z);
+    const int s = slit_of(P, z);
+    if (s < 0) return;
+    const int j = z - P.sl[s].zlo;
+    const float d = n_z[(long long)s * hmax + j] / P.sl[s].rho0 - 1.f;
+    const float ux = ux_z ? ux_z[(long long)s * hmax + j] : 0.f;
+    const float uu = ux * ux, opd = 1.f + d;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, eq_excess(i, opd, ux, 0.f, 0.f, uu));
     for_images(P.g, x, y, z, [&](int p) { dn[p] = d; });
 }
 
@@ -218,6 +246,7 @@ __global__ void k_write_ref(Params P, const float* ref, float* dn)
     if (idx >= P.g.N) return;
     int x, y, z;
     decompose(P.g, idx, x, y, z);
+    if (slit_of(P, z) < 0) return;
     float v = ref[idx];
     for_images(P.g, x, y, z, [&](int p) { dn[p] = v; });
 }
@@ -238,14 +267,16 @@ __global__ void k_read_ref(Params P, const float* dn, float* ref)
 template <typename T>
 __global__ void __launch_bounds__(256) k_moments(Params P, const T* __restrict__ pop,
                                                  const float* dref, float* dnew, float* oux,
-                                                 float* ouy, float* ouz, int* status)
+                                                 float* ouy, float* ouz, int* status, int skip_done)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
-    float g[Q];
-    load_pops(P, pop, idx, g);
     int x, y, z;
     decompose(P.g, idx, x, y, z);
+    const int s = slit_of(P, z);
+    if (s < 0 || (skip_done && frozen(P, s))) return;
+    float g[Q];
+    load_pops(P, pop, idx, g);
     float R = dref[pidx(P.g, x, y, z)];
     float S, jx, jy, jz;
     sums_of(g, S, jx, jy, jz);
@@ -265,11 +296,10 @@ __global__ void __launch_bounds__(256) k_moments(Params P, const T* __restrict__
 // step 2: coarse-grained density over the ball |d| <= sigma/2 and the contact
 // value g2(etabar) (Sec. Methods, Fischer-Methfessel prescription)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float g2_deviation(const Params& P, float dnb, bool& bad)
+__device__ __forceinline__ float g2_deviation(const Params& P, float e0, float dnb, bool& bad)
 {
     // g2(eta0 (1 + dnb)) - g2(eta0) written so that every term carries
     // Delta = eta0 dnb: (dN D0 - N0 dD) / (D1 D0), D = (1 - eta)^3
-    float e0 = P.eta0;
     float d = e0 * dnb;
     float a = 1.f - e0 - d, b = 1.f - e0;
     float N0, dN;
@@ -307,7 +337,8 @@ constexpr int ball_smem_floats()
 // register ring of the 2R+1 output planes it touches, emit the completed one.
 template <int R>
 __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __restrict__ dn,
-                                              float* __restrict__ dG, int* status, int zchunk)
+                                              float* __restrict__ dG, int* status, int zchunk,
+                                              int skip_done)
 {
     constexpr int TX = BALL_TX, TY = BALL_TY;
     constexpr int W = TX + 2 * R, H = TY + 2 * R;
@@ -357,9 +388,10 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
             if (k) acc[R + k] += D;
         }
         const int zo = zi - R;
-        if (zo >= z0 && active) {
+        const int so = zo >= z0 ? slit_of(P, zo) : -1;
+        if (so >= 0 && active && !(skip_done && frozen(P, so))) {
             bool bad;
-            float v = g2_deviation(P, acc[0] * P.ball_inv, bad);
+            float v = g2_deviation(P, P.sl[so].eta0, acc[0] * P.ball_inv, bad);
             if (bad) atomicOr(status, 2);
             for_images(g, x, y, zo, [&](int q) { dG[q] = v; });
         }
@@ -388,22 +420,22 @@ __device__ __forceinline__ const float* ufield(const Fields& f)
 // generic path: one node per thread, scalar loads (any even sigma)
 template <int A>
 __device__ __forceinline__ void axis_pair(const Params& P, const Fields& fl, int p, const float u0[3],
-                                          float lk, float f[3])
+                                          float G0, float lk, float f[3])
 {
     const int o = P.sh.ax_nb[A], om = P.sh.ax_md[A];
     const float* uf = ufield<A>(fl);
     float dp = __ldg(fl.dn + p + o), dm = __ldg(fl.dn + p - o);
     float up = __ldg(uf + p + o), um = __ldg(uf + p - o);
     float gp = __ldg(fl.dG + p + om), gm = __ldg(fl.dG + p - om);
-    float Ap = shell_A(dp, gp, P.G0), Am = shell_A(dm, gm, P.G0);
-    float tp = Ap - (P.G0 + Ap) * lk * (up - u0[A]);
-    float tm = Am - (P.G0 + Am) * lk * (u0[A] - um);
+    float Ap = shell_A(dp, gp, G0), Am = shell_A(dm, gm, G0);
+    float tp = Ap - (G0 + Ap) * lk * (up - u0[A]);
+    float tm = Am - (G0 + Am) * lk * (u0[A] - um);
     f[A] += (1.f / 30.f) * (tp - tm);
 }
 
 template <int PL>
 __device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, int p,
-                                             const float u0[3], float lk, float f[3])
+                                             const float u0[3], float G0, float lk, float f[3])
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
@@ -432,8 +464,8 @@ __device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, 
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
         const float sa = (m & 1) ? -1.f : 1.f, sb = (m & 2) ? -1.f : 1.f;
-        Aq[m] = shell_A(dq[m], gq[m], P.G0);
-        float c = (P.G0 + Aq[m]) * lk * h;
+        Aq[m] = shell_A(dq[m], gq[m], G0);
+        float c = (G0 + Aq[m]) * lk * h;
         Pa[m] = c * (sa * (ua[m] - u0[a]));
         Pb[m] = c * (sb * (ub[m] - u0[b]));
     }
@@ -446,38 +478,39 @@ __device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, 
     f[b] += (h / 15.f) * db;
 }
 
-__device__ __forceinline__ float coupling_factor(const Params& P, int z)
+__device__ __forceinline__ float coupling_factor(const Params& P, const SlitParam& S, int z)
 {
     if (!P.coupling) return 0.f;
     float lam = 1.f;
     if (P.regularize && !P.g.zper) {
-        float dw = fminf(z + 0.5f, P.g.nz - 0.5f - z);
+        float dw = fminf(z - S.zlo + 0.5f, S.zhi + 0.5f - z);
         lam = 1.f - expf(-dw * P.inv_sigma);
     }
     return lam * P.kappa;
 }
 
 // total force F / n0 at a node (body + hard sphere + tail)
-__device__ __forceinline__ void node_force(const Params& P, const Fields& fl,
+__device__ __forceinline__ void node_force(const Params& P, const SlitParam& S, const Fields& fl,
                                            const float4* __restrict__ Ft, long long idx, int z,
                                            int p, float& fx, float& fy, float& fz)
 {
     const float d0 = __ldg(fl.dn + p);
     const float u0[3] = {__ldg(fl.ux + p), __ldg(fl.uy + p), __ldg(fl.uz + p)};
     float opd = 1.f + d0;
-    fx = opd * P.body[0];
-    fy = opd * P.body[1];
-    fz = opd * P.body[2];
+    fx = opd * S.body[0];
+    fy = opd * S.body[1];
+    fz = opd * S.body[2];
     if (P.hs) {
-        const float lk = coupling_factor(P, z);
+        const float lk = coupling_factor(P, S, z);
+        const float G0 = S.G0;
         float f[3] = {0.f, 0.f, 0.f};
-        axis_pair<0>(P, fl, p, u0, lk, f);
-        axis_pair<1>(P, fl, p, u0, lk, f);
-        axis_pair<2>(P, fl, p, u0, lk, f);
-        diag_quartet<0>(P, fl, p, u0, lk, f);
-        diag_quartet<1>(P, fl, p, u0, lk, f);
-        diag_quartet<2>(P, fl, p, u0, lk, f);
-        float pre = P.hs_pref * opd;
+        axis_pair<0>(P, fl, p, u0, G0, lk, f);
+        axis_pair<1>(P, fl, p, u0, G0, lk, f);
+        axis_pair<2>(P, fl, p, u0, G0, lk, f);
+        diag_quartet<0>(P, fl, p, u0, G0, lk, f);
+        diag_quartet<1>(P, fl, p, u0, G0, lk, f);
+        diag_quartet<2>(P, fl, p, u0, G0, lk, f);
+        float pre = S.hs_pref * opd;
         fx += pre * f[0];
         fy += pre * f[1];
         fz += pre * f[2];
@@ -496,11 +529,14 @@ __global__ void __launch_bounds__(256) k_force(Params P, TileMap tm, Fields fl,
     const Geom& g = P.g;
     int tx, ty, z;
     if (!tile_origin(g, tm, tx, ty, z)) return;
+    const int s = slit_of(P, z);
+    if (s < 0 || frozen(P, s)) return;
     const int x = tx * tm.tx + threadIdx.x % 32, y = ty * tm.ty + threadIdx.x / 32;
     if (x >= g.nx || y >= g.ny) return;
     const long long idx = ((long long)z * g.ny + y) * g.nx + x;
+    const SlitParam S = P.sl[s];
     float fx, fy, fz;
-    node_force(P, fl, Ft, idx, z, pidx(g, x, y, z), fx, fy, fz);
+    node_force(P, S, fl, Ft, idx, z, pidx(g, x, y, z), fx, fy, fz);
     F[idx] = make_float4(fx, fy, fz, 0.f);
 }
 
@@ -639,8 +675,8 @@ __device__ __forceinline__ void member_yz(const Params& P, const Fields& fl, int
 
 template <int SIG, int PL, int M>
 __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, int pb,
-                                             const v4 ua0, const v4 ub0, float lk, v4 Aq, v4 Pa,
-                                             v4 Pb)
+                                             const v4 ua0, const v4 ub0, float G0, float lk, v4 Aq,
+                                             v4 Pa, v4 Pb)
 {
     constexpr float h = 0.70710678118654752f;
     constexpr float sa = (M & 1) ? -1.f : 1.f, sb = (M & 2) ? -1.f : 1.f;
@@ -653,8 +689,8 @@ __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, 
         member_x<SIG, PL, M>(P, fl, pb, dq, ua, ub, gq);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        Aq[j] = shell_A(dq[j], gq[j], P.G0);
-        float c = (P.G0 + Aq[j]) * lk * h;
+        Aq[j] = shell_A(dq[j], gq[j], G0);
+        float c = (G0 + Aq[j]) * lk * h;
         Pa[j] = c * (sa * (ua[j] - ua0[j]));
         Pb[j] = c * (sb * (ub[j] - ub0[j]));
     }
@@ -662,16 +698,16 @@ __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, 
 
 template <int SIG, int PL>
 __device__ __forceinline__ void quartet4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
-                                         float lk, v4 f[3])
+                                         float G0, float lk, v4 f[3])
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
     constexpr float c = 0.70710678118654752f / 15.f;
     v4 A0, P0a, P0b, A1, P1a, P1b, A2, P2a, P2b, A3, P3a, P3b;
-    member_terms<SIG, PL, 0>(P, fl, pb, u0[a], u0[b], lk, A0, P0a, P0b);
-    member_terms<SIG, PL, 1>(P, fl, pb, u0[a], u0[b], lk, A1, P1a, P1b);
-    member_terms<SIG, PL, 2>(P, fl, pb, u0[a], u0[b], lk, A2, P2a, P2b);
-    member_terms<SIG, PL, 3>(P, fl, pb, u0[a], u0[b], lk, A3, P3a, P3b);
+    member_terms<SIG, PL, 0>(P, fl, pb, u0[a], u0[b], G0, lk, A0, P0a, P0b);
+    member_terms<SIG, PL, 1>(P, fl, pb, u0[a], u0[b], G0, lk, A1, P1a, P1b);
+    member_terms<SIG, PL, 2>(P, fl, pb, u0[a], u0[b], G0, lk, A2, P2a, P2b);
+    member_terms<SIG, PL, 3>(P, fl, pb, u0[a], u0[b], G0, lk, A3, P3a, P3b);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         float da = ((A0[j] - A1[j]) - (P0a[j] - P1a[j]) - (P0b[j] - P1b[j])) +
@@ -685,7 +721,7 @@ __device__ __forceinline__ void quartet4(const Params& P, const Fields& fl, int 
 
 template <int SIG, int A>
 __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
-                                      float lk, v4 f[3])
+                                      float G0, float lk, v4 f[3])
 {
     const float* uf = ufield<A>(fl);
     v4 dp, dm, up, um, gp, gm;
@@ -707,9 +743,9 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float Ap = shell_A(dp[j], gp[j], P.G0), Am = shell_A(dm[j], gm[j], P.G0);
-        float tp = Ap - (P.G0 + Ap) * lk * (up[j] - u0[A][j]);
-        float tm = Am - (P.G0 + Am) * lk * (u0[A][j] - um[j]);
+        float Ap = shell_A(dp[j], gp[j], G0), Am = shell_A(dm[j], gm[j], G0);
+        float tp = Ap - (G0 + Ap) * lk * (up[j] - u0[A][j]);
+        float tm = Am - (G0 + Am) * lk * (u0[A][j] - um[j]);
         f[A][j] += (1.f / 30.f) * (tp - tm);
     }
 }
@@ -721,6 +757,9 @@ __global__ void __launch_bounds__(128) k_force4(Params P, TileMap tm, Fields fl,
     const Geom& g = P.g;
     int tx, ty, z;
     if (!tile_origin(g, tm, tx, ty, z)) return;
+    const int s = slit_of(P, z);
+    if (s < 0 || frozen(P, s)) return;
+    const SlitParam S = P.sl[s];
     const int x = tx * 128 + 4 * (threadIdx.x % 32), y = ty * tm.ty + threadIdx.x / 32;
     if (x >= g.nx || y >= g.ny) return;
     const int pb = pidx(g, x, y, z);  // 16-byte aligned: x, hw, px multiples of 4
@@ -735,23 +774,23 @@ __global__ void __launch_bounds__(128) k_force4(Params P, TileMap tm, Fields fl,
 #pragma unroll
         for (int j = 0; j < 4; ++j) f[a][j] = 0.f;
     if (P.hs) {
-        const float lk = coupling_factor(P, z);
-        axis4<SIG, 0>(P, fl, pb, u0, lk, f);
-        axis4<SIG, 1>(P, fl, pb, u0, lk, f);
-        axis4<SIG, 2>(P, fl, pb, u0, lk, f);
-        quartet4<SIG, 0>(P, fl, pb, u0, lk, f);
-        quartet4<SIG, 1>(P, fl, pb, u0, lk, f);
-        quartet4<SIG, 2>(P, fl, pb, u0, lk, f);
+        const float lk = coupling_factor(P, S, z);
+        axis4<SIG, 0>(P, fl, pb, u0, S.G0, lk, f);
+        axis4<SIG, 1>(P, fl, pb, u0, S.G0, lk, f);
+        axis4<SIG, 2>(P, fl, pb, u0, S.G0, lk, f);
+        quartet4<SIG, 0>(P, fl, pb, u0, S.G0, lk, f);
+        quartet4<SIG, 1>(P, fl, pb, u0, S.G0, lk, f);
+        quartet4<SIG, 2>(P, fl, pb, u0, S.G0, lk, f);
     }
     const long long idx0 = ((long long)z * g.ny + y) * g.nx + x;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         if (x + j >= g.nx) break;
         const float opd = 1.f + d0[j];
-        const float pre = P.hs_pref * opd;
-        float fx = opd * P.body[0] + pre * f[0][j];
-        float fy = opd * P.body[1] + pre * f[1][j];
-        float fz = opd * P.body[2] + pre * f[2][j];
+        const float pre = S.hs_pref * opd;
+        float fx = opd * S.body[0] + pre * f[0][j];
+        float fy = opd * S.body[1] + pre * f[1][j];
+        float fz = opd * S.body[2] + pre * f[2][j];
         if (P.tail) {
             float4 t = Ft[idx0 + j];
             fx += t.x;
@@ -775,6 +814,8 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
     if (idx >= P.g.N) return;
     int x, y, z;
     decompose(P.g, idx, x, y, z);
+    const int s = slit_of(P, z);
+    if (s < 0 || frozen(P, s)) return;
     int p = pidx(P.g, x, y, z);
     float sx = 0.f, sy = 0.f, sz = 0.f;
     for (int k = 0; k < npairs; ++k) {
@@ -785,7 +826,7 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
         sy += kk.y * d;
         sz += kk.z * d;
     }
-    float pre = P.rho0 * (1.f + __ldg(dn + p));
+    float pre = P.sl[s].rho0 * (1.f + __ldg(dn + p));
     Ft[idx] = make_float4(pre * sx, pre * sy, pre * sz, 0.f);
 }
 
@@ -805,6 +846,10 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
     const Geom& g = P.g;
     int x, y, z;
     decompose(g, idx, x, y, z);
+    const int s = slit_of(P, z);
+    if (s < 0 || frozen(P, s)) return;
+    const int zlo = P.sl[s].zlo, zhi = P.sl[s].zhi;
+    const float inv_tau = P.sl[s].inv_tau;
     const int p = pidx(g, x, y, z);
     float gi[Q];
     load_pops(P, pin, idx, gi);
@@ -815,7 +860,7 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
     sums_of(gi, S, jx, jy, jz);
     const float opd = 1.f + d0;
     const float uu = ux * ux + uy * uy + uz * uz;
-    const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > 0 && z < g.nz - 1;
+    const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi;
     if (interior) {
         // no wrap, no wall: target = idx + constant offset. The neighbour
         // densities are fetched together first so their latencies overlap.
@@ -829,7 +874,7 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
         for (int i = 0; i < Q; ++i) {
             float k = gi[i] - S;
             float e = eq_excess(i, opd, ux, uy, uz, uu);
-            float ks = k - (k - e) * P.inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
+            float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
             stp(pout + (long long)i * g.Npad + (idx + P.soff[i]), ks + dd[i]);
         }
         return;
@@ -838,13 +883,13 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
     for (int i = 0; i < Q; ++i) {
         float k = gi[i] - S;
         float e = eq_excess(i, opd, ux, uy, uz, uu);
-        float ks = k - (k - e) * P.inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
+        float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
         int tx = x + kCx(i), ty = y + kCy(i), tz = z + kCz(i);
         tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
         ty = ty < 0 ? ty + g.ny : (ty >= g.ny ? ty - g.ny : ty);
         if (g.zper) {
             tz = tz < 0 ? tz + g.nz : (tz >= g.nz ? tz - g.nz : tz);
-        } else if (tz < 0 || tz >= g.nz) {
+        } else if (tz < zlo || tz > zhi) {
             stp(pout + (long long)opp_of(i) * g.Npad + idx, ks);
             continue;
         }
@@ -868,14 +913,14 @@ __global__ void k_force_soa(Params P, const float4* __restrict__ F, float* __res
 }
 
 // sum over the 18 points of W_q A_q (A_q = G_q n_q / n0 - G0)
-__device__ __forceinline__ float shell_A_sum(const Params& P, const Fields& fl, int p)
+__device__ __forceinline__ float shell_A_sum(const Params& P, const Fields& fl, int p, float G0)
 {
     float s = 0.f;
     for (int a = 0; a < 3; ++a)
         for (int sg = -1; sg <= 1; sg += 2) {
             float dq = __ldg(fl.dn + p + sg * P.sh.ax_nb[a]);
             float gq = __ldg(fl.dG + p + sg * P.sh.ax_md[a]);
-            s += (1.f / 30.f) * shell_A(dq, gq, P.G0);
+            s += (1.f / 30.f) * shell_A(dq, gq, G0);
         }
     for (int pl = 0; pl < 3; ++pl)
         for (int m = 0; m < 4; ++m) {
@@ -885,7 +930,7 @@ __device__ __forceinline__ float shell_A_sum(const Params& P, const Fields& fl, 
                 dq += P.sh.nb_w[pl][k] * __ldg(fl.dn + p + sa * P.sh.nb_a[pl][k] + sb * P.sh.nb_b[pl][k]);
                 gq += P.sh.md_w[pl][k] * __ldg(fl.dG + p + sa * P.sh.md_a[pl][k] + sb * P.sh.md_b[pl][k]);
             }
-            s += (1.f / 15.f) * shell_A(dq, gq, P.G0);
+            s += (1.f / 15.f) * shell_A(dq, gq, G0);
         }
     return s;
 }
@@ -897,9 +942,17 @@ __global__ void k_moments_out(Params P, Fields fl, float* rho, float* u, float* 
     if (idx >= P.g.N) return;
     int x, y, z;
     decompose(P.g, idx, x, y, z);
+    const int sl = slit_of(P, z);
+    if (sl < 0) {
+        if (rho) rho[idx] = 0.f;
+        if (u) u[idx] = u[P.g.N + idx] = u[2 * P.g.N + idx] = 0.f;
+        if (pr) pr[idx] = 0.f;
+        return;
+    }
+    const SlitParam S = P.sl[sl];
     int p = pidx(P.g, x, y, z);
     const float d = fl.dn[p];
-    if (rho) rho[idx] = P.rho0 * (1.f + d);
+    if (rho) rho[idx] = S.rho0 * (1.f + d);
     if (u) {
         u[idx] = fl.ux[p];
         u[P.g.N + idx] = fl.uy[p];
@@ -907,8 +960,8 @@ __global__ void k_moments_out(Params P, Fields fl, float* rho, float* u, float* 
     }
     if (pr) {
         float s = 0.f;
-        if (P.hs) s = (P.G0 + shell_A_sum(P, fl, p)) * P.p_pref * (1.f + d);
-        pr[idx] = (1.f / 3.f) * P.rho0 * (1.f + d) + s;
+        if (P.hs) s = (S.G0 + shell_A_sum(P, fl, p, S.G0)) * S.p_pref * (1.f + d);
+        pr[idx] = (1.f / 3.f) * S.rho0 * (1.f + d) + s;
     }
 }
 
@@ -973,6 +1026,16 @@ cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t se
     return cudaGetLastError();
 }
 
+cudaError_t launch_init_profiles(const Params& P, void* pop, float* dn, const float* n_z,
+                                 const float* ux_z, int hmax, cudaStream_t s)
+{
+    if (P.storage == LBIF_STORE_F16)
+        k_init_profiles<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, dn, n_z, ux_z, hmax);
+    else
+        k_init_profiles<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, dn, n_z, ux_z, hmax);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_fields(const Params& P, void* pop, float* dn, const float* rho,
                                const float* u, cudaStream_t s)
 {
@@ -996,19 +1059,21 @@ cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaSt
 }
 
 cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, float* dnew,
-                           float* ux, float* uy, float* uz, int* status, cudaStream_t s)
+                           float* ux, float* uy, float* uz, int* status, int skip_done,
+                           cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
         k_moments<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pop, dref, dnew, ux,
-                                                               uy, uz, status);
+                                                               uy, uz, status, skip_done);
     else
         k_moments<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pop, dref, dnew, ux,
-                                                              uy, uz, status);
+                                                              uy, uz, status, skip_done);
     return cudaGetLastError();
 }
 
 template <int R>
-static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s)
+static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* status, int want,
+                         int skip_done, cudaStream_t s)
 {
     const Geom& g = P.g;
     size_t smem = sizeof(float) * ball_smem_floats<R>();
@@ -1020,7 +1085,7 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
         configured = true;
     }
     int gx = (g.nx + BALL_TX - 1) / BALL_TX, gy = (g.ny + BALL_TY - 1) / BALL_TY;
-    int want = 1216;  // ~8 CTAs per SM on 152 SMs
+    if (want <= 0) want = 1216;  // ~8 CTAs per SM on 152 SMs
     int nchunk = (want + gx * gy - 1) / (gx * gy);
     int maxchunk = g.nz / (2 * R) > 1 ? g.nz / (2 * R) : 1;
     if (nchunk > maxchunk) nchunk = maxchunk;
@@ -1028,25 +1093,26 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
     int zchunk = (g.nz + nchunk - 1) / nchunk;
     nchunk = (g.nz + zchunk - 1) / zchunk;
     dim3 grid(gx, gy, nchunk);
-    k_ball<R><<<grid, BALL_THREADS, smem, s>>>(P, dn, dG, status, zchunk);
+    k_ball<R><<<grid, BALL_THREADS, smem, s>>>(P, dn, dG, status, zchunk, skip_done);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, cudaStream_t s)
+cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, int want,
+                        int skip_done, cudaStream_t s)
 {
     switch (P.sigma / 2) {
-    case 1: return ball_r<1>(P, dn, dG, status, s);
-    case 2: return ball_r<2>(P, dn, dG, status, s);
-    case 3: return ball_r<3>(P, dn, dG, status, s);
-    case 4: return ball_r<4>(P, dn, dG, status, s);
-    case 5: return ball_r<5>(P, dn, dG, status, s);
-    case 6: return ball_r<6>(P, dn, dG, status, s);
-    case 7: return ball_r<7>(P, dn, dG, status, s);
-    case 8: return ball_r<8>(P, dn, dG, status, s);
-    case 9: return ball_r<9>(P, dn, dG, status, s);
-    case 10: return ball_r<10>(P, dn, dG, status, s);
-    case 11: return ball_r<11>(P, dn, dG, status, s);
-    case 12: return ball_r<12>(P, dn, dG, status, s);
+    case 1: return ball_r<1>(P, dn, dG, status, want, skip_done, s);
+    case 2: return ball_r<2>(P, dn, dG, status, want, skip_done, s);
+    case 3: return ball_r<3>(P, dn, dG, status, want, skip_done, s);
+    case 4: return ball_r<4>(P, dn, dG, status, want, skip_done, s);
+    case 5: return ball_r<5>(P, dn, dG, status, want, skip_done, s);
+    case 6: return ball_r<6>(P, dn, dG, status, want, skip_done, s);
+    case 7: return ball_r<7>(P, dn, dG, status, want, skip_done, s);
+    case 8: return ball_r<8>(P, dn, dG, status, want, skip_done, s);
+    case 9: return ball_r<9>(P, dn, dG, status, want, skip_done, s);
+    case 10: return ball_r<10>(P, dn, dG, status, want, skip_done, s);
+    case 11: return ball_r<11>(P, dn, dG, status, want, skip_done, s);
+    case 12: return ball_r<12>(P, dn, dG, status, want, skip_done, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -1058,18 +1124,20 @@ cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F, cudaStream_t s)
+cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F, int group,
+                         cudaStream_t s)
 {
     unsigned blocks;
+    if (group <= 0) group = 128;
     if (force_vectorised(P.sigma)) {
-        TileMap tm = make_tilemap(P.g, 128, 4, blocks);
+        TileMap tm = make_tilemap(P.g, 128, 4, group, blocks);
         switch (P.sigma) {
         case 4: k_force4<4><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
         case 8: k_force4<8><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
         default: k_force4<12><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
         }
     } else {
-        TileMap tm = make_tilemap(P.g, 32, 8, blocks);
+        TileMap tm = make_tilemap(P.g, 32, 8, group, blocks);
         k_force<<<blocks, 256, 0, s>>>(P, tm, f, Ft, F);
     }
     return cudaGetLastError();

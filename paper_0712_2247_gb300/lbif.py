@@ -60,6 +60,13 @@ SIGNATURES = {
     "lbif_status": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "lbif_save": (_i32, [_vp, ctypes.c_char_p]),
     "lbif_load": (_i32, [_vp, ctypes.c_char_p]),
+    "lbif_batch_create": (_i32, [ctypes.POINTER(_vp), _i32, ctypes.POINTER(_i32), _pd, _pd, _pd, _f64,
+                                 _i32, _i32, ctypes.POINTER(Force), ctypes.POINTER(Opts)]),
+    "lbif_batch_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
+    "lbif_batch_seed": (_i32, [_vp, _vp, _vp, _i32]),
+    "lbif_batch_run": (_i32, [_vp, _f64, _i64, _i32, ctypes.POINTER(_i64)]),
+    "lbif_batch_profiles": (_i32, [_vp, _pd, _pd, _i32]),
+    "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "lbif_destroy": (_i32, [_vp]),
     "lbif_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -227,3 +234,72 @@ class Slit:
 
     def load(self, path: str):
         self._check(self._lib.lbif_load(self._h, path.encode()))
+
+
+class Ensemble(Slit):
+    """Many slits (widths H, packing fractions eta, forces F along x, relaxation
+    times tau) advanced together through the C ABI; one stacked grid on the GPU."""
+
+    def __init__(self, H, eta, F, tau, sigma: float, nx: int = 32, ny: int = 32, *,
+                 hs: bool = True, coupling: bool = True, regularize: bool = True,
+                 g2_form: int = 0, storage: int = STORE_F16, seed: int = 0, noise: float = 1e-3,
+                 stream: Optional[int] = None):
+        self._lib = load_library()
+        H = np.ascontiguousarray(H, dtype=np.int32)
+        eta = np.ascontiguousarray(eta, dtype=np.float64)
+        F = np.ascontiguousarray(F, dtype=np.float64)
+        tau = np.ascontiguousarray(tau, dtype=np.float64)
+        n = len(H)
+        assert len(eta) == len(F) == len(tau) == n
+        f = Force((ctypes.c_double * 3)(0.0, 0.0, 0.0), int(hs), int(coupling), int(regularize),
+                  int(g2_form), 0, 1.0, 2.5)
+        o = Opts(int(storage), int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), stream)
+        h = _vp()
+        pd = lambda a: a.ctypes.data_as(_pd)
+        rc = self._lib.lbif_batch_create(ctypes.byref(h), n, H.ctypes.data_as(ctypes.POINTER(_i32)),
+                                         pd(eta), pd(F), pd(tau), float(sigma), int(nx), int(ny),
+                                         ctypes.byref(f), ctypes.byref(o))
+        if rc != LBIF_OK:
+            raise LbifError(rc, self._lib.lbif_last_error(None).decode())
+        self._h = h
+        self.H, self.eta_s, self.F_s, self.tau_s = H, eta, F, tau
+        self.nslits = n
+        self.sigma = sigma
+        self.n0_s = 6.0 * eta / (np.pi * sigma ** 3)
+        zlo = np.zeros(n, np.int32)
+        nodes = ctypes.c_int64()
+        self._check(self._lib.lbif_batch_info(self._h, None, zlo.ctypes.data_as(ctypes.POINTER(_i32)),
+                                              ctypes.byref(nodes)))
+        self.zlo = zlo
+        self.nodes = nodes.value
+        nz = int(zlo[-1] + H[-1])
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+
+    def seed(self, n_z, ux_z=None):
+        """Set every slit to the equilibrium of profiles n_z[s, j], ux_z[s, j] (j < H[s])."""
+        n_z = np.ascontiguousarray(n_z, dtype=np.float32)
+        hmax = n_z.shape[1]
+        ux = None if ux_z is None else np.ascontiguousarray(ux_z, dtype=np.float32)
+        self._check(self._lib.lbif_batch_seed(self._h, n_z.ctypes.data,
+                                              None if ux is None else ux.ctypes.data, hmax))
+
+    def run(self, tol: float = 1e-8, max_steps: int = 100000, check_every: int = 100):
+        """Run to steady state; returns steps taken per slit (-1: not converged, -2: diverged)."""
+        out = np.zeros(self.nslits, np.int64)
+        self._check(self._lib.lbif_batch_run(self._h, float(tol), int(max_steps), int(check_every),
+                                             out.ctypes.data_as(ctypes.POINTER(_i64))))
+        return out
+
+    def slit_profiles(self, hmax: Optional[int] = None):
+        hmax = int(hmax or self.H.max())
+        n = np.zeros((self.nslits, hmax))
+        ux = np.zeros((self.nslits, hmax))
+        pd = lambda a: a.ctypes.data_as(_pd)
+        self._check(self._lib.lbif_batch_profiles(self._h, pd(n), pd(ux), hmax), True)
+        return n, ux
+
+    def autotune(self, trials: int = 3):
+        b, g = ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.lbif_autotune(self._h, int(trials), ctypes.byref(b), ctypes.byref(g)))
+        return b.value, g.value
