@@ -164,10 +164,13 @@ int lbif_batch_seed(lbif_handle h, const float* n_z, const float* ux_z, int32_t 
  * even), until every slit's residual (lbif_residual's definition over its own
  * x,y-averaged profiles, with t - t0 = check_every) is below tol, or
  * max_steps. Converged slits are frozen (their kernels exit at once) while the
- * others continue. steps_taken[s] (may be NULL) = steps at which slit s met
- * tol, -1 if it did not within max_steps, -2 if it diverged. */
+ * others continue. With patience > 0 a slit whose residual has not improved
+ * for patience consecutive checks is frozen too: its rounding floor (FP32 /
+ * FP16 state) lies above tol. steps_taken[s] (may be NULL) = steps at which
+ * slit s met tol, -1 if it did not within max_steps, -2 if it diverged, -3 if
+ * it stalled; residual[s] (may be NULL) = the smallest residual it reached. */
 int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int32_t check_every,
-                   int64_t* steps_taken);
+                   int32_t patience, int64_t* steps_taken, double* residual);
 
 /* FP64 x,y-averaged profiles of every slit, n_z / ux_z[s*hmax + j] (host
  * arrays, either may be NULL; zero beyond H[s]). Synchronises. */

@@ -909,9 +909,9 @@ static int run_graph(lbif_ctx* h, int steps)
 }
 
 extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int32_t check_every,
-                              int64_t* steps_taken)
+                              int32_t patience, int64_t* steps_taken, double* residual)
 {
-    if (!h || !(tol > 0) || max_steps < 0 || check_every < 2)
+    if (!h || !(tol > 0) || max_steps < 0 || check_every < 2 || patience < 0)
         return fail(h, LBIF_ERR_ARG, "lbif_batch_run: bad arguments");
     const int K = (check_every + 1) / 2 * 2;
     const size_t S = h->sl.size();
@@ -920,6 +920,8 @@ extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int3
     int rc = upload_done(h);
     if (rc) return rc;
     std::vector<int64_t> taken(S, -1);
+    std::vector<double> best(S, INFINITY);
+    std::vector<int> since_best(S, 0);
     std::vector<std::vector<double>> pn(S), pu(S);  // previous profiles
     int64_t t0 = h->t;
     size_t active = S;
@@ -947,9 +949,19 @@ extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int3
             }
             if (!pn[s].empty()) {
                 double R = profile_residual(n.data(), pn[s].data(), u.data(), pu[s].data(), len, (double)K);
+                if (R < best[s]) {
+                    best[s] = R;
+                    since_best[s] = 0;
+                } else {
+                    ++since_best[s];
+                }
                 if (R < tol) {
                     h->done[s] = 1;
                     taken[s] = h->t - t0;
+                    --active;
+                } else if (patience > 0 && since_best[s] >= patience) {
+                    h->done[s] = 1;  // rounding floor above tol: frozen, reported as -3
+                    taken[s] = -3;
                     --active;
                 }
             }
@@ -960,6 +972,8 @@ extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int3
     }
     if (steps_taken)
         for (size_t s = 0; s < S; ++s) steps_taken[s] = taken[s];
+    if (residual)
+        for (size_t s = 0; s < S; ++s) residual[s] = best[s];
     // unfreeze: later calls step every slit again
     std::fill(h->done.begin(), h->done.end(), 0);
     if ((rc = upload_done(h))) return rc;

@@ -64,7 +64,7 @@ SIGNATURES = {
                                  _i32, _i32, ctypes.POINTER(Force), ctypes.POINTER(Opts)]),
     "lbif_batch_info": (_i32, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i64)]),
     "lbif_batch_seed": (_i32, [_vp, _vp, _vp, _i32]),
-    "lbif_batch_run": (_i32, [_vp, _f64, _i64, _i32, ctypes.POINTER(_i64)]),
+    "lbif_batch_run": (_i32, [_vp, _f64, _i64, _i32, _i32, ctypes.POINTER(_i64), _pd]),
     "lbif_batch_profiles": (_i32, [_vp, _pd, _pd, _i32]),
     "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "lbif_destroy": (_i32, [_vp]),
@@ -284,12 +284,16 @@ class Ensemble(Slit):
         self._check(self._lib.lbif_batch_seed(self._h, n_z.ctypes.data,
                                               None if ux is None else ux.ctypes.data, hmax))
 
-    def run(self, tol: float = 1e-8, max_steps: int = 100000, check_every: int = 100):
-        """Run to steady state; returns steps taken per slit (-1: not converged, -2: diverged)."""
+    def run(self, tol: float = 1e-8, max_steps: int = 100000, check_every: int = 100,
+            patience: int = 0, return_residual: bool = False):
+        """Run to steady state; returns steps taken per slit (-1: not within max_steps,
+        -2: diverged, -3: stalled above tol for `patience` checks) [and the best residual]."""
         out = np.zeros(self.nslits, np.int64)
+        res = np.zeros(self.nslits)
         self._check(self._lib.lbif_batch_run(self._h, float(tol), int(max_steps), int(check_every),
-                                             out.ctypes.data_as(ctypes.POINTER(_i64))))
-        return out
+                                             int(patience), out.ctypes.data_as(ctypes.POINTER(_i64)),
+                                             res.ctypes.data_as(_pd)))
+        return (out, res) if return_residual else out
 
     def slit_profiles(self, hmax: Optional[int] = None):
         hmax = int(hmax or self.H.max())
