@@ -182,6 +182,30 @@ int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax);
  * tile-group edge in nodes. */
 int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group);
 
+/* ---- profiles without allocation ------------------------------------------
+ * No counterpart in the paper: an operational entry point. It gives the same
+ * FP64 x,y-averaged profiles n(z), u_x(z) and totals {mass, momentum} as
+ * lbif_profiles, but of fields the caller holds - rho (nx*ny*nz floats) and
+ * u (3 SoA planes), device pointers, layout as lbif_moments - and it
+ * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ * It is meant for callers that cannot allocate device memory when they need
+ * the profiles (code running during stream capture, services whose device
+ * memory is reserved up front by their own allocator, fixed-footprint loops).
+ * Its scratch is a fixed 320 KB array in the library's device image, which
+ * every GPU that loads the library keeps until the process exits; nz above
+ * 8192 is rejected with LBIF_ERR_UNSUPPORTED. All calls share that array:
+ * calls that overlap on the GPU (other streams, other threads) race on it.
+ * Every call overwrites what it uses, nothing needs clearing. The first call
+ * on a device looks the array's device address up (cudaGetSymbolAddress, with
+ * that device current); make that first call before any stream capture.
+ * n_z, ux_z (nz doubles) and out4 are host pointers (any may be NULL); work is
+ * enqueued on `stream` (cudaStream_t, NULL = default) and synchronised. On
+ * error, lbif_noalloc_last_error() gives a message. */
+int lbif_field_profiles_noalloc(const float* rho, const float* u, int32_t nx, int32_t ny,
+                                int32_t nz, double* n_z, double* ux_z, double* out4,
+                                void* stream);
+const char* lbif_noalloc_last_error(void);
+
 int lbif_destroy(lbif_handle h);
 
 /* Message of the last error of a handle; NULL handle = last global error

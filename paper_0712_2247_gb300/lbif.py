@@ -67,6 +67,8 @@ SIGNATURES = {
     "lbif_batch_run": (_i32, [_vp, _f64, _i64, _i32, _i32, ctypes.POINTER(_i64), _pd]),
     "lbif_batch_profiles": (_i32, [_vp, _pd, _pd, _i32]),
     "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "lbif_field_profiles_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _pd, _pd, _pd, _vp]),
+    "lbif_noalloc_last_error": (ctypes.c_char_p, []),
     "lbif_destroy": (_i32, [_vp]),
     "lbif_last_error": (ctypes.c_char_p, [_vp]),
 }
