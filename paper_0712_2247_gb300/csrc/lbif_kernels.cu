@@ -6,6 +6,8 @@
 // (dn = n/n0 - 1, dG = g2 - g2(eta0)), and mirror-image quadrature points are
 // combined before they are summed, so a uniform state gives an exactly zero
 // force. FP64 appears only in the profile / mass reductions.
+#include <string.h>
+
 #include "lbif_internal.h"
 
 namespace lbif {
@@ -78,6 +80,7 @@ __device__ __forceinline__ void for_images(const Geom& g, int x, int y, int z, F
 // footprint stays in L2 instead of spanning 2 sigma + 1 full planes.
 struct TileMap {
     int tx, ty, tiles_x, tiles_y, gtx, gty, ngx;
+    int flat;  // 1: narrow grid, threads run over (x block, y, z) in order
 };
 
 __device__ __forceinline__ bool tile_origin(const Geom& g, const TileMap& tm, int& tile_x,
@@ -107,7 +110,34 @@ static inline TileMap make_tilemap(const Geom& g, int tx, int ty, int group, uns
     tm.ngx = (tm.tiles_x + tm.gtx - 1) / tm.gtx;
     int ngy = (tm.tiles_y + tm.gty - 1) / tm.gty;
     blocks = (unsigned)tm.gtx * tm.gty * g.nz * tm.ngx * ngy;
+    tm.flat = 0;
     return tm;
+}
+
+// narrow grids (nx below one tile row): one thread per block of xw x-nodes,
+// consecutive threads over x blocks, then y, then z
+static inline TileMap make_flatmap(const Geom& g, int xw, int threads, unsigned& blocks)
+{
+    TileMap tm;
+    memset(&tm, 0, sizeof(tm));
+    tm.flat = 1;
+    tm.tx = (g.nx + xw - 1) / xw;  // x blocks per row
+    long long n = (long long)tm.tx * g.ny * g.nz;
+    blocks = (unsigned)((n + threads - 1) / threads);
+    return tm;
+}
+
+__device__ __forceinline__ bool flat_node(const Geom& g, const TileMap& tm, int xw, int& x, int& y, int& z)
+{
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long rows = (long long)g.ny * g.nz;
+    if (k >= rows * tm.tx) return false;
+    int xb = (int)(k % tm.tx);
+    long long r = k / tm.tx;
+    y = (int)(r % g.ny);
+    z = (int)(r / g.ny);
+    x = xb * xw;
+    return true;
 }
 
 // slit of plane z (-1 for a gap plane between stacked slits)
@@ -402,6 +432,34 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
     }
 }
 
+// Narrow grids (a 32 x 8 tile would leave most lanes idle): one thread per
+// node, the ball as x-row segments read from the padded field.
+__global__ void __launch_bounds__(256) k_ball_direct(Params P, const float* __restrict__ dn,
+                                                     float* __restrict__ dG, int* status, int skip_done)
+{
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    const int so = slit_of(P, z);
+    if (so < 0 || (skip_done && frozen(P, so))) return;
+    const int R = P.sigma / 2;
+    const int p = pidx(P.g, x, y, z);
+    float s = 0.f;
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy) {
+            const int rem = R * R - dy * dy - dz * dz;
+            if (rem < 0) continue;
+            const int w = cisqrt(rem);
+            const float* row = dn + p + (dz * P.g.py + dy) * P.g.px;
+            for (int dx = -w; dx <= w; ++dx) s += __ldg(row + dx);
+        }
+    bool bad;
+    float v = g2_deviation(P, P.sl[so].eta0, s * P.ball_inv, bad);
+    if (bad) atomicOr(status, 2);
+    for_images(P.g, x, y, z, [&](int q) { dG[q] = v; });
+}
+
 // ---------------------------------------------------------------------------
 // step 3: hard-sphere shell force, Eq. LBHS at constant T, 18-point rule.
 //   T_q = A_q - (G0 + A_q) lk s_q.(u_q - u),  A_q = G_q n_q / n0 - G0
@@ -527,12 +585,18 @@ __global__ void __launch_bounds__(256) k_force(Params P, TileMap tm, Fields fl,
                                                const float4* __restrict__ Ft, float4* __restrict__ F)
 {
     const Geom& g = P.g;
-    int tx, ty, z;
-    if (!tile_origin(g, tm, tx, ty, z)) return;
+    int x, y, z;
+    if (tm.flat) {
+        if (!flat_node(g, tm, 1, x, y, z)) return;
+    } else {
+        int tx, ty;
+        if (!tile_origin(g, tm, tx, ty, z)) return;
+        x = tx * tm.tx + threadIdx.x % 32;
+        y = ty * tm.ty + threadIdx.x / 32;
+        if (x >= g.nx || y >= g.ny) return;
+    }
     const int s = slit_of(P, z);
     if (s < 0 || frozen(P, s)) return;
-    const int x = tx * tm.tx + threadIdx.x % 32, y = ty * tm.ty + threadIdx.x / 32;
-    if (x >= g.nx || y >= g.ny) return;
     const long long idx = ((long long)z * g.ny + y) * g.nx + x;
     const SlitParam S = P.sl[s];
     float fx, fy, fz;
@@ -755,13 +819,19 @@ __global__ void __launch_bounds__(128) k_force4(Params P, TileMap tm, Fields fl,
                                                 const float4* __restrict__ Ft, float4* __restrict__ F)
 {
     const Geom& g = P.g;
-    int tx, ty, z;
-    if (!tile_origin(g, tm, tx, ty, z)) return;
+    int x, y, z;
+    if (tm.flat) {
+        if (!flat_node(g, tm, 4, x, y, z)) return;
+    } else {
+        int tx, ty;
+        if (!tile_origin(g, tm, tx, ty, z)) return;
+        x = tx * 128 + 4 * (threadIdx.x % 32);
+        y = ty * tm.ty + threadIdx.x / 32;
+        if (x >= g.nx || y >= g.ny) return;
+    }
     const int s = slit_of(P, z);
     if (s < 0 || frozen(P, s)) return;
     const SlitParam S = P.sl[s];
-    const int x = tx * 128 + 4 * (threadIdx.x % 32), y = ty * tm.ty + threadIdx.x / 32;
-    if (x >= g.nx || y >= g.ny) return;
     const int pb = pidx(g, x, y, z);  // 16-byte aligned: x, hw, px multiples of 4
     v4 d0, u0[3];
     set4(d0, ld4(fl.dn + pb));
@@ -1100,6 +1170,10 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
 cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, int want,
                         int skip_done, cudaStream_t s)
 {
+    if (P.g.nx < BALL_TX / 2 || P.g.ny < BALL_TY / 2) {
+        k_ball_direct<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, dn, dG, status, skip_done);
+        return cudaGetLastError();
+    }
     switch (P.sigma / 2) {
     case 1: return ball_r<1>(P, dn, dG, status, want, skip_done, s);
     case 2: return ball_r<2>(P, dn, dG, status, want, skip_done, s);
@@ -1130,14 +1204,14 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
     unsigned blocks;
     if (group <= 0) group = 128;
     if (force_vectorised(P.sigma)) {
-        TileMap tm = make_tilemap(P.g, 128, 4, group, blocks);
+        TileMap tm = P.g.nx < 128 ? make_flatmap(P.g, 4, 128, blocks) : make_tilemap(P.g, 128, 4, group, blocks);
         switch (P.sigma) {
         case 4: k_force4<4><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
         case 8: k_force4<8><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
         default: k_force4<12><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
         }
     } else {
-        TileMap tm = make_tilemap(P.g, 32, 8, group, blocks);
+        TileMap tm = P.g.nx < 32 ? make_flatmap(P.g, 1, 256, blocks) : make_tilemap(P.g, 32, 8, group, blocks);
         k_force<<<blocks, 256, 0, s>>>(P, tm, f, Ft, F);
     }
     return cudaGetLastError();
