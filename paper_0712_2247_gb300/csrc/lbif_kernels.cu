@@ -433,7 +433,9 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
 }
 
 // Narrow grids (a 32 x 8 tile would leave most lanes idle): one thread per
-// node, the ball as x-row segments read from the padded field.
+// node, reading the padded field directly. The additions run in the order of
+// k_ball (row sums grown outwards from the centre, disc sums over y, then the
+// planes in increasing z), so both kernels give bit-identical results.
 __global__ void __launch_bounds__(256) k_ball_direct(Params P, const float* __restrict__ dn,
                                                      float* __restrict__ dG, int* status, int skip_done)
 {
@@ -446,14 +448,19 @@ __global__ void __launch_bounds__(256) k_ball_direct(Params P, const float* __re
     const int R = P.sigma / 2;
     const int p = pidx(P.g, x, y, z);
     float s = 0.f;
-    for (int dz = -R; dz <= R; ++dz)
+    for (int dz = -R; dz <= R; ++dz) {
+        float D = 0.f;
         for (int dy = -R; dy <= R; ++dy) {
             const int rem = R * R - dy * dy - dz * dz;
             if (rem < 0) continue;
             const int w = cisqrt(rem);
             const float* row = dn + p + (dz * P.g.py + dy) * P.g.px;
-            for (int dx = -w; dx <= w; ++dx) s += __ldg(row + dx);
+            float r = __ldg(row);
+            for (int dx = 1; dx <= w; ++dx) r += __ldg(row - dx) + __ldg(row + dx);
+            D += r;
         }
+        s += D;
+    }
     bool bad;
     float v = g2_deviation(P, P.sl[so].eta0, s * P.ball_inv, bad);
     if (bad) atomicOr(status, 2);

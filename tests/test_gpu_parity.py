@@ -302,3 +302,23 @@ def test_thin_and_degenerate_grids(L, O):
         rg, ug = g.moments()
         ro, uo = o.moments()
         assert nerr(rg, ro) < 1e-5, shape
+
+
+@pytest.mark.parametrize("sigma,wide", [(4, (128, 8)), (6, (32, 8)), (12, (128, 8))])
+def test_narrow_grid_kernels_bit_identical_to_tiled(L, sigma, wide):
+    """x,y-uniform slits: the thin-grid kernels (flat force mapping, direct
+    ball sums) give exactly the per-node values of the tiled kernels."""
+    nz = 5 * sigma
+    kw = dict(body=(1e-5, 0, 0), noise=0.0)
+    a = L.Slit(4, 4, nz, sigma, 0.2, 0.9, **kw)
+    b = L.Slit(wide[0], wide[1], nz, sigma, 0.2, 0.9, **kw)
+    a.step(60)
+    b.step(60)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert np.array_equal(ra[:, 0, 0], rb[:, 0, 0])
+    assert np.array_equal(ua[:, :, 0, 0], ub[:, :, 0, 0])
+    # and both are x,y-uniform
+    assert np.array_equal(rb, np.broadcast_to(rb[:, :1, :1], rb.shape))
+    a.close()
+    b.close()
