@@ -182,6 +182,35 @@ int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax);
  * tile-group edge in nodes. */
 int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group);
 
+/* ---- warm-start network -------------------------------------------------
+ * A multilayer perceptron nin -> nhidden layers of width `hidden` (GELU, erf
+ * form) -> nout, mapping slit parameters to predicted steady profiles; it only
+ * seeds populations (lbif_batch_seed), the lattice Boltzmann iteration always
+ * runs to convergence. Products run on the tensor cores with bfloat16
+ * operands and FP32 accumulation; master weights, Adam moments and all
+ * element-wise work are FP32. Parameters are one flat FP32 vector: for each
+ * layer W (out x in, row-major) then b (out). Widths <= 256. */
+typedef struct lbif_mlp_ctx* lbif_mlp;
+
+int lbif_mlp_create(lbif_mlp* out, int32_t nin, int32_t hidden, int32_t nhidden, int32_t nout,
+                    int32_t max_batch, void* stream);
+int64_t lbif_mlp_num_params(lbif_mlp m);
+/* host arrays of lbif_mlp_num_params floats; set_params also resets Adam */
+int lbif_mlp_set_params(lbif_mlp m, const float* params);
+int lbif_mlp_get_params(lbif_mlp m, float* params);
+/* Y (batch x nout) = network(X (batch x nin)); on_device selects device or
+ * host pointers. Synchronises. */
+int lbif_mlp_forward(lbif_mlp m, const float* X, int32_t batch, float* Y, int32_t on_device);
+/* Loss = sum(mask (Y - T)^2) / sum(mask) and its gradient (flat, like the
+ * parameters; grads may be NULL). */
+int lbif_mlp_gradients(lbif_mlp m, const float* X, const float* T, const float* mask, int32_t batch,
+                       float* grads, double* loss, int32_t on_device);
+/* One Adam step (bias-corrected) on that loss; *loss receives it. */
+int lbif_mlp_train_step(lbif_mlp m, const float* X, const float* T, const float* mask, int32_t batch,
+                        float lr, float beta1, float beta2, float eps, double* loss, int32_t on_device);
+int lbif_mlp_destroy(lbif_mlp m);
+const char* lbif_mlp_last_error(lbif_mlp m);
+
 /* ---- profiles without allocation ------------------------------------------
  * No counterpart in the paper: an operational entry point. It gives the same
  * FP64 x,y-averaged profiles n(z), u_x(z) and totals {mass, momentum} as

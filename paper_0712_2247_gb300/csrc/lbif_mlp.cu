@@ -1,0 +1,733 @@
+// Warm-start network: a multilayer perceptron whose products run on the
+// 5th-generation tensor cores (tcgen05, BF16 operands, FP32 accumulation in
+// tensor memory), trained with Adam on FP32 master weights.
+//
+// GEMM convention: C[M x N] = A[M x K] . B[N x K]^T with A and B bfloat16,
+// row-major (K contiguous), K a multiple of 16 (buffers are zero-padded along
+// K); rows of A beyond M and of B beyond N read as zero. One CTA computes a
+// 128-row block with all N <= 256 columns in one accumulator.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "lbif.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------------------
+// PTX wrappers (tcgen05 / mbarrier)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// D[tmem] (+)= A[smem] . B[smem]^T, kind::f16 (BF16 in, FP32 accumulate)
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(mbar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+        "%13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major: the operand is laid
+// out as 8-row x 16-byte core matrices; lbo = byte step between core
+// matrices along K, sbo = byte step between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version; base offset 0; layout type 0 = no swizzle
+    return d;
+}
+
+// instruction descriptor, kind::f16: D F32, A and B BF16, both K-major, M x N
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z)
+{
+    return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// ---------------------------------------------------------------------------
+// GEMM with fused epilogue
+// ---------------------------------------------------------------------------
+enum { EPI_NONE = 0, EPI_GELU = 1, EPI_GELU_GRAD = 2 };
+
+struct Gemm {
+    const bf16* A;
+    int lda;
+    const bf16* B;
+    int ldb;
+    int M, N, K;
+    const float* bias;  // per column, may be null
+    int epi;
+    const float* zprev; // EPI_GELU_GRAD: pre-activation multiplied in (ld = ldz)
+    float* Z;           // FP32 result (after bias / gradient factor), may be null
+    int ldz;
+    bf16* H;            // bf16 of the activated result, row-major, may be null
+    int ldh;
+    bf16* HT;           // bf16 transposed, may be null
+    int ldht;
+    int* err;
+};
+
+constexpr int GEMM_KC = 64;   // K staged per round
+constexpr int GEMM_SMEM = 128 * GEMM_KC * 2 + 256 * GEMM_KC * 2 + 64;
+// dynamic shared memory requested at launch: large enough that at most two
+// CTAs share an SM, so their two 256-column accumulators always fit in the
+// 512 TMEM columns and no allocation ever waits on another CTA
+constexpr int GEMM_SMEM_LAUNCH = 100 * 1024;
+constexpr long long WAIT_LIMIT = 1LL << 22;  // try_wait polls; seconds at most
+
+__global__ void __launch_bounds__(128) k_gemm_tc(Gemm g)
+{
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;
+    uint8_t* sB = smem + 128 * GEMM_KC * 2;
+    uint64_t* mbar = (uint64_t*)(sB + 256 * GEMM_KC * 2);
+    uint32_t* tslot = (uint32_t*)(mbar + 1);
+    const int m0 = blockIdx.x * 128;
+    const int NT = (g.N + 15) / 16 * 16;  // <= 256
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    if (warp == 0) {
+        tmem_alloc(tslot, 256);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = idesc_bf16(128, NT);
+    uint32_t phase = 0;
+    int timed_out = 0;
+
+    for (int k0 = 0; k0 < g.K; k0 += GEMM_KC) {
+        const int kc = min(GEMM_KC, g.K - k0);  // multiple of 16
+        const int kcore = kc / 8;                // core matrices along K
+        // stage A (128 x kc) and B (NT x kc) as 8x16-byte core matrices
+        for (int t = threadIdx.x; t < 128 * kcore; t += 128) {
+            const int r = t / kcore, kp = t - r * kcore;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (m0 + r < g.M) v = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + kp * 8);
+            *reinterpret_cast<uint4*>(sA + ((r >> 3) * kcore + kp) * 128 + (r & 7) * 16) = v;
+        }
+        for (int t = threadIdx.x; t < NT * kcore; t += 128) {
+            const int r = t / kcore, kp = t - r * kcore;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (r < g.N) v = *reinterpret_cast<const uint4*>(g.B + (size_t)r * g.ldb + k0 + kp * 8);
+            *reinterpret_cast<uint4*>(sB + ((r >> 3) * kcore + kp) * 128 + (r & 7) * 16) = v;
+        }
+        fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (threadIdx.x == 0) {
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            const uint32_t sbo = kcore * 128;
+            for (int kk = 0; kk < kc / 16; ++kk) {
+                const uint64_t ad = smem_desc(a0 + kk * 256, 128, sbo);
+                const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
+                mma_bf16(tmem, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(mbar);
+        }
+        // bounded wait for the products of this round before the stage is reused
+        long long spins = 0;
+        int to = 0;
+        while (!mbar_try_wait(mbar, phase)) {
+            if (++spins > WAIT_LIMIT) {
+                to = 1;
+                break;
+            }
+        }
+        phase ^= 1u;
+        timed_out = __syncthreads_or(to);
+        tc_fence_after();
+        if (timed_out) break;
+    }
+
+    if (!timed_out) {
+        const int row = m0 + 32 * warp + lane;
+        for (int c = 0; c < NT; c += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            if (row < g.M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = c + j;
+                    if (n >= g.N) break;
+                    float z = v[j] + (g.bias ? g.bias[n] : 0.f);
+                    float h = z;
+                    if (g.epi == EPI_GELU) {
+                        h = gelu(z);
+                    } else if (g.epi == EPI_GELU_GRAD) {
+                        z = z * gelu_grad(g.zprev[(size_t)row * g.ldz + n]);
+                        h = z;
+                    }
+                    if (g.Z) g.Z[(size_t)row * g.ldz + n] = z;
+                    const bf16 hb = __float2bfloat16_rn(h);
+                    if (g.H) g.H[(size_t)row * g.ldh + n] = hb;
+                    if (g.HT) g.HT[(size_t)n * g.ldht + row] = hb;
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(g.err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------------------------------------
+// element-wise kernels
+// ---------------------------------------------------------------------------
+// X (batch x nin, FP32) -> bf16 rows (bp x kpad) and transposed (kpad x bp), zero padded
+__global__ void k_pack_input(const float* X, int batch, int nin, int bp, int kpad, bf16* H, bf16* HT)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= bp * kpad) return;
+    int r = i / kpad, c = i - r * kpad;
+    float v = (r < batch && c < nin) ? X[(size_t)r * nin + c] : 0.f;
+    bf16 b = __float2bfloat16_rn(v);
+    H[i] = b;
+    HT[(size_t)c * bp + r] = b;
+}
+
+// sum of the mask (one block, fixed order), at least 1
+__global__ void k_msum(const float* mask, long long n, double* out)
+{
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (long long i = threadIdx.x; i < n; i += blockDim.x) s += mask[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = fmax(sh[0], 1.0);
+}
+
+// dY = 2 mask (Y - T) / sum(mask): FP32 (bp x nout), bf16 rows (bp x opad) and
+// bf16 transposed (nout x bp); per-block FP64 partial sums of the loss
+__global__ void k_loss(const float* Y, const float* T, const float* mask, int batch, int nout, int opad, int bp,
+                       const double* msum, float* dY, bf16* dYb, bf16* dYT, double* partial)
+{
+    __shared__ double sh[256];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (i < bp * nout) {
+        int r = i / nout, c = i - r * nout;
+        float d = 0.f;
+        if (r < batch) {
+            float m = mask[(size_t)r * nout + c];
+            float e = (Y[(size_t)r * nout + c] - T[(size_t)r * nout + c]) * m;
+            l = (double)e * e;
+            d = (float)(2.0 * e / *msum);
+        }
+        dY[i] = d;
+        bf16 b = __float2bfloat16_rn(d);
+        dYb[(size_t)r * opad + c] = b;
+        dYT[(size_t)c * bp + r] = b;
+    }
+    sh[threadIdx.x] = l;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// column sums of D (rows x cols, FP32) -> out (fixed-order, one thread per column)
+__global__ void k_colsum(const float* D, int rows, int cols, float* out)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cols) return;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += D[(size_t)r * cols + c];
+    out[c] = (float)s;
+}
+
+// copy the first ncopy columns of a (rows x ld) FP32 matrix into dst (rows x ncopy)
+__global__ void k_copy_cols(const float* src, int rows, int ld, int ncopy, float* dst)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows * ncopy) return;
+    int r = i / ncopy, c = i - r * ncopy;
+    dst[i] = src[(size_t)r * ld + c];
+}
+
+__global__ void k_adam(float* p, const float* g, float* m, float* v, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2)
+{
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float gi = g[i];
+    float mi = b1 * m[i] + (1.f - b1) * gi;
+    float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// bf16 shadows of W (nout x nin): row-major padded to kpad columns, and
+// transposed (nin x opad, columns beyond nout stay zero)
+__global__ void k_shadow(const float* W, int nout, int nin, int kpad, int opad, bf16* Wb, bf16* WTb)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nout * kpad) return;
+    int r = i / kpad, c = i - r * kpad;
+    float w = c < nin ? W[(size_t)r * nin + c] : 0.f;
+    bf16 b = __float2bfloat16_rn(w);
+    Wb[i] = b;
+    if (c < nin) WTb[(size_t)c * opad + r] = b;
+}
+
+inline int up16(int v) { return (v + 15) / 16 * 16; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct lbif_mlp_ctx {
+    int nin, hidden, nhidden, nout, max_batch, bp_max;
+    int L;                      // layers
+    std::vector<int> din, dout, kpad, opad;  // kpad, opad: widths rounded up to 16
+    std::vector<long long> woff, boff;  // offsets into the flat parameter vector
+    long long nparams;
+    cudaStream_t stream = nullptr;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // flat FP32
+    std::vector<bf16*> Wb, WTb;
+    std::vector<float*> Z;       // pre-activations per layer (bp x dout)
+    std::vector<bf16*> H, HT;    // layer inputs (bp x kpad) and transposed (kpad x bp)
+    float* dY = nullptr;         // output error FP32 (bp x nout)
+    std::vector<float*> dZ;      // per layer FP32 error (bp x dout)
+    std::vector<bf16*> dZb, dZT; // bf16 copies
+    float* dWtmp = nullptr;      // dW with padded columns
+    float* Xd = nullptr;         // device staging for host inputs (max_batch x nin)
+    float *Td = nullptr, *Md = nullptr, *Yd = nullptr;
+    double* partial = nullptr;
+    double* msum = nullptr;
+    int* err = nullptr;
+    long long adam_t = 0;
+    std::string msg;
+};
+
+static thread_local std::string g_mlp_err = "no error";
+
+static int mfail(lbif_mlp_ctx* m, int code, const std::string& s)
+{
+    if (m) m->msg = s;
+    g_mlp_err = s;
+    return code;
+}
+
+#define MCK(m, call)                                                                         \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return mfail((m), LBIF_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static void mlp_free(lbif_mlp_ctx* m)
+{
+    if (!m) return;
+    std::vector<void*> bufs = {m->p, m->g, m->m, m->v, m->dY, m->dWtmp, m->Xd, m->Td, m->Md, m->Yd, m->partial, m->msum, m->err};
+    for (auto* b : m->Wb) bufs.push_back(b);
+    for (auto* b : m->WTb) bufs.push_back(b);
+    for (auto* b : m->Z) bufs.push_back(b);
+    for (auto* b : m->H) bufs.push_back(b);
+    for (auto* b : m->HT) bufs.push_back(b);
+    for (auto* b : m->dZ) bufs.push_back(b);
+    for (auto* b : m->dZb) bufs.push_back(b);
+    for (auto* b : m->dZT) bufs.push_back(b);
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete m;
+}
+
+template <class T>
+static bool dalloc(T** p, size_t n)
+{
+    if (cudaMalloc((void**)p, sizeof(T) * (n ? n : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return cudaMemset(*p, 0, sizeof(T) * (n ? n : 1)) == cudaSuccess;
+}
+
+extern "C" int lbif_mlp_create(lbif_mlp* out, int32_t nin, int32_t hidden, int32_t nhidden, int32_t nout,
+                               int32_t max_batch, void* stream)
+{
+    if (!out || nin < 1 || nin > 256 || hidden < 16 || hidden > 256 || hidden % 16 || nhidden < 1 ||
+        nout < 1 || nout > 256 || max_batch < 1)
+        return mfail(nullptr, LBIF_ERR_ARG, "lbif_mlp_create: widths must be in [1, 256] (hidden a multiple of 16)");
+    *out = nullptr;
+    lbif_mlp_ctx* m = new lbif_mlp_ctx();
+    m->nin = nin;
+    m->hidden = hidden;
+    m->nhidden = nhidden;
+    m->nout = nout;
+    m->max_batch = max_batch;
+    m->bp_max = up16(max_batch);
+    m->L = nhidden + 1;
+    m->stream = (cudaStream_t)stream;
+    long long off = 0;
+    for (int l = 0; l < m->L; ++l) {
+        int di = l == 0 ? nin : hidden, dq = l == m->L - 1 ? nout : hidden;
+        m->din.push_back(di);
+        m->dout.push_back(dq);
+        m->kpad.push_back(up16(di));
+        m->opad.push_back(up16(dq));
+        m->woff.push_back(off);
+        off += (long long)di * dq;
+        m->boff.push_back(off);
+        off += dq;
+    }
+    m->nparams = off;
+    const int bp = m->bp_max;
+    bool ok = dalloc(&m->p, off) && dalloc(&m->g, off) && dalloc(&m->m, off) && dalloc(&m->v, off) &&
+              dalloc(&m->dY, (size_t)bp * nout) && dalloc(&m->dWtmp, (size_t)256 * 256) &&
+              dalloc(&m->Xd, (size_t)max_batch * nin) && dalloc(&m->Td, (size_t)max_batch * nout) &&
+              dalloc(&m->Md, (size_t)max_batch * nout) && dalloc(&m->Yd, (size_t)bp * nout) &&
+              dalloc(&m->partial, (size_t)(bp * nout + 255) / 256 + 1) && dalloc(&m->msum, 1) &&
+              dalloc(&m->err, 1);
+    for (int l = 0; ok && l < m->L; ++l) {
+        bf16 *wb, *wtb, *h, *ht, *dzb, *dzt;
+        float *z, *dz;
+        ok = dalloc(&wb, (size_t)m->dout[l] * m->kpad[l]) && dalloc(&wtb, (size_t)m->din[l] * m->opad[l]) &&
+             dalloc(&z, (size_t)bp * m->dout[l]) && dalloc(&h, (size_t)bp * m->kpad[l]) &&
+             dalloc(&ht, (size_t)m->kpad[l] * bp) && dalloc(&dz, (size_t)bp * m->dout[l]) &&
+             dalloc(&dzb, (size_t)bp * m->opad[l]) && dalloc(&dzt, (size_t)m->dout[l] * bp);
+        m->Wb.push_back(ok ? wb : nullptr);
+        m->WTb.push_back(ok ? wtb : nullptr);
+        m->Z.push_back(ok ? z : nullptr);
+        m->H.push_back(ok ? h : nullptr);
+        m->HT.push_back(ok ? ht : nullptr);
+        m->dZ.push_back(ok ? dz : nullptr);
+        m->dZb.push_back(ok ? dzb : nullptr);
+        m->dZT.push_back(ok ? dzt : nullptr);
+    }
+    if (!ok) {
+        mlp_free(m);
+        return mfail(nullptr, LBIF_ERR_NOMEM, "lbif_mlp_create: device allocation failed");
+    }
+    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM_LAUNCH) != cudaSuccess) {
+        cudaGetLastError();
+        mlp_free(m);
+        return mfail(nullptr, LBIF_ERR_CUDA, "lbif_mlp_create: shared memory configuration failed");
+    }
+    *out = m;
+    return LBIF_OK;
+}
+
+extern "C" int lbif_mlp_destroy(lbif_mlp m)
+{
+    if (!m) return mfail(nullptr, LBIF_ERR_ARG, "lbif_mlp_destroy: NULL handle");
+    cudaStreamSynchronize(m->stream);
+    mlp_free(m);
+    return LBIF_OK;
+}
+
+extern "C" int64_t lbif_mlp_num_params(lbif_mlp m) { return m ? m->nparams : -1; }
+
+extern "C" const char* lbif_mlp_last_error(lbif_mlp m) { return m ? m->msg.c_str() : g_mlp_err.c_str(); }
+
+static int refresh_shadows(lbif_mlp_ctx* m)
+{
+    for (int l = 0; l < m->L; ++l) {
+        int n = m->dout[l] * m->kpad[l];
+        k_shadow<<<(n + 255) / 256, 256, 0, m->stream>>>(m->p + m->woff[l], m->dout[l], m->din[l], m->kpad[l],
+                                                         m->opad[l], m->Wb[l], m->WTb[l]);
+    }
+    MCK(m, cudaGetLastError());
+    return LBIF_OK;
+}
+
+extern "C" int lbif_mlp_set_params(lbif_mlp m, const float* params)
+{
+    if (!m || !params) return mfail(m, LBIF_ERR_ARG, "lbif_mlp_set_params: bad arguments");
+    MCK(m, cudaMemcpyAsync(m->p, params, sizeof(float) * m->nparams, cudaMemcpyHostToDevice, m->stream));
+    MCK(m, cudaMemsetAsync(m->m, 0, sizeof(float) * m->nparams, m->stream));
+    MCK(m, cudaMemsetAsync(m->v, 0, sizeof(float) * m->nparams, m->stream));
+    m->adam_t = 0;
+    int rc = refresh_shadows(m);
+    if (rc) return rc;
+    MCK(m, cudaStreamSynchronize(m->stream));
+    return LBIF_OK;
+}
+
+extern "C" int lbif_mlp_get_params(lbif_mlp m, float* params)
+{
+    if (!m || !params) return mfail(m, LBIF_ERR_ARG, "lbif_mlp_get_params: bad arguments");
+    MCK(m, cudaMemcpyAsync(params, m->p, sizeof(float) * m->nparams, cudaMemcpyDeviceToHost, m->stream));
+    MCK(m, cudaStreamSynchronize(m->stream));
+    return LBIF_OK;
+}
+
+static int gemm(lbif_mlp_ctx* m, const Gemm& g)
+{
+    if (g.N > 256 || g.K % 16) return mfail(m, LBIF_ERR_UNSUPPORTED, "gemm: N > 256 or K not a multiple of 16");
+    dim3 grid((g.M + 127) / 128);
+    k_gemm_tc<<<grid, 128, GEMM_SMEM_LAUNCH, m->stream>>>(g);
+    MCK(m, cudaGetLastError());
+    return LBIF_OK;
+}
+
+static Gemm blank(lbif_mlp_ctx* m)
+{
+    Gemm g;
+    memset(&g, 0, sizeof(g));
+    g.err = m->err;
+    return g;
+}
+
+// forward of `batch` rows already packed in H[0] / HT[0]
+static int forward(lbif_mlp_ctx* m, int batch)
+{
+    const int bp = up16(batch);
+    for (int l = 0; l < m->L; ++l) {
+        const bool last = l == m->L - 1;
+        Gemm g = blank(m);
+        g.A = m->H[l];
+        g.lda = m->kpad[l];
+        g.B = m->Wb[l];
+        g.ldb = m->kpad[l];
+        g.M = bp;
+        g.N = m->dout[l];
+        g.K = m->kpad[l];
+        g.bias = m->p + m->boff[l];
+        g.epi = last ? EPI_NONE : EPI_GELU;
+        g.Z = m->Z[l];
+        g.ldz = m->dout[l];
+        if (!last) {
+            g.H = m->H[l + 1];
+            g.ldh = m->kpad[l + 1];
+            g.HT = m->HT[l + 1];
+            g.ldht = bp;
+        }
+        int rc = gemm(m, g);
+        if (rc) return rc;
+    }
+    return LBIF_OK;
+}
+
+static int pack_input(lbif_mlp_ctx* m, const float* X, int batch, int on_device)
+{
+    const float* Xd = X;
+    if (!on_device) {
+        MCK(m, cudaMemcpyAsync(m->Xd, X, sizeof(float) * (size_t)batch * m->nin, cudaMemcpyHostToDevice, m->stream));
+        Xd = m->Xd;
+    }
+    const int bp = up16(batch);
+    int n = bp * m->kpad[0];
+    k_pack_input<<<(n + 255) / 256, 256, 0, m->stream>>>(Xd, batch, m->nin, bp, m->kpad[0], m->H[0], m->HT[0]);
+    MCK(m, cudaGetLastError());
+    return LBIF_OK;
+}
+
+static int check_err(lbif_mlp_ctx* m)
+{
+    int e = 0;
+    MCK(m, cudaMemcpyAsync(&e, m->err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    MCK(m, cudaStreamSynchronize(m->stream));
+    if (e) return mfail(m, LBIF_ERR_TIMEOUT, "tensor-core product did not complete within its wait limit");
+    return LBIF_OK;
+}
+
+extern "C" int lbif_mlp_forward(lbif_mlp m, const float* X, int32_t batch, float* Y, int32_t on_device)
+{
+    if (!m || !X || !Y || batch < 1 || batch > m->max_batch)
+        return mfail(m, LBIF_ERR_ARG, "lbif_mlp_forward: bad arguments");
+    int rc = pack_input(m, X, batch, on_device);
+    if (rc) return rc;
+    if ((rc = forward(m, batch))) return rc;
+    const float* Zl = m->Z[m->L - 1];
+    MCK(m, cudaMemcpyAsync(Y, Zl, sizeof(float) * (size_t)batch * m->nout,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+    return check_err(m);
+}
+
+// loss and gradients into m->g
+static int backward(lbif_mlp_ctx* m, const float* T, const float* mask, int batch, int on_device, double* loss)
+{
+    const int bp = up16(batch);
+    const int nout = m->nout;
+    const float *Td = T, *Md = mask;
+    if (!on_device) {
+        MCK(m, cudaMemcpyAsync(m->Td, T, sizeof(float) * (size_t)batch * nout, cudaMemcpyHostToDevice, m->stream));
+        MCK(m, cudaMemcpyAsync(m->Md, mask, sizeof(float) * (size_t)batch * nout, cudaMemcpyHostToDevice, m->stream));
+        Td = m->Td;
+        Md = m->Md;
+    }
+    const int L = m->L;
+    const int n = bp * nout;
+    const int nb = (n + 255) / 256;
+    k_msum<<<1, 256, 0, m->stream>>>(Md, (long long)batch * nout, m->msum);
+    k_loss<<<nb, 256, 0, m->stream>>>(m->Z[L - 1], Td, Md, batch, nout, m->opad[L - 1], bp, m->msum,
+                                      m->dZ[L - 1], m->dZb[L - 1], m->dZT[L - 1], m->partial);
+    MCK(m, cudaGetLastError());
+    for (int l = L - 1; l >= 0; --l) {
+        // dW_l = dZ_l^T . H_l  (M = dout, N = kpad_l, K = bp)
+        Gemm gw = blank(m);
+        gw.A = m->dZT[l];
+        gw.lda = bp;
+        gw.B = m->HT[l];
+        gw.ldb = bp;
+        gw.M = m->dout[l];
+        gw.N = m->kpad[l];
+        gw.K = bp;
+        gw.Z = m->dWtmp;
+        gw.ldz = m->kpad[l];
+        int rc = gemm(m, gw);
+        if (rc) return rc;
+        int cnt = m->dout[l] * m->din[l];
+        k_copy_cols<<<(cnt + 255) / 256, 256, 0, m->stream>>>(m->dWtmp, m->dout[l], m->kpad[l], m->din[l],
+                                                              m->g + m->woff[l]);
+        k_colsum<<<(m->dout[l] + 127) / 128, 128, 0, m->stream>>>(m->dZ[l], bp, m->dout[l], m->g + m->boff[l]);
+        MCK(m, cudaGetLastError());
+        if (l == 0) break;
+        // dZ_{l-1} = (dZ_l . W_l) * gelu'(Z_{l-1})  (M = bp, N = din_l, K = dout_l)
+        Gemm gd = blank(m);
+        gd.A = m->dZb[l];
+        gd.lda = m->opad[l];
+        gd.B = m->WTb[l];
+        gd.ldb = m->opad[l];
+        gd.M = bp;
+        gd.N = m->din[l];
+        gd.K = m->opad[l];
+        gd.epi = EPI_GELU_GRAD;
+        gd.zprev = m->Z[l - 1];
+        gd.Z = m->dZ[l - 1];
+        gd.ldz = m->dout[l - 1];
+        gd.H = m->dZb[l - 1];
+        gd.ldh = m->opad[l - 1];
+        gd.HT = m->dZT[l - 1];
+        gd.ldht = bp;
+        if ((rc = gemm(m, gd))) return rc;
+    }
+    std::vector<double> part(nb + 1);
+    MCK(m, cudaMemcpyAsync(part.data(), m->partial, sizeof(double) * nb, cudaMemcpyDeviceToHost, m->stream));
+    MCK(m, cudaMemcpyAsync(part.data() + nb, m->msum, sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+    int rc = check_err(m);
+    if (rc) return rc;
+    double s = 0.0;
+    for (int i = 0; i < nb; ++i) s += part[i];
+    if (loss) *loss = s / part[nb];
+    return LBIF_OK;
+}
+
+extern "C" int lbif_mlp_gradients(lbif_mlp m, const float* X, const float* T, const float* mask, int32_t batch,
+                                  float* grads, double* loss, int32_t on_device)
+{
+    if (!m || !X || !T || !mask || batch < 1 || batch > m->max_batch)
+        return mfail(m, LBIF_ERR_ARG, "lbif_mlp_gradients: bad arguments");
+    int rc = pack_input(m, X, batch, on_device);
+    if (rc) return rc;
+    if ((rc = forward(m, batch))) return rc;
+    if ((rc = backward(m, T, mask, batch, on_device, loss))) return rc;
+    if (grads) {
+        MCK(m, cudaMemcpyAsync(grads, m->g, sizeof(float) * m->nparams,
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+        MCK(m, cudaStreamSynchronize(m->stream));
+    }
+    return LBIF_OK;
+}
+
+extern "C" int lbif_mlp_train_step(lbif_mlp m, const float* X, const float* T, const float* mask, int32_t batch,
+                                   float lr, float beta1, float beta2, float eps, double* loss, int32_t on_device)
+{
+    if (!m || !X || !T || !mask || batch < 1 || batch > m->max_batch || !(lr >= 0))
+        return mfail(m, LBIF_ERR_ARG, "lbif_mlp_train_step: bad arguments");
+    int rc = pack_input(m, X, batch, on_device);
+    if (rc) return rc;
+    if ((rc = forward(m, batch))) return rc;
+    if ((rc = backward(m, T, mask, batch, on_device, loss))) return rc;
+    m->adam_t += 1;
+    const float c1 = (float)(1.0 - pow((double)beta1, (double)m->adam_t));
+    const float c2 = (float)(1.0 - pow((double)beta2, (double)m->adam_t));
+    k_adam<<<(unsigned)((m->nparams + 255) / 256), 256, 0, m->stream>>>(m->p, m->g, m->m, m->v, m->nparams, lr,
+                                                                         beta1, beta2, eps, c1, c2);
+    MCK(m, cudaGetLastError());
+    if ((rc = refresh_shadows(m))) return rc;
+    return LBIF_OK;
+}

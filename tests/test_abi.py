@@ -99,3 +99,26 @@ def test_oracle_builds_and_is_independent():
         if f.endswith((".c", ".py")):
             assert "paper_0712_2247_gb300" not in open(f).read().replace(
                 "paper_0712_2247_gb300.inputs", ""), f
+
+
+@pytest.mark.parametrize("args", [
+    (0, 256, 3, 160, 16), (4, 8, 3, 160, 16), (4, 264, 3, 160, 16), (4, 250, 3, 160, 16),
+    (4, 256, 0, 160, 16), (4, 256, 3, 0, 16), (4, 256, 3, 257, 16), (4, 256, 3, 160, 0),
+])
+def test_mlp_create_rejects_bad_widths(lib, args):
+    from paper_0712_2247_gb300 import mlp
+
+    mlp.load_library()
+    h = ctypes.c_void_p()
+    assert lib.lbif_mlp_create(ctypes.byref(h), *args, None) == -1
+    assert not h.value
+    assert b"lbif_mlp_create" in lib.lbif_mlp_last_error(None)
+
+
+def test_mlp_null_handle(lib):
+    from paper_0712_2247_gb300 import mlp
+
+    mlp.load_library()
+    assert lib.lbif_mlp_num_params(None) == -1
+    assert lib.lbif_mlp_destroy(None) == -1
+    assert lib.lbif_mlp_forward(None, None, 1, None, 0) == -1
