@@ -355,10 +355,15 @@ __host__ __device__ constexpr int cisqrt(int n)
 
 constexpr int BALL_TX = 32, BALL_TY = 8, BALL_THREADS = 256;
 
+// x halo of the staged plane tile: R rounded up to 4, so that tile rows and
+// their global sources are float4-aligned
+template <int R>
+constexpr int ball_c4() { return (R + 3) / 4 * 4; }
+
 template <int R>
 constexpr int ball_smem_floats()
 {
-    return (BALL_TY + 2 * R) * (BALL_TX + 2 * R) + (R + 1) * (BALL_TY + 2 * R) * BALL_TX;
+    return (BALL_TY + 2 * R) * (BALL_TX + 2 * ball_c4<R>()) + (R + 1) * (BALL_TY + 2 * R) * BALL_TX;
 }
 
 // One CTA = a 32 x 8 column of nodes marching up a z chunk. Per input plane:
@@ -371,9 +376,11 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
                                               int skip_done)
 {
     constexpr int TX = BALL_TX, TY = BALL_TY;
-    constexpr int W = TX + 2 * R, H = TY + 2 * R;
-    extern __shared__ float sm[];
-    float* T = sm;           // H x W plane tile
+    constexpr int C4 = ball_c4<R>();
+    constexpr int W = TX + 2 * C4, H = TY + 2 * R;
+    constexpr int NF = (C4 + R + 7) / 4;  // float4s a 4-column row-sum group reads
+    extern __shared__ __align__(16) float sm[];
+    float* T = sm;           // H x W plane tile, column C4 + c holds node column c
     float* RS = sm + H * W;  // (R+1) x H x TX row sums
     const Geom& g = P.g;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -388,21 +395,41 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
 
     for (int zi = z0 - R; zi < z1 + R; ++zi) {
         const float* plane = dn + (long long)(zi + g.hw) * g.py * g.px;
-        for (int k = threadIdx.x; k < H * W; k += blockDim.x) {
-            int row = k / W, col = k - row * W;
-            int xp = x0 - R + col + g.hw, yp = y0 - R + row + g.hw;
-            T[k] = (xp < g.px && yp < g.py) ? __ldg(plane + (long long)yp * g.px + xp) : 0.f;
+        // stage the plane tile with float4 copies (padded rows are 16-byte
+        // aligned and hw >= C4, so every source float4 lies inside its row or
+        // entirely past its end)
+        for (int k = threadIdx.x; k < H * (W / 4); k += blockDim.x) {
+            int row = k / (W / 4), q = k - row * (W / 4);
+            int xp = x0 - C4 + g.hw + 4 * q, yp = y0 - R + row + g.hw;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (xp + 3 < g.px && yp < g.py) v = ld4(plane + (long long)yp * g.px + xp);
+            *reinterpret_cast<float4*>(T + row * W + 4 * q) = v;
         }
         __syncthreads();
-        for (int k = threadIdx.x; k < H * TX; k += blockDim.x) {
-            int row = k / TX, c = k - row * TX;
-            const float* tr = T + row * W + c + R;
-            float s = tr[0];
-            RS[row * TX + c] = s;
+        // row sums of every half-width 0..R for four adjacent columns per
+        // thread: the window sits in registers, additions grow outwards from
+        // the centre column
+        for (int k = threadIdx.x; k < H * (TX / 4); k += blockDim.x) {
+            int row = k / (TX / 4), c = 4 * (k - row * (TX / 4));
+            const float* tr = T + row * W + c;
+            float t[4 * NF];
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                float4 v = *reinterpret_cast<const float4*>(tr + 4 * i);
+                t[4 * i] = v.x;
+                t[4 * i + 1] = v.y;
+                t[4 * i + 2] = v.z;
+                t[4 * i + 3] = v.w;
+            }
+            float s[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[j] = t[C4 + j];
+            *reinterpret_cast<float4*>(RS + row * TX + c) = make_float4(s[0], s[1], s[2], s[3]);
 #pragma unroll
             for (int w = 1; w <= R; ++w) {
-                s += tr[-w] + tr[w];
-                RS[(w * H + row) * TX + c] = s;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) s[j] += t[C4 + j - w] + t[C4 + j + w];
+                *reinterpret_cast<float4*>(RS + (w * H + row) * TX + c) = make_float4(s[0], s[1], s[2], s[3]);
             }
         }
         __syncthreads();
@@ -821,8 +848,11 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
     }
 }
 
+// At most 128 registers, so that four CTAs (16 warps) share an SM: the
+// kernel waits on L1 far more than it computes, and the extra warps hide
+// that latency (measured: 146 registers / 3 CTAs per SM is 6 % slower).
 template <int SIG>
-__global__ void __launch_bounds__(128) k_force4(Params P, TileMap tm, Fields fl,
+__global__ void __launch_bounds__(128, 4) k_force4(Params P, TileMap tm, Fields fl,
                                                 const float4* __restrict__ Ft, float4* __restrict__ F)
 {
     const Geom& g = P.g;
