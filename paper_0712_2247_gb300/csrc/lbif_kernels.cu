@@ -8,6 +8,8 @@
 // force. FP64 appears only in the profile / mass reductions.
 #include <string.h>
 
+#include <utility>
+
 #include "lbif_internal.h"
 
 namespace lbif {
@@ -353,7 +355,11 @@ __host__ __device__ constexpr int cisqrt(int n)
     return w;
 }
 
-constexpr int BALL_TX = 32, BALL_TY = 8, BALL_THREADS = 256;
+// tile of the z-marching ball kernel: 32 x 16 nodes, 256 threads, each
+// thread a column of BALL_YT = 2 nodes in y (measured at sigma = 12 on a
+// 512 x 512 x 192 slit: 1 node per thread 0.86 ms, 2 nodes 0.72 ms, 4 nodes
+// 0.90 ms, each with its best CTA count)
+constexpr int BALL_TX = 32, BALL_YT = 2, BALL_TY = 8 * BALL_YT, BALL_THREADS = 256;
 
 // x halo of the staged plane tile: R rounded up to 4, so that tile rows and
 // their global sources are float4-aligned
@@ -366,10 +372,65 @@ constexpr int ball_smem_floats()
     return (BALL_TY + 2 * R) * (BALL_TX + 2 * ball_c4<R>()) + (R + 1) * (BALL_TY + 2 * R) * BALL_TX;
 }
 
-// One CTA = a 32 x 8 column of nodes marching up a z chunk. Per input plane:
+// does tile row r (relative to a thread's first node row minus R) enter a
+// disc sum D_k of any of the thread's BALL_YT nodes with row half-width w?
+__host__ __device__ constexpr bool ball_row_used(int R, int r, int w)
+{
+    for (int j = 0; j < BALL_YT; ++j) {
+        const int dy = r - R - j;
+        if (dy < -R || dy > R) continue;
+        for (int k = 0; k <= R; ++k) {
+            const int rem = R * R - k * k - dy * dy;
+            if (rem >= 0 && cisqrt(rem) == w) return true;
+        }
+    }
+    return false;
+}
+
+// Compile-time expansion of the disc sums of one thread: for every tile row r
+// (in increasing order) and half-width w that some D[k][i] uses, one shared
+// memory read, added into exactly those D[k][i].
+template <int R, int r, int w, int M>
+__device__ __forceinline__ void ball_add_one(float v, float (&D)[R + 1][BALL_YT])
+{
+    constexpr int i = M / (R + 1), k = M % (R + 1);
+    constexpr int dy = r - R - i;
+    constexpr int rem = R * R - k * k - dy * dy;
+    if constexpr (dy >= -R && dy <= R && rem >= 0 && cisqrt(rem) == w) D[k][i] += v;
+}
+
+template <int R, int r, int w, int... M>
+__device__ __forceinline__ void ball_add_row(float v, float (&D)[R + 1][BALL_YT],
+                                             std::integer_sequence<int, M...>)
+{
+    (ball_add_one<R, r, w, M>(v, D), ...);
+}
+
+template <int R, int N>
+__device__ __forceinline__ void ball_disc_row(const float* __restrict__ RS, int off, float (&D)[R + 1][BALL_YT])
+{
+    constexpr int r = N / (R + 1), w = N % (R + 1);
+    constexpr int H = BALL_TY + 2 * R;
+    if constexpr (ball_row_used(R, r, w)) {
+        const float v = RS[(w * H + r) * BALL_TX + off];
+        ball_add_row<R, r, w>(v, D, std::make_integer_sequence<int, BALL_YT * (R + 1)>{});
+    }
+}
+
+// the comma fold runs the rows in increasing order
+template <int R, int... N>
+__device__ __forceinline__ void ball_disc_rows(const float* __restrict__ RS, int off, float (&D)[R + 1][BALL_YT],
+                                               std::integer_sequence<int, N...>)
+{
+    (ball_disc_row<R, N>(RS, off, D), ...);
+}
+
+// One CTA = a 32 x 16 column of nodes marching up a z chunk. Per input plane:
 // stage the plane (+R halo) in shared memory, build x-row sums of every
-// half-width 0..R, add the disc sums D_k (disc of radius^2 R^2 - k^2) into a
-// register ring of the 2R+1 output planes it touches, emit the completed one.
+// half-width 0..R, form the disc sums D_k (disc of radius^2 R^2 - k^2; a
+// thread reads each row sum it needs once for its two nodes in y) and add
+// them into a register ring of the 2R+1 output planes they touch, emit the
+// completed plane.
 template <int R>
 __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __restrict__ dn,
                                               float* __restrict__ dG, int* status, int zchunk,
@@ -386,12 +447,14 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * zchunk;
     const int z1 = min(z0 + zchunk, g.nz);
-    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool active = x < g.nx && y < g.ny;
-    float acc[2 * R + 1];
+    constexpr int YT = BALL_YT;
+    const int tx = threadIdx.x % TX, ty0 = (threadIdx.x / TX) * YT;
+    const int x = x0 + tx;
+    float acc[2 * R + 1][YT];
 #pragma unroll
-    for (int j = 0; j <= 2 * R; ++j) acc[j] = 0.f;
+    for (int j = 0; j <= 2 * R; ++j)
+#pragma unroll
+        for (int i = 0; i < YT; ++i) acc[j][i] = 0.f;
 
     for (int zi = z0 - R; zi < z1 + R; ++zi) {
         const float* plane = dn + (long long)(zi + g.hw) * g.py * g.px;
@@ -433,28 +496,41 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
             }
         }
         __syncthreads();
+        // D[k][i] = sum over dy = -R..R (in that order) of the row sum of
+        // half-width cisqrt(R^2 - k^2 - dy^2) at row ty0 + i + dy
+        float D[R + 1][YT];
 #pragma unroll
-        for (int k = 0; k <= R; ++k) {
-            float D = 0.f;
+        for (int k = 0; k <= R; ++k)
 #pragma unroll
-            for (int dy = -R; dy <= R; ++dy) {
-                const int rem = R * R - k * k - dy * dy;
-                if (rem >= 0) D += RS[(cisqrt(rem) * H + ty + R + dy) * TX + tx];
+            for (int i = 0; i < YT; ++i) D[k][i] = 0.f;
+        ball_disc_rows<R>(RS, ty0 * TX + tx, D, std::make_integer_sequence<int, (YT + 2 * R) * (R + 1)>{});
+#pragma unroll
+        for (int k = 0; k <= R; ++k)
+#pragma unroll
+            for (int i = 0; i < YT; ++i) {
+                acc[R - k][i] += D[k][i];
+                if (k) acc[R + k][i] += D[k][i];
             }
-            acc[R - k] += D;
-            if (k) acc[R + k] += D;
-        }
         const int zo = zi - R;
         const int so = zo >= z0 ? slit_of(P, zo) : -1;
-        if (so >= 0 && active && !(skip_done && frozen(P, so))) {
-            bool bad;
-            float v = g2_deviation(P, P.sl[so].eta0, acc[0] * P.ball_inv, bad);
-            if (bad) atomicOr(status, 2);
-            for_images(g, x, y, zo, [&](int q) { dG[q] = v; });
+        if (so >= 0 && x < g.nx && !(skip_done && frozen(P, so))) {
+            const float e0 = P.sl[so].eta0;
+#pragma unroll
+            for (int i = 0; i < YT; ++i) {
+                const int y = y0 + ty0 + i;
+                if (y >= g.ny) break;
+                bool bad;
+                float v = g2_deviation(P, e0, acc[0][i] * P.ball_inv, bad);
+                if (bad) atomicOr(status, 2);
+                for_images(g, x, y, zo, [&](int q) { dG[q] = v; });
+            }
         }
 #pragma unroll
-        for (int j = 0; j < 2 * R; ++j) acc[j] = acc[j + 1];
-        acc[2 * R] = 0.f;
+        for (int j = 0; j < 2 * R; ++j)
+#pragma unroll
+            for (int i = 0; i < YT; ++i) acc[j][i] = acc[j + 1][i];
+#pragma unroll
+        for (int i = 0; i < YT; ++i) acc[2 * R][i] = 0.f;
         __syncthreads();
     }
 }
@@ -1192,7 +1268,7 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
         configured = true;
     }
     int gx = (g.nx + BALL_TX - 1) / BALL_TX, gy = (g.ny + BALL_TY - 1) / BALL_TY;
-    if (want <= 0) want = 1216;  // ~8 CTAs per SM on 152 SMs
+    if (want <= 0) want = 608;  // ~4 CTAs per SM on 152 SMs
     int nchunk = (want + gx * gy - 1) / (gx * gy);
     int maxchunk = g.nz / (2 * R) > 1 ? g.nz / (2 * R) : 1;
     if (nchunk > maxchunk) nchunk = maxchunk;

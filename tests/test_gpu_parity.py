@@ -304,7 +304,7 @@ def test_thin_and_degenerate_grids(L, O):
         assert nerr(rg, ro) < 1e-5, shape
 
 
-@pytest.mark.parametrize("sigma,wide", [(4, (128, 8)), (6, (32, 8)), (12, (128, 8))])
+@pytest.mark.parametrize("sigma,wide", [(4, (128, 16)), (6, (32, 16)), (12, (128, 32))])
 def test_narrow_grid_kernels_bit_identical_to_tiled(L, sigma, wide):
     """x,y-uniform slits: the thin-grid kernels (flat force mapping, direct
     ball sums) give exactly the per-node values of the tiled kernels."""
