@@ -108,6 +108,14 @@ def kernel_bytes(storage: int):
             "collide_stream": 2 * 19 * s + 36}
 
 
+# DRAM bytes per node (dram__bytes_read.sum + dram__bytes_write.sum) of each
+# step kernel, FP32 storage, from one ncu --set full capture of the
+# 256x256x192 sigma = 12 slit of the current kernels; a full-size launch moves
+# these bytes times its node count (traffic grows with the nodes). Must be
+# re-measured whenever a kernel changes.
+TRAFFIC_B_PER_NODE_F32 = {"moments": 98.1, "ball_g2": 6.3, "force": 45.7, "collide_stream": 183.8}
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -141,6 +149,51 @@ def cpu_sample(steps_hint: float = 15.0):
     return {"value": nodes * k / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, {nx}x{ny}x{W.nz} slit of the same sigma/eta/tau/F_e, "
                       f"{k} steps after 1 untimed, {dt:.1f} s"}, dt, k, nodes
+
+
+def warm_start_leg(args):
+    """Time to steady state, warm vs cold (reduced form of the learned warm
+    start study): steady profiles of thin slits drawn from the ensemble
+    distribution (training set, seed 4), the network trained on the tensor
+    cores, then held-out 32x32xH slits (seed 5) run to the FP64 residual
+    1e-8 from a cold uniform start and from the network's prediction."""
+    import numpy as np
+    import torch
+
+    from paper_0712_2247_gb300 import inputs
+    from paper_0712_2247_gb300 import surrogate as S
+    from paper_0712_2247_gb300.mlp import MLP
+
+    ptr = inputs.ensemble(args.ws_train, seed=4, nx=4, ny=4)
+    n_z, ux_z, steps, res, gen_wall = S.steady_profiles(ptr)
+    use = np.nonzero(steps != -2)[0]
+    raw = S.raw_features(ptr.H, ptr.eta, ptr.F, ptr.tau, ptr.sigma)
+    sc = S.Scaling.fit(raw[use])
+    T, M = S.encode(n_z, ux_z, ptr)
+    batch = 512
+    net = MLP(S.NFEAT, 256, 3, 2 * S.HMAX, max_batch=1024, seed=4)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = S.train(net, sc(raw[use]), T[use], M[use], steps=args.ws_adam, batch=batch)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # tensor-core work of one training step: forward and two backward products per layer
+    flops = 3 * 2 * batch * sum(o * i for o, i in net.shapes)
+    phe = inputs.ensemble(args.ws_heldout, seed=5)
+    r = S.warm_vs_cold(net, sc, phe, 32, 32)
+    net.close()
+    return {
+        "workload": f"train {args.ws_train} thin 4x4xH slits (H in [8,80], eta in [0.10,0.25], "
+                    f"F log-uniform [1e-7,1e-5], tau in [0.6,1.2]); evaluate {args.ws_heldout} held-out "
+                    f"32x32xH slits to residual 1e-8 (FP32)",
+        "generation_s": gen_wall, "train_s": train_s, "adam_steps": args.ws_adam, "batch": batch,
+        "loss_first": float(losses[0]), "loss_last": float(losses[-50:].mean()),
+        "train_step_tflops": flops * args.ws_adam / train_s / 1e12,
+        "cold_s": r["cold"]["wall_s"], "warm_s": r["warm"]["wall_s"], "wall_speedup": r["wall_speedup"],
+        "steps_mean_cold": r["cold"]["steps_mean"], "steps_mean_warm": r["warm"]["steps_mean"],
+        "floored_cold": r["cold"]["not_converged"], "floored_warm": r["warm"]["not_converged"],
+        "final_profile_diff": r["final_profile_diff"], "prediction_error": r["prediction_error"],
+    }
 
 
 def run_reference(args, world, rank):
@@ -250,6 +303,12 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, _, _, _ = cpu_sample(args.cpu_seconds)
+    warm = None
+    if not args.no_warm_start and world == 1:
+        try:
+            warm = warm_start_leg(args)
+        except Exception as e:  # reported, never hides the throughput line
+            warm = {"error": f"{type(e).__name__}: {e}"}
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -265,8 +324,12 @@ def run_ours(args, world, rank, local):
                    "status": status},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind + " hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "bytes_alg_per_launch": dom_bytes},
+                     "traffic": (TRAFFIC_B_PER_NODE_F32[dom] * N
+                                 if storage == 0 and dom in TRAFFIC_B_PER_NODE_F32 else None),
+                     "traffic_unit": "bytes per launch (ncu capture, scaled by nodes)",
+                     "bytes_alg_per_launch": dom_bytes},
         "cpu_baseline": cpu,
+        "warm_start": warm,
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk.summary(),
@@ -285,6 +348,10 @@ def main():
     ap.add_argument("--eta", type=float, default=0.25)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true", help="skip the warm vs cold study")
+    ap.add_argument("--ws-train", type=int, default=4096, help="training slits of the warm-start leg")
+    ap.add_argument("--ws-adam", type=int, default=3000, help="Adam steps of the warm-start leg")
+    ap.add_argument("--ws-heldout", type=int, default=128, help="held-out slits of the warm-start leg")
     ap.add_argument("--grid", default=None,
                     help="override the slit extents NXxNYxNZ (profiling captures on a smaller case)")
     args = ap.parse_args()
