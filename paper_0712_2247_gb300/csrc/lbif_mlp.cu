@@ -144,84 +144,132 @@ struct Gemm {
     int* err;
 };
 
-constexpr int GEMM_KC = 64;   // K staged per round
-constexpr int GEMM_SMEM = 128 * GEMM_KC * 2 + 256 * GEMM_KC * 2 + 64;
-// dynamic shared memory requested at launch: large enough that at most two
-// CTAs share an SM, so their two 256-column accumulators always fit in the
-// 512 TMEM columns and no allocation ever waits on another CTA
-constexpr int GEMM_SMEM_LAUNCH = 100 * 1024;
+constexpr int GEMM_KC = 64;  // K staged per round
 constexpr long long WAIT_LIMIT = 1LL << 22;  // try_wait polls; seconds at most
 
-__global__ void __launch_bounds__(128) k_gemm_tc(Gemm g)
+// shared memory of one CTA: two stages of A (128 x 64) and B (ntile x 64)
+// bf16 tiles, then two mbarriers and the TMEM address slot
+__host__ __device__ inline int gemm_stage_bytes(int ntile) { return (128 + ntile) * GEMM_KC * 2; }
+__host__ __device__ inline int gemm_smem_bytes(int ntile) { return 2 * gemm_stage_bytes(ntile) + 32; }
+__host__ __device__ inline uint32_t tmem_cols(int ntile)
+{
+    uint32_t c = 32;
+    while (c < (uint32_t)ntile) c <<= 1;
+    return c;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Issue the copies of K round k0 into a stage: A rows m0.., B rows n0.., as
+// 8-row x 16-byte core matrices (K-major, no swizzle); rows past M / N read zero.
+__device__ __forceinline__ void gemm_stage(const Gemm& g, uint8_t* sA, uint8_t* sB, int m0, int n0, int NT, int k0)
+{
+    const int kc = min(GEMM_KC, g.K - k0);  // multiple of 16
+    const int kcore = kc / 8;
+    for (int t = threadIdx.x; t < 128 * kcore; t += blockDim.x) {
+        const int r = t / kcore, kp = t - r * kcore;
+        const bool ok = m0 + r < g.M;
+        const bf16* src = g.A + (size_t)(ok ? m0 + r : 0) * g.lda + k0 + kp * 8;
+        cp_async16(sA + ((r >> 3) * kcore + kp) * 128 + (r & 7) * 16, src, ok);
+    }
+    for (int t = threadIdx.x; t < NT * kcore; t += blockDim.x) {
+        const int r = t / kcore, kp = t - r * kcore;
+        const bool ok = n0 + r < g.N;
+        const bf16* src = g.B + (size_t)(ok ? n0 + r : 0) * g.ldb + k0 + kp * 8;
+        cp_async16(sB + ((r >> 3) * kcore + kp) * 128 + (r & 7) * 16, src, ok);
+    }
+    cp_async_commit();
+}
+
+// Bounded wait of every thread on an mbarrier phase; one verdict per CTA.
+__device__ __forceinline__ bool cta_wait(uint64_t* mbar, uint32_t parity)
+{
+    long long spins = 0;
+    bool ok;
+    while (!(ok = mbar_try_wait(mbar, parity)) && ++spins < WAIT_LIMIT) {
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// One CTA: a 128-row block (blockIdx.x) x an ntile-column block (blockIdx.y)
+// of C, accumulated in TMEM over K in rounds of 64; the copies of round k+1
+// are in flight while the tensor core works on round k.
+__global__ void __launch_bounds__(128) k_gemm_tc(Gemm g, int ntile)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sA = smem;
-    uint8_t* sB = smem + 128 * GEMM_KC * 2;
-    uint64_t* mbar = (uint64_t*)(sB + 256 * GEMM_KC * 2);
-    uint32_t* tslot = (uint32_t*)(mbar + 1);
-    const int m0 = blockIdx.x * 128;
-    const int NT = (g.N + 15) / 16 * 16;  // <= 256
+    const int SB = gemm_stage_bytes(ntile);
+    uint64_t* mbar = (uint64_t*)(smem + 2 * SB);
+    uint32_t* tslot = (uint32_t*)(mbar + 2);
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * ntile;
+    const int NT = min(ntile, (g.N - n0 + 15) / 16 * 16);
+    const uint32_t cols = tmem_cols(ntile);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
     if (warp == 0) {
-        tmem_alloc(tslot, 256);
+        tmem_alloc(tslot, cols);
         tmem_relinquish();
     }
-    if (threadIdx.x == 0) mbar_init(mbar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(mbar, 1);
+        mbar_init(mbar + 1, 1);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
     const uint32_t idesc = idesc_bf16(128, NT);
-    uint32_t phase = 0;
-    int timed_out = 0;
+    uint32_t parity[2] = {0u, 0u};
+    bool ok = true;
+    const int nk = (g.K + GEMM_KC - 1) / GEMM_KC;
 
-    for (int k0 = 0; k0 < g.K; k0 += GEMM_KC) {
-        const int kc = min(GEMM_KC, g.K - k0);  // multiple of 16
-        const int kcore = kc / 8;                // core matrices along K
-        // stage A (128 x kc) and B (NT x kc) as 8x16-byte core matrices
-        for (int t = threadIdx.x; t < 128 * kcore; t += 128) {
-            const int r = t / kcore, kp = t - r * kcore;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (m0 + r < g.M) v = *reinterpret_cast<const uint4*>(g.A + (size_t)(m0 + r) * g.lda + k0 + kp * 8);
-            *reinterpret_cast<uint4*>(sA + ((r >> 3) * kcore + kp) * 128 + (r & 7) * 16) = v;
+    gemm_stage(g, smem, smem + 128 * GEMM_KC * 2, m0, n0, NT, 0);
+    for (int k = 0; k < nk && ok; ++k) {
+        const int st = k & 1;
+        uint8_t* sA = smem + st * SB;
+        uint8_t* sB = sA + 128 * GEMM_KC * 2;
+        if (k + 1 < nk) {
+            // the other stage was read by the products of round k - 1
+            if (k >= 1) {
+                ok = cta_wait(mbar + (st ^ 1), parity[st ^ 1]);
+                parity[st ^ 1] ^= 1u;
+                if (!ok) break;
+            }
+            uint8_t* oA = smem + (st ^ 1) * SB;
+            gemm_stage(g, oA, oA + 128 * GEMM_KC * 2, m0, n0, NT, (k + 1) * GEMM_KC);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
-        for (int t = threadIdx.x; t < NT * kcore; t += 128) {
-            const int r = t / kcore, kp = t - r * kcore;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (r < g.N) v = *reinterpret_cast<const uint4*>(g.B + (size_t)r * g.ldb + k0 + kp * 8);
-            *reinterpret_cast<uint4*>(sB + ((r >> 3) * kcore + kp) * 128 + (r & 7) * 16) = v;
-        }
-        fence_proxy_async();  // generic-proxy stores -> visible to the tensor core
+        fence_proxy_async();  // copies of round k -> visible to the tensor core
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
         if (threadIdx.x == 0) {
+            const int kc = min(GEMM_KC, g.K - k * GEMM_KC);
+            const uint32_t sbo = (kc / 8) * 128;
             const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-            const uint32_t sbo = kcore * 128;
-            for (int kk = 0; kk < kc / 16; ++kk) {
-                const uint64_t ad = smem_desc(a0 + kk * 256, 128, sbo);
-                const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
-                mma_bf16(tmem, ad, bd, idesc, (k0 > 0 || kk > 0) ? 1u : 0u);
-            }
-            mma_commit(mbar);
+            for (int kk = 0; kk < kc / 16; ++kk)
+                mma_bf16(tmem, smem_desc(a0 + kk * 256, 128, sbo), smem_desc(b0 + kk * 256, 128, sbo), idesc,
+                         (k > 0 || kk > 0) ? 1u : 0u);
+            mma_commit(mbar + st);
         }
-        // bounded wait for the products of this round before the stage is reused
-        long long spins = 0;
-        int to = 0;
-        while (!mbar_try_wait(mbar, phase)) {
-            if (++spins > WAIT_LIMIT) {
-                to = 1;
-                break;
-            }
-        }
-        phase ^= 1u;
-        timed_out = __syncthreads_or(to);
+    }
+    // the last round's products (and, with one round only, the only ones)
+    if (ok) {
+        const int st = (nk - 1) & 1;
+        ok = cta_wait(mbar + st, parity[st]);
         tc_fence_after();
-        if (timed_out) break;
     }
 
-    if (!timed_out) {
+    if (ok) {
         const int row = m0 + 32 * warp + lane;
         for (int c = 0; c < NT; c += 16) {
             float v[16];
@@ -229,7 +277,7 @@ __global__ void __launch_bounds__(128) k_gemm_tc(Gemm g)
             if (row < g.M) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int n = c + j;
+                    const int n = n0 + c + j;
                     if (n >= g.N) break;
                     float z = v[j] + (g.bias ? g.bias[n] : 0.f);
                     float h = z;
@@ -249,9 +297,10 @@ __global__ void __launch_bounds__(128) k_gemm_tc(Gemm g)
     } else if (threadIdx.x == 0) {
         atomicExch(g.err, 1);
     }
+    cp_async_wait<0>();
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, cols);
 }
 
 // ---------------------------------------------------------------------------
@@ -491,7 +540,7 @@ extern "C" int lbif_mlp_create(lbif_mlp* out, int32_t nin, int32_t hidden, int32
         mlp_free(m);
         return mfail(nullptr, LBIF_ERR_NOMEM, "lbif_mlp_create: device allocation failed");
     }
-    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM_LAUNCH) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, gemm_smem_bytes(256)) != cudaSuccess) {
         cudaGetLastError();
         mlp_free(m);
         return mfail(nullptr, LBIF_ERR_CUDA, "lbif_mlp_create: shared memory configuration failed");
@@ -544,11 +593,21 @@ extern "C" int lbif_mlp_get_params(lbif_mlp m, float* params)
     return LBIF_OK;
 }
 
+// Column block of a product: the whole N (<= 256) when there are enough row
+// blocks to fill the GPU, else blocks of 64 columns for more CTAs.
 static int gemm(lbif_mlp_ctx* m, const Gemm& g)
 {
-    if (g.N > 256 || g.K % 16) return mfail(m, LBIF_ERR_UNSUPPORTED, "gemm: N > 256 or K not a multiple of 16");
-    dim3 grid((g.M + 127) / 128);
-    k_gemm_tc<<<grid, 128, GEMM_SMEM_LAUNCH, m->stream>>>(g);
+    if (g.N > 256 || g.K % 16 || g.K < 16)
+        return mfail(m, LBIF_ERR_UNSUPPORTED, "gemm: N > 256 or K not a positive multiple of 16");
+    const int mt = (g.M + 127) / 128;
+    const int nfull = (g.N + 15) / 16 * 16;
+    const int ntile = (mt >= 64 || nfull <= 64) ? nfull : 64;
+    dim3 grid(mt, (g.N + ntile - 1) / ntile);
+    // shared memory per CTA bounds the CTAs per SM so that their TMEM
+    // columns (32..256 each) always fit in the SM's 512 together
+    int smem = gemm_smem_bytes(ntile);
+    if (tmem_cols(ntile) == 256 && smem < 80 * 1024) smem = 80 * 1024;
+    k_gemm_tc<<<grid, 128, smem, m->stream>>>(g, ntile);
     MCK(m, cudaGetLastError());
     return LBIF_OK;
 }
