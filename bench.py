@@ -196,6 +196,35 @@ def warm_start_leg(args):
     }
 
 
+def ensemble_leg(args):
+    """Throughput of the batched ensemble: 256 slits of 32x32xH (H in
+    [8, 80], eta in [0.10, 0.25], F log-uniform in [1e-7, 1e-5], tau in
+    [0.6, 1.2], SplitMix64 seed 3), FP16 population storage, advanced by the
+    CUDA-graph runner (graphs of 100 steps, FP64 residual check after each)
+    after the autotuner has picked the launch shapes. The tolerance is set
+    below reach, so every slit runs all steps."""
+    import numpy as np
+    import torch
+
+    from paper_0712_2247_gb300 import inputs, lbif
+
+    p = inputs.ensemble(256, seed=3)
+    e = lbif.Ensemble(p.H, p.eta, p.F, p.tau, p.sigma, p.nx, p.ny, storage=lbif.STORE_F16, seed=3)
+    ball, group = e.autotune(trials=3)
+    e.run(tol=1e-300, max_steps=200, check_every=100)  # builds the graph
+    steps = args.ens_steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e.run(tol=1e-300, max_steps=steps, check_every=100)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    fluid = int(np.sum(p.H)) * p.nx * p.ny
+    e.close()
+    return {"workload": "256 slits 32x32xH, sigma=4, FP16 storage, graph-captured steps",
+            "fluid_nodes": fluid, "stacked_nodes": e.N, "steps": steps, "seconds": dt,
+            "mlups_fluid": fluid * steps / dt / 1e6, "autotuned": {"ball_ctas": ball, "force_group": group}}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -303,6 +332,12 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, _, _, _ = cpu_sample(args.cpu_seconds)
+    ens = None
+    if not args.no_ensemble and world == 1:
+        try:
+            ens = ensemble_leg(args)
+        except Exception as e:
+            ens = {"error": f"{type(e).__name__}: {e}"}
     warm = None
     if not args.no_warm_start and world == 1:
         try:
@@ -329,6 +364,7 @@ def run_ours(args, world, rank, local):
                      "traffic_unit": "bytes per launch (ncu capture, scaled by nodes)",
                      "bytes_alg_per_launch": dom_bytes},
         "cpu_baseline": cpu,
+        "ensemble": ens,
         "warm_start": warm,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -349,6 +385,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the warm vs cold study")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble throughput")
+    ap.add_argument("--ens-steps", type=int, default=2000, help="timed steps of the ensemble leg")
     ap.add_argument("--ws-train", type=int, default=4096, help="training slits of the warm-start leg")
     ap.add_argument("--ws-adam", type=int, default=3000, help="Adam steps of the warm-start leg")
     ap.add_argument("--ws-heldout", type=int, default=128, help="held-out slits of the warm-start leg")

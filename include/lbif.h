@@ -189,7 +189,13 @@ int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* fo
  * runs to convergence. Products run on the tensor cores with bfloat16
  * operands and FP32 accumulation; master weights, Adam moments and all
  * element-wise work are FP32. Parameters are one flat FP32 vector: for each
- * layer W (out x in, row-major) then b (out). Widths <= 256. */
+ * layer W (out x in, row-major) then b (out). Widths <= 256. The paper has no
+ * counterpart: the network is an added way to choose the starting state.
+ * Errors: LBIF_ERR_ARG for bad widths, sizes or NULL pointers (checked before
+ * any device work), LBIF_ERR_NOMEM, LBIF_ERR_CUDA, LBIF_ERR_UNSUPPORTED for a
+ * product outside the kernel's shapes, LBIF_ERR_TIMEOUT when a bounded wait of
+ * the tensor-core kernel ran out. The handle owns its device memory; arrays
+ * passed in stay the caller's. All calls run on the handle's stream. */
 typedef struct lbif_mlp_ctx* lbif_mlp;
 
 int lbif_mlp_create(lbif_mlp* out, int32_t nin, int32_t hidden, int32_t nhidden, int32_t nout,
