@@ -43,6 +43,13 @@ def _dg2(eta):
 
 
 def growth_factor(oracle_mod, k, sigma, eta, tau, coupling=True):
+    M = linear_map(oracle_mod, k, sigma, eta, tau, coupling)
+    return float(np.abs(np.linalg.eigvals(M)).max())
+
+
+def linear_map(oracle_mod, k, sigma, eta, tau, coupling=True):
+    """One step of the scheme linearised about the uniform rest state, for
+    perturbations a_i = delta f_i / n0 of wave vector k (a 19 x 19 matrix)."""
     c, w = oracle_mod.lattice()
     cf = c.astype(float)
     d, sw = oracle_mod.sphere_rule()
@@ -64,8 +71,7 @@ def growth_factor(oracle_mod, k, sigma, eta, tau, coupling=True):
     Fa = -C * n0 * np.outer(An, Mn) + C * n0 * G0 * kap * (Au @ Mj)
     aeq = w[:, None] * (Mn[None, :] + 3 * cf @ Mj)
     col = np.eye(19) - (np.eye(19) - aeq) / tau + 3 * (w[:, None] * cf) @ Fa
-    M = np.diag(np.exp(-1j * cf @ k)) @ col
-    return float(np.abs(np.linalg.eigvals(M)).max())
+    return np.diag(np.exp(-1j * cf @ k)) @ col
 
 
 def _scan(oracle_mod, sigma, eta, tau, L=8):
