@@ -68,6 +68,7 @@ def _load():
             "or_init_noise": (None, [vp, u64, f64, i64]),
             "or_init_fields": (None, [vp, _D, _D, _D, _D]),
             "or_step": (None, [vp, ctypes.c_long]),
+            "or_step_lagged": (None, [vp, ctypes.c_long]),
             "or_moments": (None, [vp, _D, _D, _D, _D, _D]),
             "or_forces": (None, [vp, _D, _D, _D, _D]),
             "or_profiles": (None, [vp, _D, _D]),
@@ -231,8 +232,10 @@ class Oracle:
             ux, uy, uz = (_f64(u[k], self.N) for k in range(3))
         self._lib.or_init_fields(self._h, _p(a), _p(ux), _p(uy), _p(uz))
 
-    def step(self, nsteps: int = 1):
-        self._lib.or_step(self._h, int(nsteps))
+    def step(self, nsteps: int = 1, lagged: bool = False):
+        """Plain steps, or steps of the lagged-force variant (the force of the
+        previous step's moments drives the collision)."""
+        (self._lib.or_step_lagged if lagged else self._lib.or_step)(self._h, int(nsteps))
 
     def moments(self, pressure: bool = False):
         n = np.zeros(self.shape)

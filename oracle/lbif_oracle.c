@@ -343,6 +343,8 @@ typedef struct {
     double *f, *fn;                   /* [NV][N] */
     double *n, *ux, *uy, *uz;         /* moments */
     double *nbar, *G, *Fx, *Fy, *Fz, *pc;
+    double *Lx, *Ly, *Lz;             /* lagged force (variant), NULL until used */
+    int lag_ok;                       /* Lx.. hold the force of the previous step */
     long t;
 } or_state;
 
@@ -375,6 +377,7 @@ void or_destroy(void* h)
     if (!s) return;
     free(s->f); free(s->fn); free(s->n); free(s->ux); free(s->uy); free(s->uz);
     free(s->nbar); free(s->G); free(s->Fx); free(s->Fy); free(s->Fz); free(s->pc);
+    free(s->Lx); free(s->Ly); free(s->Lz);
     free(s);
 }
 
@@ -486,6 +489,39 @@ void or_step(void* h, long nsteps)
     for (long k = 0; k < nsteps; ++k) {
         compute_moments(s);
         compute_forces(s, 0);
+        collide_stream(s);
+        s->t += 1;
+    }
+    s->lag_ok = 0;
+}
+
+/* Lagged-force variant of the step: the collision at step t uses the force
+ * computed from the moments of step t - 1 (the first step after plain steps
+ * or creation uses the current one). Same equilibrium, source and streaming;
+ * a steady state of the plain step is a steady state of this one.          */
+void or_step_lagged(void* h, long nsteps)
+{
+    or_state* s = (or_state*)h;
+    long N = s->N;
+    if (!s->Lx) {
+        s->Lx = (double*)calloc((size_t)N, sizeof(double));
+        s->Ly = (double*)calloc((size_t)N, sizeof(double));
+        s->Lz = (double*)calloc((size_t)N, sizeof(double));
+    }
+    for (long k = 0; k < nsteps; ++k) {
+        compute_moments(s);
+        compute_forces(s, 0);                  /* F(t) */
+        if (!s->lag_ok) {
+            memcpy(s->Lx, s->Fx, sizeof(double) * N);
+            memcpy(s->Ly, s->Fy, sizeof(double) * N);
+            memcpy(s->Lz, s->Fz, sizeof(double) * N);
+            s->lag_ok = 1;
+        }
+        /* collide with the lagged force, keep F(t) for the next step */
+        double* t;
+        t = s->Fx; s->Fx = s->Lx; s->Lx = t;
+        t = s->Fy; s->Fy = s->Ly; s->Ly = t;
+        t = s->Fz; s->Fz = s->Lz; s->Lz = t;
         collide_stream(s);
         s->t += 1;
     }

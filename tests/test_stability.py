@@ -50,6 +50,13 @@ def growth_factor(oracle_mod, k, sigma, eta, tau, coupling=True):
 def linear_map(oracle_mod, k, sigma, eta, tau, coupling=True):
     """One step of the scheme linearised about the uniform rest state, for
     perturbations a_i = delta f_i / n0 of wave vector k (a 19 x 19 matrix)."""
+    A, B = linear_map_parts(oracle_mod, k, sigma, eta, tau, coupling)
+    return A + B
+
+
+def linear_map_parts(oracle_mod, k, sigma, eta, tau, coupling=True):
+    """The linearised step split into streaming x (BGK collision) and
+    streaming x (force source driven by the force's linear response)."""
     c, w = oracle_mod.lattice()
     cf = c.astype(float)
     d, sw = oracle_mod.sphere_rule()
@@ -70,8 +77,8 @@ def linear_map(oracle_mod, k, sigma, eta, tau, coupling=True):
     Mj = cf.T                 # dj = sum_i c_i a_i ;  u = dj / n0
     Fa = -C * n0 * np.outer(An, Mn) + C * n0 * G0 * kap * (Au @ Mj)
     aeq = w[:, None] * (Mn[None, :] + 3 * cf @ Mj)
-    col = np.eye(19) - (np.eye(19) - aeq) / tau + 3 * (w[:, None] * cf) @ Fa
-    return np.diag(np.exp(-1j * cf @ k)) @ col
+    D = np.diag(np.exp(-1j * cf @ k))
+    return D @ (np.eye(19) - (np.eye(19) - aeq) / tau), D @ (3 * (w[:, None] * cf) @ Fa)
 
 
 def _scan(oracle_mod, sigma, eta, tau, L=8):
@@ -135,3 +142,33 @@ def test_without_coupling_bulk_is_stable_but_slits_diverge(oracle_mod):
     assert not np.all(np.isfinite(n)) or n.max() > 100 * n0
     n, n0 = runs[1]
     assert np.all(np.isfinite(n)) and 0.1 * n0 < n.min() and n.max() < 5 * n0
+
+
+def _lagged_radius(oracle_mod, sigma, eta, tau, coupling):
+    ks = 2 * np.pi * np.arange(5) / 8
+    worst = 0.0
+    for kx, ky, kz in itertools.product(ks, ks, ks):
+        if ky > kx or kz > ky:
+            continue
+        A, B = linear_map_parts(oracle_mod, np.array([kx, ky, kz]), sigma, eta, tau, coupling)
+        # state (a_t, a_{t-1}): the force of the previous step drives the collision
+        L = np.block([[A, B], [np.eye(19), np.zeros((19, 19))]])
+        worst = max(worst, float(np.abs(np.linalg.eigvals(L)).max()))
+    return worst
+
+
+def test_lagged_force_single_pass_variant_is_unstable(oracle_mod):
+    """Driving the collision of step t with the force of step t - 1 (what a
+    single pass fusing moments and collision needs) makes the scheme
+    unstable: the linearised two-step map grows even at eta = 0.02 with the
+    density-current term (at 0.25 without it), and the FP64 oracle's lagged
+    steps diverge where plain steps stay at rest."""
+    assert _lagged_radius(oracle_mod, 4, 0.02, 0.9, True) > 1.02
+    assert _lagged_radius(oracle_mod, 4, 0.02, 0.9, False) < 1 + 1e-9
+    assert _lagged_radius(oracle_mod, 4, 0.25, 0.9, False) > 1.05
+    for lagged in (False, True):
+        o = oracle_mod.Oracle(8, 8, 8, 4, 0.02, 0.9, zper=True, noise=1e-3, seed=1)
+        o.step(1500, lagged=lagged)
+        n, _ = o.moments()
+        dev = np.abs(n / o.n0 - 1).max() if np.all(np.isfinite(n)) else np.inf
+        assert (dev > 1.0) if lagged else (dev < 1e-3)
