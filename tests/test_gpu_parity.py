@@ -304,12 +304,15 @@ def test_thin_and_degenerate_grids(L, O):
         assert nerr(rg, ro) < 1e-5, shape
 
 
-@pytest.mark.parametrize("sigma,wide", [(4, (128, 16)), (6, (32, 16)), (12, (128, 32))])
-def test_narrow_grid_kernels_bit_identical_to_tiled(L, sigma, wide):
+@pytest.mark.parametrize("sigma,wide,storage", [(4, (128, 16), 0), (6, (32, 16), 0), (12, (128, 32), 0),
+                                                (4, (128, 16), 1), (12, (128, 32), 1)])
+def test_narrow_grid_kernels_bit_identical_to_tiled(L, sigma, wide, storage):
     """x,y-uniform slits: the thin-grid kernels (flat force mapping, direct
-    ball sums) give exactly the per-node values of the tiled kernels."""
+    ball sums; for FP16 the per-node wrap path of every pair on a 4-wide
+    row) give exactly the per-node values of the tiled kernels (the FP16
+    two-node interior path on wide rows)."""
     nz = 5 * sigma
-    kw = dict(body=(1e-5, 0, 0), noise=0.0)
+    kw = dict(body=(1e-5, 0, 0), noise=0.0, storage=storage)
     a = L.Slit(4, 4, nz, sigma, 0.2, 0.9, **kw)
     b = L.Slit(wide[0], wide[1], nz, sigma, 0.2, 0.9, **kw)
     a.step(60)
