@@ -225,6 +225,39 @@ def ensemble_leg(args):
             "mlups_fluid": fluid * steps / dt / 1e6, "autotuned": {"ball_ctas": ball, "force_group": group}}
 
 
+def mlp_leg(args):
+    """Tensor-core throughput of the warm-start network's forward pass on a
+    large batch (every layer one tcgen05 product with its fused epilogue),
+    inputs and outputs resident on the device."""
+    import torch
+
+    from paper_0712_2247_gb300.mlp import MLP
+
+    B = args.mlp_batch
+    net = MLP(4, 256, 3, 160, max_batch=B, seed=1)
+    X = torch.randn(B, 4, device="cuda", dtype=torch.float32)
+    for _ in range(3):
+        net.forward(X)
+    torch.cuda.synchronize()
+    reps = 20
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        net.forward(X)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / reps
+    net.close()
+    kpad = [16, 256, 256, 256]  # K of each product (the 4 inputs padded to 16)
+    flops = 2 * B * sum(k * o for k, o in zip(kpad, [256, 256, 256, 160]))
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak, kind = float(json.load(f)["bf16_tflops"]), "measured bf16_tflops (burst)"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    tf = flops / dt / 1e12
+    return {"batch": B, "ms_per_forward": dt * 1e3, "tflops": tf, "peak_tflops": peak, "peak_kind": kind,
+            "frac": tf / peak, "note": "4 products per forward, host-synchronised call (includes launch and sync)"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -332,6 +365,12 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, _, _, _ = cpu_sample(args.cpu_seconds)
+    mlp = None
+    if not args.no_mlp and world == 1:
+        try:
+            mlp = mlp_leg(args)
+        except Exception as e:
+            mlp = {"error": f"{type(e).__name__}: {e}"}
     ens = None
     if not args.no_ensemble and world == 1:
         try:
@@ -365,6 +404,7 @@ def run_ours(args, world, rank, local):
                      "bytes_alg_per_launch": dom_bytes},
         "cpu_baseline": cpu,
         "ensemble": ens,
+        "mlp_forward": mlp,
         "warm_start": warm,
         "e2e": e2e,
         "gpu_launches": launches,
@@ -386,6 +426,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm-start", action="store_true", help="skip the warm vs cold study")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble throughput")
+    ap.add_argument("--no-mlp", action="store_true", help="skip the tensor-core forward throughput")
+    ap.add_argument("--mlp-batch", type=int, default=65536, help="rows of the tensor-core forward leg")
     ap.add_argument("--ens-steps", type=int, default=2000, help="timed steps of the ensemble leg")
     ap.add_argument("--ws-train", type=int, default=4096, help="training slits of the warm-start leg")
     ap.add_argument("--ws-adam", type=int, default=3000, help="Adam steps of the warm-start leg")

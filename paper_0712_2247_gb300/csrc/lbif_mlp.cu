@@ -270,27 +270,76 @@ __global__ void __launch_bounds__(128) k_gemm_tc(Gemm g, int ntile)
     }
 
     if (ok) {
+        // each thread owns one row (its TMEM lane) and 16 consecutive columns
+        // per chunk: a full chunk is written with 16-byte vector stores
         const int row = m0 + 32 * warp + lane;
         for (int c = 0; c < NT; c += 16) {
             float v[16];
             tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
-            if (row < g.M) {
+            if (row >= g.M) continue;
+            const int nb = n0 + c;
+            const bool full = nb + 16 <= g.N && (g.ldz % 4) == 0 && (g.ldh % 8) == 0;
+            float z[16], h[16];
+            float zp[16];
+            if (g.epi == EPI_GELU_GRAD) {
+                if (full) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 t = *reinterpret_cast<const float4*>(g.zprev + (size_t)row * g.ldz + nb + 4 * q);
+                        zp[4 * q] = t.x, zp[4 * q + 1] = t.y, zp[4 * q + 2] = t.z, zp[4 * q + 3] = t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) zp[j] = nb + j < g.N ? g.zprev[(size_t)row * g.ldz + nb + j] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int n = nb + j;
+                float zz = v[j] + ((g.bias && n < g.N) ? g.bias[n] : 0.f);
+                float hh = zz;
+                if (g.epi == EPI_GELU) {
+                    hh = gelu(zz);
+                } else if (g.epi == EPI_GELU_GRAD) {
+                    zz = zz * gelu_grad(zp[j]);
+                    hh = zz;
+                }
+                z[j] = zz;
+                h[j] = hh;
+            }
+            if (full) {
+                if (g.Z) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<float4*>(g.Z + (size_t)row * g.ldz + nb + 4 * q) =
+                            make_float4(z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]);
+                }
+                if (g.H) {
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        uint4 pk;
+                        uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const __nv_bfloat162 b2 = __floats2bfloat162_rn(h[8 * q + 2 * e], h[8 * q + 2 * e + 1]);
+                            w[e] = *reinterpret_cast<const uint32_t*>(&b2);
+                        }
+                        *reinterpret_cast<uint4*>(g.H + (size_t)row * g.ldh + nb + 8 * q) = pk;
+                    }
+                }
+            } else {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + c + j;
-                    if (n >= g.N) break;
-                    float z = v[j] + (g.bias ? g.bias[n] : 0.f);
-                    float h = z;
-                    if (g.epi == EPI_GELU) {
-                        h = gelu(z);
-                    } else if (g.epi == EPI_GELU_GRAD) {
-                        z = z * gelu_grad(g.zprev[(size_t)row * g.ldz + n]);
-                        h = z;
-                    }
-                    if (g.Z) g.Z[(size_t)row * g.ldz + n] = z;
-                    const bf16 hb = __float2bfloat16_rn(h);
-                    if (g.H) g.H[(size_t)row * g.ldh + n] = hb;
-                    if (g.HT) g.HT[(size_t)n * g.ldht + row] = hb;
+                    if (nb + j >= g.N) break;
+                    if (g.Z) g.Z[(size_t)row * g.ldz + nb + j] = z[j];
+                    if (g.H) g.H[(size_t)row * g.ldh + nb + j] = __float2bfloat16_rn(h[j]);
+                }
+            }
+            if (g.HT) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (nb + j >= g.N) break;
+                    g.HT[(size_t)(nb + j) * g.ldht + row] = __float2bfloat16_rn(h[j]);
                 }
             }
         }
