@@ -11,6 +11,10 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "lbif_internal.h"
 
 using namespace lbif;
@@ -48,6 +52,8 @@ struct lbif_ctx {
     std::vector<int> done;
     bool batch = false;
     int ball_want = 0, force_group = 0;  // launch shapes (0 = defaults; set by the autotuner)
+    CUtensorMap ball_map[2];             // tensor maps of dn[0], dn[1] for the ball kernel's tiles
+    bool ball_map_ok = false;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     int64_t t = 0;
@@ -75,6 +81,46 @@ static int fail(lbif_ctx* h, int code, const std::string& msg)
     } while (0)
 
 static size_t pop_bytes(const Params& P) { return (P.storage == LBIF_STORE_F16 ? 2 : 4); }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); NULL if the driver does not provide it.
+static PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D map (x, y, z of the padded grid, FP32) of a padded field, with the
+// ball kernel's plane tile as its box; out-of-range elements read as zero.
+static bool make_ball_map(const Geom& g, int sigma, float* base, CUtensorMap* out)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return false;
+    int W, H;
+    ball_box(sigma, &W, &H);
+    if (W > 256 || H > 256 || (W * 4) % 16) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)g.pz};
+    cuuint64_t strides[2] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.px * g.py * 4};
+    cuuint32_t box[3] = {(cuuint32_t)W, (cuuint32_t)H, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the map of the buffer the ball kernel reads (dn[i]), or NULL
+static const CUtensorMap* ball_map(const lbif_ctx* h, int i) { return h->ball_map_ok ? &h->ball_map[i] : nullptr; }
 
 // padded fields carry PAD_SLACK floats before their first element
 static float* padded_alloc(size_t P)
@@ -342,6 +388,8 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
                 return fail(nullptr, LBIF_ERR_NOMEM, "create: device allocation failed");
             }
         }
+        h->ball_map_ok = make_ball_map(g, P.sigma, h->dn[0], &h->ball_map[0]) &&
+                         make_ball_map(g, P.sigma, h->dn[1], &h->ball_map[1]);
     }
     P.sl = h->d_sl;
     P.zslit = h->d_zslit;
@@ -496,7 +544,7 @@ static int refresh_fields(lbif_ctx* h, bool want_G, int skip_done)
         h->fields_t = skip_done ? -1 : h->t;
     }
     if (want_G && h->G_t != h->t) {
-        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, skip_done, h->stream));
+        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, skip_done, h->stream, ball_map(h, h->dcur ^ 1)));
         h->G_t = skip_done ? -1 : h->t;
     }
     if (P.tail && h->tail_t != h->t) {
@@ -560,7 +608,7 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
         cls[j] = 0;
         CK(h, cudaEventRecord(ev[++j], h->stream));
         if (P.hs) {
-            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, 1, h->stream));
+            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, 1, h->stream, ball_map(h, h->dcur ^ 1)));
             cls[j] = 1;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
@@ -597,6 +645,7 @@ static int check_status(lbif_ctx* h)
     CK(h, cudaMemcpyAsync(&st, h->status_d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (st) h->sticky |= st;
+    if (h->sticky & 4) return fail(h, LBIF_ERR_TIMEOUT, "a bounded device wait for a tile copy ran out");
     if (h->sticky)
         return fail(h, LBIF_ERR_DIVERGED,
                     (h->sticky & 2) ? "state diverged: coarse-grained packing fraction reached 1"
@@ -1004,7 +1053,7 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
         float tot = 0.f;
         for (int k = 0; k < trials + 1; ++k) {
             CK(h, cudaEventRecord(e0, h->stream));
-            CK(h, launch_ball(P, dnew, h->dG, h->status_d, b, 0, h->stream));
+            CK(h, launch_ball(P, dnew, h->dG, h->status_d, b, 0, h->stream, ball_map(h, h->dcur ^ 1)));
             CK(h, cudaEventRecord(e1, h->stream));
             CK(h, cudaEventSynchronize(e1));
             float ms;

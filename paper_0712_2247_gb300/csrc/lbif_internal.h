@@ -21,6 +21,7 @@
 //   nodes are one float4; every padded array has 64 floats of slack on both
 //   sides for the vector windows of the stencils.
 #pragma once
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -114,9 +115,14 @@ cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaSt
 cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, float* dnew,
                            float* ux, float* uy, float* uz, int* status, int skip_done,
                            cudaStream_t s);
-// want: CTAs to aim for when splitting z into chunks (<= 0: default)
+// want: CTAs to aim for when splitting z into chunks (<= 0: default).
+// tmap: a 3-D tensor map of dn (padded extents px, py, pz; box from
+// ball_box) to stage the plane tiles with the tensor-memory accelerator, or
+// NULL for plain loads. Bit 4 of status records a bounded wait that ran out.
 cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, int want,
-                        int skip_done, cudaStream_t s);
+                        int skip_done, cudaStream_t s, const CUtensorMap* tmap = nullptr);
+// box (x extent W, y extent H) of the ball kernel's plane tile for sigma
+void ball_box(int sigma, int* W, int* H);
 cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const float4* K,
                         int npairs, float4* Ft, cudaStream_t s);
 // group: edge (nodes) of the x-y block the resident CTAs sweep together (<= 0: default)

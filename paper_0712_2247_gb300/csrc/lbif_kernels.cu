@@ -372,6 +372,23 @@ constexpr int ball_smem_floats()
     return (BALL_TY + 2 * R) * (BALL_TX + 2 * ball_c4<R>()) + (R + 1) * (BALL_TY + 2 * R) * BALL_TX;
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait_parity(uint64_t* mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr long long BALL_WAIT_LIMIT = 1LL << 22;  // try_wait polls; seconds at most
+
 // does tile row r (relative to a thread's first node row minus R) enter a
 // disc sum D_k of any of the thread's BALL_YT nodes with row half-width w?
 __host__ __device__ constexpr bool ball_row_used(int R, int r, int w)
@@ -425,6 +442,89 @@ __device__ __forceinline__ void ball_disc_rows(const float* __restrict__ RS, int
     (ball_disc_row<R, N>(RS, off, D), ...);
 }
 
+// Row sums of every half-width 0..R for four adjacent columns per thread,
+// from a staged plane tile T (H x W, column C4 + c holds node column c): the
+// window sits in registers, additions grow outwards from the centre column.
+template <int R>
+__device__ __forceinline__ void ball_rowsums(const float* __restrict__ T, float* __restrict__ RS)
+{
+    constexpr int TX = BALL_TX, TY = BALL_TY;
+    constexpr int C4 = ball_c4<R>();
+    constexpr int W = TX + 2 * C4, H = TY + 2 * R;
+    constexpr int NF = (C4 + R + 7) / 4;  // float4s a 4-column row-sum group reads
+    for (int k = threadIdx.x; k < H * (TX / 4); k += blockDim.x) {
+        int row = k / (TX / 4), c = 4 * (k - row * (TX / 4));
+        const float* tr = T + row * W + c;
+        float t[4 * NF];
+#pragma unroll
+        for (int i = 0; i < NF; ++i) {
+            float4 v = *reinterpret_cast<const float4*>(tr + 4 * i);
+            t[4 * i] = v.x;
+            t[4 * i + 1] = v.y;
+            t[4 * i + 2] = v.z;
+            t[4 * i + 3] = v.w;
+        }
+        float s[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[j] = t[C4 + j];
+        *reinterpret_cast<float4*>(RS + row * TX + c) = make_float4(s[0], s[1], s[2], s[3]);
+#pragma unroll
+        for (int w = 1; w <= R; ++w) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) s[j] += t[C4 + j - w] + t[C4 + j + w];
+            *reinterpret_cast<float4*>(RS + (w * H + row) * TX + c) = make_float4(s[0], s[1], s[2], s[3]);
+        }
+    }
+}
+
+// Disc sums of input plane zi for the thread's BALL_YT nodes, added into the
+// register ring acc of the 2R+1 output planes they touch; the completed plane
+// zi - R is written (g2 deviation, with its periodic images), the ring shifts.
+template <int R>
+__device__ __forceinline__ void ball_disc_out(const Params& P, const float* __restrict__ RS,
+                                              float (&acc)[2 * R + 1][BALL_YT], int zi, int z0, int x,
+                                              int y0, int ty0, int tx, float* __restrict__ dG, int* status,
+                                              int skip_done)
+{
+    constexpr int YT = BALL_YT, TX = BALL_TX;
+    const Geom& g = P.g;
+    // D[k][i] = sum over dy = -R..R (in that order) of the row sum of
+    // half-width cisqrt(R^2 - k^2 - dy^2) at row ty0 + i + dy
+    float D[R + 1][YT];
+#pragma unroll
+    for (int k = 0; k <= R; ++k)
+#pragma unroll
+        for (int i = 0; i < YT; ++i) D[k][i] = 0.f;
+    ball_disc_rows<R>(RS, ty0 * TX + tx, D, std::make_integer_sequence<int, (YT + 2 * R) * (R + 1)>{});
+#pragma unroll
+    for (int k = 0; k <= R; ++k)
+#pragma unroll
+        for (int i = 0; i < YT; ++i) {
+            acc[R - k][i] += D[k][i];
+            if (k) acc[R + k][i] += D[k][i];
+        }
+    const int zo = zi - R;
+    const int so = zo >= z0 ? slit_of(P, zo) : -1;
+    if (so >= 0 && x < g.nx && !(skip_done && frozen(P, so))) {
+        const float e0 = P.sl[so].eta0;
+#pragma unroll
+        for (int i = 0; i < YT; ++i) {
+            const int y = y0 + ty0 + i;
+            if (y >= g.ny) break;
+            bool bad;
+            float v = g2_deviation(P, e0, acc[0][i] * P.ball_inv, bad);
+            if (bad) atomicOr(status, 2);
+            for_images(g, x, y, zo, [&](int q) { dG[q] = v; });
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 2 * R; ++j)
+#pragma unroll
+        for (int i = 0; i < YT; ++i) acc[j][i] = acc[j + 1][i];
+#pragma unroll
+    for (int i = 0; i < YT; ++i) acc[2 * R][i] = 0.f;
+}
+
 // One CTA = a 32 x 16 column of nodes marching up a z chunk. Per input plane:
 // stage the plane (+R halo) in shared memory, build x-row sums of every
 // half-width 0..R, form the disc sums D_k (disc of radius^2 R^2 - k^2; a
@@ -439,9 +539,8 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
     constexpr int TX = BALL_TX, TY = BALL_TY;
     constexpr int C4 = ball_c4<R>();
     constexpr int W = TX + 2 * C4, H = TY + 2 * R;
-    constexpr int NF = (C4 + R + 7) / 4;  // float4s a 4-column row-sum group reads
     extern __shared__ __align__(16) float sm[];
-    float* T = sm;           // H x W plane tile, column C4 + c holds node column c
+    float* T = sm;           // H x W plane tile
     float* RS = sm + H * W;  // (R+1) x H x TX row sums
     const Geom& g = P.g;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
@@ -469,68 +568,92 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
             *reinterpret_cast<float4*>(T + row * W + 4 * q) = v;
         }
         __syncthreads();
-        // row sums of every half-width 0..R for four adjacent columns per
-        // thread: the window sits in registers, additions grow outwards from
-        // the centre column
-        for (int k = threadIdx.x; k < H * (TX / 4); k += blockDim.x) {
-            int row = k / (TX / 4), c = 4 * (k - row * (TX / 4));
-            const float* tr = T + row * W + c;
-            float t[4 * NF];
-#pragma unroll
-            for (int i = 0; i < NF; ++i) {
-                float4 v = *reinterpret_cast<const float4*>(tr + 4 * i);
-                t[4 * i] = v.x;
-                t[4 * i + 1] = v.y;
-                t[4 * i + 2] = v.z;
-                t[4 * i + 3] = v.w;
-            }
-            float s[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) s[j] = t[C4 + j];
-            *reinterpret_cast<float4*>(RS + row * TX + c) = make_float4(s[0], s[1], s[2], s[3]);
-#pragma unroll
-            for (int w = 1; w <= R; ++w) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) s[j] += t[C4 + j - w] + t[C4 + j + w];
-                *reinterpret_cast<float4*>(RS + (w * H + row) * TX + c) = make_float4(s[0], s[1], s[2], s[3]);
-            }
-        }
+        ball_rowsums<R>(T, RS);
         __syncthreads();
-        // D[k][i] = sum over dy = -R..R (in that order) of the row sum of
-        // half-width cisqrt(R^2 - k^2 - dy^2) at row ty0 + i + dy
-        float D[R + 1][YT];
+        ball_disc_out<R>(P, RS, acc, zi, z0, x, y0, ty0, tx, dG, status, skip_done);
+        __syncthreads();
+    }
+}
+
+// The same kernel with the plane tiles brought in by the tensor-memory
+// accelerator: one cp.async.bulk.tensor copy per plane (a W x H x 1 box of
+// the padded density field, out-of-range rows filled with zeros), issued by
+// one thread two planes ahead into alternating buffers, completion counted
+// in bytes on an mbarrier per buffer. The arithmetic is k_ball's.
+template <int R>
+__global__ void __launch_bounds__(BALL_THREADS) k_ball_tma(Params P, const __grid_constant__ CUtensorMap tmap,
+                                                  float* __restrict__ dG, int* status, int zchunk,
+                                                  int skip_done)
+{
+    constexpr int TX = BALL_TX, TY = BALL_TY;
+    constexpr int C4 = ball_c4<R>();
+    constexpr int W = TX + 2 * C4, H = TY + 2 * R;
+    constexpr int TB = (H * W * 4 + 127) / 128 * 128;  // bytes of one tile buffer
+    extern __shared__ __align__(128) unsigned char bsm[];
+    float* RS = reinterpret_cast<float*>(bsm + 2 * TB);                 // (R+1) x H x TX
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(RS + (R + 1) * H * TX);  // 2 barriers
+    const Geom& g = P.g;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk;
+    const int z1 = min(z0 + zchunk, g.nz);
+    constexpr int YT = BALL_YT;
+    const int tx = threadIdx.x % TX, ty0 = (threadIdx.x / TX) * YT;
+    const int x = x0 + tx;
+    const int np = (z1 + R) - (z0 - R);  // input planes of this chunk
+    // box origin in padded coordinates; x0 - C4 + hw is a multiple of 4 (16 bytes)
+    const int bx = x0 - C4 + g.hw, by = y0 - R + g.hw;
+    if (threadIdx.x == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int q) {  // plane z0 - R + q into buffer q & 1 (one thread)
+        const int b = q & 1;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar + b)),
+                     "r"((uint32_t)(H * W * 4))
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];" ::"r"(smem_addr(bsm + b * TB)),
+            "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(bx), "r"(by), "r"(z0 - R + q + g.hw), "r"(smem_addr(mbar + b))
+            : "memory");
+    };
+    if (threadIdx.x == 0) {
+        issue(0);
+        if (np > 1) issue(1);
+    }
+    float acc[2 * R + 1][YT];
 #pragma unroll
-        for (int k = 0; k <= R; ++k)
+    for (int j = 0; j <= 2 * R; ++j)
 #pragma unroll
-            for (int i = 0; i < YT; ++i) D[k][i] = 0.f;
-        ball_disc_rows<R>(RS, ty0 * TX + tx, D, std::make_integer_sequence<int, (YT + 2 * R) * (R + 1)>{});
-#pragma unroll
-        for (int k = 0; k <= R; ++k)
-#pragma unroll
-            for (int i = 0; i < YT; ++i) {
-                acc[R - k][i] += D[k][i];
-                if (k) acc[R + k][i] += D[k][i];
-            }
-        const int zo = zi - R;
-        const int so = zo >= z0 ? slit_of(P, zo) : -1;
-        if (so >= 0 && x < g.nx && !(skip_done && frozen(P, so))) {
-            const float e0 = P.sl[so].eta0;
-#pragma unroll
-            for (int i = 0; i < YT; ++i) {
-                const int y = y0 + ty0 + i;
-                if (y >= g.ny) break;
-                bool bad;
-                float v = g2_deviation(P, e0, acc[0][i] * P.ball_inv, bad);
-                if (bad) atomicOr(status, 2);
-                for_images(g, x, y, zo, [&](int q) { dG[q] = v; });
-            }
+        for (int i = 0; i < YT; ++i) acc[j][i] = 0.f;
+    uint32_t pbits = 0u;  // bit b: phase parity expected next on buffer b
+    for (int q = 0; q < np; ++q) {
+        const int b = q & 1;
+        long long spins = 0;
+        bool ok;
+        while (!(ok = mbar_wait_parity(mbar + b, (pbits >> b) & 1u)) && ++spins < BALL_WAIT_LIMIT) {
         }
-#pragma unroll
-        for (int j = 0; j < 2 * R; ++j)
-#pragma unroll
-            for (int i = 0; i < YT; ++i) acc[j][i] = acc[j + 1][i];
-#pragma unroll
-        for (int i = 0; i < YT; ++i) acc[2 * R][i] = 0.f;
+        if (!__syncthreads_and(ok)) {
+            // record the timeout and wait (bounded) for the copies in flight
+            if (threadIdx.x == 0) atomicOr(status, 4);
+            for (int k = 0; k < 2; ++k) {
+                if (q + k >= np) break;
+                const int bk = (q + k) & 1;
+                spins = 0;
+                while (!mbar_wait_parity(mbar + bk, (pbits >> bk) & 1u) && ++spins < BALL_WAIT_LIMIT) {
+                }
+            }
+            return;
+        }
+        pbits ^= 1u << b;
+        ball_rowsums<R>(reinterpret_cast<const float*>(bsm + b * TB), RS);
+        __syncthreads();  // buffer b is read: refill it two planes ahead
+        if (threadIdx.x == 0 && q + 2 < np) issue(q + 2);
+        ball_disc_out<R>(P, RS, acc, z0 - R + q, z0, x, y0, ty0, tx, dG, status, skip_done);
         __syncthreads();
     }
 }
@@ -1256,16 +1379,24 @@ cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, 
 
 template <int R>
 static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* status, int want,
-                         int skip_done, cudaStream_t s)
+                         int skip_done, const CUtensorMap* tmap, cudaStream_t s)
 {
     const Geom& g = P.g;
-    size_t smem = sizeof(float) * ball_smem_floats<R>();
-    static bool configured = false;
-    if (!configured) {
+    constexpr int H = BALL_TY + 2 * R, W = BALL_TX + 2 * ball_c4<R>();
+    const size_t smem = tmap ? (size_t)2 * ((H * W * 4 + 127) / 128 * 128) + sizeof(float) * (R + 1) * H * BALL_TX + 16
+                             : sizeof(float) * ball_smem_floats<R>();
+    static bool configured = false, configured_tma = false;
+    if (!tmap && !configured) {
         cudaError_t e = cudaFuncSetAttribute(k_ball<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
+    }
+    if (tmap && !configured_tma) {
+        cudaError_t e = cudaFuncSetAttribute(k_ball_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured_tma = true;
     }
     int gx = (g.nx + BALL_TX - 1) / BALL_TX, gy = (g.ny + BALL_TY - 1) / BALL_TY;
     if (want <= 0) want = 608;  // ~4 CTAs per SM on 152 SMs
@@ -1276,30 +1407,40 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
     int zchunk = (g.nz + nchunk - 1) / nchunk;
     nchunk = (g.nz + zchunk - 1) / zchunk;
     dim3 grid(gx, gy, nchunk);
-    k_ball<R><<<grid, BALL_THREADS, smem, s>>>(P, dn, dG, status, zchunk, skip_done);
+    if (tmap)
+        k_ball_tma<R><<<grid, BALL_THREADS, smem, s>>>(P, *tmap, dG, status, zchunk, skip_done);
+    else
+        k_ball<R><<<grid, BALL_THREADS, smem, s>>>(P, dn, dG, status, zchunk, skip_done);
     return cudaGetLastError();
 }
 
+void ball_box(int sigma, int* W, int* H)
+{
+    const int R = sigma / 2;
+    *W = BALL_TX + 2 * ((R + 3) / 4 * 4);
+    *H = BALL_TY + 2 * R;
+}
+
 cudaError_t launch_ball(const Params& P, const float* dn, float* dG, int* status, int want,
-                        int skip_done, cudaStream_t s)
+                        int skip_done, cudaStream_t s, const CUtensorMap* tmap)
 {
     if (P.g.nx < BALL_TX / 2 || P.g.ny < BALL_TY / 2) {
         k_ball_direct<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, dn, dG, status, skip_done);
         return cudaGetLastError();
     }
     switch (P.sigma / 2) {
-    case 1: return ball_r<1>(P, dn, dG, status, want, skip_done, s);
-    case 2: return ball_r<2>(P, dn, dG, status, want, skip_done, s);
-    case 3: return ball_r<3>(P, dn, dG, status, want, skip_done, s);
-    case 4: return ball_r<4>(P, dn, dG, status, want, skip_done, s);
-    case 5: return ball_r<5>(P, dn, dG, status, want, skip_done, s);
-    case 6: return ball_r<6>(P, dn, dG, status, want, skip_done, s);
-    case 7: return ball_r<7>(P, dn, dG, status, want, skip_done, s);
-    case 8: return ball_r<8>(P, dn, dG, status, want, skip_done, s);
-    case 9: return ball_r<9>(P, dn, dG, status, want, skip_done, s);
-    case 10: return ball_r<10>(P, dn, dG, status, want, skip_done, s);
-    case 11: return ball_r<11>(P, dn, dG, status, want, skip_done, s);
-    case 12: return ball_r<12>(P, dn, dG, status, want, skip_done, s);
+    case 1: return ball_r<1>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 2: return ball_r<2>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 3: return ball_r<3>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 4: return ball_r<4>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 5: return ball_r<5>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 6: return ball_r<6>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 7: return ball_r<7>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 8: return ball_r<8>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 9: return ball_r<9>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 10: return ball_r<10>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 11: return ball_r<11>(P, dn, dG, status, want, skip_done, tmap, s);
+    case 12: return ball_r<12>(P, dn, dG, status, want, skip_done, tmap, s);
     default: return cudaErrorInvalidValue;
     }
 }
