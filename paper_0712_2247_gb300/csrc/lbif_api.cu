@@ -877,15 +877,27 @@ extern "C" int lbif_batch_seed(lbif_handle h, const float* n_z, const float* ux_
         if (s.zhi - s.zlo + 1 > hmax) return fail(h, LBIF_ERR_ARG, "lbif_batch_seed: hmax below a slit width");
     size_t cnt = h->sl.size() * (size_t)hmax;
     float* d = nullptr;
+    float* tmp = nullptr;  // profiles larger than the scratch (very thin slits): own buffer
     int rc = ensure_scratch(h);
     if (rc) return rc;
-    if ((size_t)3 * h->P.g.N < 2 * cnt) return fail(h, LBIF_ERR_ARG, "lbif_batch_seed: profiles too large");
-    d = h->scratch;
-    CK(h, cudaMemcpyAsync(d, n_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream));
-    if (ux_z) CK(h, cudaMemcpyAsync(d + cnt, ux_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream));
-    CK(h, launch_init_profiles(h->P, h->pop[h->cur], h->dn[h->dcur], d, ux_z ? d + cnt : nullptr, hmax,
-                               h->stream));
-    CK(h, cudaStreamSynchronize(h->stream));
+    if ((size_t)3 * h->P.g.N >= 2 * cnt) {
+        d = h->scratch;
+    } else {
+        if (cudaMalloc((void**)&tmp, sizeof(float) * 2 * cnt) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, LBIF_ERR_NOMEM, "lbif_batch_seed: device allocation failed");
+        }
+        d = tmp;
+    }
+    cudaError_t e = cudaMemcpyAsync(d, n_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && ux_z)
+        e = cudaMemcpyAsync(d + cnt, ux_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_init_profiles(h->P, h->pop[h->cur], h->dn[h->dcur], d, ux_z ? d + cnt : nullptr, hmax,
+                                 h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail(h, LBIF_ERR_CUDA, std::string("lbif_batch_seed: ") + cudaGetErrorString(e));
     std::fill(h->done.begin(), h->done.end(), 0);
     if ((rc = upload_done(h))) return rc;
     reset_time(h);

@@ -8,6 +8,7 @@
 // force. FP64 appears only in the profile / mass reductions.
 #include <string.h>
 
+#include <atomic>
 #include <utility>
 
 #include "lbif_internal.h"
@@ -1385,18 +1386,19 @@ static cudaError_t ball_r(const Params& P, const float* dn, float* dG, int* stat
     constexpr int H = BALL_TY + 2 * R, W = BALL_TX + 2 * ball_c4<R>();
     const size_t smem = tmap ? (size_t)2 * ((H * W * 4 + 127) / 128 * 128) + sizeof(float) * (R + 1) * H * BALL_TX + 16
                              : sizeof(float) * ball_smem_floats<R>();
-    static bool configured = false, configured_tma = false;
-    if (!tmap && !configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_ball<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    // the shared-memory limit is a per-device function attribute: set it
+    // once per device that launches the kernel
+    static std::atomic<uint64_t> configured{0}, configured_tma{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    std::atomic<uint64_t>& flags = tmap ? configured_tma : configured;
+    if (!(flags.load() & bit)) {
+        e = tmap ? cudaFuncSetAttribute(k_ball_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                 : cudaFuncSetAttribute(k_ball<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    if (tmap && !configured_tma) {
-        cudaError_t e = cudaFuncSetAttribute(k_ball_tma<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured_tma = true;
+        flags.fetch_or(bit);
     }
     int gx = (g.nx + BALL_TX - 1) / BALL_TX, gy = (g.ny + BALL_TY - 1) / BALL_TY;
     if (want <= 0) want = 608;  // ~4 CTAs per SM on 152 SMs
