@@ -9,8 +9,8 @@ The populations (3.8 GB FP32) exceed the 129 MB L2, so no flush is needed.
 
 Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload instead.
-Multi-GPU (torchrun): independent replicas, one slit per GPU (the slit does
-not shard in this build), max time over ranks, weak scaling.
+Multi-GPU (torchrun): independent replicas, one slit per GPU (one slit is not
+split across GPUs), max time over ranks, weak scaling.
 """
 from __future__ import annotations
 

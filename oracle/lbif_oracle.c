@@ -24,7 +24,7 @@
  *   6. two-array push streaming, halfway bounce-back at the slit walls,
  *      periodic x and y.
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - walls sit half-way, at z = -1/2 and z = nz - 1/2; all nz nodes are fluid
  *   - the ball is the lattice solid sphere |d|^2 <= (sigma/2)^2, normalised
  *     by its node count
