@@ -41,6 +41,9 @@ struct lbif_ctx {
     int* tail_off = nullptr;
     float4* tail_K = nullptr;
     int tail_pairs = 0;
+    float2* tail_work = nullptr;      // spectral tail: fields, kernel transform, twiddles
+    int tail_D = 0;                   // z reach of the tail kernel (planes)
+    bool tail_fft = false;
     int* status_d = nullptr;
     double* prof_d = nullptr;
     float* scratch = nullptr;         // 3 N floats, for host-side outputs
@@ -122,6 +125,13 @@ static bool make_ball_map(const Geom& g, int sigma, float* base, CUtensorMap* ou
 // the map of the buffer the ball kernel reads (dn[i]), or NULL
 static const CUtensorMap* ball_map(const lbif_ctx* h, int i) { return h->ball_map_ok ? &h->ball_map[i] : nullptr; }
 
+// tail force of the density field dn: spectral in x, y when available
+static cudaError_t run_tail(lbif_ctx* h, const float* dn)
+{
+    if (h->tail_fft) return launch_tail_spectral(h->P, dn, h->tail_D, h->tail_work, h->Ft, h->stream);
+    return launch_tail(h->P, dn, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream);
+}
+
 // padded fields carry PAD_SLACK floats before their first element
 static float* padded_alloc(size_t P)
 {
@@ -142,7 +152,7 @@ static void free_ctx(lbif_ctx* h)
 {
     if (!h) return;
     if (h->graph) cudaGraphExecDestroy(h->graph);
-    void* bufs[] = {h->pop[0], h->pop[1], h->Ft,    h->F,       h->tail_off, h->tail_K, h->status_d,
+    void* bufs[] = {h->pop[0], h->pop[1], h->Ft, h->F, h->tail_off, h->tail_K, h->tail_work, h->status_d,
                     h->prof_d, h->scratch, h->d_sl, h->d_zslit, h->d_done};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -336,11 +346,12 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     }
 
     // tail taps: one representative of each +-d pair with sigma <= |d| <= rcut sigma
-    std::vector<int> toff;
+    std::vector<int> toff, tdx, tdy, tdz;
     std::vector<float4> tK;
     if (P.tail) {
         double rmax = F.rcut * sigma;
         int R = (int)ceil(rmax);
+        h->tail_D = R;
         double s6 = pow((double)sigma, 6.0), s12 = s6 * s6;
         for (int dz = 0; dz <= R; ++dz)
             for (int dy = (dz == 0 ? 0 : -R); dy <= R; ++dy)
@@ -350,6 +361,9 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
                     double r = sqrt(r2);
                     double dphi = 4.0 * F.eps * (-12.0 * s12 / pow(r, 13.0) + 6.0 * s6 / pow(r, 7.0));
                     toff.push_back(padded_offset(g, dx, dy, dz));
+                    tdx.push_back(dx);
+                    tdy.push_back(dy);
+                    tdz.push_back(dz);
                     tK.push_back(make_float4((float)(dphi * dx / r), (float)(dphi * dy / r),
                                              (float)(dphi * dz / r), 0.f));
                 }
@@ -435,6 +449,18 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     if (P.tail) {
         CKC(cudaMemcpyAsync(h->tail_off, toff.data(), sizeof(int) * toff.size(),
                             cudaMemcpyHostToDevice, h->stream));
+        // spectral path when the lateral extents allow it; else the direct sum
+        if (tail_spectral_ok(g)) {
+            if (cudaMalloc((void**)&h->tail_work, tail_spectral_bytes(g, h->tail_D)) == cudaSuccess &&
+                tail_spectral_init(g, h->tail_D, tdx.data(), tdy.data(), tdz.data(), tK.data(), (int)tK.size(),
+                                   h->zslit.data(), h->tail_work, h->stream) == cudaSuccess) {
+                h->tail_fft = true;
+            } else {
+                cudaGetLastError();
+                if (h->tail_work) cudaFree(h->tail_work);
+                h->tail_work = nullptr;
+            }
+        }
         CKC(cudaMemcpyAsync(h->tail_K, tK.data(), sizeof(float4) * tK.size(),
                             cudaMemcpyHostToDevice, h->stream));
     }
@@ -548,7 +574,7 @@ static int refresh_fields(lbif_ctx* h, bool want_G, int skip_done)
         h->G_t = skip_done ? -1 : h->t;
     }
     if (P.tail && h->tail_t != h->t) {
-        CK(h, launch_tail(P, dnew, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
+        CK(h, run_tail(h, dnew));
         h->tail_t = skip_done ? -1 : h->t;
     }
     return LBIF_OK;
@@ -613,7 +639,7 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
         if (P.tail) {
-            CK(h, launch_tail(P, dnew, h->tail_off, h->tail_K, h->tail_pairs, h->Ft, h->stream));
+            CK(h, run_tail(h, dnew));
             cls[j] = 2;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }

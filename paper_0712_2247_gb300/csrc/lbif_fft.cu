@@ -1,0 +1,326 @@
+// Attractive mean-field tail through the convolution theorem.
+//
+// The tail force of a node (Sec. Conclusions: a mean-field attraction added
+// to the hard-sphere force; Lennard-Jones form with the Barker-Henderson
+// split, cut at rcut sigma) is F_att(r)/n0 = n0 m(r) T(r) with m = n/n0 (zero
+// outside the fluid) and T(r) = sum_d K(d) m(r + d), K(d) = phi'(|d|) d/|d|
+// over sigma <= |d| <= rcut sigma: a correlation of m with a fixed, odd,
+// vector kernel. Split m = f + dn with f = 1 on fluid planes and 0 outside:
+// the part of f is x,y-uniform, has a z component only,
+//   w(z) = sum_dz kappa(dz) f(z + dz),  kappa(dz) = sum_{dx,dy} K_z(dx, dy, dz),
+// and is tabulated in double once (it carries the wall attraction; the odd
+// kernel cancels it exactly in a periodic box). The small part dn is done in
+// the x-y Fourier modes, where the correlation is diagonal; along z it stays
+// a short direct sum (walls need no padding):
+//   M(k, z)  = FFT_xy[dn(., ., z) f(z)](k)
+//   T^(k, z) = sum_dz conj(FFT_xy[K(., ., dz)](k)) M(k, z + dz)
+//   T(r)     = IFFT_xy[T^](r) / (nx ny) + (0, 0, w(z))
+// T_x and T_y are real, so they share one inverse transform (T_x + i T_y);
+// T_z takes the second. The kernel's transform is computed once per handle
+// with the same FFT kernels. Cost per step: about eight passes over a
+// complex field, instead of ~2 * 10^4 neighbour reads per node.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "lbif_internal.h"
+
+namespace lbif {
+namespace {
+
+constexpr int FFT_THREADS = 256;
+constexpr int FFT_GL = 2048;  // lines x line length held by one CTA
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ int padded(const Geom& g, int x, int y, int z)
+{
+    return ((z + g.hw) * g.py + (y + g.hw)) * g.px + (x + g.hw);
+}
+
+// Batched radix-2 Stockham FFT (natural order in and out) of lines of
+// length L = 2^logL <= 1024 held in shared memory, FFT_GL / L lines per CTA.
+// Along x: line l holds elements l L .. l L + L - 1. Along y: line l = z nx + x
+// holds elements z nx L + x + i nx (consecutive lines are consecutive x, so
+// the loads and stores of a CTA are row segments). tw[j] = exp(-2 pi i j / L)
+// for j < L/2; inverse = 1 uses the conjugate twiddles (unnormalised).
+template <bool ALONG_Y>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft(float2* __restrict__ data, int L, int logL, int nx,
+                                                     long long nlines, const float2* __restrict__ tw, int inverse)
+{
+    extern __shared__ float2 fsm[];
+    const int G = FFT_GL / L;
+    float2* X = fsm;
+    float2* Y = fsm + G * L;
+    const long long l0 = (long long)blockIdx.x * G;
+    auto addr = [&](long long l, int i) -> long long {
+        if (ALONG_Y) {
+            const long long z = l / nx, x = l - z * nx;
+            return z * nx * (long long)L + x + (long long)i * nx;
+        }
+        return l * L + i;
+    };
+    for (int t = threadIdx.x; t < G * L; t += blockDim.x) {
+        const int g = ALONG_Y ? t % G : t / L;
+        const int i = ALONG_Y ? t / G : t % L;
+        const long long l = l0 + g;
+        X[g * L + i] = l < nlines ? data[addr(l, i)] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int half = L >> 1;
+    int st = 1;
+    for (int s = 0; s < logL; ++s) {
+        const int m = half >> s;  // half of the current sub-transform length
+        for (int t = threadIdx.x; t < G * half; t += blockDim.x) {
+            const int g = t / half, b = t - g * half;
+            const int p = b >> s, q = b & (st - 1);
+            const float2 a = X[g * L + q + st * p], c = X[g * L + q + st * (p + m)];
+            float2 w = tw[p * st];
+            if (inverse) w.y = -w.y;
+            Y[g * L + q + 2 * st * p] = cadd(a, c);
+            Y[g * L + q + 2 * st * p + st] = cmul(csub(a, c), w);
+        }
+        __syncthreads();
+        float2* tmp = X;
+        X = Y;
+        Y = tmp;
+        st <<= 1;
+    }
+    for (int t = threadIdx.x; t < G * L; t += blockDim.x) {
+        const int g = ALONG_Y ? t % G : t / L;
+        const int i = ALONG_Y ? t / G : t % L;
+        const long long l = l0 + g;
+        if (l < nlines) data[addr(l, i)] = X[g * L + i];
+    }
+}
+
+// dn of every fluid node as a complex field (gap planes give 0)
+__global__ void k_tail_pack(Params P, const float* __restrict__ dn, float2* __restrict__ A)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const Geom& g = P.g;
+    if (idx >= g.N) return;
+    const int x = (int)(idx % g.nx);
+    const long long r = idx / g.nx;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    const float v = P.zslit[z] >= 0 ? dn[padded(g, x, y, z)] : 0.f;
+    A[idx] = make_float2(v, 0.f);
+}
+
+// T^(k, z) = sum_dz conj(Kh_c(k, dz)) A(k, z + dz) for 32 modes (one CTA row)
+// and a chunk of ZC planes; A and Kh staged in shared memory. Output
+// O1 = T^_x + i T^_y, O2 = T^_z. Planes outside the grid read 0 (walls) or
+// their periodic image.
+constexpr int ZC = 64, ZB = 8;
+
+__global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ A, const float2* __restrict__ Kh,
+                                                    float2* __restrict__ O1, float2* __restrict__ O2,
+                                                    long long nxy, int nz, int D, int zper)
+{
+    extern __shared__ float2 zsm[];
+    float2* slab = zsm;                      // (ZC + 2D) x 32
+    float2* kh = zsm + (ZC + 2 * D) * 32;    // (2D + 1) x 3 x 32
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const long long col = (long long)blockIdx.x * 32 + tx;
+    const int z0 = blockIdx.y * ZC;
+    for (int r = ty; r < ZC + 2 * D; r += 8) {
+        int z = z0 - D + r;
+        float2 v = make_float2(0.f, 0.f);
+        if (zper) {
+            z %= nz;
+            if (z < 0) z += nz;
+            v = A[(long long)z * nxy + col];
+        } else if (z >= 0 && z < nz) {
+            v = A[(long long)z * nxy + col];
+        }
+        slab[r * 32 + tx] = v;
+    }
+    for (int r = ty; r < (2 * D + 1) * 3; r += 8) kh[r * 32 + tx] = Kh[(long long)r * nxy + col];
+    __syncthreads();
+    for (int zb = ty * ZB; zb < ZC; zb += 8 * ZB) {
+        float2 acc[ZB][3];
+#pragma unroll
+        for (int j = 0; j < ZB; ++j)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[j][c] = make_float2(0.f, 0.f);
+        for (int d = 0; d <= 2 * D; ++d) {
+            float2 k[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) k[c] = kh[(d * 3 + c) * 32 + tx];
+#pragma unroll
+            for (int j = 0; j < ZB; ++j) {
+                const float2 a = slab[(zb + j + d) * 32 + tx];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    // conj(k) * a
+                    acc[j][c].x += k[c].x * a.x + k[c].y * a.y;
+                    acc[j][c].y += k[c].x * a.y - k[c].y * a.x;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < ZB; ++j) {
+            const int z = z0 + zb + j;
+            if (z >= nz) break;
+            O1[(long long)z * nxy + col] = make_float2(acc[j][0].x - acc[j][1].y, acc[j][0].y + acc[j][1].x);
+            O2[(long long)z * nxy + col] = acc[j][2];
+        }
+    }
+}
+
+// Ft = n0 m T for the nodes of unfrozen slits
+__global__ void k_tail_finish(Params P, const float* __restrict__ dn, const float2* __restrict__ O1,
+                              const float2* __restrict__ O2, const float* __restrict__ w, float4* __restrict__ Ft)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const Geom& g = P.g;
+    if (idx >= g.N) return;
+    const int x = (int)(idx % g.nx);
+    const long long r = idx / g.nx;
+    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
+    const int s = P.zslit[z];
+    if (s < 0 || P.done[s]) return;
+    const float inv = 1.f / ((float)g.nx * (float)g.ny);
+    const float pre = P.sl[s].rho0 * (1.f + dn[padded(g, x, y, z)]);
+    const float2 a = O1[idx], b = O2[idx];
+    Ft[idx] = make_float4(pre * (a.x * inv), pre * (a.y * inv), pre * (b.x * inv + w[z]), 0.f);
+}
+
+inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+int ilog2(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+cudaError_t fft_pass(float2* data, int L, int nx, long long nlines, bool along_y, const float2* tw, int inverse,
+                     cudaStream_t s)
+{
+    const int G = FFT_GL / L;
+    const size_t smem = sizeof(float2) * 2 * FFT_GL;
+    const unsigned blocks = nblk(nlines, G);
+    if (along_y)
+        k_fft<true><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), nx, nlines, tw, inverse);
+    else
+        k_fft<false><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), nx, nlines, tw, inverse);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tail_spectral_ok(const Geom& g)
+{
+    auto pow2 = [](int v) { return v >= 2 && (v & (v - 1)) == 0; };
+    return pow2(g.nx) && pow2(g.ny) && g.nx <= 1024 && g.ny <= 1024 && (long long)g.nx * g.ny >= 32;
+}
+
+size_t tail_spectral_bytes(const Geom& g, int D)
+{
+    const size_t nxy = (size_t)g.nx * g.ny;
+    return sizeof(float2) * (3 * nxy * (size_t)g.nz + (size_t)(2 * D + 1) * 3 * nxy + g.nx / 2 + g.ny / 2 +
+                             (g.nz + 1) / 2);
+}
+
+// Layout of the work buffer: A, O1, O2 (nz nx ny complex each), Kh
+// ((2D+1) x 3 x ny x nx), the twiddles of nx and of ny, then w (nz floats).
+cudaError_t tail_spectral_init(const Geom& g, int D, const int* pdx, const int* pdy, const int* pdz,
+                               const float4* K, int npairs, const int* zslit, float2* work, cudaStream_t s)
+{
+    const long long nxy = (long long)g.nx * g.ny;
+    float2* Kh = work + 3 * nxy * g.nz;
+    float2* twx = Kh + (long long)(2 * D + 1) * 3 * nxy;
+    float2* twy = twx + g.nx / 2;
+    std::vector<float2> tx(g.nx / 2), ty(g.ny / 2);
+    for (int j = 0; j < g.nx / 2; ++j)
+        tx[j] = make_float2((float)cos(-2.0 * M_PI * j / g.nx), (float)sin(-2.0 * M_PI * j / g.nx));
+    for (int j = 0; j < g.ny / 2; ++j)
+        ty[j] = make_float2((float)cos(-2.0 * M_PI * j / g.ny), (float)sin(-2.0 * M_PI * j / g.ny));
+    // the full odd kernel on the periodic x-y grid, one slice per dz and component
+    std::vector<float2> host((size_t)(2 * D + 1) * 3 * nxy, make_float2(0.f, 0.f));
+    std::vector<double> acc((size_t)(2 * D + 1) * 3 * nxy, 0.0);
+    auto put = [&](int dx, int dy, int dz, int c, double v) {
+        const int x = ((dx % g.nx) + g.nx) % g.nx, y = ((dy % g.ny) + g.ny) % g.ny;
+        acc[((size_t)(dz + D) * 3 + c) * nxy + (size_t)y * g.nx + x] += v;
+    };
+    for (int k = 0; k < npairs; ++k) {
+        const double kv[3] = {K[k].x, K[k].y, K[k].z};
+        for (int c = 0; c < 3; ++c) {
+            put(pdx[k], pdy[k], pdz[k], c, kv[c]);
+            put(-pdx[k], -pdy[k], -pdz[k], c, -kv[c]);
+        }
+    }
+    for (size_t i = 0; i < host.size(); ++i) host[i] = make_float2((float)acc[i], 0.f);
+    // w(z): the x,y-uniform response to the fluid indicator, in double
+    std::vector<double> kappa(2 * D + 1, 0.0);
+    for (int k = 0; k < npairs; ++k) {
+        kappa[pdz[k] + D] += K[k].z;
+        kappa[-pdz[k] + D] -= K[k].z;
+    }
+    std::vector<float> wz(g.nz);
+    for (int z = 0; z < g.nz; ++z) {
+        double a = 0.0;
+        for (int d = -D; d <= D; ++d) {
+            int zz = z + d;
+            if (g.zper) {
+                zz %= g.nz;
+                if (zz < 0) zz += g.nz;
+            } else if (zz < 0 || zz >= g.nz) {
+                continue;
+            }
+            if (zslit[zz] >= 0) a += kappa[d + D];
+        }
+        wz[z] = (float)a;
+    }
+    float* wdev = reinterpret_cast<float*>(twy + g.ny / 2);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(twx, tx.data(), sizeof(float2) * tx.size(), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(twy, ty.data(), sizeof(float2) * ty.size(), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(Kh, host.data(), sizeof(float2) * host.size(), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaMemcpyAsync(wdev, wz.data(), sizeof(float) * wz.size(), cudaMemcpyHostToDevice, s))) return e;
+    if ((e = cudaFuncSetAttribute(k_tail_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float2) * ((ZC + 2 * D) * 32 + (2 * D + 1) * 3 * 32)))))
+        return e;
+    const long long slices = (long long)(2 * D + 1) * 3;
+    if ((e = fft_pass(Kh, g.nx, g.nx, slices * g.ny, false, twx, 0, s))) return e;
+    if ((e = fft_pass(Kh, g.ny, g.nx, slices * g.nx, true, twy, 0, s))) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t launch_tail_spectral(const Params& P, const float* dn, int D, float2* work, float4* Ft, cudaStream_t s)
+{
+    const Geom& g = P.g;
+    const long long nxy = (long long)g.nx * g.ny;
+    float2* A = work;
+    float2* O1 = A + nxy * g.nz;
+    float2* O2 = O1 + nxy * g.nz;
+    float2* Kh = O2 + nxy * g.nz;
+    float2* twx = Kh + (long long)(2 * D + 1) * 3 * nxy;
+    float2* twy = twx + g.nx / 2;
+    cudaError_t e;
+    k_tail_pack<<<nblk(g.N, 256), 256, 0, s>>>(P, dn, A);
+    if ((e = cudaGetLastError())) return e;
+    if ((e = fft_pass(A, g.nx, g.nx, (long long)g.ny * g.nz, false, twx, 0, s))) return e;
+    if ((e = fft_pass(A, g.ny, g.nx, (long long)g.nx * g.nz, true, twy, 0, s))) return e;
+    const size_t zs = sizeof(float2) * ((ZC + 2 * D) * 32 + (2 * D + 1) * 3 * 32);
+    dim3 grid((unsigned)(nxy / 32), (unsigned)((g.nz + ZC - 1) / ZC));
+    k_tail_zconv<<<grid, 256, zs, s>>>(A, Kh, O1, O2, nxy, g.nz, D, g.zper);
+    if ((e = cudaGetLastError())) return e;
+    for (float2* O : {O1, O2}) {
+        if ((e = fft_pass(O, g.ny, g.nx, (long long)g.nx * g.nz, true, twy, 1, s))) return e;
+        if ((e = fft_pass(O, g.nx, g.nx, (long long)g.ny * g.nz, false, twx, 1, s))) return e;
+    }
+    const float* w = reinterpret_cast<const float*>(twy + g.ny / 2);
+    k_tail_finish<<<nblk(g.N, 256), 256, 0, s>>>(P, dn, O1, O2, w, Ft);
+    return cudaGetLastError();
+}
+
+}  // namespace lbif

@@ -128,6 +128,18 @@ cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const 
 // group: edge (nodes) of the x-y block the resident CTAs sweep together (<= 0: default)
 cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F, int group,
                          cudaStream_t s);
+// ---- spectral tail (lbif_fft.cu) -------------------------------------------
+// usable when nx and ny are powers of two in [2, 1024] and nx ny >= 32
+bool tail_spectral_ok(const Geom& g);
+// bytes of the work buffer for a kernel reaching D planes in z
+size_t tail_spectral_bytes(const Geom& g, int D);
+// transform the tail kernel (pairs +-d with displacements pdx, pdy, pdz and
+// vector weights K) into the work buffer; synchronises s
+cudaError_t tail_spectral_init(const Geom& g, int D, const int* pdx, const int* pdy, const int* pdz,
+                               const float4* K, int npairs, const int* zslit, float2* work, cudaStream_t s);
+// Ft = the tail force / n0 from the density deviation field dn (padded)
+cudaError_t launch_tail_spectral(const Params& P, const float* dn, int D, float2* work, float4* Ft,
+                                 cudaStream_t s);
 cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields& f,
                       const float4* F, cudaStream_t s);
 cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s);

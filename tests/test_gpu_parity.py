@@ -195,9 +195,16 @@ def test_fp16_storage_velocity_profile(L, O):
     assert nerr(uxg, uxo) < 1e-3
 
 
-def test_tail_parity(L, O):
-    g, o = make_pair(L, O, 26, 22, 28, 4, 0.2, 0.9, fields_seed=5, body=(1e-5, 0, 0), tail=True,
-                     eps=1.0, rcut=2.5)
+@pytest.mark.parametrize("shape,sigma,zper", [
+    ((26, 22, 28), 4, False),   # direct pair sum (lateral extents not powers of two)
+    ((32, 16, 28), 4, False),   # spectral in x, y, direct in z between walls
+    ((16, 16, 20), 4, True),    # spectral, periodic z
+    ((32, 32, 48), 8, False),   # spectral, sigma = 8 (reach 20 planes)
+])
+def test_tail_parity(L, O, shape, sigma, zper):
+    nx, ny, nz = shape
+    g, o = make_pair(L, O, nx, ny, nz, sigma, 0.2, 0.9, fields_seed=5, body=(1e-5, 0, 0), tail=True,
+                     eps=1.0, rcut=2.5, periodic_z=zper)
     Fg = g.forces()
     Fo, _ = o.forces()
     Fo = Fo / o.n0
