@@ -258,6 +258,23 @@ def mlp_leg(args):
             "frac": tf / peak, "note": "4 products per forward, host-synchronised call (includes launch and sync)"}
 
 
+def tail_leg(args):
+    """The attractive-tail workload's shape: 256 x 256 x 128 slit, sigma = 8,
+    LJ tail eps = 1 cut at 2.5 sigma, tau = 0.8, F_e = 1e-6; eta = 0.25 (the
+    kernels' cost does not depend on eta; 0.40 is beyond the scheme's
+    stability at sigma = 8). Per-kernel CUDA-event times of 20 steps."""
+    from paper_0712_2247_gb300 import lbif
+
+    g = lbif.Slit(256, 256, 128, 8, 0.25, 0.8, body=(1e-6, 0, 0), tail=True, eps=1.0, rcut=2.5, seed=1)
+    g.step(3)
+    kms, nl = g.step_profiled(20)
+    g.close()
+    per = {k: kms[k] / nl[k] for k in kms if nl[k]}
+    ms = sum(per.values())
+    return {"workload": "slit 256x256x128 sigma=8 eta=0.25 tau=0.8 F_e=1e-6, LJ tail eps=1 rcut=2.5 sigma",
+            "ms_per_step": ms, "mlups": 256 * 256 * 128 / (ms * 1e-3) / 1e6, "kernels_ms": per}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -365,6 +382,12 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, _, _, _ = cpu_sample(args.cpu_seconds)
+    tail = None
+    if not args.no_tail and world == 1:
+        try:
+            tail = tail_leg(args)
+        except Exception as e:
+            tail = {"error": f"{type(e).__name__}: {e}"}
     mlp = None
     if not args.no_mlp and world == 1:
         try:
@@ -404,6 +427,7 @@ def run_ours(args, world, rank, local):
                      "bytes_alg_per_launch": dom_bytes},
         "cpu_baseline": cpu,
         "ensemble": ens,
+        "tail_workload": tail,
         "mlp_forward": mlp,
         "warm_start": warm,
         "e2e": e2e,
@@ -427,6 +451,7 @@ def main():
     ap.add_argument("--no-warm-start", action="store_true", help="skip the warm vs cold study")
     ap.add_argument("--no-ensemble", action="store_true", help="skip the batched-ensemble throughput")
     ap.add_argument("--no-mlp", action="store_true", help="skip the tensor-core forward throughput")
+    ap.add_argument("--no-tail", action="store_true", help="skip the attractive-tail workload")
     ap.add_argument("--mlp-batch", type=int, default=65536, help="rows of the tensor-core forward leg")
     ap.add_argument("--ens-steps", type=int, default=2000, help="timed steps of the ensemble leg")
     ap.add_argument("--ws-train", type=int, default=4096, help="training slits of the warm-start leg")
