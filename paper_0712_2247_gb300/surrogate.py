@@ -248,8 +248,8 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description="train the warm-start network and compare warm and cold starts")
     ap.add_argument("--train", type=int, default=20000, help="training slits (thin 4x4xH)")
     ap.add_argument("--heldout", type=int, default=512)
-    ap.add_argument("--steps", type=int, default=8000, help="Adam steps")
-    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=20000, help="Adam steps")
+    ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--cache", default=None, help="directory for the generated profiles and weights")
     ap.add_argument("--eval-nx", type=int, default=32)
     ap.add_argument("--max-steps", type=int, default=400000)
