@@ -210,7 +210,7 @@ def ensemble_leg(args):
 
     p = inputs.ensemble(256, seed=3)
     e = lbif.Ensemble(p.H, p.eta, p.F, p.tau, p.sigma, p.nx, p.ny, storage=lbif.STORE_F16, seed=3)
-    ball, group = e.autotune(trials=3)
+    ball, group, staging = e.autotune(trials=3)
     e.run(tol=1e-300, max_steps=200, check_every=100)  # builds the graph
     steps = args.ens_steps
     torch.cuda.synchronize()
@@ -222,7 +222,8 @@ def ensemble_leg(args):
     e.close()
     return {"workload": "256 slits 32x32xH, sigma=4, FP16 storage, graph-captured steps",
             "fluid_nodes": fluid, "stacked_nodes": e.N, "steps": steps, "seconds": dt,
-            "mlups_fluid": fluid * steps / dt / 1e6, "autotuned": {"ball_ctas": ball, "force_group": group}}
+            "mlups_fluid": fluid * steps / dt / 1e6, "autotuned": {"ball_ctas": ball, "force_group": group,
+                                                        "ball_staging": "tma" if staging else "loads"}}
 
 
 def mlp_leg(args):

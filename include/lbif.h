@@ -177,10 +177,13 @@ int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int32_t check_e
 int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax);
 
 /* Time the candidate launch shapes of the ball and force kernels on this
- * handle's current state (trials launches each) and keep the fastest. The
- * state is unchanged. Chosen values (may be NULL): ball CTA target, force
- * tile-group edge in nodes. */
-int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group);
+ * handle's current state (trials launches each) and keep the fastest: the
+ * ball kernel's CTA target and its plane staging (1 = tensor-memory-
+ * accelerator copies, 0 = plain loads), the force kernel's tile-group edge.
+ * The state is unchanged. Chosen values (each may be NULL): ball CTA target,
+ * force tile-group edge in nodes, ball staging. */
+int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group,
+                  int32_t* ball_staging);
 
 /* ---- warm-start network -------------------------------------------------
  * A multilayer perceptron nin -> nhidden layers of width `hidden` (GELU, erf

@@ -57,6 +57,7 @@ struct lbif_ctx {
     int ball_want = 0, force_group = 0;  // launch shapes (0 = defaults; set by the autotuner)
     CUtensorMap ball_map[2];             // tensor maps of dn[0], dn[1] for the ball kernel's tiles
     bool ball_map_ok = false;
+    bool ball_tma = true;                // stage the ball tiles with the maps (autotuner's choice)
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     int64_t t = 0;
@@ -123,7 +124,10 @@ static bool make_ball_map(const Geom& g, int sigma, float* base, CUtensorMap* ou
 }
 
 // the map of the buffer the ball kernel reads (dn[i]), or NULL
-static const CUtensorMap* ball_map(const lbif_ctx* h, int i) { return h->ball_map_ok ? &h->ball_map[i] : nullptr; }
+static const CUtensorMap* ball_map(const lbif_ctx* h, int i)
+{
+    return h->ball_map_ok && h->ball_tma ? &h->ball_map[i] : nullptr;
+}
 
 // tail force of the density field dn: spectral in x, y when available
 static cudaError_t run_tail(lbif_ctx* h, const float* dn)
@@ -1071,7 +1075,8 @@ extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int3
 // Time each candidate launch shape on the handle's own state and keep the
 // fastest: the ball kernel's CTA target (z-chunking) and the force kernel's
 // tile-group edge. The state is saved and restored around the trials.
-extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group)
+extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group,
+                             int32_t* ball_staging)
 {
     if (!h || trials < 1) return fail(h, LBIF_ERR_ARG, "lbif_autotune: bad arguments");
     const Params& P = h->P;
@@ -1084,23 +1089,30 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
     const int groups[] = {64, 128, 256, 1 << 20};
     float best = 1e30f;
     int best_ball = 0, best_group = 0;
+    bool best_tma = h->ball_map_ok;
     float* dnew = h->dn[h->dcur ^ 1];
     // the ball kernel writes dG only; the force kernel writes F only: both
-    // are pure functions of the current fields, so trials change no state
-    for (int b : balls) {
-        float tot = 0.f;
-        for (int k = 0; k < trials + 1; ++k) {
-            CK(h, cudaEventRecord(e0, h->stream));
-            CK(h, launch_ball(P, dnew, h->dG, h->status_d, b, 0, h->stream, ball_map(h, h->dcur ^ 1)));
-            CK(h, cudaEventRecord(e1, h->stream));
-            CK(h, cudaEventSynchronize(e1));
-            float ms;
-            CK(h, cudaEventElapsedTime(&ms, e0, e1));
-            if (k) tot += ms;
-        }
-        if (tot < best) {
-            best = tot;
-            best_ball = b;
+    // are pure functions of the current fields, so trials change no state.
+    // Ball candidates: CTA target x plane staging (tensor-memory-accelerator
+    // copies when the handle has tensor maps, plain loads).
+    for (int staging = h->ball_map_ok ? 1 : 0; staging >= 0; --staging) {
+        const CUtensorMap* tm = staging ? &h->ball_map[h->dcur ^ 1] : nullptr;
+        for (int b : balls) {
+            float tot = 0.f;
+            for (int k = 0; k < trials + 1; ++k) {
+                CK(h, cudaEventRecord(e0, h->stream));
+                CK(h, launch_ball(P, dnew, h->dG, h->status_d, b, 0, h->stream, tm));
+                CK(h, cudaEventRecord(e1, h->stream));
+                CK(h, cudaEventSynchronize(e1));
+                float ms;
+                CK(h, cudaEventElapsedTime(&ms, e0, e1));
+                if (k) tot += ms;
+            }
+            if (tot < best) {
+                best = tot;
+                best_ball = b;
+                best_tma = staging != 0;
+            }
         }
     }
     best = 1e30f;
@@ -1124,12 +1136,14 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
     cudaEventDestroy(e1);
     h->ball_want = best_ball;
     h->force_group = best_group;
+    h->ball_tma = best_tma;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
     }
     if (ball_want) *ball_want = best_ball;
     if (force_group) *force_group = best_group;
+    if (ball_staging) *ball_staging = best_tma ? 1 : 0;
     return check_status(h);
 }
 

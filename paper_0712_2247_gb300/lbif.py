@@ -66,7 +66,7 @@ SIGNATURES = {
     "lbif_batch_seed": (_i32, [_vp, _vp, _vp, _i32]),
     "lbif_batch_run": (_i32, [_vp, _f64, _i64, _i32, _i32, ctypes.POINTER(_i64), _pd]),
     "lbif_batch_profiles": (_i32, [_vp, _pd, _pd, _i32]),
-    "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "lbif_field_profiles_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _pd, _pd, _pd, _vp]),
     "lbif_noalloc_last_error": (ctypes.c_char_p, []),
     "lbif_destroy": (_i32, [_vp]),
@@ -306,6 +306,10 @@ class Ensemble(Slit):
         return n, ux
 
     def autotune(self, trials: int = 3):
-        b, g = ctypes.c_int32(), ctypes.c_int32()
-        self._check(self._lib.lbif_autotune(self._h, int(trials), ctypes.byref(b), ctypes.byref(g)))
-        return b.value, g.value
+        """Pick the fastest launch shapes on the current state; returns (ball CTA
+        target, force tile-group edge, ball staging: 1 tensor-memory accelerator,
+        0 plain loads)."""
+        b, g, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.lbif_autotune(self._h, int(trials), ctypes.byref(b), ctypes.byref(g),
+                                            ctypes.byref(st)))
+        return b.value, g.value, st.value
