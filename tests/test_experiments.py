@@ -93,3 +93,77 @@ def test_static_profile_matches_oracle_and_balances_forces(oracle_mod):
     # exact discrete balances of the steady state, to FP32 rounding
     assert r["force_balance"] < 1e-4
     assert r["uz_relation"] < 1e-4
+
+
+def _figures():
+    import json
+    import os
+
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_figure_parameters.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.gpu
+def test_fig1_collisional_viscosity_is_lhp_and_below_enskog():
+    """Fig. 1: the transverse-wave viscosity of the method, less the BGK part
+    c_s^2 (tau - 1/2), is the Longuet-Higgins-Pople collisional viscosity and
+    lies below the Enskog value (coefficients printed in the caption)."""
+    from paper_0712_2247_gb300.experiments import g2_printed, nu_closed_form, shear_decay
+
+    fig = _figures()["fig1_shear_viscosity"]
+    sigma, tau = 8, 0.8
+    for eta in (0.10, 0.20, 0.30):
+        n_star = 6 * eta / math.pi
+        nu_coll = shear_decay(sigma, eta, tau, L=128)["nu"] - (tau - 0.5) / 3
+        lhp = nu_closed_form(sigma, eta, tau) - (tau - 0.5) / 3
+        # Enskog, per unit mass density m n = n* / sigma^3 (m = 1, kT = 1/3)
+        eta_e = 5 / (16 * sigma ** 2) * math.sqrt(1 / (3 * math.pi)) * (
+            fig["a1"] * 2 * math.pi / 3 * n_star + fig["a2"] * g2_printed(eta) * 4 * math.pi ** 2 / 9 * n_star ** 2)
+        enskog = eta_e / (n_star / sigma ** 3)
+        assert abs(nu_coll / lhp - 1) < 1e-2, (eta, nu_coll, lhp)
+        assert nu_coll < enskog, (eta, nu_coll, enskog)
+
+
+@pytest.mark.gpu
+def test_fig3_streaming_slows_and_layers_with_density():
+    """Fig. 3 (L = 10 sigma, the caption's five densities, sigma = 8): the
+    mean streaming velocity falls as the density rises, the contact density
+    rises, and the current n u_x is monotonic next to the walls at the two
+    lowest densities but develops a non-monotonic structure at the higher ones."""
+    from paper_0712_2247_gb300.experiments import poiseuille_profiles
+
+    fig = _figures()["fig3_poiseuille"]
+    r = poiseuille_profiles(fig["n_star_bulk"], fig["L_over_sigma"], F=fig["F_e_reading"])
+    mean_u = [float(np.mean(s["ux"])) for s in r]
+    contact = [s["n_over_n0"][0] for s in r]
+    assert all(a > b for a, b in zip(mean_u, mean_u[1:])), mean_u
+    assert all(a < b for a, b in zip(contact, contact[1:])), contact
+    for s in r:
+        J = np.array(s["n_over_n0"]) * np.array(s["ux"])
+        rises = np.all(np.diff(J[: s["H"] // 2]) > 0)
+        assert rises == (s["n_star"] < 0.2), s["n_star"]
+
+
+@pytest.mark.gpu
+def test_fig4_centre_parabolic_walls_structured():
+    """Fig. 4 (n* = 0.512, L = 5, 10, 15, 20 sigma): the central half of the
+    streaming profile is close to a parabola, more so for wider slits, and
+    the deviation from that parabola next to the walls grows as the slit
+    narrows."""
+    from paper_0712_2247_gb300.experiments import poiseuille_profiles
+
+    fig = _figures()["fig4_widths"]
+    widths = sorted(fig["L_over_sigma"])
+    r = poiseuille_profiles([fig["n_star_bulk"]] * len(widths), widths, F=2.4e-6)
+    centre, wall = [], []
+    for s in r:
+        u = np.array(s["ux"])
+        h = s["H"]
+        z = np.arange(h) - (h - 1) / 2
+        c = np.abs(z) < h / 4
+        fit = np.polyval(np.polyfit(z[c], u[c], 2), z)
+        centre.append(np.abs(fit[c] - u[c]).max() / u.max())
+        wall.append(np.abs(fit[~c] - u[~c]).max() / u.max())
+    assert all(a > b for a, b in zip(centre, centre[1:])), centre
+    assert all(a > b for a, b in zip(wall, wall[1:])), wall
+    assert max(centre[1:]) < 0.02
