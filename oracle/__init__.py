@@ -69,6 +69,8 @@ def _load():
             "or_init_fields": (None, [vp, _D, _D, _D, _D]),
             "or_step": (None, [vp, ctypes.c_long]),
             "or_step_lagged": (None, [vp, ctypes.c_long]),
+            "or_set_c2": (None, [vp, ctypes.c_int]),
+            "or_c2_field": (None, [vp, _D]),
             "or_moments": (None, [vp, _D, _D, _D, _D, _D]),
             "or_forces": (None, [vp, _D, _D, _D, _D]),
             "or_profiles": (None, [vp, _D, _D]),
@@ -191,7 +193,7 @@ class Oracle:
 
     def __init__(self, nx, ny, nz, sigma, eta, tau, *, zper=False, body=(0.0, 0.0, 0.0),
                  hs=True, coupling=True, regularize=True, g2form=0, tail=False, eps=1.0,
-                 rcut=2.5, seed=None, noise=1e-3, offset=0):
+                 rcut=2.5, seed=None, noise=1e-3, offset=0, c2=False):
         lib = _load()
         b = _f64(body, 3)
         self._lib = lib
@@ -204,6 +206,14 @@ class Oracle:
             raise ValueError("oracle: invalid parameters")
         if seed is not None:
             lib.or_init_noise(self._h, int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), int(offset))
+        if c2:
+            lib.or_set_c2(self._h, 1)
+
+    def c2_field(self):
+        """The energy source of Eq. C2eq (constant T) of the current state."""
+        out = np.zeros(self.shape)
+        self._lib.or_c2_field(self._h, _p(out))
+        return out
 
     def close(self):
         if self._h:

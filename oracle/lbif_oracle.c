@@ -227,10 +227,13 @@ static double regulariser(const geom* g, int z, int sigma, int on)
  *   F(r) = -kT sigma^2 4pi sum_q W_q s_q G(r + sigma s_q/2) n(r) n(r + sigma s_q)
  *          x [1 - lambda(z) (2/(v_T sqrt(pi))) s_q.(u(r + sigma s_q) - u(r))]
  * with G the g2 field built from nbar. Also returns the local collisional
- * pressure (trace of the static part, divided by 3) when p != NULL.        */
+ * pressure (trace of the static part, divided by 3) when p != NULL, and,
+ * when C2 != NULL, the energy source of Eq. C2eq at constant T,
+ *   C2(r) = kT sigma^2 4pi sum_q W_q G(r + sigma s_q/2) n(r) n(r + sigma s_q)
+ *           x ( - s_q.(u(r + sigma s_q) - u(r)) / 2 ).                      */
 static void hs_force(const geom* g, int sigma, double kT, int coupling, int regularize,
                      const double* n, const double* ux, const double* uy, const double* uz,
-                     const double* G, double* Fx, double* Fy, double* Fz, double* pc)
+                     const double* G, double* Fx, double* Fy, double* Fz, double* pc, double* C2)
 {
     const double vT = sqrt(kT);
     const double kappa = 2.0 / (vT * sqrt(M_PI));
@@ -241,20 +244,22 @@ static void hs_force(const geom* g, int sigma, double kT, int coupling, int regu
     for (long id = 0; id < N; ++id) {
         int x = (int)(id % g->nx), y = (int)((id / g->nx) % g->ny), z = (int)(id / ((long)g->nx * g->ny));
         double lam = regulariser(g, z, sigma, regularize);
-        double fx = 0.0, fy = 0.0, fz = 0.0, ps = 0.0;
+        double fx = 0.0, fy = 0.0, fz = 0.0, ps = 0.0, c2 = 0.0;
         for (int q = 0; q < NS; ++q) {
             double px = x + s * sdir[q][0], py = y + s * sdir[q][1], pz = z + s * sdir[q][2];
             double mx = x + 0.5 * s * sdir[q][0], my = y + 0.5 * s * sdir[q][1], mz = z + 0.5 * s * sdir[q][2];
             double nq = interp(g, n, px, py, pz);
             double Gq = interp(g, G, mx, my, mz);
             double bracket = 1.0;
-            if (coupling) {
-                double du = sdir[q][0] * (interp(g, ux, px, py, pz) - ux[id])
-                          + sdir[q][1] * (interp(g, uy, px, py, pz) - uy[id])
-                          + sdir[q][2] * (interp(g, uz, px, py, pz) - uz[id]);
-                bracket -= lam * kappa * du;
+            double du = 0.0;
+            if (coupling || C2) {
+                du = sdir[q][0] * (interp(g, ux, px, py, pz) - ux[id])
+                   + sdir[q][1] * (interp(g, uy, px, py, pz) - uy[id])
+                   + sdir[q][2] * (interp(g, uz, px, py, pz) - uz[id]);
             }
+            if (coupling) bracket -= lam * kappa * du;
             double t = swt[q] * Gq * n[id] * nq;
+            c2 += t * (-0.5 * du);
             fx += sdir[q][0] * t * bracket;
             fy += sdir[q][1] * t * bracket;
             fz += sdir[q][2] * t * bracket;
@@ -265,6 +270,7 @@ static void hs_force(const geom* g, int sigma, double kT, int coupling, int regu
         Fz[id] = -pref * fz;
         /* P^c_aa/3 = (kT sigma^3/6) 4pi sum_q W_q G_q n n_q (static part) */
         if (pc) pc[id] = kT * s * s * s / 6.0 * 4.0 * M_PI * ps;
+        if (C2) C2[id] = pref * c2;
     }
 }
 
@@ -344,6 +350,8 @@ typedef struct {
     double *n, *ux, *uy, *uz;         /* moments */
     double *nbar, *G, *Fx, *Fy, *Fz, *pc;
     double *Lx, *Ly, *Lz;             /* lagged force (variant), NULL until used */
+    int c2;                           /* energy source of Eq. C2eq on */
+    double* C2f;                      /* its field, NULL until used */
     int lag_ok;                       /* Lx.. hold the force of the previous step */
     long t;
 } or_state;
@@ -377,7 +385,7 @@ void or_destroy(void* h)
     if (!s) return;
     free(s->f); free(s->fn); free(s->n); free(s->ux); free(s->uy); free(s->uz);
     free(s->nbar); free(s->G); free(s->Fx); free(s->Fy); free(s->Fz); free(s->pc);
-    free(s->Lx); free(s->Ly); free(s->Lz);
+    free(s->Lx); free(s->Ly); free(s->Lz); free(s->C2f);
     free(s);
 }
 
@@ -452,8 +460,9 @@ static void compute_forces(or_state* s, int want_pressure)
         double* hx = (double*)malloc(sizeof(double) * N);
         double* hy = (double*)malloc(sizeof(double) * N);
         double* hz = (double*)malloc(sizeof(double) * N);
+        if (s->c2 && !s->C2f) s->C2f = (double*)calloc((size_t)N, sizeof(double));
         hs_force(&s->g, s->sigma, s->kT, s->coupling, s->regularize, s->n, s->ux, s->uy, s->uz,
-                 s->G, hx, hy, hz, s->pc);
+                 s->G, hx, hy, hz, s->pc, s->c2 ? s->C2f : NULL);
         for (long id = 0; id < N; ++id) { s->Fx[id] += hx[id]; s->Fy[id] += hy[id]; s->Fz[id] += hz[id]; }
         free(hx); free(hy); free(hz);
     } else if (want_pressure) {
@@ -474,6 +483,16 @@ static void collide_stream(or_state* s)
         double f[NV], fo[NV], F[3] = {s->Fx[id], s->Fy[id], s->Fz[id]};
         for (int i = 0; i < NV; ++i) f[i] = s->f[(long)i * N + id];
         or_collide_node(f, F, s->tau, fo);
+        if (s->c2 && s->hs) {
+            /* second-order Hermite source of the scalar C2, read as the trace
+             * of an isotropic C2_ab = C2 delta_ab / 3:
+             *   w_i C2 (c_i^2 - 3 kT) / (6 kT^2)                             */
+            const double kT = s->kT;
+            for (int i = 0; i < NV; ++i) {
+                double c2i = (double)(cv[i][0] * cv[i][0] + cv[i][1] * cv[i][1] + cv[i][2] * cv[i][2]);
+                fo[i] += wv[i] * s->C2f[id] * (c2i - 3.0 * kT) / (6.0 * kT * kT);
+            }
+        }
         for (int i = 0; i < NV; ++i) {
             long t = node_at(g, x + cv[i][0], y + cv[i][1], z + cv[i][2]);
             if (t < 0) s->fn[(long)opp[i] * N + id] = fo[i];
@@ -481,6 +500,21 @@ static void collide_stream(or_state* s)
         }
     }
     double* tmp = s->f; s->f = s->fn; s->fn = tmp;
+}
+
+/* switch the energy source of Eq. C2eq (constant T) on or off */
+void or_set_c2(void* h, int on) { ((or_state*)h)->c2 = on; }
+
+/* the C2 field of the current state (NULL-safe: zeros when the source is off) */
+void or_c2_field(void* h, double* out)
+{
+    or_state* s = (or_state*)h;
+    int was = s->c2;
+    s->c2 = 1;
+    compute_moments(s);
+    compute_forces(s, 0);
+    for (long id = 0; id < s->N; ++id) out[id] = s->hs ? s->C2f[id] : 0.0;
+    s->c2 = was;
 }
 
 void or_step(void* h, long nsteps)
@@ -604,7 +638,7 @@ void or_hs_force_fields(int nx, int ny, int nz, int zper, int sigma, int couplin
     or_coarse_density(nx, ny, nz, zper, sigma, n, nbar);
     g2_field(N, sigma, g2form, nbar, Gl);
     hs_force(&g, sigma, 1.0 / 3.0, coupling, regularize, n, ux ? ux : zero, uy ? uy : zero,
-             uz ? uz : zero, Gl, Fx, Fy, Fz, pc);
+             uz ? uz : zero, Gl, Fx, Fy, Fz, pc, NULL);
     if (!G) free(Gl);
     free(nbar);
     free(zero);
