@@ -62,6 +62,11 @@ typedef struct {
     int32_t tail;      /* 1: Lennard-Jones mean-field attractive tail       */
     double  eps;       /* tail well depth (k_B T = 1/3 units)               */
     double  rcut;      /* tail cut-off in units of sigma                    */
+    int32_t c2;        /* 1: energy source of Eq. C2eq at constant T, added
+                          as the isotropic second-order Hermite source
+                          w_i C2 (|c_i|^2 - 3 kT) / (6 kT^2) (no mass, no
+                          momentum; C2 from the same shell quadrature and
+                          interpolants as the force, not regularised)       */
 } lbif_force;
 
 #define LBIF_STORE_F32 0 /* populations stored as FP32 h_i = f_i/(w_i n0) - 1 */

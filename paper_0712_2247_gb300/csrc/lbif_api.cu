@@ -278,6 +278,7 @@ static int check_common(double sigma, const lbif_force& F, const lbif_opts& O, c
     if (F.tail && !(F.rcut >= 1.0 && F.rcut <= 4.0 && F.eps >= 0.0))
         return fail(nullptr, LBIF_ERR_ARG, w + ": tail needs rcut in [1,4] and eps >= 0");
     if ((F.g2_form != 0 && F.g2_form != 1)) return fail(nullptr, LBIF_ERR_ARG, w + ": g2_form must be 0 or 1");
+    if (F.c2 != 0 && F.c2 != 1) return fail(nullptr, LBIF_ERR_ARG, w + ": c2 must be 0 or 1");
     for (int a = 0; a < 3; ++a)
         if (!isfinite(F.body[a])) return fail(nullptr, LBIF_ERR_ARG, w + ": body force not finite");
     return LBIF_OK;
@@ -318,6 +319,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     P.regularize = F.regularize ? 1 : 0;
     P.g2form = F.g2_form;
     P.tail = F.tail ? 1 : 0;
+    P.c2 = F.c2 ? 1 : 0;
     P.storage = O.storage;
     P.nslits = (int)slits.size();
     {

@@ -83,6 +83,7 @@ struct Params {
     float ball_inv;  // 1 / ball node count
     int sigma;
     int hs, coupling, regularize, g2form, tail, storage;
+    int c2;               // energy source of Eq. C2eq on (F.w carries C2 / n0)
     int nslits;
     const SlitParam* sl;  // device table, nslits entries
     const int* zslit;     // device table, nz entries

@@ -37,6 +37,8 @@ __device__ __forceinline__ constexpr float kW(int i)
 {
     return i == 0 ? 1.f / 3.f : (i <= 6 ? 1.f / 18.f : 1.f / 36.f);
 }
+// |c_i|^2 (0, 1 or 2 on D3Q19)
+__device__ __forceinline__ constexpr int kC2(int i) { return kCx(i) * kCx(i) + kCy(i) * kCy(i) + kCz(i) * kCz(i); }
 __device__ __forceinline__ constexpr int opp_of(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
 __device__ __forceinline__ float ldp(const float* p) { return __ldg(p); }
@@ -712,7 +714,7 @@ __device__ __forceinline__ const float* ufield(const Fields& f)
 // generic path: one node per thread, scalar loads (any even sigma)
 template <int A>
 __device__ __forceinline__ void axis_pair(const Params& P, const Fields& fl, int p, const float u0[3],
-                                          float G0, float lk, float f[3])
+                                          float G0, float lk, float f[3], float* cc)
 {
     const int o = P.sh.ax_nb[A], om = P.sh.ax_md[A];
     const float* uf = ufield<A>(fl);
@@ -723,11 +725,13 @@ __device__ __forceinline__ void axis_pair(const Params& P, const Fields& fl, int
     float tp = Ap - (G0 + Ap) * lk * (up - u0[A]);
     float tm = Am - (G0 + Am) * lk * (u0[A] - um);
     f[A] += (1.f / 30.f) * (tp - tm);
+    // Eq. C2eq: sum_q W_q (G_q n_q / n0) s_q.(u_q - u)
+    if (cc) *cc += (1.f / 30.f) * ((G0 + Ap) * (up - u0[A]) + (G0 + Am) * (u0[A] - um));
 }
 
 template <int PL>
 __device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, int p,
-                                             const float u0[3], float G0, float lk, float f[3])
+                                             const float u0[3], float G0, float lk, float f[3], float* cc)
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
@@ -768,6 +772,15 @@ __device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, 
                ((Aq[1] - Aq[3]) - (Pa[1] - Pa[3]) - (Pb[1] - Pb[3]));
     f[a] += (h / 15.f) * da;
     f[b] += (h / 15.f) * db;
+    if (cc) {
+        float t = 0.f;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float sa = (m & 1) ? -1.f : 1.f, sb = (m & 2) ? -1.f : 1.f;
+            t += (G0 + Aq[m]) * h * (sa * (ua[m] - u0[a]) + sb * (ub[m] - u0[b]));
+        }
+        *cc += t / 15.f;
+    }
 }
 
 __device__ __forceinline__ float coupling_factor(const Params& P, const SlitParam& S, int z)
@@ -781,10 +794,11 @@ __device__ __forceinline__ float coupling_factor(const Params& P, const SlitPara
     return lam * P.kappa;
 }
 
-// total force F / n0 at a node (body + hard sphere + tail)
+// total force F / n0 at a node (body + hard sphere + tail), and the energy
+// source of Eq. C2eq over n0 when it is on (0 otherwise)
 __device__ __forceinline__ void node_force(const Params& P, const SlitParam& S, const Fields& fl,
                                            const float4* __restrict__ Ft, long long idx, int z,
-                                           int p, float& fx, float& fy, float& fz)
+                                           int p, float& fx, float& fy, float& fz, float& c2)
 {
     const float d0 = __ldg(fl.dn + p);
     const float u0[3] = {__ldg(fl.ux + p), __ldg(fl.uy + p), __ldg(fl.uz + p)};
@@ -792,20 +806,25 @@ __device__ __forceinline__ void node_force(const Params& P, const SlitParam& S, 
     fx = opd * S.body[0];
     fy = opd * S.body[1];
     fz = opd * S.body[2];
+    c2 = 0.f;
     if (P.hs) {
         const float lk = coupling_factor(P, S, z);
         const float G0 = S.G0;
         float f[3] = {0.f, 0.f, 0.f};
-        axis_pair<0>(P, fl, p, u0, G0, lk, f);
-        axis_pair<1>(P, fl, p, u0, G0, lk, f);
-        axis_pair<2>(P, fl, p, u0, G0, lk, f);
-        diag_quartet<0>(P, fl, p, u0, G0, lk, f);
-        diag_quartet<1>(P, fl, p, u0, G0, lk, f);
-        diag_quartet<2>(P, fl, p, u0, G0, lk, f);
+        float cc = 0.f;
+        float* pc = P.c2 ? &cc : nullptr;
+        axis_pair<0>(P, fl, p, u0, G0, lk, f, pc);
+        axis_pair<1>(P, fl, p, u0, G0, lk, f, pc);
+        axis_pair<2>(P, fl, p, u0, G0, lk, f, pc);
+        diag_quartet<0>(P, fl, p, u0, G0, lk, f, pc);
+        diag_quartet<1>(P, fl, p, u0, G0, lk, f, pc);
+        diag_quartet<2>(P, fl, p, u0, G0, lk, f, pc);
         float pre = S.hs_pref * opd;
         fx += pre * f[0];
         fy += pre * f[1];
         fz += pre * f[2];
+        // C2 / n0 = -(kT sigma^2 4 pi n0 / 2) (1 + dn) sum_q W_q (G_q n_q / n0) s_q.(u_q - u)
+        if (P.c2) c2 = 0.5f * pre * cc;
     }
     if (P.tail) {
         float4 t = Ft[idx];
@@ -833,9 +852,9 @@ __global__ void __launch_bounds__(256) k_force(Params P, TileMap tm, Fields fl,
     if (s < 0 || frozen(P, s)) return;
     const long long idx = ((long long)z * g.ny + y) * g.nx + x;
     const SlitParam S = P.sl[s];
-    float fx, fy, fz;
-    node_force(P, S, fl, Ft, idx, z, pidx(g, x, y, z), fx, fy, fz);
-    F[idx] = make_float4(fx, fy, fz, 0.f);
+    float fx, fy, fz, c2;
+    node_force(P, S, fl, Ft, idx, z, pidx(g, x, y, z), fx, fy, fz, c2);
+    F[idx] = make_float4(fx, fy, fz, c2);
 }
 
 // ---- vectorised path: four consecutive x nodes per thread, float4 loads ----
@@ -971,10 +990,10 @@ __device__ __forceinline__ void member_yz(const Params& P, const Fields& fl, int
     }
 }
 
-template <int SIG, int PL, int M>
+template <int SIG, int PL, int M, bool C2>
 __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, int pb,
                                              const v4 ua0, const v4 ub0, float G0, float lk, v4 Aq,
-                                             v4 Pa, v4 Pb)
+                                             v4 Pa, v4 Pb, v4 Cq)
 {
     constexpr float h = 0.70710678118654752f;
     constexpr float sa = (M & 1) ? -1.f : 1.f, sb = (M & 2) ? -1.f : 1.f;
@@ -991,21 +1010,26 @@ __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, 
         float c = (G0 + Aq[j]) * lk * h;
         Pa[j] = c * (sa * (ua[j] - ua0[j]));
         Pb[j] = c * (sb * (ub[j] - ub0[j]));
+        if constexpr (C2) Cq[j] = (G0 + Aq[j]) * h * (sa * (ua[j] - ua0[j]) + sb * (ub[j] - ub0[j]));
     }
 }
 
-template <int SIG, int PL>
+template <int SIG, int PL, bool C2>
 __device__ __forceinline__ void quartet4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
-                                         float G0, float lk, v4 f[3])
+                                         float G0, float lk, v4 f[3], v4 cc)
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
     constexpr float c = 0.70710678118654752f / 15.f;
-    v4 A0, P0a, P0b, A1, P1a, P1b, A2, P2a, P2b, A3, P3a, P3b;
-    member_terms<SIG, PL, 0>(P, fl, pb, u0[a], u0[b], G0, lk, A0, P0a, P0b);
-    member_terms<SIG, PL, 1>(P, fl, pb, u0[a], u0[b], G0, lk, A1, P1a, P1b);
-    member_terms<SIG, PL, 2>(P, fl, pb, u0[a], u0[b], G0, lk, A2, P2a, P2b);
-    member_terms<SIG, PL, 3>(P, fl, pb, u0[a], u0[b], G0, lk, A3, P3a, P3b);
+    v4 A0, P0a, P0b, A1, P1a, P1b, A2, P2a, P2b, A3, P3a, P3b, C0, C1, C2m, C3;
+    member_terms<SIG, PL, 0, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A0, P0a, P0b, C0);
+    member_terms<SIG, PL, 1, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A1, P1a, P1b, C1);
+    member_terms<SIG, PL, 2, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A2, P2a, P2b, C2m);
+    member_terms<SIG, PL, 3, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A3, P3a, P3b, C3);
+    if constexpr (C2) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cc[j] += (1.f / 15.f) * ((C0[j] + C1[j]) + (C2m[j] + C3[j]));
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         float da = ((A0[j] - A1[j]) - (P0a[j] - P1a[j]) - (P0b[j] - P1b[j])) +
@@ -1017,9 +1041,9 @@ __device__ __forceinline__ void quartet4(const Params& P, const Fields& fl, int 
     }
 }
 
-template <int SIG, int A>
+template <int SIG, int A, bool C2>
 __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
-                                      float G0, float lk, v4 f[3])
+                                      float G0, float lk, v4 f[3], v4 cc)
 {
     const float* uf = ufield<A>(fl);
     v4 dp, dm, up, um, gp, gm;
@@ -1045,13 +1069,14 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
         float tp = Ap - (G0 + Ap) * lk * (up[j] - u0[A][j]);
         float tm = Am - (G0 + Am) * lk * (u0[A][j] - um[j]);
         f[A][j] += (1.f / 30.f) * (tp - tm);
+        if constexpr (C2) cc[j] += (1.f / 30.f) * ((G0 + Ap) * (up[j] - u0[A][j]) + (G0 + Am) * (u0[A][j] - um[j]));
     }
 }
 
 // At most 128 registers, so that four CTAs (16 warps) share an SM: the
 // kernel waits on L1 far more than it computes, and the extra warps hide
 // that latency (measured: 146 registers / 3 CTAs per SM is 6 % slower).
-template <int SIG>
+template <int SIG, bool C2>
 __global__ void __launch_bounds__(128, 4) k_force4(Params P, TileMap tm, Fields fl,
                                                 const float4* __restrict__ Ft, float4* __restrict__ F)
 {
@@ -1075,19 +1100,21 @@ __global__ void __launch_bounds__(128, 4) k_force4(Params P, TileMap tm, Fields 
     set4(u0[0], ld4(fl.ux + pb));
     set4(u0[1], ld4(fl.uy + pb));
     set4(u0[2], ld4(fl.uz + pb));
-    v4 f[3];
+    v4 f[3], cc;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int j = 0; j < 4; ++j) f[a][j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) cc[j] = 0.f;
     if (P.hs) {
         const float lk = coupling_factor(P, S, z);
-        axis4<SIG, 0>(P, fl, pb, u0, S.G0, lk, f);
-        axis4<SIG, 1>(P, fl, pb, u0, S.G0, lk, f);
-        axis4<SIG, 2>(P, fl, pb, u0, S.G0, lk, f);
-        quartet4<SIG, 0>(P, fl, pb, u0, S.G0, lk, f);
-        quartet4<SIG, 1>(P, fl, pb, u0, S.G0, lk, f);
-        quartet4<SIG, 2>(P, fl, pb, u0, S.G0, lk, f);
+        axis4<SIG, 0, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
+        axis4<SIG, 1, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
+        axis4<SIG, 2, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
+        quartet4<SIG, 0, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
+        quartet4<SIG, 1, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
+        quartet4<SIG, 2, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
     }
     const long long idx0 = ((long long)z * g.ny + y) * g.nx + x;
 #pragma unroll
@@ -1104,7 +1131,9 @@ __global__ void __launch_bounds__(128, 4) k_force4(Params P, TileMap tm, Fields 
             fy += t.y;
             fz += t.z;
         }
-        F[idx0 + j] = make_float4(fx, fy, fz, 0.f);
+        // energy source of Eq. C2eq over n0 (when on)
+        const float c2 = C2 && P.hs ? 0.5f * pre * cc[j] : 0.f;
+        F[idx0 + j] = make_float4(fx, fy, fz, c2);
     }
 }
 
@@ -1181,7 +1210,8 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
         for (int i = 0; i < Q; ++i) {
             float k = gi[i] - S;
             float e = eq_excess(i, opd, ux, uy, uz, uu);
-            float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
+            float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z) +
+                       1.5f * f.w * (float)(kC2(i) - 1);
             stp(pout + (long long)i * g.Npad + (idx + P.soff[i]), ks + dd[i]);
         }
         return;
@@ -1190,7 +1220,8 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
     for (int i = 0; i < Q; ++i) {
         float k = gi[i] - S;
         float e = eq_excess(i, opd, ux, uy, uz, uu);
-        float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z);
+        float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z) +
+                       1.5f * f.w * (float)(kC2(i) - 1);
         int tx = x + kCx(i), ty = y + kCy(i), tz = z + kCz(i);
         tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
         ty = ty < 0 ? ty + g.ny : (ty >= g.ny ? ty - g.ny : ty);
@@ -1462,9 +1493,18 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
     if (force_vectorised(P.sigma)) {
         TileMap tm = P.g.nx < 128 ? make_flatmap(P.g, 4, 128, blocks) : make_tilemap(P.g, 128, 4, group, blocks);
         switch (P.sigma) {
-        case 4: k_force4<4><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
-        case 8: k_force4<8><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
-        default: k_force4<12><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F); break;
+        case 4:
+            if (P.c2) k_force4<4, true><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            else k_force4<4, false><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            break;
+        case 8:
+            if (P.c2) k_force4<8, true><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            else k_force4<8, false><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            break;
+        default:
+            if (P.c2) k_force4<12, true><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            else k_force4<12, false><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            break;
         }
     } else {
         TileMap tm = P.g.nx < 32 ? make_flatmap(P.g, 1, 256, blocks) : make_tilemap(P.g, 32, 8, group, blocks);

@@ -38,7 +38,7 @@ class Walls(ctypes.Structure):
 class Force(ctypes.Structure):
     _fields_ = [("body", ctypes.c_double * 3), ("hs", ctypes.c_int32), ("coupling", ctypes.c_int32),
                 ("regularize", ctypes.c_int32), ("g2_form", ctypes.c_int32), ("tail", ctypes.c_int32),
-                ("eps", ctypes.c_double), ("rcut", ctypes.c_double)]
+                ("eps", ctypes.c_double), ("rcut", ctypes.c_double), ("c2", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
@@ -127,10 +127,10 @@ class Slit:
                  periodic_z: bool = False, body: Sequence[float] = (0.0, 0.0, 0.0), hs: bool = True,
                  coupling: bool = True, regularize: bool = True, g2_form: int = 0,
                  tail: bool = False, eps: float = 1.0, rcut: float = 2.5, storage: int = STORE_F32,
-                 seed: int = 0, noise: float = 1e-3, stream: Optional[int] = None):
+                 seed: int = 0, noise: float = 1e-3, stream: Optional[int] = None, c2: bool = False):
         self._lib = load_library()
         f = Force((ctypes.c_double * 3)(*[float(b) for b in body]), int(hs), int(coupling),
-                  int(regularize), int(g2_form), int(tail), float(eps), float(rcut))
+                  int(regularize), int(g2_form), int(tail), float(eps), float(rcut), int(c2))
         o = Opts(int(storage), int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), stream)
         h = _vp()
         rc = self._lib.lbif_create(ctypes.byref(h), Grid(nx, ny, nz), float(sigma), float(eta),

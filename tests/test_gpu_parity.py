@@ -332,3 +332,34 @@ def test_narrow_grid_kernels_bit_identical_to_tiled(L, sigma, wide, storage):
     assert np.array_equal(rb, np.broadcast_to(rb[:, :1, :1], rb.shape))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("shape,sigma", [((20, 18, 24), 4), ((30, 20, 24), 6), ((128, 8, 40), 8)])
+def test_c2_energy_source_parity(L, O, shape, sigma):
+    """The energy source of Eq. C2eq (constant T) against the oracle's: one
+    step and 50 steps from the same flowing state, flat and tiled vectorised
+    force paths (sigma = 4, 8) and the generic one (sigma = 6). The source's
+    own effect (c2 on vs off) is checked to be far above the parity error."""
+    from paper_0712_2247_gb300 import inputs
+
+    nx, ny, nz = shape
+    kw = dict(body=(1e-5, 0, 0), noise=0.0, seed=0)
+    g, o = make_pair(L, O, nx, ny, nz, sigma, 0.2, 0.9, c2=True, **kw)
+    g_off = L.Slit(nx, ny, nz, sigma, 0.2, 0.9, **kw)
+    rho, u = inputs.random_fields((nz, ny, nx), o.n0, 11, amp=0.05, uamp=1e-2)
+    for h in (g, g_off):
+        h.set_fields(rho, u)
+    o.init_fields(rho.astype(np.float64), u.astype(np.float64))
+    for k in (1, 49):
+        g.step(k)
+        g_off.step(k)
+        o.step(k)
+        rg, ug = g.moments()
+        ro, uo = o.moments()
+        r_off, u_off = g_off.moments()
+        e_r, e_u = nerr(rg, ro), nerr(ug, uo)
+        report(f"c2 sigma={sigma} steps={g.t}", rho=e_r, u=e_u, effect_rho=nerr(r_off, ro), effect_u=nerr(u_off, uo))
+        assert e_r < 1e-5 and e_u < 1e-5
+        assert nerr(r_off, ro) > 30 * max(e_r, 1e-7) or nerr(u_off, uo) > 30 * max(e_u, 1e-7)
+    for h in (g, g_off):
+        h.close()
