@@ -95,17 +95,18 @@ def bytes_alg(storage: int):
     return 2 * 19 * s + 44
 
 
-def kernel_bytes(storage: int):
+def kernel_bytes(storage: int, fused: bool):
     """Algorithmic bytes per node moved by each kernel class (each array element
     read or written once; stencil neighbours come from cache):
       moments         19 populations in, reference dn in, {dn,u} + dn out
       ball_g2         dn in, dG out
       tail            dn in, F_tail out
       force           {dn,u} + dG in, F out
-      collide_stream  19 populations in and out, {dn,u}, F and neighbour dn in"""
+      collide_stream  two-pass: 19 populations in and out, {dn,u}, F in;
+                      fused: the same, plus the next {dn,u} out"""
     s = 2 if storage == 1 else 4
     return {"moments": 19 * s + 4 + 20, "ball_g2": 8, "tail": 20, "force": 36,
-            "collide_stream": 2 * 19 * s + 36}
+            "collide_stream": 2 * 19 * s + 32 + (16 if fused else 0)}
 
 
 # DRAM bytes per node (dram__bytes_read.sum + dram__bytes_write.sum) of each
@@ -113,7 +114,8 @@ def kernel_bytes(storage: int):
 # 256x256x192 sigma = 12 slit of the current kernels; a full-size launch moves
 # these bytes times its node count (traffic grows with the nodes). Must be
 # re-measured whenever a kernel changes.
-TRAFFIC_B_PER_NODE_F32 = {"moments": 98.1, "ball_g2": 6.3, "force": 45.7, "collide_stream": 183.8}
+TRAFFIC_B_PER_NODE_F32 = {"moments": 98.1, "ball_g2": 6.3, "force": 45.7, "collide_stream": 183.8,
+                          "collide_stream_fused": None}
 
 
 def dist_setup(args):
@@ -323,6 +325,8 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream()
     g = lbif.Slit(W.nx, W.ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, storage=storage,
                   seed=W.seed + rank, stream=stream.cuda_stream)
+    if args.two_pass:
+        g.set_fused(False)
     N = W.nodes
     # warm-up
     g.step(args.warmup)
@@ -351,7 +355,8 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = _peaks()
     dom = max(kms, key=lambda k: kms[k])
     launches = sum(nl.values())
-    kb = kernel_bytes(storage)
+    kb = kernel_bytes(storage, g.fused)
+    tkey = dom + ("_fused" if dom == "collide_stream" and g.fused else "")
     dom_bytes = kb[dom] * N
     dom_ms = kms[dom] / max(nl[dom], 1)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
@@ -414,7 +419,8 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": f"slit {W.nx}x{W.ny}x{W.nz} sigma={W.sigma} eta={W.eta} tau={W.tau} "
                                f"F_e={W.body[0]} bounce-back z, periodic x,y, seeded 1e-3 noise",
-                   "storage": args.storage, "nodes": N, "parallelism": f"replicas x{world}",
+                   "storage": args.storage, "nodes": N,
+                   "pass": "fused" if g.fused else "two-pass", "parallelism": f"replicas x{world}",
                    "l2": "populations (>= 1.9 GB) exceed L2; no flush",
                    "bytes_alg_per_node": bytes_alg(storage),
                    "step_gbs_alg": step_gbs, "step_roofline_frac": step_gbs / peak,
@@ -422,8 +428,8 @@ def run_ours(args, world, rank, local):
                    "status": status},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind + " hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (TRAFFIC_B_PER_NODE_F32[dom] * N
-                                 if storage == 0 and dom in TRAFFIC_B_PER_NODE_F32 else None),
+                     "traffic": (TRAFFIC_B_PER_NODE_F32[tkey] * N
+                                 if storage == 0 and TRAFFIC_B_PER_NODE_F32.get(tkey) else None),
                      "traffic_unit": "bytes per launch (ncu capture, scaled by nodes)",
                      "bytes_alg_per_launch": dom_bytes},
         "cpu_baseline": cpu,
@@ -458,6 +464,8 @@ def main():
     ap.add_argument("--ws-train", type=int, default=4096, help="training slits of the warm-start leg")
     ap.add_argument("--ws-adam", type=int, default=3000, help="Adam steps of the warm-start leg")
     ap.add_argument("--ws-heldout", type=int, default=128, help="held-out slits of the warm-start leg")
+    ap.add_argument("--two-pass", action="store_true",
+                    help="push collide-stream + moments pass instead of the fused pass")
     ap.add_argument("--grid", default=None,
                     help="override the slit extents NXxNYxNZ (profiling captures on a smaller case)")
     args = ap.parse_args()

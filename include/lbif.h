@@ -99,7 +99,9 @@ int lbif_step(lbif_handle h, int64_t nsteps);
  * the total milliseconds of class k over the nsteps (k = 0 moments, 1 ball +
  * g2, 2 tail, 3 force, 4 collide + stream; classes not launched get 0) and
  * launches[k] the number of launches. nk = length of both arrays (>= 5).
- * Synchronises at the end. Diagnostics for the benchmark. */
+ * With the fused pass (lbif_set_fused) class 4 includes the moments of the
+ * next step and class 0 is launched only when the populations were set from
+ * outside. Synchronises at the end. Diagnostics for the benchmark. */
 int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches,
                        int32_t nk);
 
@@ -180,6 +182,20 @@ int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int32_t check_e
 /* FP64 x,y-averaged profiles of every slit, n_z / ux_z[s*hmax + j] (host
  * arrays, either may be NULL; zero beyond H[s]). Synchronises. */
 int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax);
+
+/* How a step applies collision and streaming (Sec. Methods: BGK collision
+ * with the first-order source, streaming, half-way bounce-back).
+ * fused = 1: one pass per step; each node gathers the populations streaming
+ *   into it (pull form), applies the collision of their source node, and
+ *   forms the moments n, u of the next step from the values it holds. The
+ *   populations are read and written once per step. Default where
+ *   nx >= 32 and ny >= 8.
+ * fused = 0: a push collide-stream pass, then a moments pass at the start of
+ *   the next step (any grid).
+ * Both compute the same update; results agree to FP32 rounding, not bit for
+ * bit. May be changed between steps. Errors: LBIF_ERR_ARG for a NULL handle,
+ * fused not 0 or 1, or fused = 1 with nx < 32 or ny < 8. */
+int lbif_set_fused(lbif_handle h, int32_t fused);
 
 /* Time the candidate launch shapes of the ball and force kernels on this
  * handle's current state (trials launches each) and keep the fastest: the

@@ -30,11 +30,13 @@ struct lbif_ctx {
     bool own_stream = false;
     void* pop[2] = {nullptr, nullptr};
     int cur = 0;                      // populations of the current step
-    float* dn[2] = {nullptr, nullptr};
-    int dcur = 0;                     // dn[dcur] = reference of pop[cur]
-    float* ux = nullptr;
-    float* uy = nullptr;
-    float* uz = nullptr;
+    float* dn[3] = {nullptr, nullptr, nullptr};
+    int dref = 0;                     // dn[dref] = reference R of pop[cur]
+    int dfld = 1;                     // dn[dfld] = dn of step t (when fields_t == t)
+    float* u[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int ucur = 0;                     // u[ucur] = velocity of step t
+    bool fused = false;               // one pass: collision, pull streaming, moments
+    int csm_lz = 0;                   // z planes per CTA of that pass (0 = default)
     float* dG = nullptr;
     float4* Ft = nullptr;
     float4* F = nullptr;              // F / n0 per node (force kernel -> collision kernel)
@@ -55,11 +57,12 @@ struct lbif_ctx {
     std::vector<int> done;
     bool batch = false;
     int ball_want = 0, force_group = 0;  // launch shapes (0 = defaults; set by the autotuner)
-    CUtensorMap ball_map[2];             // tensor maps of dn[0], dn[1] for the ball kernel's tiles
+    CUtensorMap ball_map[3];             // tensor maps of dn[0..2] for the ball kernel's tiles
     bool ball_map_ok = false;
     bool ball_tma = true;                // stage the ball tiles with the maps (autotuner's choice)
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
+    int graph_state = -1;             // buffer indices the graph was captured from
     int64_t t = 0;
     int64_t fields_t = -1, G_t = -1, tail_t = -1;  // step the cached fields belong to
     std::vector<double> last_n, last_ux;
@@ -160,7 +163,8 @@ static void free_ctx(lbif_ctx* h)
                     h->prof_d, h->scratch, h->d_sl, h->d_zslit, h->d_done};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    float* pads[] = {h->dn[0], h->dn[1], h->ux, h->uy, h->uz, h->dG};
+    float* pads[] = {h->dn[0], h->dn[1], h->dn[2], h->u[0][0], h->u[0][1], h->u[0][2],
+                     h->u[1][0], h->u[1][1], h->u[1][2], h->dG};
     for (float* q : pads) padded_free(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
@@ -169,10 +173,10 @@ static void free_ctx(lbif_ctx* h)
 static Fields fields_of(const lbif_ctx* h)
 {
     Fields f;
-    f.dn = h->dn[h->dcur ^ 1];
-    f.ux = h->ux;
-    f.uy = h->uy;
-    f.uz = h->uz;
+    f.dn = h->dn[h->dfld];
+    f.ux = h->u[h->ucur][0];
+    f.uy = h->u[h->ucur][1];
+    f.uz = h->u[h->ucur][2];
     f.dG = h->dG;
     return f;
 }
@@ -400,7 +404,8 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     }
 #undef ALLOC
     {
-        float** pads[] = {&h->dn[0], &h->dn[1], &h->ux, &h->uy, &h->uz, &h->dG};
+        float** pads[] = {&h->dn[0], &h->dn[1], &h->dn[2], &h->u[0][0], &h->u[0][1], &h->u[0][2],
+                          &h->u[1][0], &h->u[1][1], &h->u[1][2], &h->dG};
         for (float** q : pads) {
             *q = padded_alloc((size_t)g.P);
             if (!*q) {
@@ -409,7 +414,9 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
             }
         }
         h->ball_map_ok = make_ball_map(g, P.sigma, h->dn[0], &h->ball_map[0]) &&
-                         make_ball_map(g, P.sigma, h->dn[1], &h->ball_map[1]);
+                         make_ball_map(g, P.sigma, h->dn[1], &h->ball_map[1]) &&
+                         make_ball_map(g, P.sigma, h->dn[2], &h->ball_map[2]);
+        h->fused = csm_ok(g);
     }
     P.sl = h->d_sl;
     P.zslit = h->d_zslit;
@@ -432,21 +439,21 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     CKC(cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
     CKC(cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
     {
-        float* pads[] = {h->dn[0], h->dn[1], h->ux, h->uy, h->uz, h->dG};
-        const float outside[] = {-1.f, -1.f, 0.f, 0.f, 0.f, 0.f};
+        float* pads[] = {h->dn[0], h->dn[1], h->dn[2], h->u[0][0], h->u[0][1], h->u[0][2],
+                         h->u[1][0], h->u[1][1], h->u[1][2], h->dG};
+        const float outside[] = {-1.f, -1.f, -1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (float* q : pads)
             CKC(cudaMemsetAsync(q - PAD_SLACK, 0, sizeof(float) * ((size_t)g.P + 2 * PAD_SLACK), h->stream));
-        CKC(launch_fill_outside(P, pads, outside, 6, h->stream));
+        CKC(launch_fill_outside(P, pads, outside, 10, h->stream));
         if (batch) {
             // gap planes between stacked slits hold the outside values too
             for (int z = 0; z < g.nz; ++z) {
                 if (zslit[z] >= 0) continue;
                 size_t plane = (size_t)g.px * g.py, off = (size_t)(z + g.hw) * plane;
                 std::vector<float> minus1(plane, -1.f);
-                CKC(cudaMemcpyAsync(h->dn[0] + off, minus1.data(), sizeof(float) * plane,
-                                    cudaMemcpyHostToDevice, h->stream));
-                CKC(cudaMemcpyAsync(h->dn[1] + off, minus1.data(), sizeof(float) * plane,
-                                    cudaMemcpyHostToDevice, h->stream));
+                for (float* d : h->dn)
+                    CKC(cudaMemcpyAsync(d + off, minus1.data(), sizeof(float) * plane,
+                                        cudaMemcpyHostToDevice, h->stream));
                 CKC(cudaStreamSynchronize(h->stream));
             }
         }
@@ -563,20 +570,40 @@ extern "C" const char* lbif_last_error(lbif_handle h)
 // --------------------------------------------------------------------------
 // stepping
 // --------------------------------------------------------------------------
+// the lowest dn buffer that is neither a nor b
+static int other_dn(int a, int b)
+{
+    for (int i = 0; i < 3; ++i)
+        if (i != a && i != b) return i;
+    return 0;
+}
+
+// moments pass: dn(t) of pop[cur] (reference dn[dref]) into another buffer
+static int run_moments(lbif_ctx* h, int skip_done)
+{
+    const int f = other_dn(h->dref, h->dref);
+    float* const* u = h->u[h->ucur];
+    CK(h, launch_moments(h->P, h->pop[h->cur], h->dn[h->dref], h->dn[f], u[0], u[1], u[2], h->status_d,
+                         skip_done, h->stream));
+    h->dfld = f;
+    return LBIF_OK;
+}
+
 // Moments (and, when asked, the g2 field and the tail force) of the current
 // populations; cached per step so that output calls between steps do not
-// redo them. The new dn goes to dn[dcur^1]; the reference dn[dcur] is kept.
+// redo them. The fused pass leaves the moments of the step it produced, so
+// a moments pass runs only after the populations were set from outside.
 static int refresh_fields(lbif_ctx* h, bool want_G, int skip_done)
 {
     const Params& P = h->P;
-    float* dnew = h->dn[h->dcur ^ 1];
     if (h->fields_t != h->t) {
-        CK(h, launch_moments(P, h->pop[h->cur], h->dn[h->dcur], dnew, h->ux, h->uy, h->uz,
-                             h->status_d, skip_done, h->stream));
+        int rc = run_moments(h, skip_done);
+        if (rc) return rc;
         h->fields_t = skip_done ? -1 : h->t;
     }
+    float* dnew = h->dn[h->dfld];
     if (want_G && h->G_t != h->t) {
-        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, skip_done, h->stream, ball_map(h, h->dcur ^ 1)));
+        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, skip_done, h->stream, ball_map(h, h->dfld)));
         h->G_t = skip_done ? -1 : h->t;
     }
     if (P.tail && h->tail_t != h->t) {
@@ -586,16 +613,38 @@ static int refresh_fields(lbif_ctx* h, bool want_G, int skip_done)
     return LBIF_OK;
 }
 
+// collision and streaming of step t -> t + 1 (force F of step t computed)
+static int collide_stream(lbif_ctx* h)
+{
+    const Params& P = h->P;
+    if (h->fused) {
+        // pops relative to dn(t + 1), which is also the next step's dn
+        const int n = other_dn(h->dref, h->dfld);
+        float* const* u = h->u[h->ucur];
+        float* const* w = h->u[h->ucur ^ 1];
+        CsmIO io{h->dn[h->dref], h->dn[h->dfld], u[0], u[1], u[2], h->dn[n], w[0], w[1], w[2]};
+        CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->stream));
+        h->cur ^= 1;
+        h->dref = h->dfld = n;
+        h->ucur ^= 1;
+        h->t += 1;
+        h->fields_t = h->t;
+        return LBIF_OK;
+    }
+    // pops relative to dn(t), the fields the collision used
+    CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], fields_of(h), h->F, h->stream));
+    h->cur ^= 1;
+    h->dref = h->dfld;
+    h->t += 1;
+    return LBIF_OK;
+}
+
 static int advance(lbif_ctx* h)
 {
     const Params& P = h->P;
     const Fields f = fields_of(h);
     CK(h, launch_force(P, f, h->Ft, h->F, h->force_group, h->stream));
-    CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], f, h->F, h->stream));
-    h->cur ^= 1;
-    h->dcur ^= 1;
-    h->t += 1;
-    return LBIF_OK;
+    return collide_stream(h);
 }
 
 // one full step of the active slits (frozen slits skipped)
@@ -633,14 +682,18 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
     size_t j = 0;
     CK(h, cudaEventRecord(ev[0], h->stream));
     for (int64_t s = 0; s < nsteps; ++s) {
-        float* dnew = h->dn[h->dcur ^ 1];
+        // the same launches as one_step, each timed (the fused pass leaves
+        // the next step's moments: no moments pass after the first step)
+        if (h->fields_t != h->t) {
+            int rc = run_moments(h, 1);
+            if (rc) return rc;
+            cls[j] = 0;
+            CK(h, cudaEventRecord(ev[++j], h->stream));
+        }
+        float* dnew = h->dn[h->dfld];
         const Fields f = fields_of(h);
-        CK(h, launch_moments(P, h->pop[h->cur], h->dn[h->dcur], dnew, h->ux, h->uy, h->uz,
-                             h->status_d, 1, h->stream));
-        cls[j] = 0;
-        CK(h, cudaEventRecord(ev[++j], h->stream));
         if (P.hs) {
-            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, 1, h->stream, ball_map(h, h->dcur ^ 1)));
+            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, 1, h->stream, ball_map(h, h->dfld)));
             cls[j] = 1;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
@@ -652,14 +705,12 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
         CK(h, launch_force(P, f, h->Ft, h->F, h->force_group, h->stream));
         cls[j] = 3;
         CK(h, cudaEventRecord(ev[++j], h->stream));
-        CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], f, h->F, h->stream));
+        int rc = collide_stream(h);
+        if (rc) return rc;
         cls[j] = 4;
         CK(h, cudaEventRecord(ev[++j], h->stream));
-        h->cur ^= 1;
-        h->dcur ^= 1;
-        h->t += 1;
     }
-    invalidate(h);
+    h->G_t = h->tail_t = -1;
     CK(h, cudaEventSynchronize(ev[j]));
     for (size_t k = 0; k < j; ++k) {
         float ms = 0.f;
@@ -772,7 +823,7 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
             du = h->scratch;
         }
     }
-    CK(h, launch_init_fields(P, h->pop[h->cur], h->dn[h->dcur], drho, du, h->stream));
+    CK(h, launch_init_fields(P, h->pop[h->cur], h->dn[h->dref], drho, du, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     reset_time(h);
     return LBIF_OK;
@@ -925,7 +976,7 @@ extern "C" int lbif_batch_seed(lbif_handle h, const float* n_z, const float* ux_
     if (e == cudaSuccess && ux_z)
         e = cudaMemcpyAsync(d + cnt, ux_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = launch_init_profiles(h->P, h->pop[h->cur], h->dn[h->dcur], d, ux_z ? d + cnt : nullptr, hmax,
+        e = launch_init_profiles(h->P, h->pop[h->cur], h->dn[h->dref], d, ux_z ? d + cnt : nullptr, hmax,
                                  h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (tmp) cudaFree(tmp);
@@ -955,10 +1006,21 @@ extern "C" int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int
     return check_status(h);
 }
 
-// capture `steps` (even) steps of the active slits into a CUDA graph
+// Host-side buffer indices a captured graph depends on. They repeat with
+// period 2 in steady stepping; the unfused step recomputes the fields from
+// dn[dref] in every step, so dfld matters only to the fused one.
+static int buffer_state(const lbif_ctx* h)
+{
+    return h->cur | h->dref << 1 | h->ucur << 3 | (h->fused ? 16 | h->dfld << 5 : 0);
+}
+
+// capture `steps` (even) steps of the active slits into a CUDA graph; the
+// graph replays from the buffer state it was captured in (and, fused, from
+// current fields), so it is rebuilt when that does not hold
 static int build_graph(lbif_ctx* h, int steps)
 {
-    if (h->graph && h->graph_steps == steps) return LBIF_OK;
+    const bool fresh = !h->fused || h->fields_t == h->t;
+    if (h->graph && h->graph_steps == steps && h->graph_state == buffer_state(h) && fresh) return LBIF_OK;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -969,11 +1031,16 @@ static int build_graph(lbif_ctx* h, int steps)
     if (rc) return rc;
     CK(h, cudaStreamSynchronize(h->stream));
     cudaGraph_t g = nullptr;
+    const int state = buffer_state(h);
+    const int64_t t0 = h->t, ft0 = h->fields_t;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int64_t t0 = h->t;
     for (int k = 0; k < steps && rc == LBIF_OK; ++k) rc = one_step(h);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->t = t0;  // the capture only recorded the launches
+    h->fields_t = ft0;
+    h->G_t = h->tail_t = -1;
+    if (rc == LBIF_OK && buffer_state(h) != state)
+        rc = fail(h, LBIF_ERR_CUDA, "graph capture: buffer indices do not repeat over the captured steps");
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
@@ -986,7 +1053,7 @@ static int build_graph(lbif_ctx* h, int steps)
         return fail(h, LBIF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     }
     h->graph_steps = steps;
-    invalidate(h);
+    h->graph_state = state;
     return LBIF_OK;
 }
 
@@ -997,7 +1064,12 @@ static int run_graph(lbif_ctx* h, int steps)
     if (rc) return rc;
     CK(h, cudaGraphLaunch(h->graph, h->stream));
     h->t += steps;
-    invalidate(h);
+    if (h->fused) {
+        h->fields_t = h->t;  // the last fused pass left the fields of step t
+        h->G_t = h->tail_t = -1;
+    } else {
+        invalidate(h);
+    }
     return LBIF_OK;
 }
 
@@ -1077,6 +1149,23 @@ extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int3
 // Time each candidate launch shape on the handle's own state and keep the
 // fastest: the ball kernel's CTA target (z-chunking) and the force kernel's
 // tile-group edge. The state is saved and restored around the trials.
+extern "C" int lbif_set_fused(lbif_handle h, int32_t fused)
+{
+    if (!h || (fused != 0 && fused != 1)) return fail(h, LBIF_ERR_ARG, "lbif_set_fused: bad arguments");
+    if (fused && !csm_ok(h->P.g))
+        return fail(h, LBIF_ERR_ARG, "lbif_set_fused: the fused pass needs nx >= 32 and ny >= 8");
+    if (h->fused != (fused != 0)) {
+        // the unfused step reads dn(t) of the fused one as its reference;
+        // the fused step reads both buffers the unfused one leaves
+        h->fused = fused != 0;
+        if (h->graph) {
+            cudaGraphExecDestroy(h->graph);
+            h->graph = nullptr;
+        }
+    }
+    return LBIF_OK;
+}
+
 extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group,
                              int32_t* ball_staging)
 {
@@ -1092,13 +1181,13 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
     float best = 1e30f;
     int best_ball = 0, best_group = 0;
     bool best_tma = h->ball_map_ok;
-    float* dnew = h->dn[h->dcur ^ 1];
+    float* dnew = h->dn[h->dfld];
     // the ball kernel writes dG only; the force kernel writes F only: both
     // are pure functions of the current fields, so trials change no state.
     // Ball candidates: CTA target x plane staging (tensor-memory-accelerator
     // copies when the handle has tensor maps, plain loads).
     for (int staging = h->ball_map_ok ? 1 : 0; staging >= 0; --staging) {
-        const CUtensorMap* tm = staging ? &h->ball_map[h->dcur ^ 1] : nullptr;
+        const CUtensorMap* tm = staging ? &h->ball_map[h->dfld] : nullptr;
         for (int b : balls) {
             float tot = 0.f;
             for (int k = 0; k < trials + 1; ++k) {
@@ -1172,7 +1261,7 @@ extern "C" int lbif_save(lbif_handle h, const char* path)
     for (int i = 0; i < Q; ++i)
         CK(h, cudaMemcpyAsync(buf.data() + plane * i, (char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i,
                               plane, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, launch_read_ref(P, h->dn[h->dcur], h->scratch, h->stream));
+    CK(h, launch_read_ref(P, h->dn[h->dref], h->scratch, h->stream));
     CK(h, cudaMemcpyAsync(ref.data(), h->scratch, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     FILE* fp = fopen(path, "wb");
@@ -1217,7 +1306,7 @@ extern "C" int lbif_load(lbif_handle h, const char* path)
         CK(h, cudaMemcpyAsync((char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i, buf.data() + plane * i,
                               plane, cudaMemcpyHostToDevice, h->stream));
     CK(h, cudaMemcpyAsync(h->scratch, ref.data(), sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
-    CK(h, launch_write_ref(P, h->scratch, h->dn[h->dcur], h->stream));
+    CK(h, launch_write_ref(P, h->scratch, h->dn[h->dref], h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     reset_time(h);
     h->t = hd.t;

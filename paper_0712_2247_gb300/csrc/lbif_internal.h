@@ -102,6 +102,20 @@ struct Fields {
     const float* dG;
 };
 
+// inputs and outputs of the fused collide-stream-moments kernel (padded
+// fields; dref may be the same buffer as dn, the outputs are other buffers)
+struct CsmIO {
+    const float* dref;  // reference R of the stored populations
+    const float* dn;    // dn(t)
+    const float* ux;
+    const float* uy;
+    const float* uz;    // u(t)
+    float* dnw;         // dn(t + 1), also the reference of the new populations
+    float* uxw;
+    float* uyw;
+    float* uzw;         // u(t + 1)
+};
+
 // ---- launchers (lbif_kernels.cu) -------------------------------------------
 cudaError_t launch_fill_outside(const Params& P, float* const* planes, const float* values,
                                 int nplanes, cudaStream_t s);
@@ -143,6 +157,11 @@ cudaError_t launch_tail_spectral(const Params& P, const float* dn, int D, float2
                                  cudaStream_t s);
 cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields& f,
                       const float4* F, cudaStream_t s);
+// one step's collision, pull streaming and the moments of the new
+// populations (CsmIO); lz: z planes per CTA segment (<= 0: default)
+bool csm_ok(const Geom& g);
+cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
+                       int* status, int lz, cudaStream_t s);
 cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s);
 cudaError_t launch_moments_out(const Params& P, const Fields& f, float* rho, float* u, float* p,
                                cudaStream_t s);

@@ -186,8 +186,8 @@ __device__ __forceinline__ float eq_excess(int i, float opd, float ux, float uy,
 // initialisation and reference-field plumbing
 // ---------------------------------------------------------------------------
 struct OutsidePlanes {
-    float* p[8];
-    float v[8];
+    float* p[12];
+    float v[12];
     int n;
 };
 
@@ -1238,6 +1238,191 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
 }
 
 // ---------------------------------------------------------------------------
+// steps 5-6 fused with step 1 of the next step, in pull form: every node
+// gathers the populations that stream into it, applies to each the collision
+// of its source node, and forms the new moments from the 19 values it holds,
+// so the populations are read and written once per step (push collide-stream
+// followed by a moments pass reads them twice). What a source node
+// contributes is staged per node in shared memory: a CTA owns a 32 x 8 tile
+// of x-y nodes, keeps three planes of it (plus a one-node halo) in a ring,
+// and marches up a segment of z planes.
+//
+// With k_i = h_i - dn (a population relative to its node's current density),
+// omega = 1/tau and q = omega (1 + dn), the post-collision value (BGK towards
+// the local equilibrium, source 3 c.F + (3/2) F.w (|c|^2 - 1)) is
+//   k_i' = (1 - omega) k_i + 3 c.(q u + F) + (9/2) q (c.u)^2 - (3/2) q u.u
+//          + (3/2) F.w (|c|^2 - 1),
+// which splits by lattice-velocity class into
+//   axis a, sign s:            (1 - omega) k + s P_a + C_a
+//   plane (a, b), signs sa sb: (1 - omega) k + sa P_a + sb P_b + C_ab + sa sb X_ab
+//   rest:                      (1 - omega) k + C_0
+// with P = 3 (q u + F), B = K - (3/2) q u.u, C_a = B + (9/2) q u_a^2,
+// C_ab = B + (9/2) q (u_a^2 + u_b^2) + (3/2) F.w, X_ab = 9 q u_a u_b and
+// C_0 = B - (3/2) F.w = (2 (C_x + C_y + C_z) - (C_xy + C_xz + C_yz)) / 3;
+// K = (1 - omega)(R - dn) re-references populations stored relative to R.
+// The value reaching r from s = r - c_i, relative to dn(r), is
+// k_i'(s) + (dn(s) - dn(r)); at a wall it is k'_{opp i}(r) (half-way
+// bounce-back). The new populations are stored relative to the new density
+// dn(r) + S, S = sum_i w_i v_i, which is also the next step's reference.
+// ---------------------------------------------------------------------------
+constexpr int CSM_TX = 32, CSM_TY = 8, CSM_THREADS = CSM_TX * CSM_TY;
+constexpr int CSM_HX = CSM_TX + 2, CSM_HN = CSM_HX * (CSM_TY + 2);  // staged nodes per plane
+// staged quantities: dn, P_x..z, C_x..z, C_xy C_xz C_yz, X_xy X_xz X_yz
+constexpr int SQ_DN = 0, SQ_P = 1, SQ_CA = 4, SQ_CP = 7, SQ_X = 10, CSM_NF = 13;
+constexpr int CSM_SLOT = CSM_NF * CSM_HN;  // floats per staged plane
+
+size_t csm_smem_bytes() { return sizeof(float) * 3 * CSM_SLOT; }
+
+__device__ __forceinline__ int csm_slot(int q) { return (q + 3) % 3; }
+
+// stage plane q (-1 <= q <= nz) of the tile at (x0, y0) into `slot`
+__device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, const float4* __restrict__ F,
+                                          float* slot, int x0, int y0, int q)
+{
+    const Geom& g = P.g;
+    int zq = q;
+    if (g.zper)
+        zq = q < 0 ? q + g.nz : (q >= g.nz ? q - g.nz : q);
+    else if (q < 0 || q >= g.nz)
+        return;  // beyond the walls: only reached through bounce-back
+    const int sq = slit_of(P, zq);
+    if (sq < 0 || frozen(P, sq)) return;
+    const float om = P.sl[sq].inv_tau;
+    for (int h = threadIdx.x; h < CSM_HN; h += CSM_THREADS) {
+        const int X = x0 - 1 + h % CSM_HX, Y = y0 - 1 + h / CSM_HX;
+        if (X > g.nx || Y > g.ny) continue;  // past a partial tile: never gathered
+        const int p = pidx(g, X, Y, q);       // x, y halo images hold the periodic values
+        const int xw = X < 0 ? X + g.nx : (X >= g.nx ? X - g.nx : X);
+        const int yw = Y < 0 ? Y + g.ny : (Y >= g.ny ? Y - g.ny : Y);
+        const float4 f = __ldg(F + ((long long)zq * g.ny + yw) * g.nx + xw);
+        const float d = __ldg(io.dn + p);
+        const float ux = __ldg(io.ux + p), uy = __ldg(io.uy + p), uz = __ldg(io.uz + p);
+        const float K = io.dref == io.dn ? 0.f : (1.f - om) * (__ldg(io.dref + p) - d);
+        const float q1 = om * (1.f + d);
+        const float B = K - 1.5f * q1 * (ux * ux + uy * uy + uz * uz);
+        const float a = 4.5f * q1, ax = a * ux * ux, ay = a * uy * uy, az = a * uz * uz;
+        const float fw = 1.5f * f.w, b = 9.f * q1;
+        slot[SQ_DN * CSM_HN + h] = d;
+        slot[(SQ_P + 0) * CSM_HN + h] = 3.f * fmaf(q1, ux, f.x);
+        slot[(SQ_P + 1) * CSM_HN + h] = 3.f * fmaf(q1, uy, f.y);
+        slot[(SQ_P + 2) * CSM_HN + h] = 3.f * fmaf(q1, uz, f.z);
+        slot[(SQ_CA + 0) * CSM_HN + h] = B + ax;
+        slot[(SQ_CA + 1) * CSM_HN + h] = B + ay;
+        slot[(SQ_CA + 2) * CSM_HN + h] = B + az;
+        slot[(SQ_CP + 0) * CSM_HN + h] = B + (ax + ay) + fw;
+        slot[(SQ_CP + 1) * CSM_HN + h] = B + (ax + az) + fw;
+        slot[(SQ_CP + 2) * CSM_HN + h] = B + (ay + az) + fw;
+        slot[(SQ_X + 0) * CSM_HN + h] = b * ux * uy;
+        slot[(SQ_X + 1) * CSM_HN + h] = b * ux * uz;
+        slot[(SQ_X + 2) * CSM_HN + h] = b * uy * uz;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CSM_THREADS, 3) k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout,
+                                                        CsmIO io, const float4* __restrict__ F, int lz,
+                                                        int tiles_x, int tiles_y, int* status)
+{
+    extern __shared__ float sm[];
+    const Geom& g = P.g;
+    const int tiles = tiles_x * tiles_y;
+    const int tile = blockIdx.x % tiles, seg = blockIdx.x / tiles;
+    const int x0 = (tile % tiles_x) * CSM_TX, y0 = (tile / tiles_x) * CSM_TY;
+    const int x = x0 + threadIdx.x % CSM_TX, y = y0 + threadIdx.x / CSM_TX;
+    const int hc = (threadIdx.x / CSM_TX + 1) * CSM_HX + threadIdx.x % CSM_TX + 1;
+    const bool in_xy = x < g.nx && y < g.ny;
+    const int zb = seg * lz, ze = min(zb + lz, g.nz);
+    csm_stage(P, io, F, sm + csm_slot(zb - 1) * CSM_SLOT, x0, y0, zb - 1);
+    csm_stage(P, io, F, sm + csm_slot(zb) * CSM_SLOT, x0, y0, zb);
+    for (int z = zb; z < ze; ++z) {
+        // issue the population loads first: they do not depend on the ring
+        const int s = slit_of(P, z);
+        const bool act = in_xy && s >= 0 && !frozen(P, s);
+        float v[Q];
+        unsigned bb = 0;  // bit i: direction i arrives from a wall (bounce-back)
+        const long long idx = ((long long)z * g.ny + y) * g.nx + x;
+        float om = 0.f;
+        if (act) {
+            const int zlo = P.sl[s].zlo, zhi = P.sl[s].zhi;
+            om = P.sl[s].inv_tau;
+            if (x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) v[i] = ldp(pin + (long long)i * g.Npad + (idx - P.soff[i]));
+            } else {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    int sx = x - kCx(i), sy = y - kCy(i), sz = z - kCz(i);
+                    sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
+                    sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
+                    if (g.zper) {
+                        sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
+                    } else if (sz < zlo || sz > zhi) {
+                        bb |= 1u << i;
+                        v[i] = ldp(pin + (long long)opp_of(i) * g.Npad + idx);
+                        continue;
+                    }
+                    v[i] = ldp(pin + (long long)i * g.Npad + (((long long)sz * g.ny + sy) * g.nx + sx));
+                }
+            }
+        }
+        __syncthreads();  // the slot of plane z - 2 is free
+        csm_stage(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, x0, y0, z + 1);
+        __syncthreads();
+        if (!act) continue;
+        const float* own = sm + csm_slot(z) * CSM_SLOT;
+        const float* below = sm + csm_slot(z - 1) * CSM_SLOT;
+        const float* above = sm + csm_slot(z + 1) * CSM_SLOT;
+        const float om1 = 1.f - om;
+        const float dnr = own[SQ_DN * CSM_HN + hc];
+        {
+            const float c0 = (2.f * (own[(SQ_CA + 0) * CSM_HN + hc] + own[(SQ_CA + 1) * CSM_HN + hc] +
+                                     own[(SQ_CA + 2) * CSM_HN + hc]) -
+                              (own[(SQ_CP + 0) * CSM_HN + hc] + own[(SQ_CP + 1) * CSM_HN + hc] +
+                               own[(SQ_CP + 2) * CSM_HN + hc])) * (1.f / 3.f);
+            v[0] = fmaf(om1, v[0], c0);
+        }
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+            const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+            const bool wall = (bb >> i) & 1u;
+            // source node: r - c_i in plane z - c_z, or r itself with -c_i at a wall
+            const float* sl = wall ? own : (cz > 0 ? below : (cz < 0 ? above : own));
+            const int h = wall ? hc : hc - cx - cy * CSM_HX;
+            const float sg = wall ? -1.f : 1.f;
+            float t;
+            if (kC2(i) == 1) {
+                const int a = cx ? 0 : (cy ? 1 : 2);
+                const float ca = (float)(cx + cy + cz);
+                t = fmaf(sg * ca, sl[(SQ_P + a) * CSM_HN + h], sl[(SQ_CA + a) * CSM_HN + h]);
+            } else {
+                const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
+                const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
+                const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
+                t = sl[(SQ_CP + pl) * CSM_HN + h] +
+                    sg * (ca * sl[(SQ_P + a) * CSM_HN + h] + cb * sl[(SQ_P + b) * CSM_HN + h]) +
+                    (ca * cb) * sl[(SQ_X + pl) * CSM_HN + h];
+            }
+            const float d = wall ? 0.f : sl[SQ_DN * CSM_HN + h] - dnr;
+            v[i] = fmaf(om1, v[i], t) + d;
+        }
+        float S, jx, jy, jz;
+        sums_of(v, S, jx, jy, jz);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) stp(pout + (long long)i * g.Npad + idx, v[i] - S);
+        const float dn = dnr + S;
+        const float inv = 1.f / (1.f + dn);
+        const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+        if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
+        for_images(g, x, y, z, [&](int p) {
+            io.dnw[p] = dn;
+            io.uxw[p] = ux;
+            io.uyw[p] = uy;
+            io.uzw[p] = uz;
+        });
+    }
+}
+
+// ---------------------------------------------------------------------------
 // outputs
 // ---------------------------------------------------------------------------
 __global__ void k_force_soa(Params P, const float4* __restrict__ F, float* __restrict__ out)
@@ -1343,7 +1528,7 @@ cudaError_t launch_fill_outside(const Params& P, float* const* planes, const flo
 {
     long long total = (long long)P.g.px * P.g.py * 2 * P.g.hw;
     if (P.g.zper || total == 0) return cudaSuccess;
-    if (nplanes > 8) return cudaErrorInvalidValue;
+    if (nplanes > 12) return cudaErrorInvalidValue;
     OutsidePlanes op;
     op.n = nplanes;
     for (int j = 0; j < nplanes; ++j) {
@@ -1520,6 +1705,40 @@ cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields
         k_cs<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pin, (__half*)pout, f, F);
     else
         k_cs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, f, F);
+    return cudaGetLastError();
+}
+
+bool csm_ok(const Geom& g) { return g.nx >= CSM_TX && g.ny >= CSM_TY; }
+
+cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
+                       int* status, int lz, cudaStream_t s)
+{
+    const Geom& g = P.g;
+    if (lz <= 0) lz = 16;
+    const int tx = (g.nx + CSM_TX - 1) / CSM_TX, ty = (g.ny + CSM_TY - 1) / CSM_TY;
+    const int segs = (g.nz + lz - 1) / lz;
+    const long long blocks = (long long)tx * ty * segs;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const size_t smem = csm_smem_bytes();
+    // the shared-memory limit is a per-device function attribute
+    static std::atomic<uint64_t> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(k_csm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_csm<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured.fetch_or(bit);
+    }
+    if (P.storage == LBIF_STORE_F16)
+        k_csm<__half><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const __half*)pin, (__half*)pout, io, F, lz,
+                                                                 tx, ty, status);
+    else
+        k_csm<float><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const float*)pin, (float*)pout, io, F, lz,
+                                                                tx, ty, status);
     return cudaGetLastError();
 }
 

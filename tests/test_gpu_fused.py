@@ -1,0 +1,201 @@
+"""The fused pass (collision, pull streaming and the next step's moments in one
+kernel) against the FP64 oracle, and against the two-pass step.
+
+Both passes compute the same forward-Euler BGK update with the first-order
+source, streaming and half-way bounce-back (Sec. Methods); they differ only in
+the order of FP32 roundings, so each is held to the oracle at the tolerances
+of the two-pass tests (1e-5 normwise, FP32) and to the other at a few FP32
+ulps of the state. Shapes span several 32 x 8 tiles with ragged tails in x and
+y, z segments of the marching CTAs, walls and periodic z.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def nerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    s = np.abs(b).max()
+    return float(np.abs(a - b).max() / s) if s > 0 else float(np.abs(a).max())
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_0712_2247_gb300 import build, lbif
+
+    build.build()
+    return lbif
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def pair(L, O, shape, sigma, zper=False, storage=0, fields_seed=11, **kw):
+    from paper_0712_2247_gb300 import inputs
+
+    nx, ny, nz = shape
+    g = L.Slit(nx, ny, nz, sigma, 0.22, 0.85, periodic_z=zper, storage=storage, **kw)
+    o = O.Oracle(nx, ny, nz, sigma, 0.22, 0.85, zper=zper, **kw)
+    rho, u = inputs.random_fields((nz, ny, nx), o.n0, fields_seed)
+    g.set_fields(rho, u)
+    o.init_fields(rho.astype(np.float64), u.astype(np.float64))
+    return g, o
+
+
+CASES = [
+    # (shape, sigma, periodic z)
+    ((32, 8, 24), 4, False),    # one tile column
+    ((40, 12, 30), 4, False),   # ragged in x and y
+    ((72, 20, 18), 4, True),    # periodic z: ring planes wrap
+    ((64, 16, 40), 8, False),   # sigma = 8, several z segments
+]
+
+
+@pytest.mark.parametrize("shape,sigma,zper", CASES)
+def test_fused_parity(L, O, shape, sigma, zper):
+    g, o = pair(L, O, shape, sigma, zper, body=(2e-5, -1e-5, 0.0))
+    g.set_fused(True)
+    for n in (1, 40):
+        g.step(n)
+        o.step(n)
+        rg, ug = g.moments()
+        ro, uo = o.moments()
+        er, eu = nerr(rg, ro), nerr(ug, uo)
+        print("fused", shape, sigma, zper, g.t, f"rho={er:.2e} u={eu:.2e}")
+        assert er < 1e-5 and eu < 1e-5, (g.t, er, eu)
+    g.close()
+
+
+def test_fused_long_run_1000_steps(L, O):
+    """1000 steps of a flowing sigma = 4 slit (one tile column, ragged y)."""
+    g = L.Slit(32, 12, 32, 4, 0.25, 1.0, body=(1e-6, 0, 0), seed=5)
+    o = O.Oracle(32, 12, 32, 4, 0.25, 1.0, body=(1e-6, 0, 0), seed=5)
+    g.set_fused(True)
+    g.step(1000)
+    o.step(1000)
+    rg, ug = g.moments()
+    ro, uo = o.moments()
+    ng, uxg, tot = g.profiles()
+    no, uxo = o.profiles()
+    e = dict(rho=nerr(rg, ro), u=nerr(ug, uo), n_z=nerr(ng, no), ux_z=nerr(uxg, uxo),
+             mass=abs(tot[0] / o.totals()[0] - 1))
+    print("fused 1000 steps", e)
+    assert e["rho"] < 1e-5 and e["u"] < 1e-5 and e["n_z"] < 1e-5 and e["ux_z"] < 1e-4
+    assert e["mass"] < 1e-6
+
+
+def test_fused_and_two_pass_agree(L):
+    """The same 200 steps through either pass: equal to FP32 rounding."""
+    kw = dict(body=(1e-5, 0, 0), seed=3)
+    a = L.Slit(48, 16, 28, 4, 0.25, 0.9, **kw)
+    b = L.Slit(48, 16, 28, 4, 0.25, 0.9, **kw)
+    a.set_fused(True)
+    b.set_fused(False)
+    a.step(200)
+    b.step(200)
+    ra, ua = a.moments()
+    rb, ub = b.moments()
+    assert nerr(ra, rb) < 2e-6 and nerr(ua, ub) < 2e-6
+    a.close()
+    b.close()
+
+
+def test_switch_between_passes(L, O):
+    """Fused -> two-pass -> fused across steps, against 90 oracle steps."""
+    g, o = pair(L, O, (40, 10, 22), 4, body=(1e-5, 0, 0))
+    for on in (True, False, True):
+        g.set_fused(on)
+        g.step(30)
+    o.step(90)
+    rg, ug = g.moments()
+    ro, uo = o.moments()
+    assert nerr(rg, ro) < 1e-5 and nerr(ug, uo) < 1e-5
+
+
+def test_fused_fp16_storage(L, O):
+    g, o = pair(L, O, (40, 12, 30), 4, storage=1, body=(1e-5, 0, 0))
+    g.set_fused(True)
+    g.step(40)
+    o.step(40)
+    rg, ug = g.moments()
+    ro, uo = o.moments()
+    assert nerr(rg, ro) < 1e-4 and nerr(ug, uo) < 1e-3
+
+
+# (the tail at eps = 1 drives these random fields unstable within 10 steps,
+# on the oracle too; eps = 0.3 keeps them bounded over the 30 steps)
+@pytest.mark.parametrize("extra", [dict(tail=True, eps=0.3, rcut=2.5), dict(c2=True),
+                                   dict(coupling=False), dict(g2_form=1)])
+def test_fused_with_options(L, O, extra):
+    okw = dict(extra)
+    g2form = okw.pop("g2_form", 0)
+    nx, ny, nz = 32, 16, 28
+    g = L.Slit(nx, ny, nz, 4, 0.2, 0.9, body=(1e-5, 0, 0), seed=8, g2_form=g2form, **okw)
+    o = O.Oracle(nx, ny, nz, 4, 0.2, 0.9, body=(1e-5, 0, 0), seed=8, g2form=g2form, **okw)
+    from paper_0712_2247_gb300 import inputs
+
+    rho, u = inputs.random_fields((nz, ny, nx), o.n0, 4)
+    g.set_fields(rho, u)
+    o.init_fields(rho.astype(np.float64), u.astype(np.float64))
+    g.set_fused(True)
+    g.step(30)
+    o.step(30)
+    rg, ug = g.moments()
+    ro, uo = o.moments()
+    assert nerr(rg, ro) < 1e-5 and nerr(ug, uo) < 1e-5, extra
+
+
+def test_fused_ensemble_matches_oracle_and_freezes(L, O):
+    """Stacked slits on 32 x 8 rows (fused by default): parity per slit, and
+    run-to-steady-state with frozen slits gives the same profiles as the
+    two-pass ensemble to FP32 rounding."""
+    H = np.array([9, 16, 12], np.int32)
+    eta = np.array([0.15, 0.25, 0.2])
+    F = np.array([2e-6, 1e-6, 5e-6])
+    tau = np.array([0.8, 1.0, 0.7])
+    e = L.Ensemble(H, eta, F, tau, sigma=4, nx=32, ny=8, storage=0, noise=0.0)
+    hmax = int(H.max())
+    nz = np.zeros((len(H), hmax), np.float32)
+    for s, h in enumerate(H):
+        nz[s, :h] = e.n0_s[s] * (1 + 0.05 * np.cos(2 * np.pi * np.arange(h) / h))
+    e.seed(nz)
+    e.step(50)
+    rho, u = e.moments()
+    for s, h in enumerate(H):
+        o = O.Oracle(32, 8, int(h), 4, eta[s], tau[s], body=(F[s], 0, 0))
+        o.init_fields(np.repeat(nz[s, :h].astype(np.float64), 256).reshape(h, 8, 32))
+        o.step(50)
+        n_o, u_o = o.moments()
+        z0 = int(e.zlo[s])
+        assert nerr(rho[z0:z0 + h], n_o) < 1e-5, s
+        assert nerr(u[:, z0:z0 + h], u_o) < 1e-5, s
+    # a slit in the stack evolves bit-identically to the same slit alone
+    n_g, ux_g = e.slit_profiles(hmax)
+    for s in (0, 2):
+        h = int(H[s])
+        g = L.Slit(32, 8, h, 4, eta[s], tau[s], body=(F[s], 0, 0), noise=0.0)
+        g.set_fields(np.repeat(nz[s, :h], 256).reshape(h, 8, 32).astype(np.float32))
+        g.step(50)
+        n1, u1, _ = g.profiles()
+        assert np.array_equal(n1, n_g[s, :h]) and np.array_equal(u1, ux_g[s, :h]), s
+        g.close()
+    e.close()
+
+    prof = []
+    for fused in (True, False):
+        e = L.Ensemble(H, eta, F, tau, sigma=4, nx=32, ny=8, storage=0, noise=0.0)
+        e.set_fused(fused)
+        e.seed(nz)
+        steps = e.run(tol=1e-7, max_steps=6000, check_every=50, patience=20)
+        assert np.all(steps != -2)
+        prof.append(e.slit_profiles())
+        e.close()
+    (na, ua), (nb, ub) = prof
+    assert nerr(na, nb) < 1e-5
