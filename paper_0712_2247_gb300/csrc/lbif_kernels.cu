@@ -78,6 +78,14 @@ __device__ __forceinline__ void for_images(const Geom& g, int x, int y, int z, F
                 fn(((zi + g.hw) * g.py + (yi + g.hw)) * g.px + (xi + g.hw));
 }
 
+// node (x, y, z) lies at least hw from every periodic edge: its padded
+// field value has no image in the halo
+__device__ __forceinline__ bool no_images(const Geom& g, int x, int y, int z)
+{
+    return x >= g.hw && x < g.nx - g.hw && y >= g.hw && y < g.ny - g.hw &&
+           (!g.zper || (z >= g.hw && z < g.nz - g.hw));
+}
+
 // Block -> node mapping of the stencil kernels: a CTA covers a TX x TY (x, y)
 // tile of one z plane; CTAs are ordered tile-in-group fastest, then z, then
 // group, where a group spans about 128 x 128 nodes. The CTAs resident at any
@@ -319,12 +327,16 @@ __global__ void __launch_bounds__(256) k_moments(Params P, const T* __restrict__
     float inv = 1.f / (1.f + dn);
     float ux = jx * inv, uy = jy * inv, uz = jz * inv;
     if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
-    for_images(P.g, x, y, z, [&](int p) {
+    auto put = [&](int p) {
         dnew[p] = dn;
         oux[p] = ux;
         ouy[p] = uy;
         ouz[p] = uz;
-    });
+    };
+    if (no_images(P.g, x, y, z))
+        put(pidx(P.g, x, y, z));
+    else
+        for_images(P.g, x, y, z, put);
 }
 
 // ---------------------------------------------------------------------------
@@ -1270,7 +1282,6 @@ constexpr int CSM_HX = CSM_TX + 2, CSM_HN = CSM_HX * (CSM_TY + 2);  // staged no
 // staged quantities: dn, P_x..z, C_x..z, C_xy C_xz C_yz, X_xy X_xz X_yz
 constexpr int SQ_DN = 0, SQ_P = 1, SQ_CA = 4, SQ_CP = 7, SQ_X = 10, CSM_NF = 13;
 constexpr int CSM_SLOT = CSM_NF * CSM_HN;  // floats per staged plane
-
 size_t csm_smem_bytes() { return sizeof(float) * 3 * CSM_SLOT; }
 
 __device__ __forceinline__ int csm_slot(int q) { return (q + 3) % 3; }
@@ -1318,8 +1329,16 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
     }
 }
 
+// CTAs per SM the register budget is sized for, and z planes per CTA segment
+#ifndef CSM_MINB
+#define CSM_MINB 3
+#endif
+#ifndef CSM_LZ
+#define CSM_LZ 16
+#endif
+
 template <typename T>
-__global__ void __launch_bounds__(CSM_THREADS, 3) k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout,
+__global__ void __launch_bounds__(CSM_THREADS, CSM_MINB) k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout,
                                                         CsmIO io, const float4* __restrict__ F, int lz,
                                                         int tiles_x, int tiles_y, int* status)
 {
@@ -1381,6 +1400,27 @@ __global__ void __launch_bounds__(CSM_THREADS, 3) k_csm(Params P, const T* __res
                                own[(SQ_CP + 2) * CSM_HN + hc])) * (1.f / 3.f);
             v[0] = fmaf(om1, v[0], c0);
         }
+        if (bb == 0) {
+            // no wall: every source is r - c_i (offsets fixed at compile time)
+#pragma unroll
+            for (int i = 1; i < Q; ++i) {
+                const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+                const float* sl = (cz > 0 ? below : (cz < 0 ? above : own)) + hc - cx - cy * CSM_HX;
+                float t;
+                if (kC2(i) == 1) {
+                    const int a = cx ? 0 : (cy ? 1 : 2);
+                    const float ca = (float)(cx + cy + cz);
+                    t = fmaf(ca, sl[(SQ_P + a) * CSM_HN], sl[(SQ_CA + a) * CSM_HN]);
+                } else {
+                    const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
+                    const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
+                    const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
+                    t = sl[(SQ_CP + pl) * CSM_HN] + (ca * sl[(SQ_P + a) * CSM_HN] + cb * sl[(SQ_P + b) * CSM_HN]) +
+                        (ca * cb) * sl[(SQ_X + pl) * CSM_HN];
+                }
+                v[i] = fmaf(om1, v[i], t) + (sl[SQ_DN * CSM_HN] - dnr);
+            }
+        } else {
 #pragma unroll
         for (int i = 1; i < Q; ++i) {
             const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
@@ -1405,6 +1445,7 @@ __global__ void __launch_bounds__(CSM_THREADS, 3) k_csm(Params P, const T* __res
             const float d = wall ? 0.f : sl[SQ_DN * CSM_HN + h] - dnr;
             v[i] = fmaf(om1, v[i], t) + d;
         }
+        }
         float S, jx, jy, jz;
         sums_of(v, S, jx, jy, jz);
 #pragma unroll
@@ -1413,12 +1454,16 @@ __global__ void __launch_bounds__(CSM_THREADS, 3) k_csm(Params P, const T* __res
         const float inv = 1.f / (1.f + dn);
         const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
         if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
-        for_images(g, x, y, z, [&](int p) {
+        auto put = [&](int p) {
             io.dnw[p] = dn;
             io.uxw[p] = ux;
             io.uyw[p] = uy;
             io.uzw[p] = uz;
-        });
+        };
+        if (no_images(g, x, y, z))
+            put(pidx(g, x, y, z));
+        else
+            for_images(g, x, y, z, put);
     }
 }
 
@@ -1714,7 +1759,7 @@ cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO
                        int* status, int lz, cudaStream_t s)
 {
     const Geom& g = P.g;
-    if (lz <= 0) lz = 16;
+    if (lz <= 0) lz = CSM_LZ;
     const int tx = (g.nx + CSM_TX - 1) / CSM_TX, ty = (g.ny + CSM_TY - 1) / CSM_TY;
     const int segs = (g.nz + lz - 1) / lz;
     const long long blocks = (long long)tx * ty * segs;
