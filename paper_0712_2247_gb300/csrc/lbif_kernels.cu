@@ -899,14 +899,27 @@ __device__ __forceinline__ void win(const float* __restrict__ f, int b, v4 r)
     }
 }
 
-// windows at x offsets D and D + 1 (the two corners along x), sharing loads
-template <int D>
-__device__ __forceinline__ void win2(const float* __restrict__ f, int b, v4 w0, v4 w1)
+// Lanes of a warp in the tiled mapping: the warp is one y row, lane l holds
+// the 4-node block at x0 + 4 l, so the value just past (before) a lane's float4
+// is the next (previous) lane's first (last) one. hi / lo: this lane loads it
+// itself (the last live lane of the row / the first lane).
+struct Lanes {
+    bool hi, lo;
+};
+
+// windows at x offsets D and D + 1 (the two corners along x), sharing loads.
+// With LN the fifth value comes from the neighbouring lane by a shuffle, so a
+// window costs the float4's wavefronts only (a strided scalar load costs as
+// many again).
+template <int D, bool LN>
+__device__ __forceinline__ void win2(const float* __restrict__ f, int b, v4 w0, v4 w1, Lanes ln)
 {
     constexpr int RR = D - floor4(D);
     if constexpr (RR == 0) {
         const float4 A = ld4(f + b + D);
-        const float s = __ldg(f + b + D + 4);
+        float s = 0.f;
+        if constexpr (LN) s = __shfl_down_sync(0xffffffffu, A.x, 1);
+        if (!LN || ln.hi) s = __ldg(f + b + D + 4);
         set4(w0, A);
         w1[0] = A.y;
         w1[1] = A.z;
@@ -914,7 +927,9 @@ __device__ __forceinline__ void win2(const float* __restrict__ f, int b, v4 w0, 
         w1[3] = s;
     } else if constexpr (RR == 3) {
         const float4 C = ld4(f + b + D + 1);
-        const float s = __ldg(f + b + D);
+        float s = 0.f;
+        if constexpr (LN) s = __shfl_up_sync(0xffffffffu, C.w, 1);
+        if (!LN || ln.lo) s = __ldg(f + b + D);
         w0[0] = s;
         w0[1] = C.x;
         w0[2] = C.y;
@@ -933,18 +948,18 @@ __device__ __forceinline__ void win2(const float* __restrict__ f, int b, v4 w0, 
 
 // x offsets of the two corners of a member with x sign SA: SA > 0: (LO, LO+1),
 // SA < 0: (-LO, -LO-1); returns the windows in corner order (ka = 0, 1)
-template <int LO, int SA>
-__device__ __forceinline__ void corners_x(const float* __restrict__ f, int b, v4 c0, v4 c1)
+template <int LO, int SA, bool LN>
+__device__ __forceinline__ void corners_x(const float* __restrict__ f, int b, v4 c0, v4 c1, Lanes ln)
 {
     if constexpr (SA > 0)
-        win2<LO>(f, b, c0, c1);
+        win2<LO, LN>(f, b, c0, c1, ln);
     else
-        win2<-LO - 1>(f, b, c1, c0);
+        win2<-LO - 1, LN>(f, b, c1, c0, ln);
 }
 
-template <int SIG, int PL, int M>
+template <int SIG, int PL, int M, bool LN>
 __device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int pb, v4 dq, v4 ua,
-                                         v4 ub, v4 gq)
+                                         v4 ub, v4 gq, Lanes ln)
 {
     // PL 0: plane (x, y); PL 1: plane (x, z); a = x
     constexpr int LO = cisqrt(SIG * SIG / 2), LOM = cisqrt((SIG / 2) * (SIG / 2) / 2);
@@ -956,18 +971,18 @@ __device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int 
         const int row = pb + SB * (LO + kb) * sbs;
         const float w0 = P.sh.nb_w[PL][2 * kb], w1 = P.sh.nb_w[PL][2 * kb + 1];
         v4 c0, c1;
-        corners_x<LO, SA>(fl.dn, row, c0, c1);
+        corners_x<LO, SA, LN>(fl.dn, row, c0, c1, ln);
 #pragma unroll
         for (int j = 0; j < 4; ++j) dq[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], dq[j]));
-        corners_x<LO, SA>(fl.ux, row, c0, c1);
+        corners_x<LO, SA, LN>(fl.ux, row, c0, c1, ln);
 #pragma unroll
         for (int j = 0; j < 4; ++j) ua[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], ua[j]));
-        corners_x<LO, SA>(fb, row, c0, c1);
+        corners_x<LO, SA, LN>(fb, row, c0, c1, ln);
 #pragma unroll
         for (int j = 0; j < 4; ++j) ub[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], ub[j]));
         const int mrow = pb + SB * (LOM + kb) * sbs;
         const float v0 = P.sh.md_w[PL][2 * kb], v1 = P.sh.md_w[PL][2 * kb + 1];
-        corners_x<LOM, SA>(fl.dG, mrow, c0, c1);
+        corners_x<LOM, SA, LN>(fl.dG, mrow, c0, c1, ln);
 #pragma unroll
         for (int j = 0; j < 4; ++j) gq[j] = fmaf(v1, c1[j], fmaf(v0, c0[j], gq[j]));
     }
@@ -1002,10 +1017,10 @@ __device__ __forceinline__ void member_yz(const Params& P, const Fields& fl, int
     }
 }
 
-template <int SIG, int PL, int M, bool C2>
+template <int SIG, int PL, int M, bool C2, bool LN>
 __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, int pb,
                                              const v4 ua0, const v4 ub0, float G0, float lk, v4 Aq,
-                                             v4 Pa, v4 Pb, v4 Cq)
+                                             v4 Pa, v4 Pb, v4 Cq, Lanes ln)
 {
     constexpr float h = 0.70710678118654752f;
     constexpr float sa = (M & 1) ? -1.f : 1.f, sb = (M & 2) ? -1.f : 1.f;
@@ -1015,7 +1030,7 @@ __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, 
     if constexpr (PL == 2)
         member_yz<SIG, M>(P, fl, pb, dq, ua, ub, gq);
     else
-        member_x<SIG, PL, M>(P, fl, pb, dq, ua, ub, gq);
+        member_x<SIG, PL, M, LN>(P, fl, pb, dq, ua, ub, gq, ln);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         Aq[j] = shell_A(dq[j], gq[j], G0);
@@ -1026,18 +1041,18 @@ __device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, 
     }
 }
 
-template <int SIG, int PL, bool C2>
+template <int SIG, int PL, bool C2, bool LN>
 __device__ __forceinline__ void quartet4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
-                                         float G0, float lk, v4 f[3], v4 cc)
+                                         float G0, float lk, v4 f[3], v4 cc, Lanes ln)
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
     constexpr float c = 0.70710678118654752f / 15.f;
     v4 A0, P0a, P0b, A1, P1a, P1b, A2, P2a, P2b, A3, P3a, P3b, C0, C1, C2m, C3;
-    member_terms<SIG, PL, 0, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A0, P0a, P0b, C0);
-    member_terms<SIG, PL, 1, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A1, P1a, P1b, C1);
-    member_terms<SIG, PL, 2, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A2, P2a, P2b, C2m);
-    member_terms<SIG, PL, 3, C2>(P, fl, pb, u0[a], u0[b], G0, lk, A3, P3a, P3b, C3);
+    member_terms<SIG, PL, 0, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A0, P0a, P0b, C0, ln);
+    member_terms<SIG, PL, 1, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A1, P1a, P1b, C1, ln);
+    member_terms<SIG, PL, 2, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A2, P2a, P2b, C2m, ln);
+    member_terms<SIG, PL, 3, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A3, P3a, P3b, C3, ln);
     if constexpr (C2) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) cc[j] += (1.f / 15.f) * ((C0[j] + C1[j]) + (C2m[j] + C3[j]));
@@ -1088,23 +1103,33 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
 // At most 128 registers, so that four CTAs (16 warps) share an SM: the
 // kernel waits on L1 far more than it computes, and the extra warps hide
 // that latency (measured: 146 registers / 3 CTAs per SM is 6 % slower).
-template <int SIG, bool C2>
+// LN: tiled mapping with lane shuffles (every exit above the node's own
+// x test is taken by whole warps; lanes past the grid's edge stay, on the
+// row's first block, until the stores)
+template <int SIG, bool C2, bool LN>
 __global__ void __launch_bounds__(128, 4) k_force4(Params P, TileMap tm, Fields fl,
                                                 const float4* __restrict__ Ft, float4* __restrict__ F)
 {
     const Geom& g = P.g;
     int x, y, z;
-    if (tm.flat) {
+    bool live = true;
+    Lanes ln{false, false};
+    if (!LN) {
         if (!flat_node(g, tm, 4, x, y, z)) return;
     } else {
         int tx, ty;
         if (!tile_origin(g, tm, tx, ty, z)) return;
-        x = tx * 128 + 4 * (threadIdx.x % 32);
+        const int x0 = tx * 128, lane = threadIdx.x % 32;
+        x = x0 + 4 * lane;
         y = ty * tm.ty + threadIdx.x / 32;
-        if (x >= g.nx || y >= g.ny) return;
+        if (x0 >= g.nx || y >= g.ny) return;  // whole warp
+        live = x < g.nx;
+        if (!live) x = x0;
+        ln.hi = lane == 31 || x + 4 >= g.nx;
+        ln.lo = lane == 0;
     }
     const int s = slit_of(P, z);
-    if (s < 0 || frozen(P, s)) return;
+    if (s < 0 || frozen(P, s)) return;  // whole warp (one z plane)
     const SlitParam S = P.sl[s];
     const int pb = pidx(g, x, y, z);  // 16-byte aligned: x, hw, px multiples of 4
     v4 d0, u0[3];
@@ -1124,10 +1149,11 @@ __global__ void __launch_bounds__(128, 4) k_force4(Params P, TileMap tm, Fields 
         axis4<SIG, 0, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
         axis4<SIG, 1, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
         axis4<SIG, 2, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
-        quartet4<SIG, 0, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
-        quartet4<SIG, 1, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
-        quartet4<SIG, 2, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
+        quartet4<SIG, 0, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
+        quartet4<SIG, 1, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
+        quartet4<SIG, 2, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
     }
+    if (!live) return;
     const long long idx0 = ((long long)z * g.ny + y) * g.nx + x;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -1715,6 +1741,16 @@ cudaError_t launch_tail(const Params& P, const float* dn, const int* off, const 
     return cudaGetLastError();
 }
 
+template <int SIG, bool LN>
+static void force4_launch(const Params& P, const TileMap& tm, const Fields& f, const float4* Ft, float4* F,
+                          unsigned blocks, cudaStream_t s)
+{
+    if (P.c2)
+        k_force4<SIG, true, LN><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+    else
+        k_force4<SIG, false, LN><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+}
+
 cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F, int group,
                          cudaStream_t s)
 {
@@ -1724,16 +1760,16 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
         TileMap tm = P.g.nx < 128 ? make_flatmap(P.g, 4, 128, blocks) : make_tilemap(P.g, 128, 4, group, blocks);
         switch (P.sigma) {
         case 4:
-            if (P.c2) k_force4<4, true><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
-            else k_force4<4, false><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            if (tm.flat) force4_launch<4, false>(P, tm, f, Ft, F, blocks, s);
+            else force4_launch<4, true>(P, tm, f, Ft, F, blocks, s);
             break;
         case 8:
-            if (P.c2) k_force4<8, true><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
-            else k_force4<8, false><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            if (tm.flat) force4_launch<8, false>(P, tm, f, Ft, F, blocks, s);
+            else force4_launch<8, true>(P, tm, f, Ft, F, blocks, s);
             break;
         default:
-            if (P.c2) k_force4<12, true><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
-            else k_force4<12, false><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+            if (tm.flat) force4_launch<12, false>(P, tm, f, Ft, F, blocks, s);
+            else force4_launch<12, true>(P, tm, f, Ft, F, blocks, s);
             break;
         }
     } else {
