@@ -114,8 +114,8 @@ def kernel_bytes(storage: int, fused: bool):
 # 256x256x192 sigma = 12 slit of the current kernels; a full-size launch moves
 # these bytes times its node count (traffic grows with the nodes). Must be
 # re-measured whenever a kernel changes.
-TRAFFIC_B_PER_NODE_F32 = {"moments": 98.1, "ball_g2": 6.3, "force": 45.7, "collide_stream": 183.8,
-                          "collide_stream_fused": None}
+TRAFFIC_B_PER_NODE_F32 = {"moments": 98.2, "ball_g2": 6.0, "force": 45.7, "collide_stream": 183.5,
+                          "collide_stream_fused": 211.6}
 
 
 def dist_setup(args):
@@ -355,8 +355,9 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = _peaks()
     dom = max(kms, key=lambda k: kms[k])
     launches = sum(nl.values())
-    kb = kernel_bytes(storage, g.fused)
-    tkey = dom + ("_fused" if dom == "collide_stream" and g.fused else "")
+    fused = g.fused
+    kb = kernel_bytes(storage, fused)
+    tkey = dom + ("_fused" if dom == "collide_stream" and fused else "")
     dom_bytes = kb[dom] * N
     dom_ms = kms[dom] / max(nl[dom], 1)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
@@ -420,7 +421,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"slit {W.nx}x{W.ny}x{W.nz} sigma={W.sigma} eta={W.eta} tau={W.tau} "
                                f"F_e={W.body[0]} bounce-back z, periodic x,y, seeded 1e-3 noise",
                    "storage": args.storage, "nodes": N,
-                   "pass": "fused" if g.fused else "two-pass", "parallelism": f"replicas x{world}",
+                   "pass": "fused" if fused else "two-pass", "parallelism": f"replicas x{world}",
                    "l2": "populations (>= 1.9 GB) exceed L2; no flush",
                    "bytes_alg_per_node": bytes_alg(storage),
                    "step_gbs_alg": step_gbs, "step_roofline_frac": step_gbs / peak,

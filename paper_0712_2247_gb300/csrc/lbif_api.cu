@@ -416,7 +416,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
         h->ball_map_ok = make_ball_map(g, P.sigma, h->dn[0], &h->ball_map[0]) &&
                          make_ball_map(g, P.sigma, h->dn[1], &h->ball_map[1]) &&
                          make_ball_map(g, P.sigma, h->dn[2], &h->ball_map[2]);
-        h->fused = csm_ok(g);
+        h->fused = csm_default(g, P.storage);
     }
     P.sl = h->d_sl;
     P.zslit = h->d_zslit;
@@ -1163,6 +1163,13 @@ extern "C" int lbif_set_fused(lbif_handle h, int32_t fused)
             h->graph = nullptr;
         }
     }
+    return LBIF_OK;
+}
+
+extern "C" int lbif_get_fused(lbif_handle h, int32_t* fused)
+{
+    if (!h || !fused) return fail(h, LBIF_ERR_ARG, "lbif_get_fused: bad arguments");
+    *fused = h->fused ? 1 : 0;
     return LBIF_OK;
 }
 

@@ -160,6 +160,8 @@ cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields
 // one step's collision, pull streaming and the moments of the new
 // populations (CsmIO); lz: z planes per CTA segment (<= 0: default)
 bool csm_ok(const Geom& g);
+// the pass a handle starts with (FP32 storage and N >= 2^23 nodes)
+bool csm_default(const Geom& g, int storage);
 cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
                        int* status, int lz, cudaStream_t s);
 cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s);

@@ -68,6 +68,7 @@ SIGNATURES = {
     "lbif_batch_profiles": (_i32, [_vp, _pd, _pd, _i32]),
     "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "lbif_set_fused": (_i32, [_vp, _i32]),
+    "lbif_get_fused": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "lbif_field_profiles_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _pd, _pd, _pd, _vp]),
     "lbif_noalloc_last_error": (ctypes.c_char_p, []),
     "lbif_destroy": (_i32, [_vp]),
@@ -144,7 +145,6 @@ class Slit:
         self.N = nx * ny * nz
         self.sigma, self.eta, self.tau = sigma, eta, tau
         self.n0 = 6.0 * eta / (np.pi * sigma ** 3)
-        self.fused = nx >= 32 and ny >= 8  # the library's default (lbif_set_fused)
 
     # -- plumbing ---------------------------------------------------------
     def _check(self, rc: int, allow_diverged: bool = False):
@@ -186,7 +186,12 @@ class Slit:
         """One pass per step (pull collide-stream with the next moments, the
         default where nx >= 32 and ny >= 8) or push collide-stream + moments."""
         self._check(self._lib.lbif_set_fused(self._h, 1 if on else 0))
-        self.fused = bool(on)
+
+    @property
+    def fused(self) -> bool:
+        v = ctypes.c_int32()
+        self._check(self._lib.lbif_get_fused(self._h, ctypes.byref(v)))
+        return bool(v.value)
 
     def moments(self, rho=None, u=None, pressure=None, allow_diverged=False):
         """Fill caller-owned buffers; with no buffers, return numpy (rho, u) arrays."""
@@ -285,7 +290,6 @@ class Ensemble(Slit):
         nz = int(zlo[-1] + H[-1])
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
-        self.fused = nx >= 32 and ny >= 8
 
     def seed(self, n_z, ux_z=None):
         """Set every slit to the equilibrium of profiles n_z[s, j], ux_z[s, j] (j < H[s])."""

@@ -84,6 +84,9 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbif_step(None, 1) == -1
     assert lib.lbif_destroy(None) == -1
     assert lib.lbif_moments(None, None, None, None, 0) == -1
+    assert lib.lbif_set_fused(None, 1) == -1
+    v = ctypes.c_int32(7)
+    assert lib.lbif_get_fused(None, ctypes.byref(v)) == -1 and v.value == 7
     assert lib.lbif_last_error(None)
 
 

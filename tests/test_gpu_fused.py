@@ -153,14 +153,15 @@ def test_fused_with_options(L, O, extra):
 
 
 def test_fused_ensemble_matches_oracle_and_freezes(L, O):
-    """Stacked slits on 32 x 8 rows (fused by default): parity per slit, and
-    run-to-steady-state with frozen slits gives the same profiles as the
+    """Stacked slits on 32 x 8 rows through the fused pass: parity per slit,
+    and run-to-steady-state with frozen slits gives the same profiles as the
     two-pass ensemble to FP32 rounding."""
     H = np.array([9, 16, 12], np.int32)
     eta = np.array([0.15, 0.25, 0.2])
     F = np.array([2e-6, 1e-6, 5e-6])
     tau = np.array([0.8, 1.0, 0.7])
     e = L.Ensemble(H, eta, F, tau, sigma=4, nx=32, ny=8, storage=0, noise=0.0)
+    e.set_fused(True)
     hmax = int(H.max())
     nz = np.zeros((len(H), hmax), np.float32)
     for s, h in enumerate(H):
@@ -181,6 +182,7 @@ def test_fused_ensemble_matches_oracle_and_freezes(L, O):
     for s in (0, 2):
         h = int(H[s])
         g = L.Slit(32, 8, h, 4, eta[s], tau[s], body=(F[s], 0, 0), noise=0.0)
+        g.set_fused(True)
         g.set_fields(np.repeat(nz[s, :h], 256).reshape(h, 8, 32).astype(np.float32))
         g.step(50)
         n1, u1, _ = g.profiles()
