@@ -165,6 +165,15 @@ __device__ __forceinline__ void load_pops(const Params& P, const T* __restrict__
     for (int i = 0; i < Q; ++i) h[i] = ldp(pop + (long long)i * P.g.Npad + idx);
 }
 
+// acc += c x for a lattice-velocity component c in {-1, 0, 1} known after
+// unrolling (a product with a zero component is not folded under IEEE rules,
+// so the zero case must not be written as one)
+__device__ __forceinline__ void add_c(float& acc, int c, float x)
+{
+    if (c > 0) acc += x;
+    if (c < 0) acc -= x;
+}
+
 // S = sum_i w_i g_i (density change since the reference), J = sum_i w_i c_i g_i
 __device__ __forceinline__ void sums_of(const float g[Q], float& S, float& jx, float& jy, float& jz)
 {
@@ -173,9 +182,9 @@ __device__ __forceinline__ void sums_of(const float g[Q], float& S, float& jx, f
     for (int i = 0; i < Q; ++i) {
         float wg = kW(i) * g[i];
         s += wg;
-        ax += kCx(i) * wg;
-        ay += kCy(i) * wg;
-        az += kCz(i) * wg;
+        add_c(ax, kCx(i), wg);
+        add_c(ay, kCy(i), wg);
+        add_c(az, kCz(i), wg);
     }
     S = s;
     jx = ax;
@@ -183,10 +192,29 @@ __device__ __forceinline__ void sums_of(const float g[Q], float& S, float& jx, f
     jz = az;
 }
 
+// c_i . (x, y, z), adding only the nonzero components (in increasing axis
+// order, as the full dot product rounds them)
+__device__ __forceinline__ float dot_c(int i, float x, float y, float z)
+{
+    const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+    if (cx != 0) {
+        float r = cx > 0 ? x : -x;
+        add_c(r, cy, y);
+        add_c(r, cz, z);
+        return r;
+    }
+    if (cy != 0) {
+        float r = cy > 0 ? y : -y;
+        add_c(r, cz, z);
+        return r;
+    }
+    return cz > 0 ? z : (cz < 0 ? -z : 0.f);
+}
+
 // e_i = h_i^eq - dn = (1 + dn)(3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
 __device__ __forceinline__ float eq_excess(int i, float opd, float ux, float uy, float uz, float uu)
 {
-    float cu = kCx(i) * ux + kCy(i) * uy + kCz(i) * uz;
+    float cu = dot_c(i, ux, uy, uz);
     return opd * (3.f * cu + 4.5f * cu * cu - 1.5f * uu);
 }
 
@@ -1248,7 +1276,7 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
         for (int i = 0; i < Q; ++i) {
             float k = gi[i] - S;
             float e = eq_excess(i, opd, ux, uy, uz, uu);
-            float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z) +
+            float ks = k - (k - e) * inv_tau + 3.f * dot_c(i, f.x, f.y, f.z) +
                        1.5f * f.w * (float)(kC2(i) - 1);
             stp(pout + (long long)i * g.Npad + (idx + P.soff[i]), ks + dd[i]);
         }
@@ -1258,7 +1286,7 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
     for (int i = 0; i < Q; ++i) {
         float k = gi[i] - S;
         float e = eq_excess(i, opd, ux, uy, uz, uu);
-        float ks = k - (k - e) * inv_tau + 3.f * (kCx(i) * f.x + kCy(i) * f.y + kCz(i) * f.z) +
+        float ks = k - (k - e) * inv_tau + 3.f * dot_c(i, f.x, f.y, f.z) +
                        1.5f * f.w * (float)(kC2(i) - 1);
         int tx = x + kCx(i), ty = y + kCy(i), tz = z + kCz(i);
         tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
@@ -1312,9 +1340,35 @@ size_t csm_smem_bytes() { return sizeof(float) * 3 * CSM_SLOT; }
 
 __device__ __forceinline__ int csm_slot(int q) { return (q + 3) % 3; }
 
-// stage plane q (-1 <= q <= nz) of the tile at (x0, y0) into `slot`
+// The (at most two) halo nodes a thread stages in every plane: h = thread,
+// thread + CSM_THREADS; their in-plane padded offset (x, y halo images hold
+// the periodic values) and the in-plane index of their periodic image in the
+// unpadded force array, or -1 (past the 340th node or a partial tile: never
+// gathered).
+struct CsmStaged {
+    int p[2], n[2];
+};
+
+__device__ __forceinline__ CsmStaged csm_staged(const Geom& g, int x0, int y0)
+{
+    CsmStaged st;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int h = threadIdx.x + k * CSM_THREADS;
+        const int X = x0 - 1 + h % CSM_HX, Y = y0 - 1 + h / CSM_HX;
+        st.p[k] = st.n[k] = -1;
+        if (h >= CSM_HN || X > g.nx || Y > g.ny) continue;
+        const int xw = X < 0 ? X + g.nx : (X >= g.nx ? X - g.nx : X);
+        const int yw = Y < 0 ? Y + g.ny : (Y >= g.ny ? Y - g.ny : Y);
+        st.p[k] = (Y + g.hw) * g.px + (X + g.hw);
+        st.n[k] = yw * g.nx + xw;
+    }
+    return st;
+}
+
+// stage plane q (-1 <= q <= nz) of the tile into `slot`
 __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, const float4* __restrict__ F,
-                                          float* slot, int x0, int y0, int q)
+                                          float* slot, const CsmStaged& st, int q)
 {
     const Geom& g = P.g;
     int zq = q;
@@ -1325,13 +1379,14 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
     const int sq = slit_of(P, zq);
     if (sq < 0 || frozen(P, sq)) return;
     const float om = P.sl[sq].inv_tau;
-    for (int h = threadIdx.x; h < CSM_HN; h += CSM_THREADS) {
-        const int X = x0 - 1 + h % CSM_HX, Y = y0 - 1 + h / CSM_HX;
-        if (X > g.nx || Y > g.ny) continue;  // past a partial tile: never gathered
-        const int p = pidx(g, X, Y, q);       // x, y halo images hold the periodic values
-        const int xw = X < 0 ? X + g.nx : (X >= g.nx ? X - g.nx : X);
-        const int yw = Y < 0 ? Y + g.ny : (Y >= g.ny ? Y - g.ny : Y);
-        const float4 f = __ldg(F + ((long long)zq * g.ny + yw) * g.nx + xw);
+    const int pq = (q + g.hw) * g.py * g.px;
+    const float4* Fq = F + (long long)zq * g.ny * g.nx;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (st.p[k] < 0) continue;
+        const int h = threadIdx.x + k * CSM_THREADS;
+        const int p = pq + st.p[k];
+        const float4 f = __ldg(Fq + st.n[k]);
         const float d = __ldg(io.dn + p);
         const float ux = __ldg(io.ux + p), uy = __ldg(io.uy + p), uz = __ldg(io.uz + p);
         const float K = io.dref == io.dn ? 0.f : (1.f - om) * (__ldg(io.dref + p) - d);
@@ -1377,8 +1432,9 @@ __global__ void __launch_bounds__(CSM_THREADS, CSM_MINB) k_csm(Params P, const T
     const int hc = (threadIdx.x / CSM_TX + 1) * CSM_HX + threadIdx.x % CSM_TX + 1;
     const bool in_xy = x < g.nx && y < g.ny;
     const int zb = seg * lz, ze = min(zb + lz, g.nz);
-    csm_stage(P, io, F, sm + csm_slot(zb - 1) * CSM_SLOT, x0, y0, zb - 1);
-    csm_stage(P, io, F, sm + csm_slot(zb) * CSM_SLOT, x0, y0, zb);
+    const CsmStaged st = csm_staged(g, x0, y0);
+    csm_stage(P, io, F, sm + csm_slot(zb - 1) * CSM_SLOT, st, zb - 1);
+    csm_stage(P, io, F, sm + csm_slot(zb) * CSM_SLOT, st, zb);
     for (int z = zb; z < ze; ++z) {
         // issue the population loads first: they do not depend on the ring
         const int s = slit_of(P, z);
@@ -1411,7 +1467,7 @@ __global__ void __launch_bounds__(CSM_THREADS, CSM_MINB) k_csm(Params P, const T
             }
         }
         __syncthreads();  // the slot of plane z - 2 is free
-        csm_stage(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, x0, y0, z + 1);
+        csm_stage(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, st, z + 1);
         __syncthreads();
         if (!act) continue;
         const float* own = sm + csm_slot(z) * CSM_SLOT;
