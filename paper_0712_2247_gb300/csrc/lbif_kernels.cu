@@ -1340,21 +1340,24 @@ size_t csm_smem_bytes() { return sizeof(float) * 3 * CSM_SLOT; }
 
 __device__ __forceinline__ int csm_slot(int q) { return (q + 3) % 3; }
 
-// The (at most two) halo nodes a thread stages in every plane: h = thread,
-// thread + CSM_THREADS; their in-plane padded offset (x, y halo images hold
-// the periodic values) and the in-plane index of their periodic image in the
-// unpadded force array, or -1 (past the 340th node or a partial tile: never
-// gathered).
+// The halo nodes a thread stages in every plane (NT threads: h = thread,
+// thread + NT, ...; at most two): their in-plane padded offset (x, y halo
+// images hold the periodic values) and the in-plane index of their periodic
+// image in the unpadded force array, or -1 (past the 340th node or a partial
+// tile: never gathered).
+constexpr int CSM_KS = 2;
 struct CsmStaged {
-    int p[2], n[2];
+    int p[CSM_KS], n[CSM_KS];
 };
 
+template <int NT>
 __device__ __forceinline__ CsmStaged csm_staged(const Geom& g, int x0, int y0)
 {
+    static_assert(NT * CSM_KS >= CSM_HN, "two staged nodes per thread at most");
     CsmStaged st;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int h = threadIdx.x + k * CSM_THREADS;
+    for (int k = 0; k < CSM_KS; ++k) {
+        const int h = threadIdx.x + k * NT;
         const int X = x0 - 1 + h % CSM_HX, Y = y0 - 1 + h / CSM_HX;
         st.p[k] = st.n[k] = -1;
         if (h >= CSM_HN || X > g.nx || Y > g.ny) continue;
@@ -1367,6 +1370,7 @@ __device__ __forceinline__ CsmStaged csm_staged(const Geom& g, int x0, int y0)
 }
 
 // stage plane q (-1 <= q <= nz) of the tile into `slot`
+template <int NT>
 __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, const float4* __restrict__ F,
                                           float* slot, const CsmStaged& st, int q)
 {
@@ -1382,9 +1386,9 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
     const int pq = (q + g.hw) * g.py * g.px;
     const float4* Fq = F + (long long)zq * g.ny * g.nx;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        if (st.p[k] < 0) continue;
-        const int h = threadIdx.x + k * CSM_THREADS;
+    for (int k = 0; k < CSM_KS; ++k) {
+        if (k * NT >= CSM_HN || st.p[k] < 0) continue;
+        const int h = threadIdx.x + k * NT;
         const int p = pq + st.p[k];
         const float4 f = __ldg(Fq + st.n[k]);
         const float d = __ldg(io.dn + p);
@@ -1418,123 +1422,166 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
 #define CSM_LZ 16
 #endif
 
-template <typename T>
-__global__ void __launch_bounds__(CSM_THREADS, CSM_MINB) k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout,
-                                                        CsmIO io, const float4* __restrict__ F, int lz,
-                                                        int tiles_x, int tiles_y, int* status)
+// the populations of directions [I0, I1) that stream into node (x, y, z):
+// v[i - I0]; bit i of bb marks a direction that arrives from a wall
+// (bounce-back: the node's own opposite population)
+template <int I0, int I1, typename T>
+__device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ pin, long long idx, int x, int y,
+                                         int z, int zlo, int zhi, float* v, unsigned& bb)
 {
+    const Geom& g = P.g;
+    if (x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi) {
+#pragma unroll
+        for (int i = I0; i < I1; ++i) v[i - I0] = ldp(pin + (long long)i * g.Npad + (idx - P.soff[i]));
+        return;
+    }
+#pragma unroll
+    for (int i = I0; i < I1; ++i) {
+        int sx = x - kCx(i), sy = y - kCy(i), sz = z - kCz(i);
+        sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
+        sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
+        if (g.zper) {
+            sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
+        } else if (sz < zlo || sz > zhi) {
+            bb |= 1u << i;
+            v[i - I0] = ldp(pin + (long long)opp_of(i) * g.Npad + idx);
+            continue;
+        }
+        v[i - I0] = ldp(pin + (long long)i * g.Npad + (((long long)sz * g.ny + sy) * g.nx + sx));
+    }
+}
+
+// the post-collision values of directions [I0, I1) reaching the node (hc in
+// the staged planes), relative to its current density dnr
+template <int I0, int I1>
+__device__ __forceinline__ void csm_collide(const float* own, const float* below, const float* above, int hc,
+                                            float om1, float dnr, unsigned bb, float* v)
+{
+    constexpr int J0 = I0 == 0 ? 1 : I0;
+    if (I0 == 0) {
+        const float c0 = (2.f * (own[(SQ_CA + 0) * CSM_HN + hc] + own[(SQ_CA + 1) * CSM_HN + hc] +
+                                 own[(SQ_CA + 2) * CSM_HN + hc]) -
+                          (own[(SQ_CP + 0) * CSM_HN + hc] + own[(SQ_CP + 1) * CSM_HN + hc] +
+                           own[(SQ_CP + 2) * CSM_HN + hc])) * (1.f / 3.f);
+        v[0] = fmaf(om1, v[0], c0);
+    }
+    if (bb == 0) {
+        // no wall: every source is r - c_i (offsets fixed at compile time)
+#pragma unroll
+        for (int i = J0; i < I1; ++i) {
+            const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+            const float* sl = (cz > 0 ? below : (cz < 0 ? above : own)) + hc - cx - cy * CSM_HX;
+            float t;
+            if (kC2(i) == 1) {
+                const int a = cx ? 0 : (cy ? 1 : 2);
+                const float ca = (float)(cx + cy + cz);
+                t = fmaf(ca, sl[(SQ_P + a) * CSM_HN], sl[(SQ_CA + a) * CSM_HN]);
+            } else {
+                const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
+                const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
+                const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
+                t = sl[(SQ_CP + pl) * CSM_HN] + (ca * sl[(SQ_P + a) * CSM_HN] + cb * sl[(SQ_P + b) * CSM_HN]) +
+                    (ca * cb) * sl[(SQ_X + pl) * CSM_HN];
+            }
+            v[i - I0] = fmaf(om1, v[i - I0], t) + (sl[SQ_DN * CSM_HN] - dnr);
+        }
+        return;
+    }
+#pragma unroll
+    for (int i = J0; i < I1; ++i) {
+        const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+        const bool wall = (bb >> i) & 1u;
+        // source node: r - c_i in plane z - c_z, or r itself with -c_i at a wall
+        const float* sl = wall ? own : (cz > 0 ? below : (cz < 0 ? above : own));
+        const int h = wall ? hc : hc - cx - cy * CSM_HX;
+        const float sg = wall ? -1.f : 1.f;
+        float t;
+        if (kC2(i) == 1) {
+            const int a = cx ? 0 : (cy ? 1 : 2);
+            const float ca = (float)(cx + cy + cz);
+            t = fmaf(sg * ca, sl[(SQ_P + a) * CSM_HN + h], sl[(SQ_CA + a) * CSM_HN + h]);
+        } else {
+            const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
+            const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
+            const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
+            t = sl[(SQ_CP + pl) * CSM_HN + h] +
+                sg * (ca * sl[(SQ_P + a) * CSM_HN + h] + cb * sl[(SQ_P + b) * CSM_HN + h]) +
+                (ca * cb) * sl[(SQ_X + pl) * CSM_HN + h];
+        }
+        const float d = wall ? 0.f : sl[SQ_DN * CSM_HN + h] - dnr;
+        v[i - I0] = fmaf(om1, v[i - I0], t) + d;
+    }
+}
+
+// sum over directions [I0, I1) of w_i v_i and w_i c_i v_i
+template <int I0, int I1>
+__device__ __forceinline__ void csm_sums(const float* v, float (&m)[4])
+{
+#pragma unroll
+    for (int i = I0; i < I1; ++i) {
+        const float wg = kW(i) * v[i - I0];
+        m[0] += wg;
+        add_c(m[1], kCx(i), wg);
+        add_c(m[2], kCy(i), wg);
+        add_c(m[3], kCz(i), wg);
+    }
+}
+
+// one node per thread, a CTA per 32 x 8 tile and z segment (measured: two
+// threads per node, each gathering half of the directions and adding the
+// partial moments through shared memory, ran slower at twice the warps)
+template <typename T>
+__global__ void __launch_bounds__(CSM_THREADS, CSM_MINB)
+    k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout, CsmIO io, const float4* __restrict__ F,
+          int lz, int tiles_x, int tiles_y, int* status)
+{
+    constexpr int NT = CSM_THREADS;
     extern __shared__ float sm[];
     const Geom& g = P.g;
     const int tiles = tiles_x * tiles_y;
     const int tile = blockIdx.x % tiles, seg = blockIdx.x / tiles;
     const int x0 = (tile % tiles_x) * CSM_TX, y0 = (tile / tiles_x) * CSM_TY;
-    const int x = x0 + threadIdx.x % CSM_TX, y = y0 + threadIdx.x / CSM_TX;
-    const int hc = (threadIdx.x / CSM_TX + 1) * CSM_HX + threadIdx.x % CSM_TX + 1;
+    const int t = threadIdx.x;
+    const int x = x0 + t % CSM_TX, y = y0 + t / CSM_TX;
+    const int hc = (t / CSM_TX + 1) * CSM_HX + t % CSM_TX + 1;
     const bool in_xy = x < g.nx && y < g.ny;
     const int zb = seg * lz, ze = min(zb + lz, g.nz);
-    const CsmStaged st = csm_staged(g, x0, y0);
-    csm_stage(P, io, F, sm + csm_slot(zb - 1) * CSM_SLOT, st, zb - 1);
-    csm_stage(P, io, F, sm + csm_slot(zb) * CSM_SLOT, st, zb);
+    const CsmStaged st = csm_staged<NT>(g, x0, y0);
+    csm_stage<NT>(P, io, F, sm + csm_slot(zb - 1) * CSM_SLOT, st, zb - 1);
+    csm_stage<NT>(P, io, F, sm + csm_slot(zb) * CSM_SLOT, st, zb);
     for (int z = zb; z < ze; ++z) {
         // issue the population loads first: they do not depend on the ring
         const int s = slit_of(P, z);
         const bool act = in_xy && s >= 0 && !frozen(P, s);
         float v[Q];
-        unsigned bb = 0;  // bit i: direction i arrives from a wall (bounce-back)
+        unsigned bb = 0;
         const long long idx = ((long long)z * g.ny + y) * g.nx + x;
         float om = 0.f;
         if (act) {
             const int zlo = P.sl[s].zlo, zhi = P.sl[s].zhi;
             om = P.sl[s].inv_tau;
-            if (x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi) {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) v[i] = ldp(pin + (long long)i * g.Npad + (idx - P.soff[i]));
-            } else {
-#pragma unroll
-                for (int i = 0; i < Q; ++i) {
-                    int sx = x - kCx(i), sy = y - kCy(i), sz = z - kCz(i);
-                    sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
-                    sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
-                    if (g.zper) {
-                        sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
-                    } else if (sz < zlo || sz > zhi) {
-                        bb |= 1u << i;
-                        v[i] = ldp(pin + (long long)opp_of(i) * g.Npad + idx);
-                        continue;
-                    }
-                    v[i] = ldp(pin + (long long)i * g.Npad + (((long long)sz * g.ny + sy) * g.nx + sx));
-                }
-            }
+            csm_pull<0, Q>(P, pin, idx, x, y, z, zlo, zhi, v, bb);
         }
         __syncthreads();  // the slot of plane z - 2 is free
-        csm_stage(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, st, z + 1);
+        csm_stage<NT>(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, st, z + 1);
         __syncthreads();
+        float m[4] = {0.f, 0.f, 0.f, 0.f};
+        float dnr = 0.f;
+        if (act) {
+            const float* own = sm + csm_slot(z) * CSM_SLOT;
+            const float* below = sm + csm_slot(z - 1) * CSM_SLOT;
+            const float* above = sm + csm_slot(z + 1) * CSM_SLOT;
+            dnr = own[SQ_DN * CSM_HN + hc];
+            csm_collide<0, Q>(own, below, above, hc, 1.f - om, dnr, bb, v);
+            csm_sums<0, Q>(v, m);
+        }
         if (!act) continue;
-        const float* own = sm + csm_slot(z) * CSM_SLOT;
-        const float* below = sm + csm_slot(z - 1) * CSM_SLOT;
-        const float* above = sm + csm_slot(z + 1) * CSM_SLOT;
-        const float om1 = 1.f - om;
-        const float dnr = own[SQ_DN * CSM_HN + hc];
-        {
-            const float c0 = (2.f * (own[(SQ_CA + 0) * CSM_HN + hc] + own[(SQ_CA + 1) * CSM_HN + hc] +
-                                     own[(SQ_CA + 2) * CSM_HN + hc]) -
-                              (own[(SQ_CP + 0) * CSM_HN + hc] + own[(SQ_CP + 1) * CSM_HN + hc] +
-                               own[(SQ_CP + 2) * CSM_HN + hc])) * (1.f / 3.f);
-            v[0] = fmaf(om1, v[0], c0);
-        }
-        if (bb == 0) {
-            // no wall: every source is r - c_i (offsets fixed at compile time)
-#pragma unroll
-            for (int i = 1; i < Q; ++i) {
-                const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
-                const float* sl = (cz > 0 ? below : (cz < 0 ? above : own)) + hc - cx - cy * CSM_HX;
-                float t;
-                if (kC2(i) == 1) {
-                    const int a = cx ? 0 : (cy ? 1 : 2);
-                    const float ca = (float)(cx + cy + cz);
-                    t = fmaf(ca, sl[(SQ_P + a) * CSM_HN], sl[(SQ_CA + a) * CSM_HN]);
-                } else {
-                    const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
-                    const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
-                    const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
-                    t = sl[(SQ_CP + pl) * CSM_HN] + (ca * sl[(SQ_P + a) * CSM_HN] + cb * sl[(SQ_P + b) * CSM_HN]) +
-                        (ca * cb) * sl[(SQ_X + pl) * CSM_HN];
-                }
-                v[i] = fmaf(om1, v[i], t) + (sl[SQ_DN * CSM_HN] - dnr);
-            }
-        } else {
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
-            const bool wall = (bb >> i) & 1u;
-            // source node: r - c_i in plane z - c_z, or r itself with -c_i at a wall
-            const float* sl = wall ? own : (cz > 0 ? below : (cz < 0 ? above : own));
-            const int h = wall ? hc : hc - cx - cy * CSM_HX;
-            const float sg = wall ? -1.f : 1.f;
-            float t;
-            if (kC2(i) == 1) {
-                const int a = cx ? 0 : (cy ? 1 : 2);
-                const float ca = (float)(cx + cy + cz);
-                t = fmaf(sg * ca, sl[(SQ_P + a) * CSM_HN + h], sl[(SQ_CA + a) * CSM_HN + h]);
-            } else {
-                const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
-                const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
-                const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
-                t = sl[(SQ_CP + pl) * CSM_HN + h] +
-                    sg * (ca * sl[(SQ_P + a) * CSM_HN + h] + cb * sl[(SQ_P + b) * CSM_HN + h]) +
-                    (ca * cb) * sl[(SQ_X + pl) * CSM_HN + h];
-            }
-            const float d = wall ? 0.f : sl[SQ_DN * CSM_HN + h] - dnr;
-            v[i] = fmaf(om1, v[i], t) + d;
-        }
-        }
-        float S, jx, jy, jz;
-        sums_of(v, S, jx, jy, jz);
+        const float S = m[0];
 #pragma unroll
         for (int i = 0; i < Q; ++i) stp(pout + (long long)i * g.Npad + idx, v[i] - S);
         const float dn = dnr + S;
         const float inv = 1.f / (1.f + dn);
-        const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
+        const float ux = m[1] * inv, uy = m[2] * inv, uz = m[3] * inv;
         if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
         auto put = [&](int p) {
             io.dnw[p] = dn;
