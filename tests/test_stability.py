@@ -159,7 +159,8 @@ def _lagged_radius(oracle_mod, sigma, eta, tau, coupling):
 
 def test_lagged_force_single_pass_variant_is_unstable(oracle_mod):
     """Driving the collision of step t with the force of step t - 1 (what a
-    single pass fusing moments and collision needs) makes the scheme
+    push-form single pass, collision then moments of the same node, needs)
+    makes the scheme
     unstable: the linearised two-step map grows even at eta = 0.02 with the
     density-current term (at 0.25 without it), and the FP64 oracle's lagged
     steps diverge where plain steps stay at rest."""
