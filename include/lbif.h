@@ -200,6 +200,17 @@ int lbif_set_fused(lbif_handle h, int32_t fused);
 /* The pass in use: *fused = 1 fused, 0 two passes. */
 int lbif_get_fused(lbif_handle h, int32_t* fused);
 
+/* Self-test of the failure path of the bounded device waits (the paper has no
+ * counterpart). The kernels that wait on an mbarrier for a tile copy give up
+ * after a fixed number of polls, record a status bit, and return, so that a
+ * lost copy surfaces as LBIF_ERR_TIMEOUT instead of a hang. This call runs the
+ * same wait on a barrier that nothing completes, with `polls` polls (>= 1),
+ * on the current device's default stream, and synchronises. *timed_out = 1
+ * and LBIF_ERR_TIMEOUT when the wait ran out (always, unless the device is
+ * broken); LBIF_ERR_ARG for polls < 1 or a NULL pointer. The CUDA context
+ * stays usable afterwards. */
+int lbif_selftest_wait(int64_t polls, int32_t* timed_out);
+
 /* Time the candidate launch shapes of the ball and force kernels on this
  * handle's current state (trials launches each) and keep the fastest: the
  * ball kernel's CTA target and its plane staging (1 = tensor-memory-

@@ -1166,6 +1166,25 @@ extern "C" int lbif_set_fused(lbif_handle h, int32_t fused)
     return LBIF_OK;
 }
 
+extern "C" int lbif_selftest_wait(int64_t polls, int32_t* timed_out)
+{
+    if (polls < 1 || !timed_out) return fail(nullptr, LBIF_ERR_ARG, "lbif_selftest_wait: bad arguments");
+    int* st = nullptr;
+    if (cudaMalloc((void**)&st, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, LBIF_ERR_NOMEM, "lbif_selftest_wait: device allocation failed");
+    }
+    int v = 0;
+    cudaError_t e = cudaMemset(st, 0, sizeof(int));
+    if (e == cudaSuccess) e = launch_wait_selftest((long long)polls, st, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(st);
+    if (e != cudaSuccess) return fail(nullptr, LBIF_ERR_CUDA, std::string("lbif_selftest_wait: ") + cudaGetErrorString(e));
+    *timed_out = (v & 4) ? 1 : 0;
+    return *timed_out ? fail(nullptr, LBIF_ERR_TIMEOUT, "lbif_selftest_wait: the bounded wait ran out")
+                      : LBIF_OK;
+}
+
 extern "C" int lbif_get_fused(lbif_handle h, int32_t* fused)
 {
     if (!h || !fused) return fail(h, LBIF_ERR_ARG, "lbif_get_fused: bad arguments");

@@ -164,6 +164,8 @@ bool csm_ok(const Geom& g);
 bool csm_default(const Geom& g, int storage);
 cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
                        int* status, int lz, cudaStream_t s);
+// bounded mbarrier wait on a barrier nothing completes: sets bit 4 of status
+cudaError_t launch_wait_selftest(long long polls, int* status, cudaStream_t s);
 cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s);
 cudaError_t launch_moments_out(const Params& P, const Fields& f, float* rho, float* u, float* p,
                                cudaStream_t s);

@@ -435,6 +435,24 @@ __device__ __forceinline__ bool mbar_wait_parity(uint64_t* mbar, uint32_t parity
 
 constexpr long long BALL_WAIT_LIMIT = 1LL << 22;  // try_wait polls; seconds at most
 
+// Self-test of the bounded wait above: the CTA waits on an mbarrier that
+// nothing arrives on (its first phase never completes), gives up after
+// `polls` polls, records bit 4 of status as the tile kernels do, and returns.
+__global__ void k_wait_selftest(long long polls, int* status)
+{
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    long long spins = 0;
+    bool ok;
+    while (!(ok = mbar_wait_parity(&mbar, 0)) && ++spins < polls) {
+    }
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(status, 4);
+}
+
 // does tile row r (relative to a thread's first node row minus R) enter a
 // disc sum D_k of any of the thread's BALL_YT nodes with row half-width w?
 __host__ __device__ constexpr bool ball_row_used(int R, int r, int w)
@@ -1939,6 +1957,12 @@ cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO
     else
         k_csm<float><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const float*)pin, (float*)pout, io, F, lz,
                                                                 tx, ty, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(long long polls, int* status, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 128, 0, s>>>(polls, status);
     return cudaGetLastError();
 }
 

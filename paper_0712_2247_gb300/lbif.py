@@ -69,6 +69,7 @@ SIGNATURES = {
     "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "lbif_set_fused": (_i32, [_vp, _i32]),
     "lbif_get_fused": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "lbif_selftest_wait": (_i32, [_i64, ctypes.POINTER(_i32)]),
     "lbif_field_profiles_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _pd, _pd, _pd, _vp]),
     "lbif_noalloc_last_error": (ctypes.c_char_p, []),
     "lbif_destroy": (_i32, [_vp]),
@@ -116,6 +117,15 @@ def _on_device(*arrays) -> int:
         if a is not None:
             return 0 if isinstance(a, np.ndarray) else int(a.is_cuda)
     return 0
+
+
+def selftest_wait(polls: int):
+    """Run the bounded device wait on a barrier nothing completes; returns
+    (return code, timed_out)."""
+    lib = load_library()
+    t = ctypes.c_int32(0)
+    rc = lib.lbif_selftest_wait(int(polls), ctypes.byref(t))
+    return rc, bool(t.value)
 
 
 class Slit:

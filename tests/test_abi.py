@@ -85,6 +85,9 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbif_destroy(None) == -1
     assert lib.lbif_moments(None, None, None, None, 0) == -1
     assert lib.lbif_set_fused(None, 1) == -1
+    t = ctypes.c_int32(3)
+    assert lib.lbif_selftest_wait(0, ctypes.byref(t)) == -1 and t.value == 3
+    assert lib.lbif_selftest_wait(10, None) == -1
     v = ctypes.c_int32(7)
     assert lib.lbif_get_fused(None, ctypes.byref(v)) == -1 and v.value == 7
     assert lib.lbif_last_error(None)

@@ -364,3 +364,15 @@ def test_c2_energy_source_parity(L, O, shape, sigma):
         assert nerr(r_off, ro) > 30 * max(e_r, 1e-7) or nerr(u_off, uo) > 30 * max(e_u, 1e-7)
     for h in (g, g_off):
         h.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(L):
+    """The bounded mbarrier wait of the tile-copy kernels, on a barrier that
+    nothing completes, gives up and reports LBIF_ERR_TIMEOUT (no trap, no
+    hang); the context then runs a normal step."""
+    rc, timed_out = L.selftest_wait(100000)
+    assert rc == -5 and timed_out
+    g = L.Slit(16, 16, 16, 4, 0.2, 0.9, seed=1)
+    g.step(3)
+    assert g.status() == 0
+    g.close()
