@@ -31,7 +31,7 @@ namespace lbif {
 namespace {
 
 constexpr int FFT_THREADS = 256;
-constexpr int FFT_GL = 2048;  // lines x line length held by one CTA
+constexpr int FFT_GL = 4096;  // lines x line length held by one CTA
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -39,65 +39,113 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// -i a
+__device__ __forceinline__ float2 cmi(float2 a) { return make_float2(a.y, -a.x); }
 
 __device__ __forceinline__ int padded(const Geom& g, int x, int y, int z)
 {
     return ((z + g.hw) * g.py + (y + g.hw)) * g.px + (x + g.hw);
 }
 
-// Batched radix-2 Stockham FFT (natural order in and out) of lines of
-// length L = 2^logL <= 1024 held in shared memory, FFT_GL / L lines per CTA.
+// Batched Stockham FFT (decimation in frequency, natural order in and out)
+// of lines of length L = 2^logL <= 1024 held in shared memory, FFT_GL / L
+// lines per CTA. A stage of radix r at stride st (the product of the radices
+// before it) maps x_j = X[q + st (p + j M)], M = L / (r st), to
+//   Y[q + st (r p + k)] = (sum_j x_j e^{-2 pi i j k / r}) e^{-2 pi i p k st / L};
+// radix-4 stages, preceded by one radix-2 stage when logL is odd.
 // Along x: line l holds elements l L .. l L + L - 1. Along y: line l = z nx + x
 // holds elements z nx L + x + i nx (consecutive lines are consecutive x, so
-// the loads and stores of a CTA are row segments). tw[j] = exp(-2 pi i j / L)
-// for j < L/2; inverse = 1 uses the conjugate twiddles (unnormalised).
+// the loads and stores of a CTA are row segments of FFT_GL / L nodes).
+// tw[j] = exp(-2 pi i j / L) for j < L/2 (copied to shared memory, extended
+// by tw[j + L/2] = -tw[j]); inverse = 1 conjugates them (unnormalised).
 template <bool ALONG_Y>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft(float2* __restrict__ data, int L, int logL, int nx,
-                                                     long long nlines, const float2* __restrict__ tw, int inverse)
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_fft(float2* __restrict__ data, int L, int logL, int lognx,
+                                                        long long nlines, const float2* __restrict__ tw, int inverse)
 {
     extern __shared__ float2 fsm[];
     const int G = FFT_GL / L;
     float2* X = fsm;
-    float2* Y = fsm + G * L;
+    float2* Y = fsm + FFT_GL;
+    float2* W = fsm + 2 * FFT_GL;  // L twiddles
     const long long l0 = (long long)blockIdx.x * G;
-    auto addr = [&](long long l, int i) -> long long {
+    const int nx = 1 << lognx;
+    // element t of the CTA's block (t = g L + i along x, t = i G + g along y):
+    // along x the block is contiguous; along y line l0 + g is node column
+    // x = (l0 + g) mod nx of plane row z = (l0 + g) / nx (nx a power of two)
+    const long long zb = l0 >> lognx;
+    const int xb = (int)(l0 & (nx - 1));
+    auto addr = [&](int t) -> long long {
         if (ALONG_Y) {
-            const long long z = l / nx, x = l - z * nx;
-            return z * nx * (long long)L + x + (long long)i * nx;
+            const int g = t & (G - 1), i = t >> (__ffs(G) - 1);
+            const int xg = xb + g;
+            return ((zb + (xg >> lognx)) << lognx) * (long long)L + (xg & (nx - 1)) + (long long)i * nx;
         }
-        return l * L + i;
+        return l0 * L + t;
     };
-    for (int t = threadIdx.x; t < G * L; t += blockDim.x) {
-        const int g = ALONG_Y ? t % G : t / L;
-        const int i = ALONG_Y ? t / G : t % L;
-        const long long l = l0 + g;
-        X[g * L + i] = l < nlines ? data[addr(l, i)] : make_float2(0.f, 0.f);
+    auto line = [&](int t) -> long long { return l0 + (ALONG_Y ? (t & (G - 1)) : (t >> logL)); };
+    const int half = L >> 1;
+    for (int j = threadIdx.x; j < half; j += blockDim.x) {
+        float2 w = tw[j];
+        if (inverse) w.y = -w.y;
+        W[j] = w;
+        W[j + half] = make_float2(-w.x, -w.y);
+    }
+    // G L = FFT_GL: a fixed count of independent loads per thread, all issued
+    // before the first store
+    constexpr int PT = FFT_GL / FFT_THREADS;
+    float2 v[PT];
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        const int t = threadIdx.x + k * FFT_THREADS;
+        v[k] = line(t) < nlines ? data[addr(t)] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        const int t = threadIdx.x + k * FFT_THREADS;
+        X[ALONG_Y ? (t & (G - 1)) * L + (t >> (__ffs(G) - 1)) : t] = v[k];
     }
     __syncthreads();
-    const int half = L >> 1;
     int st = 1;
-    for (int s = 0; s < logL; ++s) {
-        const int m = half >> s;  // half of the current sub-transform length
+    if (logL & 1) {
+        // radix 2: M = L / 2
         for (int t = threadIdx.x; t < G * half; t += blockDim.x) {
-            const int g = t / half, b = t - g * half;
-            const int p = b >> s, q = b & (st - 1);
-            const float2 a = X[g * L + q + st * p], c = X[g * L + q + st * (p + m)];
-            float2 w = tw[p * st];
-            if (inverse) w.y = -w.y;
-            Y[g * L + q + 2 * st * p] = cadd(a, c);
-            Y[g * L + q + 2 * st * p + st] = cmul(csub(a, c), w);
+            const int g = t / half, p = t - g * half;
+            const float2 a = X[g * L + p], c = X[g * L + p + half];
+            Y[g * L + 2 * p] = cadd(a, c);
+            Y[g * L + 2 * p + 1] = cmul(csub(a, c), W[p]);
         }
         __syncthreads();
         float2* tmp = X;
         X = Y;
         Y = tmp;
-        st <<= 1;
+        st = 2;
     }
-    for (int t = threadIdx.x; t < G * L; t += blockDim.x) {
-        const int g = ALONG_Y ? t % G : t / L;
-        const int i = ALONG_Y ? t / G : t % L;
-        const long long l = l0 + g;
-        if (l < nlines) data[addr(l, i)] = X[g * L + i];
+    const int quarter = L >> 2;
+    for (; st < L; st <<= 2) {
+        const int M = L / (4 * st);
+        for (int t = threadIdx.x; t < G * quarter; t += blockDim.x) {
+            const int g = t / quarter, b = t - g * quarter;
+            const int p = b / st, q = b - p * st;
+            const float2* xs = X + g * L + q + st * p;
+            const float2 x0 = xs[0], x1 = xs[st * M], x2 = xs[2 * st * M], x3 = xs[3 * st * M];
+            const float2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3);
+            const float2 t3 = inverse ? cmi(csub(x3, x1)) : cmi(csub(x1, x3));
+            const int e = p * st;  // twiddle exponents e k, k = 1, 2, 3 (all < L)
+            float2* ys = Y + g * L + q + 4 * st * p;
+            ys[0] = cadd(t0, t2);
+            ys[st] = cmul(cadd(t1, t3), W[e]);
+            ys[2 * st] = cmul(csub(t0, t2), W[2 * e]);
+            ys[3 * st] = cmul(csub(t1, t3), W[3 * e]);
+        }
+        __syncthreads();
+        float2* tmp = X;
+        X = Y;
+        Y = tmp;
+    }
+#pragma unroll
+    for (int k = 0; k < PT; ++k) {
+        const int t = threadIdx.x + k * FFT_THREADS;
+        if (line(t) < nlines) data[addr(t)] = X[ALONG_Y ? (t & (G - 1)) * L + (t >> (__ffs(G) - 1)) : t];
     }
 }
 
@@ -202,16 +250,18 @@ int ilog2(int v)
     return l;
 }
 
+size_t fft_smem() { return sizeof(float2) * (2 * FFT_GL + 1024); }
+
 cudaError_t fft_pass(float2* data, int L, int nx, long long nlines, bool along_y, const float2* tw, int inverse,
                      cudaStream_t s)
 {
     const int G = FFT_GL / L;
-    const size_t smem = sizeof(float2) * 2 * FFT_GL;
+    const size_t smem = fft_smem();
     const unsigned blocks = nblk(nlines, G);
     if (along_y)
-        k_fft<true><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), nx, nlines, tw, inverse);
+        k_fft<true><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse);
     else
-        k_fft<false><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), nx, nlines, tw, inverse);
+        k_fft<false><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse);
     return cudaGetLastError();
 }
 
@@ -288,6 +338,10 @@ cudaError_t tail_spectral_init(const Geom& g, int D, const int* pdx, const int* 
     if ((e = cudaMemcpyAsync(wdev, wz.data(), sizeof(float) * wz.size(), cudaMemcpyHostToDevice, s))) return e;
     if ((e = cudaFuncSetAttribute(k_tail_zconv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(float2) * ((ZC + 2 * D) * 32 + (2 * D + 1) * 3 * 32)))))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_fft<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem())))
         return e;
     const long long slices = (long long)(2 * D + 1) * 3;
     if ((e = fft_pass(Kh, g.nx, g.nx, slices * g.ny, false, twx, 0, s))) return e;

@@ -403,9 +403,7 @@ __host__ __device__ constexpr int cisqrt(int n)
 // 512 x 512 x 192 slit: 1 node per thread 0.86 ms, 2 nodes 0.72 ms, 4 nodes
 // 0.90 ms, each with its best CTA count)
 constexpr int BALL_TX = 32, BALL_YT = 2, BALL_TY = 8 * BALL_YT, BALL_THREADS = 256;
-// the tensor-memory-accelerator ball kernel is sized for 4 CTAs per SM (64
-// registers; measured 0.582 ms vs 0.594 ms at 60-72 registers and 3-4 CTAs)
-constexpr int BALL_MINB = 4;
+
 
 // x halo of the staged plane tile: R rounded up to 4, so that tile rows and
 // their global sources are float4-aligned
@@ -648,7 +646,7 @@ __global__ void __launch_bounds__(BALL_THREADS) k_ball(Params P, const float* __
 // one thread two planes ahead into alternating buffers, completion counted
 // in bytes on an mbarrier per buffer. The arithmetic is k_ball's.
 template <int R>
-__global__ void __launch_bounds__(BALL_THREADS, BALL_MINB) k_ball_tma(Params P, const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(BALL_THREADS) k_ball_tma(Params P, const __grid_constant__ CUtensorMap tmap,
                                                   float* __restrict__ dG, int* status, int zchunk,
                                                   int skip_done)
 {
