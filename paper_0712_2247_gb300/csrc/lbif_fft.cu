@@ -15,10 +15,15 @@
 //   M(k, z)  = FFT_xy[dn(., ., z) f(z)](k)
 //   T^(k, z) = sum_dz conj(FFT_xy[K(., ., dz)](k)) M(k, z + dz)
 //   T(r)     = IFFT_xy[T^](r) / (nx ny) + (0, 0, w(z))
-// T_x and T_y are real, so they share one inverse transform (T_x + i T_y);
-// T_z takes the second. The kernel's transform is computed once per handle
-// with the same FFT kernels. Cost per step: about eight passes over a
-// complex field, instead of ~2 * 10^4 neighbour reads per node.
+// The fields are real, so two planes share a complex transform: the forward
+// one takes P_j = m(2j) + i m(2j+1) (m = dn f), whose spectrum gives both
+// planes' as M(k, 2j) = (P(k) + conj P(-k)) / 2, M(k, 2j+1) = (P(k) -
+// conj P(-k)) / 2i; the inverse ones take T_x + i T_y of each plane and
+// T_z(2j) + i T_z(2j+1) of each pair. The kernel's transform is computed once
+// per handle with the same FFT kernels. The packing of the density rides on
+// the first x pass and the product n0 m T on the last one. Cost per step:
+// about four passes over a complex field of nx ny nz, instead of ~2 * 10^4
+// neighbour reads per node.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -58,9 +63,40 @@ __device__ __forceinline__ int padded(const Geom& g, int x, int y, int z)
 // the loads and stores of a CTA are row segments of FFT_GL / L nodes).
 // tw[j] = exp(-2 pi i j / L) for j < L/2 (copied to shared memory, extended
 // by tw[j + L/2] = -tw[j]); inverse = 1 conjugates them (unnormalised).
-template <bool ALONG_Y>
+// Fused ends of the x passes (lines l = j ny + y of a plane-pair field):
+// IN reads m(x, y, 2j) + i m(x, y, 2j+1) from the padded density instead of
+// `data`; OUT writes Ft = n0 m T of both planes (T_x, T_y from O1, T_z the
+// real / imaginary part of the transformed pair) instead of `data`.
+struct FftEnds {
+    Params P;
+    const float* dn;
+    const float2* O1;
+    const float* w;
+    float4* Ft;
+};
+
+__device__ __forceinline__ float fluid_dn(const Params& P, const float* dn, int x, int y, int z)
+{
+    return z < P.g.nz && P.zslit[z] >= 0 ? dn[padded(P.g, x, y, z)] : 0.f;
+}
+
+__device__ __forceinline__ void tail_out(const FftEnds& e, int x, int y, int z, float tz)
+{
+    const Geom& g = e.P.g;
+    if (z >= g.nz) return;
+    const int s = e.P.zslit[z];
+    if (s < 0 || e.P.done[s]) return;
+    const float inv = 1.f / ((float)g.nx * (float)g.ny);
+    const long long idx = ((long long)z * g.ny + y) * g.nx + x;
+    const float pre = e.P.sl[s].rho0 * (1.f + e.dn[padded(g, x, y, z)]);
+    const float2 a = e.O1[idx];
+    e.Ft[idx] = make_float4(pre * (a.x * inv), pre * (a.y * inv), pre * (tz * inv + e.w[z]), 0.f);
+}
+
+template <bool ALONG_Y, bool IN = false, bool OUT = false>
 __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft(float2* __restrict__ data, int L, int logL, int lognx,
-                                                        long long nlines, const float2* __restrict__ tw, int inverse)
+                                                        long long nlines, const float2* __restrict__ tw, int inverse,
+                                                        FftEnds ends)
 {
     extern __shared__ float2 fsm[];
     const int G = FFT_GL / L;
@@ -97,7 +133,16 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft(float2* __restrict__ dat
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
         const int t = threadIdx.x + k * FFT_THREADS;
-        v[k] = line(t) < nlines ? data[addr(t)] : make_float2(0.f, 0.f);
+        const long long l = line(t);
+        if (IN) {
+            const int ny = ends.P.g.ny;
+            const int y = (int)(l % ny), j = (int)(l / ny), x = t & (L - 1);
+            v[k] = l < nlines ? make_float2(fluid_dn(ends.P, ends.dn, x, y, 2 * j),
+                                            fluid_dn(ends.P, ends.dn, x, y, 2 * j + 1))
+                              : make_float2(0.f, 0.f);
+        } else {
+            v[k] = l < nlines ? data[addr(t)] : make_float2(0.f, 0.f);
+        }
     }
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
@@ -145,48 +190,57 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft(float2* __restrict__ dat
 #pragma unroll
     for (int k = 0; k < PT; ++k) {
         const int t = threadIdx.x + k * FFT_THREADS;
-        if (line(t) < nlines) data[addr(t)] = X[ALONG_Y ? (t & (G - 1)) * L + (t >> (__ffs(G) - 1)) : t];
+        const long long l = line(t);
+        if (l >= nlines) continue;
+        const float2 r = X[ALONG_Y ? (t & (G - 1)) * L + (t >> (__ffs(G) - 1)) : t];
+        if (OUT) {
+            const int ny = ends.P.g.ny;
+            const int y = (int)(l % ny), j = (int)(l / ny), x = t & (L - 1);
+            tail_out(ends, x, y, 2 * j, r.x);
+            tail_out(ends, x, y, 2 * j + 1, r.y);
+        } else {
+            data[addr(t)] = r;
+        }
     }
 }
 
-// dn of every fluid node as a complex field (gap planes give 0)
-__global__ void k_tail_pack(Params P, const float* __restrict__ dn, float2* __restrict__ A)
-{
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const Geom& g = P.g;
-    if (idx >= g.N) return;
-    const int x = (int)(idx % g.nx);
-    const long long r = idx / g.nx;
-    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-    const float v = P.zslit[z] >= 0 ? dn[padded(g, x, y, z)] : 0.f;
-    A[idx] = make_float2(v, 0.f);
-}
-
-// T^(k, z) = sum_dz conj(Kh_c(k, dz)) A(k, z + dz) for 32 modes (one CTA row)
-// and a chunk of ZC planes; A and Kh staged in shared memory. Output
-// O1 = T^_x + i T^_y, O2 = T^_z. Planes outside the grid read 0 (walls) or
-// their periodic image.
+// T^(k, z) = sum_dz conj(Kh_c(k, dz)) M(k, z + dz) for 32 modes (one CTA row)
+// and a chunk of ZC planes; M (unpacked from the plane-pair transform Pp at
+// k and -k) and Kh staged in shared memory. Output O1 = T^_x + i T^_y per
+// plane, O2 = T^_z(2j) + i T^_z(2j+1) per plane pair. Planes outside the grid
+// read 0 (walls) or their periodic image.
 constexpr int ZC = 64, ZB = 8;
 
-__global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ A, const float2* __restrict__ Kh,
-                                                    float2* __restrict__ O1, float2* __restrict__ O2,
-                                                    long long nxy, int nz, int D, int zper)
+__global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ Pp, const float2* __restrict__ Kh,
+                                                    float2* __restrict__ O1, float2* __restrict__ O2, int nx,
+                                                    int ny, int nz, int D, int zper)
 {
     extern __shared__ float2 zsm[];
     float2* slab = zsm;                      // (ZC + 2D) x 32
     float2* kh = zsm + (ZC + 2 * D) * 32;    // (2D + 1) x 3 x 32
+    const long long nxy = (long long)nx * ny;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const long long col = (long long)blockIdx.x * 32 + tx;
+    // the mode -k of k = (col mod nx, col / nx)
+    const int kx = (int)(col % nx), ky = (int)(col / nx);
+    const long long colm = (long long)((ny - ky) % ny) * nx + (nx - kx) % nx;
     const int z0 = blockIdx.y * ZC;
     for (int r = ty; r < ZC + 2 * D; r += 8) {
         int z = z0 - D + r;
         float2 v = make_float2(0.f, 0.f);
+        bool in = true;
         if (zper) {
             z %= nz;
             if (z < 0) z += nz;
-            v = A[(long long)z * nxy + col];
-        } else if (z >= 0 && z < nz) {
-            v = A[(long long)z * nxy + col];
+        } else {
+            in = z >= 0 && z < nz;
+        }
+        if (in) {
+            const long long j = z >> 1;
+            const float2 a = Pp[j * nxy + col], b = Pp[j * nxy + colm];
+            // M(2j) = (P(k) + conj P(-k)) / 2, M(2j+1) = (P(k) - conj P(-k)) / 2i
+            v = (z & 1) ? make_float2(0.5f * (a.y + b.y), -0.5f * (a.x - b.x))
+                        : make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
         }
         slab[r * 32 + tx] = v;
     }
@@ -218,27 +272,15 @@ __global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ A
             const int z = z0 + zb + j;
             if (z >= nz) break;
             O1[(long long)z * nxy + col] = make_float2(acc[j][0].x - acc[j][1].y, acc[j][0].y + acc[j][1].x);
-            O2[(long long)z * nxy + col] = acc[j][2];
+        }
+#pragma unroll
+        for (int j = 0; j < ZB; j += 2) {
+            const int z = z0 + zb + j;  // even: ZC, ZB even
+            if (z >= nz) break;
+            const float2 a = acc[j][2], b = z + 1 < nz ? acc[j + 1][2] : make_float2(0.f, 0.f);
+            O2[(long long)(z >> 1) * nxy + col] = make_float2(a.x - b.y, a.y + b.x);
         }
     }
-}
-
-// Ft = n0 m T for the nodes of unfrozen slits
-__global__ void k_tail_finish(Params P, const float* __restrict__ dn, const float2* __restrict__ O1,
-                              const float2* __restrict__ O2, const float* __restrict__ w, float4* __restrict__ Ft)
-{
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const Geom& g = P.g;
-    if (idx >= g.N) return;
-    const int x = (int)(idx % g.nx);
-    const long long r = idx / g.nx;
-    const int y = (int)(r % g.ny), z = (int)(r / g.ny);
-    const int s = P.zslit[z];
-    if (s < 0 || P.done[s]) return;
-    const float inv = 1.f / ((float)g.nx * (float)g.ny);
-    const float pre = P.sl[s].rho0 * (1.f + dn[padded(g, x, y, z)]);
-    const float2 a = O1[idx], b = O2[idx];
-    Ft[idx] = make_float4(pre * (a.x * inv), pre * (a.y * inv), pre * (b.x * inv + w[z]), 0.f);
 }
 
 inline unsigned nblk(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -252,16 +294,24 @@ int ilog2(int v)
 
 size_t fft_smem() { return sizeof(float2) * (2 * FFT_GL + 1024); }
 
+// one batched pass; `ends` selects the fused x-pass variants: 1 = read the
+// packed density (IN), 2 = write the tail force (OUT)
 cudaError_t fft_pass(float2* data, int L, int nx, long long nlines, bool along_y, const float2* tw, int inverse,
-                     cudaStream_t s)
+                     cudaStream_t s, int ends_mode = 0, const FftEnds* ends = nullptr)
 {
     const int G = FFT_GL / L;
     const size_t smem = fft_smem();
     const unsigned blocks = nblk(nlines, G);
+    FftEnds e0;
+    const FftEnds& e = ends ? *ends : e0;
     if (along_y)
-        k_fft<true><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse);
+        k_fft<true><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse, e);
+    else if (ends_mode == 1)
+        k_fft<false, true, false><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse, e);
+    else if (ends_mode == 2)
+        k_fft<false, false, true><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse, e);
     else
-        k_fft<false><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse);
+        k_fft<false><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse, e);
     return cudaGetLastError();
 }
 
@@ -343,6 +393,12 @@ cudaError_t tail_spectral_init(const Geom& g, int D, const int* pdx, const int* 
         return e;
     if ((e = cudaFuncSetAttribute(k_fft<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem())))
         return e;
+    if ((e = cudaFuncSetAttribute(k_fft<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fft_smem())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_fft<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)fft_smem())))
+        return e;
     const long long slices = (long long)(2 * D + 1) * 3;
     if ((e = fft_pass(Kh, g.nx, g.nx, slices * g.ny, false, twx, 0, s))) return e;
     if ((e = fft_pass(Kh, g.ny, g.nx, slices * g.nx, true, twy, 0, s))) return e;
@@ -353,28 +409,27 @@ cudaError_t launch_tail_spectral(const Params& P, const float* dn, int D, float2
 {
     const Geom& g = P.g;
     const long long nxy = (long long)g.nx * g.ny;
-    float2* A = work;
-    float2* O1 = A + nxy * g.nz;
-    float2* O2 = O1 + nxy * g.nz;
-    float2* Kh = O2 + nxy * g.nz;
+    const int nz2 = (g.nz + 1) / 2;  // plane pairs
+    // work: Pp, O2 (nz2 planes each), O1 (nz planes), then Kh and the twiddles
+    float2* Pp = work;
+    float2* O2 = Pp + nxy * nz2;
+    float2* O1 = O2 + nxy * nz2;
+    float2* Kh = work + 3 * nxy * g.nz;
     float2* twx = Kh + (long long)(2 * D + 1) * 3 * nxy;
     float2* twy = twx + g.nx / 2;
+    const float* w = reinterpret_cast<const float*>(twy + g.ny / 2);
+    FftEnds ends{P, dn, O1, w, Ft};
     cudaError_t e;
-    k_tail_pack<<<nblk(g.N, 256), 256, 0, s>>>(P, dn, A);
-    if ((e = cudaGetLastError())) return e;
-    if ((e = fft_pass(A, g.nx, g.nx, (long long)g.ny * g.nz, false, twx, 0, s))) return e;
-    if ((e = fft_pass(A, g.ny, g.nx, (long long)g.nx * g.nz, true, twy, 0, s))) return e;
+    if ((e = fft_pass(Pp, g.nx, g.nx, (long long)g.ny * nz2, false, twx, 0, s, 1, &ends))) return e;
+    if ((e = fft_pass(Pp, g.ny, g.nx, (long long)g.nx * nz2, true, twy, 0, s))) return e;
     const size_t zs = sizeof(float2) * ((ZC + 2 * D) * 32 + (2 * D + 1) * 3 * 32);
     dim3 grid((unsigned)(nxy / 32), (unsigned)((g.nz + ZC - 1) / ZC));
-    k_tail_zconv<<<grid, 256, zs, s>>>(A, Kh, O1, O2, nxy, g.nz, D, g.zper);
+    k_tail_zconv<<<grid, 256, zs, s>>>(Pp, Kh, O1, O2, g.nx, g.ny, g.nz, D, g.zper);
     if ((e = cudaGetLastError())) return e;
-    for (float2* O : {O1, O2}) {
-        if ((e = fft_pass(O, g.ny, g.nx, (long long)g.nx * g.nz, true, twy, 1, s))) return e;
-        if ((e = fft_pass(O, g.nx, g.nx, (long long)g.ny * g.nz, false, twx, 1, s))) return e;
-    }
-    const float* w = reinterpret_cast<const float*>(twy + g.ny / 2);
-    k_tail_finish<<<nblk(g.N, 256), 256, 0, s>>>(P, dn, O1, O2, w, Ft);
-    return cudaGetLastError();
+    if ((e = fft_pass(O1, g.ny, g.nx, (long long)g.nx * g.nz, true, twy, 1, s))) return e;
+    if ((e = fft_pass(O1, g.nx, g.nx, (long long)g.ny * g.nz, false, twx, 1, s))) return e;
+    if ((e = fft_pass(O2, g.ny, g.nx, (long long)g.nx * nz2, true, twy, 1, s))) return e;
+    return fft_pass(O2, g.nx, g.nx, (long long)g.ny * nz2, false, twx, 1, s, 2, &ends);
 }
 
 }  // namespace lbif

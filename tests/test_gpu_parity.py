@@ -200,6 +200,8 @@ def test_fp16_storage_velocity_profile(L, O):
     ((32, 16, 28), 4, False),   # spectral in x, y, direct in z between walls
     ((16, 16, 20), 4, True),    # spectral, periodic z
     ((32, 32, 48), 8, False),   # spectral, sigma = 8 (reach 20 planes)
+    ((32, 16, 27), 4, False),   # spectral, odd nz: the last plane pairs with an empty one
+    ((16, 32, 21), 4, True),    # spectral, periodic odd nz
 ])
 def test_tail_parity(L, O, shape, sigma, zper):
     nx, ny, nz = shape
