@@ -208,7 +208,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fft(float2* __restrict__ dat
 // and a chunk of ZC planes; M (unpacked from the plane-pair transform Pp at
 // k and -k) and Kh staged in shared memory. Output O1 = T^_x + i T^_y per
 // plane, O2 = T^_z(2j) + i T^_z(2j+1) per plane pair. Planes outside the grid
-// read 0 (walls) or their periodic image.
+// read 0 (walls) or their periodic image. T is real, T^(-k) = conj T^(k):
+// only the modes with ky <= ny/2 are computed; those with 0 < ky < ny/2 also
+// write their mirror -k (rows 0 and ny/2 hold both members of their pairs and
+// write only their own mode, so every output has one writer).
 constexpr int ZC = 64, ZB = 8;
 
 __global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ Pp, const float2* __restrict__ Kh,
@@ -220,10 +223,13 @@ __global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ P
     float2* kh = zsm + (ZC + 2 * D) * 32;    // (2D + 1) x 3 x 32
     const long long nxy = (long long)nx * ny;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const long long col = (long long)blockIdx.x * 32 + tx;
+    const long long nhalf = (long long)(ny / 2 + 1) * nx;  // modes with ky <= ny/2
+    const bool live = (long long)blockIdx.x * 32 + tx < nhalf;
+    const long long col = live ? (long long)blockIdx.x * 32 + tx : 0;
     // the mode -k of k = (col mod nx, col / nx)
     const int kx = (int)(col % nx), ky = (int)(col / nx);
     const long long colm = (long long)((ny - ky) % ny) * nx + (nx - kx) % nx;
+    const bool mirror = live && ky > 0 && 2 * ky < ny;
     const int z0 = blockIdx.y * ZC;
     for (int r = ty; r < ZC + 2 * D; r += 8) {
         int z = z0 - D + r;
@@ -267,11 +273,14 @@ __global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ P
                 }
             }
         }
+        if (!live) continue;
 #pragma unroll
         for (int j = 0; j < ZB; ++j) {
             const int z = z0 + zb + j;
             if (z >= nz) break;
-            O1[(long long)z * nxy + col] = make_float2(acc[j][0].x - acc[j][1].y, acc[j][0].y + acc[j][1].x);
+            const float2 a = acc[j][0], b = acc[j][1];
+            O1[(long long)z * nxy + col] = make_float2(a.x - b.y, a.y + b.x);  // a + i b
+            if (mirror) O1[(long long)z * nxy + colm] = make_float2(a.x + b.y, b.x - a.y);  // conj a + i conj b
         }
 #pragma unroll
         for (int j = 0; j < ZB; j += 2) {
@@ -279,6 +288,7 @@ __global__ void __launch_bounds__(256) k_tail_zconv(const float2* __restrict__ P
             if (z >= nz) break;
             const float2 a = acc[j][2], b = z + 1 < nz ? acc[j + 1][2] : make_float2(0.f, 0.f);
             O2[(long long)(z >> 1) * nxy + col] = make_float2(a.x - b.y, a.y + b.x);
+            if (mirror) O2[(long long)(z >> 1) * nxy + colm] = make_float2(a.x + b.y, b.x - a.y);
         }
     }
 }
@@ -423,7 +433,8 @@ cudaError_t launch_tail_spectral(const Params& P, const float* dn, int D, float2
     if ((e = fft_pass(Pp, g.nx, g.nx, (long long)g.ny * nz2, false, twx, 0, s, 1, &ends))) return e;
     if ((e = fft_pass(Pp, g.ny, g.nx, (long long)g.nx * nz2, true, twy, 0, s))) return e;
     const size_t zs = sizeof(float2) * ((ZC + 2 * D) * 32 + (2 * D + 1) * 3 * 32);
-    dim3 grid((unsigned)(nxy / 32), (unsigned)((g.nz + ZC - 1) / ZC));
+    const long long nhalf = (long long)(g.ny / 2 + 1) * g.nx;
+    dim3 grid((unsigned)((nhalf + 31) / 32), (unsigned)((g.nz + ZC - 1) / ZC));
     k_tail_zconv<<<grid, 256, zs, s>>>(Pp, Kh, O1, O2, g.nx, g.ny, g.nz, D, g.zper);
     if ((e = cudaGetLastError())) return e;
     if ((e = fft_pass(O1, g.ny, g.nx, (long long)g.nx * g.nz, true, twy, 1, s))) return e;
