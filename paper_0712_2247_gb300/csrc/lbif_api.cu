@@ -393,7 +393,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     ALLOC(h->pop[1], pb);
     ALLOC(h->F, sizeof(float4) * (size_t)g.N);
     ALLOC(h->status_d, sizeof(int));
-    ALLOC(h->prof_d, sizeof(double) * 5 * (size_t)g.nz);
+    ALLOC(h->prof_d, sizeof(double) * profile_doubles(g));
     ALLOC(h->d_sl, sizeof(SlitParam) * h->sl.size());
     ALLOC(h->d_zslit, sizeof(int) * (size_t)g.nz);
     ALLOC(h->d_done, sizeof(int) * h->sl.size());

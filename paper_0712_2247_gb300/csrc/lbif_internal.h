@@ -169,6 +169,9 @@ cudaError_t launch_wait_selftest(long long polls, int* status, cudaStream_t s);
 cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s);
 cudaError_t launch_moments_out(const Params& P, const Fields& f, float* rho, float* u, float* p,
                                cudaStream_t s);
+// prof: at least profile_doubles(g) doubles; the first 5 nz receive the
+// per-plane sums (dn, ux, (1+dn) ux, (1+dn) uy, (1+dn) uz), the rest is work space
+size_t profile_doubles(const Geom& g);
 cudaError_t launch_profiles(const Params& P, const Fields& f, double* prof, cudaStream_t s);
 bool force_vectorised(int sigma);
 

@@ -1685,17 +1685,22 @@ __global__ void k_moments_out(Params P, Fields fl, float* rho, float* u, float* 
 }
 
 // per z plane: sum dn, sum ux, sum (1+dn) u  (FP64, fixed-order tree)
+// Per z plane: sum dn, sum ux, sum (1+dn) u (FP64, fixed order): CTA (z, c)
+// reduces rows [c rc, (c+1) rc) of plane z by a fixed tree into part, then
+// k_profiles_sum adds the chunks of a plane in order.
 constexpr int PROF_K = 5;
-__global__ void k_profiles(Params P, Fields fl, double* prof)
+__global__ void k_profiles(Params P, Fields fl, double* part, int chunks)
 {
     __shared__ double sh[PROF_K][256];
     const Geom& g = P.g;
-    int z = blockIdx.x;
+    const int z = blockIdx.x, c = blockIdx.y;
+    const int rc = (g.ny + chunks - 1) / chunks;
+    const int y0 = min(g.ny, c * rc), y1 = min(g.ny, y0 + rc);
     double a[PROF_K] = {0, 0, 0, 0, 0};
-    int A = g.nx * g.ny;
-    for (int k = threadIdx.x; k < A; k += blockDim.x) {
-        int y = k / g.nx, x = k - y * g.nx;
-        int p = pidx(g, x, y, z);
+    const int n = (y1 - y0) * g.nx;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int dy = k / g.nx, x = k - dy * g.nx;
+        const int p = pidx(g, x, y0 + dy, z);
         double d = (double)fl.dn[p], vx = fl.ux[p], vy = fl.uy[p], vz = fl.uz[p];
         double opd = 1.0 + d;
         a[0] += d;
@@ -1711,7 +1716,17 @@ __global__ void k_profiles(Params P, Fields fl, double* prof)
             for (int j = 0; j < PROF_K; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x < PROF_K) prof[(long long)z * PROF_K + threadIdx.x] = sh[threadIdx.x][0];
+    if (threadIdx.x < PROF_K) part[((long long)z * chunks + c) * PROF_K + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_profiles_sum(const double* __restrict__ part, int nz, int chunks, double* __restrict__ prof)
+{
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)nz * PROF_K) return;
+    const long long z = i / PROF_K, j = i - z * PROF_K;
+    double s = 0.0;
+    for (int c = 0; c < chunks; ++c) s += part[(z * chunks + c) * PROF_K + j];
+    prof[i] = s;
 }
 
 // ---------------------------------------------------------------------------
@@ -1977,9 +1992,25 @@ cudaError_t launch_moments_out(const Params& P, const Fields& f, float* rho, flo
     return cudaGetLastError();
 }
 
+// chunks per plane: enough CTAs to fill the GPU several times over
+static int profile_chunks(const Geom& g)
+{
+    int c = (1216 + g.nz - 1) / g.nz;
+    if (c > 32) c = 32;
+    if (c > g.ny) c = g.ny;
+    return c < 1 ? 1 : c;
+}
+
+size_t profile_doubles(const Geom& g) { return (size_t)PROF_K * g.nz * (1 + profile_chunks(g)); }
+
 cudaError_t launch_profiles(const Params& P, const Fields& f, double* prof, cudaStream_t s)
 {
-    k_profiles<<<P.g.nz, 256, 0, s>>>(P, f, prof);
+    const int chunks = profile_chunks(P.g);
+    double* part = prof + (size_t)PROF_K * P.g.nz;
+    k_profiles<<<dim3(P.g.nz, chunks), 256, 0, s>>>(P, f, part, chunks);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_profiles_sum<<<nblocks((long long)P.g.nz * PROF_K, 256), 256, 0, s>>>(part, P.g.nz, chunks, prof);
     return cudaGetLastError();
 }
 
