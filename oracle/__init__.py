@@ -78,6 +78,7 @@ def _load():
             "or_hs_force_fields": (None, [i32, i32, i32, i32, i32, i32, i32, i32, _D, _D, _D,
                                           _D, _D, _D, _D, _D, _D]),
             "or_tail_force_field": (None, [i32, i32, i32, i32, i32, f64, f64, _D, _D, _D, _D]),
+            "or_step_shifted": (i32, [vp, ctypes.c_long]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -242,9 +243,14 @@ class Oracle:
             ux, uy, uz = (_f64(u[k], self.N) for k in range(3))
         self._lib.or_init_fields(self._h, _p(a), _p(ux), _p(uy), _p(uz))
 
-    def step(self, nsteps: int = 1, lagged: bool = False):
-        """Plain steps, or steps of the lagged-force variant (the force of the
-        previous step's moments drives the collision)."""
+    def step(self, nsteps: int = 1, lagged: bool = False, shifted: bool = False):
+        """Plain steps, steps of the lagged-force variant (the force of the
+        previous step's moments drives the collision), or steps with the
+        velocity-shifted second-order forcing (body force only)."""
+        if shifted:
+            if self._lib.or_step_shifted(self._h, int(nsteps)) != 0:
+                raise ValueError("oracle: the shifted forcing needs a force independent of u")
+            return
         (self._lib.or_step_lagged if lagged else self._lib.or_step)(self._h, int(nsteps))
 
     def moments(self, pressure: bool = False):

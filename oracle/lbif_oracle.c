@@ -502,6 +502,59 @@ static void collide_stream(or_state* s)
     double* tmp = s->f; s->f = s->fn; s->fn = tmp;
 }
 
+/* Collision and streaming with velocity-shifted (second-order) forcing, for
+ * comparison with the paper's first-order source: the equilibrium takes
+ * u = (j + F/2)/n and the source is
+ *   (1 - 1/(2 tau)) w_i [ (c_i - u).F / c_s^2 + (c_i.u)(c_i.F) / c_s^4 ].
+ * Explicit only when F does not depend on u (body force alone).           */
+static void collide_stream_shifted(or_state* s)
+{
+    long N = s->N;
+    const geom* g = &s->g;
+    const double cs2 = 1.0 / 3.0, a = 1.0 - 0.5 / s->tau;
+#pragma omp parallel for schedule(static)
+    for (long id = 0; id < N; ++id) {
+        int x = (int)(id % g->nx), y = (int)((id / g->nx) % g->ny), z = (int)(id / ((long)g->nx * g->ny));
+        double f[NV], fo[NV], feq[NV], F[3] = {s->Fx[id], s->Fy[id], s->Fz[id]};
+        double n = 0.0, j[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < NV; ++i) {
+            f[i] = s->f[(long)i * N + id];
+            n += f[i];
+            for (int c = 0; c < 3; ++c) j[c] += cv[i][c] * f[i];
+        }
+        double u[3] = {(j[0] + 0.5 * F[0]) / n, (j[1] + 0.5 * F[1]) / n, (j[2] + 0.5 * F[2]) / n};
+        or_equilibrium(n, u, feq);
+        for (int i = 0; i < NV; ++i) {
+            double cu = cv[i][0] * u[0] + cv[i][1] * u[1] + cv[i][2] * u[2];
+            double cF = cv[i][0] * F[0] + cv[i][1] * F[1] + cv[i][2] * F[2];
+            double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+            fo[i] = f[i] - (f[i] - feq[i]) / s->tau + a * wv[i] * ((cF - uF) / cs2 + cu * cF / (cs2 * cs2));
+        }
+        for (int i = 0; i < NV; ++i) {
+            long t = node_at(g, x + cv[i][0], y + cv[i][1], z + cv[i][2]);
+            if (t < 0) s->fn[(long)opp[i] * N + id] = fo[i];
+            else s->fn[(long)i * N + t] = fo[i];
+        }
+    }
+    double* tmp = s->f; s->f = s->fn; s->fn = tmp;
+}
+
+/* steps with the velocity-shifted forcing; -1 (nothing done) when the force
+ * depends on u (hard-sphere or tail force on)                               */
+int or_step_shifted(void* h, long nsteps)
+{
+    or_state* s = (or_state*)h;
+    if (s->hs || s->tail) return -1;
+    for (long k = 0; k < nsteps; ++k) {
+        compute_moments(s);
+        compute_forces(s, 0);
+        collide_stream_shifted(s);
+        s->t += 1;
+    }
+    s->lag_ok = 0;
+    return 0;
+}
+
 /* switch the energy source of Eq. C2eq (constant T) on or off */
 void or_set_c2(void* h, int on) { ((or_state*)h)->c2 = on; }
 
