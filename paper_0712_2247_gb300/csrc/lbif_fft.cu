@@ -304,16 +304,143 @@ int ilog2(int v)
 
 size_t fft_smem() { return sizeof(float2) * (2 * FFT_GL + 1024); }
 
+// 256-point lines by the four-step split 256 = 16 x 16: a thread holds the
+// stride-16 subsequence n = 16 n1 + s of its line, takes the 16-point DFT
+// over n1 in registers, multiplies by W_256^(s k1), exchanges through padded
+// shared memory (thread k1 then holds k1 of every subsequence) and takes the
+// 16-point DFT over the subsequences: X[k1 + 16 k2]. One exchange instead of
+// four shared-memory stages. 16 lines per CTA, 16 threads per line; along y
+// the 16 threads of a half-warp are 16 consecutive x columns at one y, along
+// x 16 consecutive x of one line, so every access is a 128-byte segment.
+__device__ __forceinline__ float2 cmi_dir(float2 a, int inverse)
+{
+    return inverse ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);  // +i a or -i a
+}
+
+// in-place 4-point DFT of (x0, x1, x2, x3)
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3, int inverse)
+{
+    const float2 t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3), t3 = cmi_dir(csub(x1, x3), inverse);
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
+// 16-point DFT of a[0..15] in registers (16 = 4 x 4), natural order out;
+// W = exp(-+ 2 pi i j / 256) for j < 256
+__device__ __forceinline__ void dft16(float2 (&a)[16], const float2* W, int inverse)
+{
+    // DFT4 over n1 of a[4 n1 + n2] for each n2, twiddle W_16^(n2 k1)
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        dft4(a[n2], a[4 + n2], a[8 + n2], a[12 + n2], inverse);
+#pragma unroll
+        for (int k1 = 1; k1 < 4; ++k1)
+            if (n2) a[4 * k1 + n2] = cmul(a[4 * k1 + n2], W[16 * n2 * k1]);
+    }
+    // now b[n2][k1] sits in a[4 k1 + n2]; DFT4 over n2 gives A[k1 + 4 k2]
+    float2 r[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 x0 = a[4 * k1], x1 = a[4 * k1 + 1], x2 = a[4 * k1 + 2], x3 = a[4 * k1 + 3];
+        dft4(x0, x1, x2, x3, inverse);
+        r[k1] = x0;
+        r[k1 + 4] = x1;
+        r[k1 + 8] = x2;
+        r[k1 + 12] = x3;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = r[k];
+}
+
+template <bool ALONG_Y, bool IN = false, bool OUT = false>
+__global__ void __launch_bounds__(256, 3) k_fft256(float2* __restrict__ data, int lognx, long long nlines,
+                                                   const float2* __restrict__ tw, int inverse, FftEnds ends)
+{
+    constexpr int L = 256, G = 16, TP = 16 * 17 + 1;  // padded line stride of the exchange
+    __shared__ float2 W[L];
+    __shared__ float2 T[G * TP];
+    const int tid = threadIdx.x;
+    const int g = ALONG_Y ? (tid & 15) : (tid >> 4);
+    const int s = ALONG_Y ? (tid >> 4) : (tid & 15);
+    const long long l = (long long)blockIdx.x * G + g;
+    const bool live = l < nlines;
+    const int nx = 1 << lognx;
+    auto addr = [&](int i) -> long long {
+        if (ALONG_Y) return ((l >> lognx) << lognx) * L + (l & (nx - 1)) + (long long)i * nx;
+        return l * L + i;
+    };
+    for (int j = tid; j < L / 2; j += blockDim.x) {
+        float2 w = tw[j];
+        if (inverse) w.y = -w.y;
+        W[j] = w;
+        W[j + L / 2] = make_float2(-w.x, -w.y);
+    }
+    float2 a[16];
+    int yy = 0, jj = 0;
+    if (IN || OUT) {
+        const int ny = ends.P.g.ny;
+        yy = (int)(l % ny);
+        jj = (int)(l / ny);
+    }
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        const int i = 16 * n1 + s;
+        if (!live)
+            a[n1] = make_float2(0.f, 0.f);
+        else if (IN)
+            a[n1] = make_float2(fluid_dn(ends.P, ends.dn, i, yy, 2 * jj), fluid_dn(ends.P, ends.dn, i, yy, 2 * jj + 1));
+        else
+            a[n1] = data[addr(i)];
+    }
+    __syncthreads();  // twiddles
+    dft16(a, W, inverse);
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1)
+        if (s) a[k1] = cmul(a[k1], W[s * k1]);
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) T[g * TP + s * 17 + k1] = a[k1];
+    __syncthreads();
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) a[n2] = T[g * TP + n2 * 17 + s];
+    dft16(a, W, inverse);
+    if (!live) return;
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {
+        const int i = s + 16 * k2;
+        if (OUT) {
+            tail_out(ends, i, yy, 2 * jj, a[k2].x);
+            tail_out(ends, i, yy, 2 * jj + 1, a[k2].y);
+        } else {
+            data[addr(i)] = a[k2];
+        }
+    }
+}
+
 // one batched pass; `ends` selects the fused x-pass variants: 1 = read the
 // packed density (IN), 2 = write the tail force (OUT)
 cudaError_t fft_pass(float2* data, int L, int nx, long long nlines, bool along_y, const float2* tw, int inverse,
                      cudaStream_t s, int ends_mode = 0, const FftEnds* ends = nullptr)
 {
+    FftEnds e0;
+    const FftEnds& e = ends ? *ends : e0;
+    if (L == 256) {
+        const unsigned b256 = nblk(nlines, 16);
+        const int lnx = ilog2(nx);
+        if (along_y)
+            k_fft256<true><<<b256, 256, 0, s>>>(data, lnx, nlines, tw, inverse, e);
+        else if (ends_mode == 1)
+            k_fft256<false, true, false><<<b256, 256, 0, s>>>(data, lnx, nlines, tw, inverse, e);
+        else if (ends_mode == 2)
+            k_fft256<false, false, true><<<b256, 256, 0, s>>>(data, lnx, nlines, tw, inverse, e);
+        else
+            k_fft256<false><<<b256, 256, 0, s>>>(data, lnx, nlines, tw, inverse, e);
+        return cudaGetLastError();
+    }
     const int G = FFT_GL / L;
     const size_t smem = fft_smem();
     const unsigned blocks = nblk(nlines, G);
-    FftEnds e0;
-    const FftEnds& e = ends ? *ends : e0;
     if (along_y)
         k_fft<true><<<blocks, FFT_THREADS, smem, s>>>(data, L, ilog2(L), ilog2(nx), nlines, tw, inverse, e);
     else if (ends_mode == 1)

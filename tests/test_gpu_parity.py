@@ -202,6 +202,8 @@ def test_fp16_storage_velocity_profile(L, O):
     ((32, 32, 48), 8, False),   # spectral, sigma = 8 (reach 20 planes)
     ((32, 16, 27), 4, False),   # spectral, odd nz: the last plane pairs with an empty one
     ((16, 32, 21), 4, True),    # spectral, periodic odd nz
+    ((256, 4, 12), 4, False),   # spectral, 256-point lines along x (register four-step FFT)
+    ((4, 256, 11), 4, True),    # spectral, 256-point lines along y, periodic odd nz
 ])
 def test_tail_parity(L, O, shape, sigma, zper):
     nx, ny, nz = shape
