@@ -192,6 +192,15 @@ class Slit:
         self._check(self._lib.lbif_step_profiled(self._h, int(nsteps), ms, nl, 5))
         return (dict(zip(self.KERNEL_CLASSES, ms[:])), dict(zip(self.KERNEL_CLASSES, nl[:])))
 
+    def autotune(self, trials: int = 3):
+        """Pick the fastest launch shapes on the current state; returns (ball CTA
+        target, force tile-group edge, ball staging: 1 tensor-memory accelerator,
+        0 plain loads). The state is unchanged and the results are bit-identical."""
+        b, g, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self._check(self._lib.lbif_autotune(self._h, int(trials), ctypes.byref(b), ctypes.byref(g),
+                                            ctypes.byref(st)))
+        return b.value, g.value, st.value
+
     def set_fused(self, on: bool):
         """One pass per step (pull collide-stream with the next moments, the
         default where nx >= 32 and ny >= 8) or push collide-stream + moments."""
@@ -328,11 +337,4 @@ class Ensemble(Slit):
         self._check(self._lib.lbif_batch_profiles(self._h, pd(n), pd(ux), hmax), True)
         return n, ux
 
-    def autotune(self, trials: int = 3):
-        """Pick the fastest launch shapes on the current state; returns (ball CTA
-        target, force tile-group edge, ball staging: 1 tensor-memory accelerator,
-        0 plain loads)."""
-        b, g, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
-        self._check(self._lib.lbif_autotune(self._h, int(trials), ctypes.byref(b), ctypes.byref(g),
-                                            ctypes.byref(st)))
-        return b.value, g.value, st.value
+
