@@ -71,13 +71,16 @@ def _create(lib, nx=8, ny=8, nz=8, sigma=4.0, eta=0.3, tau=1.0, zbc=0, storage=0
     (dict(sigma=3.0), -6), (dict(sigma=4.5), -6), (dict(sigma=26.0), -6), (dict(sigma=0.0), -6),
     (dict(tau=0.5), -1), (dict(eta=0.0), -1), (dict(eta=1.0), -1), (dict(nx=0), -1),
     (dict(zbc=7), -1), (dict(storage=5), -1), (dict(noise=-1.0), -1),
+    (dict(ny=-3), -1), (dict(nz=0), -1),
+    # padded grid beyond 32-bit node indices: refused before any allocation
+    (dict(nx=2048, ny=2048, nz=1024), -6),
 ])
 def test_create_rejects_bad_arguments(lib, kw, code):
     rc, h = _create(lib, **kw)
     assert rc == code
     assert not h.value
     msg = lib.lbif_last_error(None)
-    assert msg and b"lbif_create" in msg
+    assert msg and b"create" in msg
 
 
 def test_null_handle_calls_fail_cleanly(lib):
