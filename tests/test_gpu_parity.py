@@ -82,6 +82,12 @@ FORCE_CASES = [
     (20, 20, 20, 4, False, dict(g2_form=1)),
     (20, 20, 20, 4, False, dict(coupling=False)),
     (20, 20, 20, 4, False, dict(regularize=False)),
+    # tiled mapping (nx >= 128: 128 x 4 node tiles, the fifth value of each
+    # x window from the neighbouring lane): ragged last tile in x and in y
+    (150, 10, 24, 4, False, {}),
+    (140, 6, 36, 8, True, {}),
+    (132, 5, 40, 12, False, {}),
+    (256, 3, 16, 4, False, dict(coupling=False)),
 ]
 
 
