@@ -161,7 +161,7 @@ def cpu_sample(steps_hint: float = 15.0):
     o.step(k)
     dt = time.perf_counter() - t0
     nodes = nx * ny * W.nz
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
     return {"value": nodes * k / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": f"FP64 oracle, {nx}x{ny}x{W.nz} slit of the same sigma/eta/tau/F_e, "
                       f"{k} steps after 1 untimed, {dt:.1f} s"}, dt, k, nodes
@@ -313,7 +313,7 @@ def run_reference(args, world, rank):
     dt = time.perf_counter() - t0
     nodes = nx * ny * W.nz
     v = nodes * steps / dt / 1e6
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    cores = oracle.threads()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPS", "n_gpus": world,
             "steps": steps, "warmup": warm, "ms_per_step": dt / steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

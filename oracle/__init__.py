@@ -57,6 +57,7 @@ def _load():
             "or_sphere_rule": (None, [_D, _D]),
             "or_g2": (f64, [f64, i32]),
             "or_ball_count": (i32, [i32]),
+            "or_threads": (i32, []),
             "or_coarse_density": (None, [i32, i32, i32, i32, i32, _D, _D]),
             "or_equilibrium": (None, [f64, _D, _D]),
             "or_collide_node": (None, [_D, _D, f64, _D]),
@@ -129,6 +130,11 @@ def g2(eta: float, form: int = 0) -> float:
 
 def ball_count(sigma: int) -> int:
     return _load().or_ball_count(int(sigma))
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops run on."""
+    return _load().or_threads()
 
 
 def equilibrium(n: float, u) -> np.ndarray:

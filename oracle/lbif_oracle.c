@@ -43,6 +43,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define NV 19 /* D3Q19 */
 #define NS 18 /* sphere quadrature points */
@@ -168,6 +171,16 @@ static double interp(const geom* g, const double* a, double px, double py, doubl
 
 /* contact value of the pair correlation, Sec. Methods (Fischer-Methfessel
  * paragraph); form 0 = as printed there, form 1 = Carnahan-Starling        */
+/* threads the parallel loops below run on (1 without OpenMP) */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 double or_g2(double eta, int form)
 {
     double d = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);

@@ -101,6 +101,7 @@ def test_oracle_builds_and_is_independent():
     import oracle
 
     oracle.build()
+    assert oracle.threads() >= 1  # what the benchmark reports as the oracle's cores
     csrc = glob.glob(os.path.join(ROOT, "paper_0712_2247_gb300", "csrc", "*"))
     for f in csrc:
         assert "oracle" not in open(f).read().lower(), f
