@@ -1150,14 +1150,17 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
     }
 }
 
-// At most 128 registers, so that four CTAs (16 warps) share an SM: the
-// kernel waits on L1 far more than it computes, and the extra warps hide
-// that latency (measured: 146 registers / 3 CTAs per SM is 6 % slower).
+// At most 128 registers, so that 16 warps share an SM: the kernel waits on
+// L1 far more than it computes, and the extra warps hide that latency
+// (measured: 146 registers / 12 warps is 6 % slower). CTAs of two warps (a
+// 128 x 2 tile), eight per SM (measured at sigma 12 on 512 x 512 x 192:
+// 32 / 64 / 128 / 256 / 512 threads 1.658 / 1.610 / 1.631 / 1.705 / 1.820 ms).
 // LN: tiled mapping with lane shuffles (every exit above the node's own
 // x test is taken by whole warps; lanes past the grid's edge stay, on the
 // row's first block, until the stores)
+constexpr int FORCE_NT = 64;
 template <int SIG, bool C2, bool LN>
-__global__ void __launch_bounds__(128, 4) k_force4(Params P, TileMap tm, Fields fl,
+__global__ void __launch_bounds__(FORCE_NT, 512 / FORCE_NT) k_force4(Params P, TileMap tm, Fields fl,
                                                 const float4* __restrict__ Ft, float4* __restrict__ F)
 {
     const Geom& g = P.g;
@@ -1886,9 +1889,9 @@ static void force4_launch(const Params& P, const TileMap& tm, const Fields& f, c
                           unsigned blocks, cudaStream_t s)
 {
     if (P.c2)
-        k_force4<SIG, true, LN><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+        k_force4<SIG, true, LN><<<blocks, FORCE_NT, 0, s>>>(P, tm, f, Ft, F);
     else
-        k_force4<SIG, false, LN><<<blocks, 128, 0, s>>>(P, tm, f, Ft, F);
+        k_force4<SIG, false, LN><<<blocks, FORCE_NT, 0, s>>>(P, tm, f, Ft, F);
 }
 
 cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, float4* F, int group,
@@ -1897,7 +1900,7 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
     unsigned blocks;
     if (group <= 0) group = 128;
     if (force_vectorised(P.sigma)) {
-        TileMap tm = P.g.nx < 128 ? make_flatmap(P.g, 4, 128, blocks) : make_tilemap(P.g, 128, 4, group, blocks);
+        TileMap tm = P.g.nx < 128 ? make_flatmap(P.g, 4, FORCE_NT, blocks) : make_tilemap(P.g, 128, FORCE_NT / 32, group, blocks);
         switch (P.sigma) {
         case 4:
             if (tm.flat) force4_launch<4, false>(P, tm, f, Ft, F, blocks, s);
