@@ -1687,11 +1687,30 @@ __global__ void k_moments_out(Params P, Fields fl, float* rho, float* u, float* 
     }
 }
 
-// per z plane: sum dn, sum ux, sum (1+dn) u  (FP64, fixed-order tree)
-// Per z plane: sum dn, sum ux, sum (1+dn) u (FP64, fixed order): CTA (z, c)
-// reduces rows [c rc, (c+1) rc) of plane z by a fixed tree into part, then
-// k_profiles_sum adds the chunks of a plane in order.
+// Per z plane: sum dn, sum ux, sum (1+dn) u (FP64 results, fixed order): CTA
+// (z, c) reduces rows [c rc, (c+1) rc) of plane z into part, then
+// k_profiles_sum adds the chunks of a plane in order. Per node the work is
+// FP32 only (FP64 runs at a small fraction of the FP32 rate on this GPU):
+// each thread keeps every sum as an unevaluated pair hi + lo of FP32 numbers,
+// updated by Knuth's two-sum, which yields the rounding error of each FP32
+// addition exactly, so the pair carries about 48 bits; the products
+// (1 + dn) u enter as u + p + e with p = fl(dn u) and e = dn u - p (exact, by
+// a fused multiply-add). Each thread converts its pairs to FP64 once; the
+// CTA adds them by a fixed FP64 tree.
 constexpr int PROF_K = 5;
+
+struct F32Pair {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void pair_add(F32Pair& a, float x)
+{
+    const float s = a.hi + x;
+    const float bb = s - a.hi;
+    a.lo += (a.hi - (s - bb)) + (x - bb);
+    a.hi = s;
+}
+
 __global__ void k_profiles(Params P, Fields fl, double* part, int chunks)
 {
     __shared__ double sh[PROF_K][256];
@@ -1699,20 +1718,36 @@ __global__ void k_profiles(Params P, Fields fl, double* part, int chunks)
     const int z = blockIdx.x, c = blockIdx.y;
     const int rc = (g.ny + chunks - 1) / chunks;
     const int y0 = min(g.ny, c * rc), y1 = min(g.ny, y0 + rc);
-    double a[PROF_K] = {0, 0, 0, 0, 0};
+    F32Pair a[PROF_K];
+#pragma unroll
+    for (int j = 0; j < PROF_K; ++j) a[j].hi = a[j].lo = 0.f;
     const int n = (y1 - y0) * g.nx;
+    int dy = threadIdx.x / g.nx, x = threadIdx.x - dy * g.nx;
+    const int step_y = blockDim.x / g.nx, step_x = blockDim.x - step_y * g.nx;
     for (int k = threadIdx.x; k < n; k += blockDim.x) {
-        const int dy = k / g.nx, x = k - dy * g.nx;
         const int p = pidx(g, x, y0 + dy, z);
-        double d = (double)fl.dn[p], vx = fl.ux[p], vy = fl.uy[p], vz = fl.uz[p];
-        double opd = 1.0 + d;
-        a[0] += d;
-        a[1] += vx;
-        a[2] += opd * vx;
-        a[3] += opd * vy;
-        a[4] += opd * vz;
+        const float d = fl.dn[p];
+        const float v[3] = {fl.ux[p], fl.uy[p], fl.uz[p]};
+        pair_add(a[0], d);
+        pair_add(a[1], v[0]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float pr = d * v[j];
+            const float e = fmaf(d, v[j], -pr);
+            pair_add(a[2 + j], v[j]);
+            pair_add(a[2 + j], pr);
+            pair_add(a[2 + j], e);
+        }
+        // next node of this thread: blockDim.x further in row-major order
+        x += step_x;
+        dy += step_y;
+        if (x >= g.nx) {
+            x -= g.nx;
+            ++dy;
+        }
     }
-    for (int j = 0; j < PROF_K; ++j) sh[j][threadIdx.x] = a[j];
+#pragma unroll
+    for (int j = 0; j < PROF_K; ++j) sh[j][threadIdx.x] = (double)a[j].hi + (double)a[j].lo;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s)

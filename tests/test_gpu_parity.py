@@ -268,6 +268,24 @@ def test_full_size_sigma12_slit_against_1d_oracle(L, O, storage):
     g.close()
 
 
+@pytest.mark.parametrize("shape", [(64, 48, 20), (300, 7, 9), (5, 3, 11)])
+def test_profile_sums_exact_to_fp64(L, shape):
+    """The per-plane sums behind the profiles (FP32 two-sum pairs per thread,
+    one FP64 tree per CTA) against exactly rounded sums (math.fsum) of the
+    same FP32 velocities: the x,y average of u_x within 1e-12 of max |u_x|."""
+    nx, ny, nz = shape
+    g = L.Slit(nx, ny, nz, 4, 0.25, 0.9, body=(1e-5, 0, 0), seed=6, noise=2e-2)
+    g.step(30)
+    _, u = g.moments()
+    _, ux_z, _ = g.profiles()
+    A = nx * ny
+    for z in range(nz):
+        plane = u[0, z].astype(np.float64).ravel()
+        exact = math.fsum(plane.tolist()) / A
+        assert abs(ux_z[z] - exact) <= 1e-12 * np.abs(plane).max(), z
+    g.close()
+
+
 def test_mass_conservation_and_determinism(L):
     def run():
         g = L.Slit(20, 18, 24, 4, 0.25, 0.9, body=(1e-5, 0, 0), seed=9)
