@@ -117,12 +117,16 @@ int lbif_moments(lbif_handle h, float* rho, float* u, float* pressure, int32_t o
 int lbif_forces(lbif_handle h, float* F, int32_t on_device);
 
 /* Re-initialise the populations to f_eq(n, u) of given fields (same layout
- * as lbif_moments; u may be NULL = 0) and reset the step counter. */
+ * as lbif_moments; u may be NULL = 0) and reset the step counter. With u NULL
+ * the stored populations are exactly 0 (relative to n itself), so the fields
+ * of step 0 are n and u = 0 without a moments pass; the state is the same,
+ * bit for bit, as with an explicit u = 0. */
 int lbif_set_fields(lbif_handle h, const float* rho, const float* u, int32_t on_device);
 
 /* FP64 x,y-averaged profiles n(z), u_x(z) (nz doubles each; either may be
  * NULL), total mass and momentum (out4 = {M, Jx, Jy, Jz}; may be NULL), from
- * a deterministic FP64 reduction on the device. Synchronises. */
+ * a deterministic reduction on the device (per thread exact FP32 two-sum
+ * pairs, about 48 bits; FP64 across threads in a fixed order). Synchronises. */
 int lbif_profiles(lbif_handle h, double* n_z, double* ux_z, double* out4);
 
 /* Steady-state residual over the steps since the previous call:

@@ -824,8 +824,21 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
         }
     }
     CK(h, launch_init_fields(P, h->pop[h->cur], h->dn[h->dref], drho, du, h->stream));
+    if (!u) {
+        // At rest the equilibrium populations, stored relative to dn itself,
+        // are all exactly 0, so their moments are dn (already in dn[dref],
+        // with its images) and u = 0, bit for bit: no moments pass.
+        float* const* uf = h->u[h->ucur];
+        for (int k = 0; k < 3; ++k)
+            CK(h, cudaMemsetAsync(uf[k] - PAD_SLACK, 0, sizeof(float) * ((size_t)P.g.P + 2 * PAD_SLACK),
+                                  h->stream));
+    }
     CK(h, cudaStreamSynchronize(h->stream));
     reset_time(h);
+    if (!u) {
+        h->dfld = h->dref;
+        h->fields_t = h->t;
+    }
     return LBIF_OK;
 }
 
