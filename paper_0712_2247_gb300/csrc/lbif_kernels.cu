@@ -46,16 +46,6 @@ __device__ __forceinline__ float ldp(const __half* p) { return __half2float(__ld
 __device__ __forceinline__ void stp(float* p, float v) { *p = v; }
 __device__ __forceinline__ void stp(__half* p, float v) { *p = __float2half_rn(v); }
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-// population gathers of the fused pass: read-only path with a 256-byte L2
-// fetch (neighbouring warps read the rest of the row; measured at 512 x 512 x
-// 192: 2.333 -> 2.319 ms; an L1 no-allocate hint on top: 2.510 ms)
-__device__ __forceinline__ float ldp_row(const float* p)
-{
-    float r;
-    asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(r) : "l"(p));
-    return r;
-}
-__device__ __forceinline__ float ldp_row(const __half* p) { return ldp(p); }
 
 __device__ __forceinline__ int pidx(const Geom& g, int x, int y, int z)
 {
@@ -1467,7 +1457,7 @@ __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ 
     const Geom& g = P.g;
     if (x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi) {
 #pragma unroll
-        for (int i = I0; i < I1; ++i) v[i - I0] = ldp_row(pin + (long long)i * g.Npad + (idx - P.soff[i]));
+        for (int i = I0; i < I1; ++i) v[i - I0] = ldp(pin + (long long)i * g.Npad + (idx - P.soff[i]));
         return;
     }
 #pragma unroll
