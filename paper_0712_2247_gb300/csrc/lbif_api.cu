@@ -140,14 +140,26 @@ static cudaError_t run_tail(lbif_ctx* h, const float* dn)
 }
 
 // padded fields carry PAD_SLACK floats before their first element
-static float* padded_alloc(size_t P)
+static cudaError_t padded_alloc(size_t P, float** out)
 {
     float* raw = nullptr;
-    if (cudaMalloc((void**)&raw, sizeof(float) * (P + 2 * PAD_SLACK)) != cudaSuccess) {
+    *out = nullptr;
+    const cudaError_t e = cudaMalloc((void**)&raw, sizeof(float) * (P + 2 * PAD_SLACK));
+    if (e != cudaSuccess) {
         cudaGetLastError();
-        return nullptr;
+        return e;
     }
-    return raw + PAD_SLACK;
+    *out = raw + PAD_SLACK;
+    return cudaSuccess;
+}
+
+// a failed device allocation during creation: LBIF_ERR_NOMEM when the device
+// is out of memory, LBIF_ERR_CUDA with the runtime's message otherwise (no
+// device, a broken context)
+static int alloc_failed(cudaError_t e)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(nullptr, LBIF_ERR_NOMEM, "create: device allocation failed");
+    return fail(nullptr, LBIF_ERR_CUDA, std::string("create: ") + cudaGetErrorString(e));
 }
 
 static void padded_free(float* p)
@@ -383,10 +395,11 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     size_t pb = pop_bytes(P) * (size_t)Q * (size_t)g.Npad;
 #define ALLOC(ptr, bytes)                                                                   \
     do {                                                                                    \
-        if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                           \
+        const cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                         \
+        if (e_ != cudaSuccess) {                                                            \
             cudaGetLastError();                                                             \
             free_ctx(h);                                                                    \
-            return fail(nullptr, LBIF_ERR_NOMEM, "create: device allocation failed");       \
+            return alloc_failed(e_);                                                        \
         }                                                                                   \
     } while (0)
     ALLOC(h->pop[0], pb);
@@ -407,10 +420,10 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
         float** pads[] = {&h->dn[0], &h->dn[1], &h->dn[2], &h->u[0][0], &h->u[0][1], &h->u[0][2],
                           &h->u[1][0], &h->u[1][1], &h->u[1][2], &h->dG};
         for (float** q : pads) {
-            *q = padded_alloc((size_t)g.P);
-            if (!*q) {
+            const cudaError_t e = padded_alloc((size_t)g.P, q);
+            if (e != cudaSuccess) {
                 free_ctx(h);
-                return fail(nullptr, LBIF_ERR_NOMEM, "create: device allocation failed");
+                return alloc_failed(e);
             }
         }
         h->ball_map_ok = make_ball_map(g, P.sigma, h->dn[0], &h->ball_map[0]) &&

@@ -96,6 +96,31 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbif_last_error(None)
 
 
+def test_no_device_fails_loudly(lib):
+    """Without a usable GPU, creation reports the CUDA runtime's error: there is
+    no CPU path to fall back on (skipped where a GPU is present)."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    rc, h = _create(lib)
+    assert rc == -3 and not h.value
+    assert lib.lbif_last_error(None).startswith(b"create: ")
+
+
+def test_missing_library_raises():
+    """The binding raises when the CUDA library is absent (fresh interpreter)."""
+    import subprocess
+    import sys
+
+    code = ("from paper_0712_2247_gb300 import lbif\n"
+            "try:\n"
+            "    lbif.load_library('/nonexistent/liblbif.so')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'missing' in str(e))\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.stdout.strip() == "raised True", out.stdout + out.stderr
+
+
 def test_oracle_builds_and_is_independent():
     """The oracle compiles on its own and shares no source with the CUDA path."""
     import oracle
