@@ -498,8 +498,8 @@ def main():
     ap.add_argument("--no-tail", action="store_true", help="skip the attractive-tail workload")
     ap.add_argument("--mlp-batch", type=int, default=65536, help="rows of the tensor-core forward leg")
     ap.add_argument("--ens-steps", type=int, default=2000, help="timed steps of the ensemble leg")
-    ap.add_argument("--ws-train", type=int, default=4096, help="training slits of the warm-start leg")
-    ap.add_argument("--ws-adam", type=int, default=3000, help="Adam steps of the warm-start leg")
+    ap.add_argument("--ws-train", type=int, default=8192, help="training slits of the warm-start leg")
+    ap.add_argument("--ws-adam", type=int, default=8000, help="Adam steps of the warm-start leg")
     ap.add_argument("--ws-heldout", type=int, default=128, help="held-out slits of the warm-start leg")
     ap.add_argument("--two-pass", action="store_true",
                     help="push collide-stream + moments pass instead of the fused pass")
