@@ -110,12 +110,13 @@ def kernel_bytes(storage: int, fused: bool):
 
 
 # DRAM bytes per node (dram__bytes_read.sum + dram__bytes_write.sum) of each
-# step kernel, FP32 storage, from one ncu --set full capture of the
-# 256x256x192 sigma = 12 slit of the current kernels; a full-size launch moves
-# these bytes times its node count (traffic grows with the nodes). Must be
-# re-measured whenever a kernel changes.
+# step kernel, FP32 storage, from ncu captures of the 256x256x192 sigma = 12
+# slit of the current kernels (--set full; the fused pass with its 32 x 4
+# tiles: those two metrics alone); a full-size launch moves these bytes times
+# its node count (traffic grows with the nodes). Must be re-measured whenever
+# a kernel changes.
 TRAFFIC_B_PER_NODE_F32 = {"moments": 98.2, "ball_g2": 6.0, "force": 45.7, "collide_stream": 183.5,
-                          "collide_stream_fused": 211.6}
+                          "collide_stream_fused": 210.6}
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:

@@ -193,13 +193,13 @@ int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax);
  *   into it (pull form), applies the collision of their source node, and
  *   forms the moments n, u of the next step from the values it holds. The
  *   populations are read and written once per step. Needs nx >= 32 and
- *   ny >= 8; the default with FP32 storage and nx ny nz >= 2^23 nodes, where
+ *   ny >= 4; the default with FP32 storage and nx ny nz >= 2^23 nodes, where
  *   it is the faster of the two.
  * fused = 0: a push collide-stream pass, then a moments pass at the start of
  *   the next step (any grid).
  * Both compute the same update; results agree to FP32 rounding, not bit for
  * bit. May be changed between steps. Errors: LBIF_ERR_ARG for a NULL handle,
- * fused not 0 or 1, or fused = 1 with nx < 32 or ny < 8. */
+ * fused not 0 or 1, or fused = 1 with nx < 32 or ny < 4. */
 int lbif_set_fused(lbif_handle h, int32_t fused);
 /* The pass in use: *fused = 1 fused, 0 two passes. */
 int lbif_get_fused(lbif_handle h, int32_t* fused);

@@ -1172,14 +1172,11 @@ extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int3
     return LBIF_OK;
 }
 
-// Time each candidate launch shape on the handle's own state and keep the
-// fastest: the ball kernel's CTA target (z-chunking) and the force kernel's
-// tile-group edge. The state is saved and restored around the trials.
 extern "C" int lbif_set_fused(lbif_handle h, int32_t fused)
 {
     if (!h || (fused != 0 && fused != 1)) return fail(h, LBIF_ERR_ARG, "lbif_set_fused: bad arguments");
     if (fused && !csm_ok(h->P.g))
-        return fail(h, LBIF_ERR_ARG, "lbif_set_fused: the fused pass needs nx >= 32 and ny >= 8");
+        return fail(h, LBIF_ERR_ARG, "lbif_set_fused: the fused pass needs nx >= 32 and ny >= 4");
     if (h->fused != (fused != 0)) {
         // the unfused step reads dn(t) of the fused one as its reference;
         // the fused step reads both buffers the unfused one leaves
@@ -1218,6 +1215,10 @@ extern "C" int lbif_get_fused(lbif_handle h, int32_t* fused)
     return LBIF_OK;
 }
 
+// Time each candidate launch shape on the handle's own state and keep the
+// fastest: the ball kernel's CTA target (z-chunking) and staging, and the
+// force kernel's tile-group edge. The state is saved and restored around the
+// trials.
 extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group,
                              int32_t* ball_staging)
 {

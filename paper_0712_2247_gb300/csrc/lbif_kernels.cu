@@ -1334,7 +1334,7 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
 // of its source node, and forms the new moments from the 19 values it holds,
 // so the populations are read and written once per step (push collide-stream
 // followed by a moments pass reads them twice). What a source node
-// contributes is staged per node in shared memory: a CTA owns a 32 x 8 tile
+// contributes is staged per node in shared memory: a CTA owns a 32 x 4 tile
 // of x-y nodes, keeps three planes of it (plus a one-node halo) in a ring,
 // and marches up a segment of z planes.
 //
@@ -1356,7 +1356,11 @@ __global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ p
 // bounce-back). The new populations are stored relative to the new density
 // dn(r) + S, S = sum_i w_i v_i, which is also the next step's reference.
 // ---------------------------------------------------------------------------
-constexpr int CSM_TX = 32, CSM_TY = 8, CSM_THREADS = CSM_TX * CSM_TY;
+// 32 x 4 tiles of 128 threads, six CTAs per SM (measured at 512 x 512 x 192, sigma 12, same
+// state: 32 x 4 / 128 threads / 6 CTAs 2.186 ms, 32 x 8 / 256 / 3 2.334 ms, 32 x 12 / 384 / 2
+// 2.508 ms): more, smaller CTAs keep more population loads in flight across the two barriers
+// of each plane
+constexpr int CSM_TX = 32, CSM_TY = 4, CSM_THREADS = CSM_TX * CSM_TY;
 constexpr int CSM_HX = CSM_TX + 2, CSM_HN = CSM_HX * (CSM_TY + 2);  // staged nodes per plane
 // staged quantities: dn, P_x..z, C_x..z, C_xy C_xz C_yz, X_xy X_xz X_yz
 constexpr int SQ_DN = 0, SQ_P = 1, SQ_CA = 4, SQ_CP = 7, SQ_X = 10, CSM_NF = 13;
@@ -1368,7 +1372,7 @@ __device__ __forceinline__ int csm_slot(int q) { return (q + 3) % 3; }
 // The halo nodes a thread stages in every plane (NT threads: h = thread,
 // thread + NT, ...; at most two): their in-plane padded offset (x, y halo
 // images hold the periodic values) and the in-plane index of their periodic
-// image in the unpadded force array, or -1 (past the 340th node or a partial
+// image in the unpadded force array, or -1 (past the last halo node or a partial
 // tile: never gathered).
 constexpr int CSM_KS = 2;
 struct CsmStaged {
@@ -1441,7 +1445,7 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
 
 // CTAs per SM the register budget is sized for, and z planes per CTA segment
 #ifndef CSM_MINB
-#define CSM_MINB 3
+#define CSM_MINB 6
 #endif
 #ifndef CSM_LZ
 #define CSM_LZ 16
@@ -1552,7 +1556,7 @@ __device__ __forceinline__ void csm_sums(const float* v, float (&m)[4])
     }
 }
 
-// one node per thread, a CTA per 32 x 8 tile and z segment (measured: two
+// one node per thread, a CTA per 32 x 4 tile and z segment (measured: two
 // threads per node, each gathering half of the directions and adding the
 // partial moments through shared memory, ran slower at twice the warps)
 template <typename T>

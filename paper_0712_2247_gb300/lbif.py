@@ -203,7 +203,7 @@ class Slit:
 
     def set_fused(self, on: bool):
         """One pass per step (pull collide-stream with the next moments; needs
-        nx >= 32 and ny >= 8, the default with FP32 storage on grids of at
+        nx >= 32 and ny >= 4, the default with FP32 storage on grids of at
         least 2^23 nodes) or push collide-stream + moments (any grid)."""
         self._check(self._lib.lbif_set_fused(self._h, 1 if on else 0))
 

@@ -5,7 +5,7 @@ Both passes compute the same forward-Euler BGK update with the first-order
 source, streaming and half-way bounce-back (Sec. Methods); they differ only in
 the order of FP32 roundings, so each is held to the oracle at the tolerances
 of the two-pass tests (1e-5 normwise, FP32) and to the other at a few FP32
-ulps of the state. Shapes span several 32 x 8 tiles with ragged tails in x and
+ulps of the state. Shapes span several 32 x 4 tiles with ragged tails in x and
 y, z segments of the marching CTAs, walls and periodic z.
 """
 import numpy as np
@@ -153,7 +153,7 @@ def test_fused_with_options(L, O, extra):
 
 
 def test_fused_ensemble_matches_oracle_and_freezes(L, O):
-    """Stacked slits on 32 x 8 rows through the fused pass: parity per slit,
+    """Stacked slits on 32 x 8 rows (two tile rows) through the fused pass: parity per slit,
     and run-to-steady-state with frozen slits gives the same profiles as the
     two-pass ensemble to FP32 rounding."""
     H = np.array([9, 16, 12], np.int32)
