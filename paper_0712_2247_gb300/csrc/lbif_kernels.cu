@@ -1974,8 +1974,9 @@ cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields
 bool csm_ok(const Geom& g) { return g.nx >= CSM_TX && g.ny >= CSM_TY; }
 
 // Measured on GB300 (per-step CUDA-event times, both passes): the fused pass
-// wins with FP32 storage on large grids (512x512x192, sigma 12: 2.32 vs
-// 2.52 ms; 8-12 M nodes: 1-3 %) and loses with FP16 storage (2.69 vs
+// wins with FP32 storage on large grids (512x512x192, sigma 12: 2.20 vs
+// 2.48 ms with 32 x 4 tiles; with 32 x 8 tiles 2.32 vs 2.52 ms, and 1-3 % at
+// 8-12 M nodes) and, with 32 x 8 tiles, lost with FP16 storage (2.69 vs
 // 2.26 ms) and on grids too small to fill the GPU with its CTAs
 // (256x256x96: 0.61 vs 0.60 ms; 64^3: 0.098 vs 0.060 ms).
 bool csm_default(const Geom& g, int storage)
