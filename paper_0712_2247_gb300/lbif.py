@@ -101,22 +101,33 @@ class LbifError(RuntimeError):
         self.code = code
 
 
-def _ptr(a) -> Optional[int]:
-    """Device pointer of a torch tensor or host pointer of a numpy array (float32, contiguous)."""
+def _ptr(a, n: Optional[int] = None) -> Optional[int]:
+    """Device pointer of a torch tensor or host pointer of a numpy array. The
+    array must be contiguous float32 and, when n is given, hold exactly n
+    elements (the library reads or writes that many); anything else raises
+    here, before the library sees the pointer."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        assert a.dtype == np.float32 and a.flags.c_contiguous, "need contiguous float32"
-        return a.ctypes.data
-    assert a.is_contiguous() and str(a.dtype) == "torch.float32", "need contiguous float32"
-    return a.data_ptr()
+        if a.dtype != np.float32 or not a.flags.c_contiguous:
+            raise TypeError("lbif: arrays must be contiguous float32")
+        size, p = a.size, a.ctypes.data
+    else:
+        if str(getattr(a, "dtype", "")) != "torch.float32" or not a.is_contiguous():
+            raise TypeError("lbif: tensors must be contiguous torch.float32")
+        size, p = a.numel(), a.data_ptr()
+    if n is not None and size != n:
+        raise ValueError(f"lbif: array of {size} elements where {n} are needed")
+    return p
 
 
 def _on_device(*arrays) -> int:
-    for a in arrays:
-        if a is not None:
-            return 0 if isinstance(a, np.ndarray) else int(a.is_cuda)
-    return 0
+    """1 when the given arrays are CUDA tensors, 0 when they are host arrays;
+    host and device arrays in one call raise."""
+    where = {0 if isinstance(a, np.ndarray) else int(a.is_cuda) for a in arrays if a is not None}
+    if len(where) > 1:
+        raise ValueError("lbif: host and device arrays mixed in one call")
+    return where.pop() if where else 0
 
 
 def selftest_wait(polls: int):
@@ -220,8 +231,10 @@ class Slit:
             u = np.empty((3,) + self.shape, np.float32)
             self._check(self._lib.lbif_moments(self._h, _ptr(rho), _ptr(u), None, 0), allow_diverged)
             return rho, u
-        self._check(self._lib.lbif_moments(self._h, _ptr(rho), _ptr(u), _ptr(pressure),
-                                           _on_device(rho, u, pressure)), allow_diverged)
+        n = self.nodes
+        dev = _on_device(rho, u, pressure)
+        self._check(self._lib.lbif_moments(self._h, _ptr(rho, n), _ptr(u, 3 * n), _ptr(pressure, n), dev),
+                    allow_diverged)
         return rho, u, pressure
 
     def pressure(self) -> np.ndarray:
@@ -232,11 +245,17 @@ class Slit:
     def forces(self, out=None) -> np.ndarray:
         """Total force density divided by n0, shape (3, nz, ny, nx)."""
         F = np.empty((3,) + self.shape, np.float32) if out is None else out
-        self._check(self._lib.lbif_forces(self._h, _ptr(F), _on_device(F)))
+        self._check(self._lib.lbif_forces(self._h, _ptr(F, 3 * self.nodes), _on_device(F)))
         return F
 
     def set_fields(self, rho, u=None):
-        self._check(self._lib.lbif_set_fields(self._h, _ptr(rho), _ptr(u), _on_device(rho, u)))
+        dev = _on_device(rho, u)
+        self._check(self._lib.lbif_set_fields(self._h, _ptr(rho, self.nodes), _ptr(u, 3 * self.nodes), dev))
+
+    @property
+    def nodes(self) -> int:
+        nz, ny, nx = self.shape
+        return nx * ny * nz
 
     def profiles(self, allow_diverged=False):
         nz = self.shape[0]

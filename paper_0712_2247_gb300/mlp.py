@@ -79,7 +79,8 @@ class MLP:
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
-        assert p.size == self.num_params
+        if p.size != self.num_params:
+            raise ValueError(f"MLP: {p.size} parameters where {self.num_params} are needed")
         self._check(self._lib.lbif_mlp_set_params(self._h, p.ctypes.data))
 
     def get_params(self):
@@ -88,11 +89,15 @@ class MLP:
         return p
 
     def _args(self, X, *rest):
-        dev = lbif._on_device(X)
+        """Host/device side and batch of X (batch x nin) and of the targets and
+        masks (batch x nout); wrong shapes or mixed sides raise."""
+        dev = lbif._on_device(X, *rest)
         b = X.shape[0]
-        assert X.shape == (b, self.nin)
+        if tuple(X.shape) != (b, self.nin):
+            raise ValueError(f"MLP: inputs of shape {tuple(X.shape)}, need (batch, {self.nin})")
         for a in rest:
-            assert a.shape == (b, self.nout)
+            if tuple(a.shape) != (b, self.nout):
+                raise ValueError(f"MLP: array of shape {tuple(a.shape)}, need ({b}, {self.nout})")
         return dev, b
 
     def forward(self, X):
