@@ -231,7 +231,7 @@ class Slit:
             u = np.empty((3,) + self.shape, np.float32)
             self._check(self._lib.lbif_moments(self._h, _ptr(rho), _ptr(u), None, 0), allow_diverged)
             return rho, u
-        n = self.nodes
+        n = self.grid_nodes
         dev = _on_device(rho, u, pressure)
         self._check(self._lib.lbif_moments(self._h, _ptr(rho, n), _ptr(u, 3 * n), _ptr(pressure, n), dev),
                     allow_diverged)
@@ -245,15 +245,17 @@ class Slit:
     def forces(self, out=None) -> np.ndarray:
         """Total force density divided by n0, shape (3, nz, ny, nx)."""
         F = np.empty((3,) + self.shape, np.float32) if out is None else out
-        self._check(self._lib.lbif_forces(self._h, _ptr(F, 3 * self.nodes), _on_device(F)))
+        self._check(self._lib.lbif_forces(self._h, _ptr(F, 3 * self.grid_nodes), _on_device(F)))
         return F
 
     def set_fields(self, rho, u=None):
         dev = _on_device(rho, u)
-        self._check(self._lib.lbif_set_fields(self._h, _ptr(rho, self.nodes), _ptr(u, 3 * self.nodes), dev))
+        self._check(self._lib.lbif_set_fields(self._h, _ptr(rho, self.grid_nodes), _ptr(u, 3 * self.grid_nodes), dev))
 
     @property
-    def nodes(self) -> int:
+    def grid_nodes(self) -> int:
+        """nx ny nz: the element count of one field array (an ensemble's gap
+        planes included)."""
         nz, ny, nx = self.shape
         return nx * ny * nz
 
