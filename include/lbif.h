@@ -12,8 +12,8 @@
  *     are fluid). Lattice units: spacing 1, time step 1, m = 1,
  *     k_B T = v_T^2 = c_s^2 = 1/3.
  *   - sigma (hard-sphere diameter) is an even integer number of lattice
- *     spacings (Sec. Methods: "sigma an even multiple of the lattice
- *     spacing"); odd or non-integer sigma returns LBIF_ERR_UNSUPPORTED.
+ *     spacings (Sec. Methods fixes it so, which puts the axis midpoints on
+ *     lattice nodes); odd or non-integer sigma returns LBIF_ERR_UNSUPPORTED.
  *   - Ownership: a handle owns every device buffer it allocates; callers own
  *     all buffers they pass in. Nothing returned aliases caller memory.
  *   - Errors: every call returns 0 (LBIF_OK) or a negative LBIF_ERR_* code
