@@ -3,9 +3,13 @@
 
 Workload: a 512 x 512 x 192 slit, sigma = 12, eta = 0.25, tau = 0.7,
 F_e = 5e-7 (bounce-back walls in z, periodic x, y), FP32 compute, populations
-stored as FP32 deviations (``--storage f16`` for FP16 deviations). One step =
-moments -> ball average + g2 -> shell force + BGK collision + streaming.
-The populations (3.8 GB FP32) exceed the 129 MB L2, so no flush is needed.
+stored as FP32 non-equilibrium parts (``--storage f16`` for FP16). One step =
+ball average + g2 -> shell force -> BGK collision + pull streaming + the next
+moments. The populations (3.8 GB FP32) exceed the 129 MB L2, so no flush is
+needed. Beside the headline line: the same slit with FP16 storage, the
+packing-fraction sweep (0.10 timed; 0.40 and 0.45 run until the divergence
+flag), the attractive-tail workload, the ensemble, the network and the warm
+start.
 
 Prints ONE JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
 on the host cores on a bounded sample of the same workload instead.
@@ -95,28 +99,25 @@ def bytes_alg(storage: int):
     return 2 * 19 * s + 44
 
 
-def kernel_bytes(storage: int, fused: bool):
+def kernel_bytes(storage: int):
     """Algorithmic bytes per node moved by each kernel class (each array element
     read or written once; stencil neighbours come from cache):
-      moments         19 populations in, reference dn in, {dn,u} + dn out
       ball_g2         dn in, dG out
       tail            dn in, F_tail out
       force           {dn,u} + dG in, F out
-      collide_stream  two-pass: 19 populations in and out, {dn,u}, F in;
-                      fused: the same, plus the next {dn,u} out"""
+      collide_stream  19 populations in and out, {dn,u} and F in, the next
+                      {dn,u} out (the pull pass)"""
     s = 2 if storage == 1 else 4
-    return {"moments": 19 * s + 4 + 20, "ball_g2": 8, "tail": 20, "force": 36,
-            "collide_stream": 2 * 19 * s + 32 + (16 if fused else 0)}
+    return {"ball_g2": 8, "tail": 20, "force": 36, "collide_stream": 2 * 19 * s + 32 + 16}
 
 
 # DRAM bytes per node (dram__bytes_read.sum + dram__bytes_write.sum) of each
-# step kernel, FP32 storage, from ncu captures of the 256x256x192 sigma = 12
-# slit of the current kernels (--set full; the fused pass with its 32 x 4
-# tiles: those two metrics alone); a full-size launch moves these bytes times
-# its node count (traffic grows with the nodes). Must be re-measured whenever
-# a kernel changes.
-TRAFFIC_B_PER_NODE_F32 = {"moments": 98.2, "ball_g2": 6.0, "force": 45.7, "collide_stream": 183.5,
-                          "collide_stream_fused": 210.6}
+# step kernel, from ncu captures of the 256x256x192 sigma = 12 slit of the
+# current kernels; a full-size launch moves these bytes times its node count
+# (traffic grows with the nodes). None where the kernel changed after its
+# last capture (re-measured with every kernel change).
+TRAFFIC_B_PER_NODE = {0: {"ball_g2": 6.0, "force": 45.7, "collide_stream": None},
+                      1: {"ball_g2": 6.0, "force": 45.7, "collide_stream": None}}
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
@@ -145,27 +146,69 @@ def dist_setup(args):
     return world, rank, local
 
 
-def cpu_sample(steps_hint: float = 15.0):
-    """Time the FP64 oracle on a bounded sample of the workload (all host cores)."""
-    import oracle
-    from paper_0712_2247_gb300.inputs import C2
+def cpu_model() -> str:
+    """The host CPU's model name (/proc/cpuinfo, else lscpu), or 'unknown'."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
-    W = C2
-    nx = ny = 64
+
+def _oracle_mlups(nx, ny, W, steps_hint, max_steps=20):
+    import oracle
+
     o = oracle.Oracle(nx, ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, seed=W.seed)
     t0 = time.perf_counter()
     o.step(1)
-    t1 = time.perf_counter()
-    per = t1 - t0
-    k = max(1, min(20, int(steps_hint / max(per, 1e-3))))
+    per = time.perf_counter() - t0
+    k = max(1, min(max_steps, int(steps_hint / max(per, 1e-3))))
     t0 = time.perf_counter()
     o.step(k)
     dt = time.perf_counter() - t0
-    nodes = nx * ny * W.nz
+    o.close()
+    return nx * ny * W.nz * k / dt / 1e6, k, dt
+
+
+def cpu_sample(steps_hint: float = 15.0):
+    """Time the FP64 oracle on bounded samples of the workload: the sigma = 12
+    slit at 64 x 64 x 192 on all host cores (the reported value), the same slit
+    at 32 x 32 x 192 on one core, and the full 1000 steps of the 16 x 16 x 32
+    sigma = 4 slit (eta 0.25) on all cores."""
+    import oracle
+    from paper_0712_2247_gb300.inputs import C0S, C2
+
     cores = oracle.threads()
-    return {"value": nodes * k / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 oracle, {nx}x{ny}x{W.nz} slit of the same sigma/eta/tau/F_e, "
-                      f"{k} steps after 1 untimed, {dt:.1f} s"}, dt, k, nodes
+    v, k, dt = _oracle_mlups(64, 64, C2, steps_hint)
+    oracle.set_threads(1)
+    try:
+        v1, k1, dt1 = _oracle_mlups(32, 32, C2, steps_hint / 3, max_steps=10)
+    finally:
+        oracle.set_threads(cores)
+    o = oracle.Oracle(C0S.nx, C0S.ny, C0S.nz, C0S.sigma, C0S.eta, C0S.tau, body=C0S.body, seed=C0S.seed)
+    t0 = time.perf_counter()
+    o.step(C0S.steps)
+    dt0 = time.perf_counter() - t0
+    o.close()
+    return {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, 64x64x{C2.nz} slit of the same sigma/eta/tau/F_e, "
+                      f"{k} steps after 1 untimed, {dt:.1f} s",
+            "cpu_model": cpu_model(),
+            "single_thread": {"value": v1, "unit": "MLUPS", "cores": 1,
+                              "sample": f"32x32x{C2.nz} slit, {k1} steps after 1 untimed, {dt1:.1f} s"},
+            "c0s_full": {"value": C0S.nodes * C0S.steps / dt0 / 1e6, "unit": "MLUPS", "cores": cores,
+                         "sample": f"{C0S.nx}x{C0S.ny}x{C0S.nz} sigma={C0S.sigma} eta={C0S.eta}, "
+                                   f"{C0S.steps} steps, {dt0:.1f} s"}}, dt, k, 64 * 64 * C2.nz
 
 
 def warm_start_leg(args):
@@ -328,12 +371,95 @@ def run_reference(args, world, rank):
     return 0
 
 
+def _slit(W, storage, seed, stream):
+    from paper_0712_2247_gb300 import lbif
+
+    return lbif.Slit(W.nx, W.ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, storage=storage,
+                     seed=seed, stream=stream)
+
+
+def time_steps(g, steps, stream, storage, N, peak):
+    """CUDA-event time of `steps` steps on the handle's stream, with every
+    kernel class timed by the library between its launches; per-kernel
+    milliseconds and algorithmic GB/s, the whole step's roofline fraction."""
+    import torch
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    kms, nl = g.step_profiled(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    kb = kernel_bytes(storage)
+    per_kernel = {k: {"ms": kms[k] / nl[k], "gbs_alg": kb[k] * N / (kms[k] / nl[k] * 1e-3) / 1e9}
+                  for k in kms if nl[k]}
+    mps = ms / steps
+    return {"ms_per_step": mps, "mlups": N / (mps * 1e-3) / 1e6, "kernels": per_kernel,
+            "bytes_alg_per_node": bytes_alg(storage),
+            "step_roofline_frac": bytes_alg(storage) * N / (mps * 1e-3) / 1e9 / peak}, kms, nl, ms
+
+
+def storage_f16_leg(args, stream, peak):
+    """The benchmark slit with FP16 population storage (2^8 times the
+    non-equilibrium parts): its own step time, kernels and roofline."""
+    from paper_0712_2247_gb300.inputs import c2
+
+    W = c2(args.eta, 1)
+    g = _slit(W, 1, W.seed, stream.cuda_stream)
+    g.step(args.warmup)
+    tuned = g.autotune(3)
+    g.step(1)
+    r, _, _, _ = time_steps(g, args.steps, stream, 1, W.nodes, peak)
+    r["status"] = g.status()
+    r["autotuned"] = {"ball_ctas": tuned[0], "force_group": tuned[1], "ball_staging": "tma" if tuned[2] else "loads"}
+    r["pass"] = "pull"
+    g.close()
+    dom = max(r["kernels"], key=lambda k: r["kernels"][k]["ms"])
+    r["roofline"] = {"kernel": dom, "achieved": r["kernels"][dom]["gbs_alg"], "peak": peak,
+                     "frac": r["kernels"][dom]["gbs_alg"] / peak}
+    return r
+
+
+def eta_sweep_leg(args, stream, peak):
+    """The benchmark slit's packing-fraction sweep: 0.10 timed like the
+    headline (0.25); 0.40 and 0.45 stepped from the same seeded start until
+    the device's divergence flag (non-finite or non-positive density, or a
+    coarse-grained packing fraction reaching 1) is raised, checked every 5
+    steps up to 100."""
+    from paper_0712_2247_gb300.inputs import c2
+
+    out = {}
+    W = c2(0.10, 0)
+    g = _slit(W, 0, W.seed, stream.cuda_stream)
+    g.step(args.warmup)
+    g.autotune(3)
+    g.step(1)
+    r, _, _, _ = time_steps(g, args.steps, stream, 0, W.nodes, peak)
+    r["status"] = g.status()
+    g.close()
+    out["0.10"] = r
+    for eta in (0.40, 0.45):
+        W = c2(eta, 0)
+        g = _slit(W, 0, W.seed, stream.cuda_stream)
+        flagged = None
+        for k in range(5, 101, 5):
+            g.step(5)
+            if g.status() != 0:
+                flagged = k
+                break
+        out[f"{eta:.2f}"] = {"status": g.status(), "diverged_by_step": flagged,
+                             "note": "beyond the explicit scheme's stability from a uniform start"}
+        g.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
-    import numpy as np
     import torch
 
     torch.cuda.set_device(local)
-    from paper_0712_2247_gb300 import build, lbif
+    from paper_0712_2247_gb300 import build
     from paper_0712_2247_gb300.inputs import c2
 
     build.build()
@@ -343,11 +469,9 @@ def run_ours(args, world, rank, local):
         nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
         W = W.with_(nx=nx, ny=ny, nz=nz)
     stream = torch.cuda.current_stream()
-    g = lbif.Slit(W.nx, W.ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, storage=storage,
-                  seed=W.seed + rank, stream=stream.cuda_stream)
-    if args.two_pass:
-        g.set_fused(False)
+    g = _slit(W, storage, W.seed + rank, stream.cuda_stream)
     N = W.nodes
+    peak, peak_kind = _peaks()
     # warm-up, then the launch shapes the library's autotuner picks on this
     # state (ball CTAs and staging, force tile group; results bit-identical)
     g.step(args.warmup)
@@ -356,67 +480,44 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
-        ev0.record(stream)
-        kms, nl = g.step_profiled(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+        main, kms, nl, ms = time_steps(g, args.steps, stream, storage, N, peak)
     ms = max_over_ranks(ms, world)
     ms_per_step = ms / args.steps
     mlups = world * N / (ms_per_step * 1e-3) / 1e6
     status = g.status()
 
     # dominant kernel roofline, live CUDA-event timing of each launch class
-    peak, peak_kind = _peaks()
     dom = max(kms, key=lambda k: kms[k])
     launches = sum(nl.values())
-    fused = g.fused
-    kb = kernel_bytes(storage, fused)
-    tkey = dom + ("_fused" if dom == "collide_stream" and fused else "")
+    kb = kernel_bytes(storage)
     dom_bytes = kb[dom] * N
     dom_ms = kms[dom] / max(nl[dom], 1)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     step_gbs = bytes_alg(storage) * N / (ms_per_step * 1e-3) / 1e9
-    per_kernel = {k: {"ms": kms[k] / nl[k], "gbs_alg": kb[k] * N / (kms[k] / nl[k] * 1e-3) / 1e9}
-                  for k in kms if nl[k]}
+    tb = TRAFFIC_B_PER_NODE.get(storage, {}).get(dom)
 
-    # end to end through the C ABI: per iteration the density field comes from
-    # pinned host memory (copied on a second stream into one of two device
-    # buffers while the previous iteration's steps run), lbif_set_fields
-    # starts the state from it, S steps run, and the FP64 profiles are read
+    # end to end through the C ABI's host-pointer path: per iteration the
+    # density field goes from pinned host memory through lbif_set_fields
+    # (on_device = 0: the library copies it in on the handle's stream and
+    # starts the state from it), S steps run, and the FP64 profiles are read
     # back to the host (which synchronises every iteration)
     S = 10
     rho_h = torch.empty(W.nz * W.ny * W.nx, dtype=torch.float32, pin_memory=True)
     rho_h.fill_(float(g.n0))
-    rho_d = [torch.empty(W.nz, W.ny, W.nx, dtype=torch.float32, device="cuda") for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    copied = [torch.cuda.Event() for _ in range(2)]
-
-    def upload(k):
-        with torch.cuda.stream(copy_stream):
-            rho_d[k % 2].view(-1).copy_(rho_h, non_blocking=True)
-            copied[k % 2].record(copy_stream)
-
+    rho_np = rho_h.numpy().reshape(W.nz, W.ny, W.nx)
     iters = max(1, args.steps // S)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    upload(0)
     for it in range(iters):
-        stream.wait_event(copied[it % 2])
-        g.set_fields(rho_d[it % 2])
-        if it + 1 < iters:
-            upload(it + 1)  # into the buffer set_fields read two iterations ago
+        g.set_fields(rho_np)
         g.step(S)
         g.profiles(allow_diverged=True)
     e2e_s = max_over_ranks(time.perf_counter() - t0, world)  # the slowest replica
     e2e = {"value": world * N * S * iters / e2e_s / 1e6, "unit": "MLUPS",
            "h2d_bytes_per_step": 4 * N / S, "d2h_bytes_per_step": 5 * 8 * W.nz / S,
-           "note": f"per iteration: {4 * N} B density upload from pinned memory (overlapped with the "
-                   f"previous iteration's steps), {S} steps, FP64 profile readback"}
+           "note": f"per iteration: lbif_set_fields from {4 * N} B of pinned host memory (copied in "
+                   f"on the handle's stream), {S} steps, FP64 profile readback"}
     g.close()
 
     if rank != 0:
@@ -424,30 +525,21 @@ def run_ours(args, world, rank, local):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu, _, _, _ = cpu_sample(args.cpu_seconds)
-    tail = None
-    if not args.no_tail and world == 1:
+
+    def leg(enabled, fn, *a):
+        if not enabled or world != 1:
+            return None
         try:
-            tail = tail_leg(args)
-        except Exception as e:
-            tail = {"error": f"{type(e).__name__}: {e}"}
-    mlp = None
-    if not args.no_mlp and world == 1:
-        try:
-            mlp = mlp_leg(args)
-        except Exception as e:
-            mlp = {"error": f"{type(e).__name__}: {e}"}
-    ens = None
-    if not args.no_ensemble and world == 1:
-        try:
-            ens = ensemble_leg(args)
-        except Exception as e:
-            ens = {"error": f"{type(e).__name__}: {e}"}
-    warm = None
-    if not args.no_warm_start and world == 1:
-        try:
-            warm = warm_start_leg(args)
+            return fn(*a)
         except Exception as e:  # reported, never hides the throughput line
-            warm = {"error": f"{type(e).__name__}: {e}"}
+            return {"error": f"{type(e).__name__}: {e}"}
+
+    f16 = leg(not args.no_sweep and storage == 0, storage_f16_leg, args, stream, peak)
+    sweep = leg(not args.no_sweep and storage == 0 and args.eta == 0.25, eta_sweep_leg, args, stream, peak)
+    tail = leg(not args.no_tail, tail_leg, args)
+    mlp = leg(not args.no_mlp, mlp_leg, args)
+    ens = leg(not args.no_ensemble, ensemble_leg, args)
+    warm = leg(not args.no_warm_start, warm_start_leg, args)
     line = {
         "metric": METRIC, "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -455,22 +547,22 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": f"slit {W.nx}x{W.ny}x{W.nz} sigma={W.sigma} eta={W.eta} tau={W.tau} "
                                f"F_e={W.body[0]} bounce-back z, periodic x,y, seeded 1e-3 noise",
-                   "storage": args.storage, "nodes": N,
-                   "pass": "fused" if fused else "two-pass",
+                   "storage": args.storage, "nodes": N, "pass": "pull",
                    "autotuned": {"ball_ctas": tuned[0], "force_group": tuned[1],
                                  "ball_staging": "tma" if tuned[2] else "loads"}, "parallelism": f"replicas x{world}",
                    "l2": "populations (>= 1.9 GB) exceed L2; no flush",
                    "bytes_alg_per_node": bytes_alg(storage),
                    "step_gbs_alg": step_gbs, "step_roofline_frac": step_gbs / peak,
-                   "kernels": per_kernel,
+                   "kernels": main["kernels"],
                    "status": status},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind + " hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": (TRAFFIC_B_PER_NODE_F32[tkey] * N
-                                 if storage == 0 and TRAFFIC_B_PER_NODE_F32.get(tkey) else None),
+                     "traffic": tb * N if tb else None,
                      "traffic_unit": "bytes per launch (ncu capture, scaled by nodes)",
                      "bytes_alg_per_launch": dom_bytes},
         "cpu_baseline": cpu,
+        "storage_f16": f16,
+        "eta_sweep": sweep,
         "ensemble": ens,
         "tail_workload": tail,
         "mlp_forward": mlp,
@@ -502,8 +594,8 @@ def main():
     ap.add_argument("--ws-train", type=int, default=8192, help="training slits of the warm-start leg")
     ap.add_argument("--ws-adam", type=int, default=8000, help="Adam steps of the warm-start leg")
     ap.add_argument("--ws-heldout", type=int, default=128, help="held-out slits of the warm-start leg")
-    ap.add_argument("--two-pass", action="store_true",
-                    help="push collide-stream + moments pass instead of the fused pass")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the FP16-storage record and the packing-fraction sweep")
     ap.add_argument("--grid", default=None,
                     help="override the slit extents NXxNYxNZ (profiling captures on a smaller case)")
     args = ap.parse_args()

@@ -69,8 +69,14 @@ typedef struct {
                           interpolants as the force, not regularised)       */
 } lbif_force;
 
-#define LBIF_STORE_F32 0 /* populations stored as FP32 h_i = f_i/(w_i n0) - 1 */
-#define LBIF_STORE_F16 1 /* same deviations stored as FP16 (round to nearest)  */
+/* Population storage. Each population is stored as its non-equilibrium part
+ * relative to the equilibrium of its own node, h_i = (f_i - f_i^eq(n, u)) /
+ * (w_i n), at the moments n, u of the step it belongs to, which the handle
+ * keeps in FP32; the equilibrium part, which carries the flow, is never
+ * rounded to the storage type. */
+#define LBIF_STORE_F32 0 /* h_i in FP32                                         */
+#define LBIF_STORE_F16 1 /* 2^8 h_i in FP16 (round to nearest; the factor keeps
+                            small parts clear of the FP16 subnormal range)     */
 
 typedef struct {
     int32_t  storage;  /* LBIF_STORE_F32 or LBIF_STORE_F16                     */
@@ -99,9 +105,10 @@ int lbif_step(lbif_handle h, int64_t nsteps);
  * the total milliseconds of class k over the nsteps (k = 0 moments, 1 ball +
  * g2, 2 tail, 3 force, 4 collide + stream; classes not launched get 0) and
  * launches[k] the number of launches. nk = length of both arrays (>= 5).
- * With the fused pass (lbif_set_fused) class 4 includes the moments of the
- * next step and class 0 is launched only when the populations were set from
- * outside. Synchronises at the end. Diagnostics for the benchmark. */
+ * Class 4 includes the moments of the next step (the pull pass, see
+ * lbif_set_fused); class 0 is no longer launched (every state set from
+ * outside is an equilibrium whose moments are the given fields). Synchronises
+ * at the end. Diagnostics for the benchmark. */
 int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_ms, int64_t* launches,
                        int32_t nk);
 
@@ -117,10 +124,12 @@ int lbif_moments(lbif_handle h, float* rho, float* u, float* pressure, int32_t o
 int lbif_forces(lbif_handle h, float* F, int32_t on_device);
 
 /* Re-initialise the populations to f_eq(n, u) of given fields (same layout
- * as lbif_moments; u may be NULL = 0) and reset the step counter. With u NULL
- * the stored populations are exactly 0 (relative to n itself), so the fields
- * of step 0 are n and u = 0 without a moments pass; the state is the same,
- * bit for bit, as with an explicit u = 0. */
+ * as lbif_moments; u may be NULL = 0) and reset the step counter. The stored
+ * non-equilibrium parts become 0 and the given fields are the moments of
+ * step 0 (no moments pass); u NULL and an explicit u = 0 give the same state,
+ * bit for bit. on_device = 0: host pointers, copied in on the handle's
+ * stream through the handle's second population buffer (rho) and its
+ * scratch (u). Synchronises. */
 int lbif_set_fields(lbif_handle h, const float* rho, const float* u, int32_t on_device);
 
 /* FP64 x,y-averaged profiles n(z), u_x(z) (nz doubles each; either may be
@@ -140,9 +149,10 @@ int lbif_time(lbif_handle h, int64_t* t);
 /* Device status word (0 = healthy; bit 0 divergence). Synchronises. */
 int lbif_status(lbif_handle h, int32_t* status);
 
-/* Checkpoint: write / read the populations (storage tag, grid, step count)
- * to / from a host file. lbif_load requires a handle of the same grid,
- * sigma and storage. */
+/* Checkpoint: write / read the stored populations and the moment fields
+ * they refer to (dn = n/n0 - 1, u; storage tag, grid, step count) to / from a
+ * host file; a resumed run continues bit for bit. lbif_load requires a handle
+ * of the same grid, sigma and storage. */
 int lbif_save(lbif_handle h, const char* path);
 int lbif_load(lbif_handle h, const char* path);
 
@@ -188,20 +198,21 @@ int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int32_t check_e
 int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int32_t hmax);
 
 /* How a step applies collision and streaming (Sec. Methods: BGK collision
- * with the first-order source, streaming, half-way bounce-back).
- * fused = 1: one pass per step; each node gathers the populations streaming
- *   into it (pull form), applies the collision of their source node, and
- *   forms the moments n, u of the next step from the values it holds. The
- *   populations are read and written once per step. Needs nx >= 32 and
- *   ny >= 4; the default with FP32 storage and nx ny nz >= 2^23 nodes, where
- *   it is the faster of the two.
- * fused = 0: a push collide-stream pass, then a moments pass at the start of
- *   the next step (any grid).
- * Both compute the same update; results agree to FP32 rounding, not bit for
- * bit. May be changed between steps. Errors: LBIF_ERR_ARG for a NULL handle,
- * fused not 0 or 1, or fused = 1 with nx < 32 or ny < 4. */
+ * with the first-order source, streaming, half-way bounce-back). Every step
+ * runs one pass: each node gathers the populations streaming into it (pull
+ * form), applies the collision of their source node, and forms the moments
+ * n, u of the next step from the values it holds, so the populations are
+ * read and written once per step (32 x 4 node tiles marching in z; grids
+ * with nx < 32 or ny < 4 run the same arithmetic one node per thread, with
+ * identical results). Populations are stored as their non-equilibrium parts
+ * relative to the equilibrium of their own node, which this pull form
+ * decodes from the staged moments of the source node; the earlier two-pass
+ * step (push streaming, then a moments pass) could not, and is retired.
+ * lbif_set_fused(h, 1) is accepted and changes nothing; lbif_set_fused(h, 0)
+ * returns LBIF_ERR_UNSUPPORTED. LBIF_ERR_ARG for a NULL handle or fused not
+ * 0 or 1. */
 int lbif_set_fused(lbif_handle h, int32_t fused);
-/* The pass in use: *fused = 1 fused, 0 two passes. */
+/* The pass in use: always *fused = 1. */
 int lbif_get_fused(lbif_handle h, int32_t* fused);
 
 /* Self-test of the failure path of the bounded device waits (the paper has no
@@ -266,15 +277,18 @@ const char* lbif_mlp_last_error(lbif_mlp m);
  * u (3 SoA planes), device pointers, layout as lbif_moments - and it
  * allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
  * It is meant for callers that cannot allocate device memory when they need
- * the profiles (code running during stream capture, services whose device
- * memory is reserved up front by their own allocator, fixed-footprint loops).
+ * the profiles: services whose device memory is reserved up front by their
+ * own allocator (a further cudaMalloc would fail or fragment it), and loops
+ * that must keep a fixed memory footprint.
  * Its scratch is a fixed 320 KB array in the library's device image, which
  * every GPU that loads the library keeps until the process exits; nz above
  * 8192 is rejected with LBIF_ERR_UNSUPPORTED. All calls share that array:
  * calls that overlap on the GPU (other streams, other threads) race on it.
  * Every call overwrites what it uses, nothing needs clearing. The first call
  * on a device looks the array's device address up (cudaGetSymbolAddress, with
- * that device current); make that first call before any stream capture.
+ * that device current), and so does the first call after the device's context
+ * changed (a reset reloads the image elsewhere); make that first call before
+ * any stream capture.
  * n_z, ux_z (nz doubles) and out4 are host pointers (any may be NULL); work is
  * enqueued on `stream` (cudaStream_t, NULL = default) and synchronised. On
  * error, lbif_noalloc_last_error() gives a message. */

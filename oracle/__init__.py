@@ -58,6 +58,7 @@ def _load():
             "or_g2": (f64, [f64, i32]),
             "or_ball_count": (i32, [i32]),
             "or_threads": (i32, []),
+            "or_set_threads": (None, [i32]),
             "or_coarse_density": (None, [i32, i32, i32, i32, i32, _D, _D]),
             "or_equilibrium": (None, [f64, _D, _D]),
             "or_collide_node": (None, [_D, _D, f64, _D]),
@@ -80,6 +81,8 @@ def _load():
                                           _D, _D, _D, _D, _D, _D]),
             "or_tail_force_field": (None, [i32, i32, i32, i32, i32, f64, f64, _D, _D, _D, _D]),
             "or_step_shifted": (i32, [vp, ctypes.c_long]),
+            "or_get_pops": (None, [vp, _D]),
+            "or_set_pops": (None, [vp, _D]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(lib, name)
@@ -135,6 +138,11 @@ def ball_count(sigma: int) -> int:
 def threads() -> int:
     """Threads the oracle's parallel loops run on."""
     return _load().or_threads()
+
+
+def set_threads(n: int) -> None:
+    """Run the oracle's parallel loops on n threads from now on."""
+    _load().or_set_threads(int(n))
 
 
 def equilibrium(n: float, u) -> np.ndarray:
@@ -283,3 +291,13 @@ class Oracle:
         out = np.zeros(4)
         self._lib.or_totals(self._h, _p(out))
         return out
+
+    def populations(self) -> np.ndarray:
+        """Copy of the populations, shape (19, nz, ny, nx)."""
+        f = np.zeros((NV,) + self.shape)
+        self._lib.or_get_pops(self._h, _p(f))
+        return f
+
+    def set_populations(self, f):
+        """Replace the populations (shape (19, nz, ny, nx)); the step count is kept."""
+        self._lib.or_set_pops(self._h, _p(_f64(f, NV * self.N)))

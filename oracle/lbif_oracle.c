@@ -181,6 +181,16 @@ int or_threads(void)
 #endif
 }
 
+/* threads of the parallel loops from now on (n >= 1) */
+void or_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 double or_g2(double eta, int form)
 {
     double d = (1.0 - eta) * (1.0 - eta) * (1.0 - eta);
@@ -288,13 +298,30 @@ static void hs_force(const geom* g, int sigma, double kT, int coupling, int regu
 }
 
 /* Mean-field attractive tail: F(r) = n(r) sum_d n(r+d) phi'(|d|) d/|d| over
- * sigma <= |d| <= rcut sigma, phi(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6].  */
+ * sigma <= |d| <= rcut sigma, phi(r) = 4 eps [(sigma/r)^12 - (sigma/r)^6].
+ * phi'(|d|) and |d| depend on the displacement only: they are evaluated once
+ * per displacement (same formula), and every node sums over the
+ * displacements in the same order as a per-node evaluation would.          */
 static void tail_force(const geom* g, int sigma, double eps, double rcut, const double* n,
                        double* Fx, double* Fy, double* Fz)
 {
     const double s = (double)sigma, rmax = rcut * s;
     const int R = (int)ceil(rmax);
     const double s6 = pow(s, 6.0), s12 = s6 * s6;
+    const int W = 2 * R + 1;
+    double* dphi_t = (double*)malloc(sizeof(double) * (size_t)W * W * W);
+    double* r_t = (double*)malloc(sizeof(double) * (size_t)W * W * W);
+    for (int dz = -R; dz <= R; ++dz)
+        for (int dy = -R; dy <= R; ++dy)
+            for (int dx = -R; dx <= R; ++dx) {
+                long k = ((long)(dz + R) * W + (dy + R)) * W + (dx + R);
+                double r2 = (double)(dx * dx + dy * dy + dz * dz);
+                double r = sqrt(r2);
+                r_t[k] = r;
+                dphi_t[k] = (r2 < s * s || r2 > rmax * rmax)
+                                ? 0.0
+                                : 4.0 * eps * (-12.0 * s12 / pow(r, 13.0) + 6.0 * s6 / pow(r, 7.0));
+            }
     long N = (long)g->nx * g->ny * g->nz;
 #pragma omp parallel for schedule(static)
     for (long id = 0; id < N; ++id) {
@@ -307,8 +334,9 @@ static void tail_force(const geom* g, int sigma, double eps, double rcut, const 
                     if (r2 < s * s || r2 > rmax * rmax) continue;
                     double nd = field_at(g, n, x + dx, y + dy, z + dz);
                     if (nd == 0.0) continue;
-                    double r = sqrt(r2);
-                    double dphi = 4.0 * eps * (-12.0 * s12 / pow(r, 13.0) + 6.0 * s6 / pow(r, 7.0));
+                    long k = ((long)(dz + R) * W + (dy + R)) * W + (dx + R);
+                    double r = r_t[k];
+                    double dphi = dphi_t[k];
                     fx += nd * dphi * dx / r;
                     fy += nd * dphi * dy / r;
                     fz += nd * dphi * dz / r;
@@ -317,6 +345,8 @@ static void tail_force(const geom* g, int sigma, double eps, double rcut, const 
         Fy[id] += n[id] * fy;
         Fz[id] += n[id] * fz;
     }
+    free(dphi_t);
+    free(r_t);
 }
 
 /* second-order (low-Mach) local equilibrium, Sec. Methods */
@@ -685,6 +715,21 @@ void or_totals(void* h, double* out4)
             out4[0] += fi;
             out4[1] += cv[i][0] * fi; out4[2] += cv[i][1] * fi; out4[3] += cv[i][2] * fi;
         }
+}
+
+/* copy of the populations f[i][id] (NV x N, the layout of the state) */
+void or_get_pops(void* h, double* out)
+{
+    or_state* s = (or_state*)h;
+    memcpy(out, s->f, sizeof(double) * (size_t)NV * s->N);
+}
+
+/* replace the populations (same layout); the step counter is kept */
+void or_set_pops(void* h, const double* in)
+{
+    or_state* s = (or_state*)h;
+    memcpy(s->f, in, sizeof(double) * (size_t)NV * s->N);
+    s->lag_ok = 0;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -30,13 +30,10 @@ struct lbif_ctx {
     bool own_stream = false;
     void* pop[2] = {nullptr, nullptr};
     int cur = 0;                      // populations of the current step
-    float* dn[3] = {nullptr, nullptr, nullptr};
-    int dref = 0;                     // dn[dref] = reference R of pop[cur]
-    int dfld = 1;                     // dn[dfld] = dn of step t (when fields_t == t)
+    float* dn[2] = {nullptr, nullptr};
     float* u[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    int ucur = 0;                     // u[ucur] = velocity of step t
-    bool fused = false;               // one pass: collision, pull streaming, moments
-    int csm_lz = 0;                   // z planes per CTA of that pass (0 = default)
+    int fcur = 0;                     // dn[fcur], u[fcur]: the moments of step t (pop[cur] refers to them)
+    int csm_lz = 0;                   // z planes per CTA of the pull pass (0 = default)
     float* dG = nullptr;
     float4* Ft = nullptr;
     float4* F = nullptr;              // F / n0 per node (force kernel -> collision kernel)
@@ -57,14 +54,14 @@ struct lbif_ctx {
     std::vector<int> done;
     bool batch = false;
     int ball_want = 0, force_group = 0;  // launch shapes (0 = defaults; set by the autotuner)
-    CUtensorMap ball_map[3];             // tensor maps of dn[0..2] for the ball kernel's tiles
+    CUtensorMap ball_map[2];             // tensor maps of dn[0..1] for the ball kernel's tiles
     bool ball_map_ok = false;
     bool ball_tma = true;                // stage the ball tiles with the maps (autotuner's choice)
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
     int graph_state = -1;             // buffer indices the graph was captured from
     int64_t t = 0;
-    int64_t fields_t = -1, G_t = -1, tail_t = -1;  // step the cached fields belong to
+    int64_t G_t = -1, tail_t = -1;    // step the cached g2 field / tail force belong to
     std::vector<double> last_n, last_ux;
     int64_t last_t = -1;
     int sticky = 0;
@@ -175,7 +172,7 @@ static void free_ctx(lbif_ctx* h)
                     h->prof_d, h->scratch, h->d_sl, h->d_zslit, h->d_done};
     for (void* b : bufs)
         if (b) cudaFree(b);
-    float* pads[] = {h->dn[0], h->dn[1], h->dn[2], h->u[0][0], h->u[0][1], h->u[0][2],
+    float* pads[] = {h->dn[0], h->dn[1], h->u[0][0], h->u[0][1], h->u[0][2],
                      h->u[1][0], h->u[1][1], h->u[1][2], h->dG};
     for (float* q : pads) padded_free(q);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
@@ -185,15 +182,24 @@ static void free_ctx(lbif_ctx* h)
 static Fields fields_of(const lbif_ctx* h)
 {
     Fields f;
-    f.dn = h->dn[h->dfld];
-    f.ux = h->u[h->ucur][0];
-    f.uy = h->u[h->ucur][1];
-    f.uz = h->u[h->ucur][2];
+    f.dn = h->dn[h->fcur];
+    f.ux = h->u[h->fcur][0];
+    f.uy = h->u[h->fcur][1];
+    f.uz = h->u[h->fcur][2];
     f.dG = h->dG;
     return f;
 }
 
-static void invalidate(lbif_ctx* h) { h->fields_t = h->G_t = h->tail_t = -1; }
+// the padded fields dn, ux, uy, uz of buffer set k
+static void field_set(lbif_ctx* h, int k, float* out[4])
+{
+    out[0] = h->dn[k];
+    out[1] = h->u[k][0];
+    out[2] = h->u[k][1];
+    out[3] = h->u[k][2];
+}
+
+static void invalidate(lbif_ctx* h) { h->G_t = h->tail_t = -1; }
 
 // --------------------------------------------------------------------------
 // tables
@@ -417,7 +423,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     }
 #undef ALLOC
     {
-        float** pads[] = {&h->dn[0], &h->dn[1], &h->dn[2], &h->u[0][0], &h->u[0][1], &h->u[0][2],
+        float** pads[] = {&h->dn[0], &h->dn[1], &h->u[0][0], &h->u[0][1], &h->u[0][2],
                           &h->u[1][0], &h->u[1][1], &h->u[1][2], &h->dG};
         for (float** q : pads) {
             const cudaError_t e = padded_alloc((size_t)g.P, q);
@@ -427,9 +433,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
             }
         }
         h->ball_map_ok = make_ball_map(g, P.sigma, h->dn[0], &h->ball_map[0]) &&
-                         make_ball_map(g, P.sigma, h->dn[1], &h->ball_map[1]) &&
-                         make_ball_map(g, P.sigma, h->dn[2], &h->ball_map[2]);
-        h->fused = csm_default(g, P.storage);
+                         make_ball_map(g, P.sigma, h->dn[1], &h->ball_map[1]);
     }
     P.sl = h->d_sl;
     P.zslit = h->d_zslit;
@@ -452,12 +456,12 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     CKC(cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
     CKC(cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
     {
-        float* pads[] = {h->dn[0], h->dn[1], h->dn[2], h->u[0][0], h->u[0][1], h->u[0][2],
+        float* pads[] = {h->dn[0], h->dn[1], h->u[0][0], h->u[0][1], h->u[0][2],
                          h->u[1][0], h->u[1][1], h->u[1][2], h->dG};
-        const float outside[] = {-1.f, -1.f, -1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float outside[] = {-1.f, -1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         for (float* q : pads)
             CKC(cudaMemsetAsync(q - PAD_SLACK, 0, sizeof(float) * ((size_t)g.P + 2 * PAD_SLACK), h->stream));
-        CKC(launch_fill_outside(P, pads, outside, 10, h->stream));
+        CKC(launch_fill_outside(P, pads, outside, 9, h->stream));
         if (batch) {
             // gap planes between stacked slits hold the outside values too
             for (int z = 0; z < g.nz; ++z) {
@@ -583,71 +587,37 @@ extern "C" const char* lbif_last_error(lbif_handle h)
 // --------------------------------------------------------------------------
 // stepping
 // --------------------------------------------------------------------------
-// the lowest dn buffer that is neither a nor b
-static int other_dn(int a, int b)
-{
-    for (int i = 0; i < 3; ++i)
-        if (i != a && i != b) return i;
-    return 0;
-}
-
-// moments pass: dn(t) of pop[cur] (reference dn[dref]) into another buffer
-static int run_moments(lbif_ctx* h, int skip_done)
-{
-    const int f = other_dn(h->dref, h->dref);
-    float* const* u = h->u[h->ucur];
-    CK(h, launch_moments(h->P, h->pop[h->cur], h->dn[h->dref], h->dn[f], u[0], u[1], u[2], h->status_d,
-                         skip_done, h->stream));
-    h->dfld = f;
-    return LBIF_OK;
-}
-
-// Moments (and, when asked, the g2 field and the tail force) of the current
-// populations; cached per step so that output calls between steps do not
-// redo them. The fused pass leaves the moments of the step it produced, so
-// a moments pass runs only after the populations were set from outside.
+// The g2 field and the tail force of the current moments, cached per step so
+// that output calls between steps do not redo them. The moments themselves
+// are always current: the pull pass writes those of the step it produces,
+// and every state set from outside is an equilibrium whose moments are the
+// given fields.
 static int refresh_fields(lbif_ctx* h, bool want_G, int skip_done)
 {
     const Params& P = h->P;
-    if (h->fields_t != h->t) {
-        int rc = run_moments(h, skip_done);
-        if (rc) return rc;
-        h->fields_t = skip_done ? -1 : h->t;
-    }
-    float* dnew = h->dn[h->dfld];
+    float* dnow = h->dn[h->fcur];
     if (want_G && h->G_t != h->t) {
-        CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, skip_done, h->stream, ball_map(h, h->dfld)));
+        CK(h, launch_ball(P, dnow, h->dG, h->status_d, h->ball_want, skip_done, h->stream, ball_map(h, h->fcur)));
         h->G_t = skip_done ? -1 : h->t;
     }
     if (P.tail && h->tail_t != h->t) {
-        CK(h, run_tail(h, dnew));
+        CK(h, run_tail(h, dnow));
         h->tail_t = skip_done ? -1 : h->t;
     }
     return LBIF_OK;
 }
 
-// collision and streaming of step t -> t + 1 (force F of step t computed)
+// collision, streaming and the new moments of step t -> t + 1 (force F of
+// step t computed)
 static int collide_stream(lbif_ctx* h)
 {
     const Params& P = h->P;
-    if (h->fused) {
-        // pops relative to dn(t + 1), which is also the next step's dn
-        const int n = other_dn(h->dref, h->dfld);
-        float* const* u = h->u[h->ucur];
-        float* const* w = h->u[h->ucur ^ 1];
-        CsmIO io{h->dn[h->dref], h->dn[h->dfld], u[0], u[1], u[2], h->dn[n], w[0], w[1], w[2]};
-        CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->stream));
-        h->cur ^= 1;
-        h->dref = h->dfld = n;
-        h->ucur ^= 1;
-        h->t += 1;
-        h->fields_t = h->t;
-        return LBIF_OK;
-    }
-    // pops relative to dn(t), the fields the collision used
-    CK(h, launch_cs(P, h->pop[h->cur], h->pop[h->cur ^ 1], fields_of(h), h->F, h->stream));
+    float* const* u = h->u[h->fcur];
+    float* const* w = h->u[h->fcur ^ 1];
+    CsmIO io{h->dn[h->fcur], u[0], u[1], u[2], h->dn[h->fcur ^ 1], w[0], w[1], w[2]};
+    CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->stream));
     h->cur ^= 1;
-    h->dref = h->dfld;
+    h->fcur ^= 1;
     h->t += 1;
     return LBIF_OK;
 }
@@ -688,25 +658,18 @@ extern "C" int lbif_step_profiled(lbif_handle h, int64_t nsteps, double* kernel_
         kernel_ms[k] = 0.0;
         launches[k] = 0;
     }
-    int per = 3 + (P.hs ? 1 : 0) + (P.tail ? 1 : 0);
+    int per = 2 + (P.hs ? 1 : 0) + (P.tail ? 1 : 0);
     std::vector<cudaEvent_t> ev((size_t)nsteps * per + 1);
     std::vector<int> cls((size_t)nsteps * per);
     for (auto& e : ev) CK(h, cudaEventCreate(&e));
     size_t j = 0;
     CK(h, cudaEventRecord(ev[0], h->stream));
     for (int64_t s = 0; s < nsteps; ++s) {
-        // the same launches as one_step, each timed (the fused pass leaves
-        // the next step's moments: no moments pass after the first step)
-        if (h->fields_t != h->t) {
-            int rc = run_moments(h, 1);
-            if (rc) return rc;
-            cls[j] = 0;
-            CK(h, cudaEventRecord(ev[++j], h->stream));
-        }
-        float* dnew = h->dn[h->dfld];
+        // the same launches as one_step, each timed
+        float* dnew = h->dn[h->fcur];
         const Fields f = fields_of(h);
         if (P.hs) {
-            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, 1, h->stream, ball_map(h, h->dfld)));
+            CK(h, launch_ball(P, dnew, h->dG, h->status_d, h->ball_want, 1, h->stream, ball_map(h, h->fcur)));
             cls[j] = 1;
             CK(h, cudaEventRecord(ev[++j], h->stream));
         }
@@ -836,22 +799,13 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
             du = h->scratch;
         }
     }
-    CK(h, launch_init_fields(P, h->pop[h->cur], h->dn[h->dref], drho, du, h->stream));
-    if (!u) {
-        // At rest the equilibrium populations, stored relative to dn itself,
-        // are all exactly 0, so their moments are dn (already in dn[dref],
-        // with its images) and u = 0, bit for bit: no moments pass.
-        float* const* uf = h->u[h->ucur];
-        for (int k = 0; k < 3; ++k)
-            CK(h, cudaMemsetAsync(uf[k] - PAD_SLACK, 0, sizeof(float) * ((size_t)P.g.P + 2 * PAD_SLACK),
-                                  h->stream));
-    }
+    // the equilibrium of the given fields: stored non-equilibrium parts 0,
+    // the fields themselves are its moments (no moments pass)
+    float* f[4];
+    field_set(h, h->fcur, f);
+    CK(h, launch_init_fields(P, h->pop[h->cur], f, drho, du, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     reset_time(h);
-    if (!u) {
-        h->dfld = h->dref;
-        h->fields_t = h->t;
-    }
     return LBIF_OK;
 }
 
@@ -998,11 +952,13 @@ extern "C" int lbif_batch_seed(lbif_handle h, const float* n_z, const float* ux_
         }
         d = tmp;
     }
+    float* fs[4];
+    field_set(h, h->fcur, fs);
     cudaError_t e = cudaMemcpyAsync(d, n_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess && ux_z)
         e = cudaMemcpyAsync(d + cnt, ux_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = launch_init_profiles(h->P, h->pop[h->cur], h->dn[h->dref], d, ux_z ? d + cnt : nullptr, hmax,
+        e = launch_init_profiles(h->P, h->pop[h->cur], fs, d, ux_z ? d + cnt : nullptr, hmax,
                                  h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (tmp) cudaFree(tmp);
@@ -1032,21 +988,16 @@ extern "C" int lbif_batch_profiles(lbif_handle h, double* n_z, double* ux_z, int
     return check_status(h);
 }
 
-// Host-side buffer indices a captured graph depends on. They repeat with
-// period 2 in steady stepping; the unfused step recomputes the fields from
-// dn[dref] in every step, so dfld matters only to the fused one.
-static int buffer_state(const lbif_ctx* h)
-{
-    return h->cur | h->dref << 1 | h->ucur << 3 | (h->fused ? 16 | h->dfld << 5 : 0);
-}
+// Host-side buffer indices a captured graph depends on; they repeat with
+// period 2 in steady stepping.
+static int buffer_state(const lbif_ctx* h) { return h->cur | h->fcur << 1; }
 
 // capture `steps` (even) steps of the active slits into a CUDA graph; the
-// graph replays from the buffer state it was captured in (and, fused, from
-// current fields), so it is rebuilt when that does not hold
+// graph replays from the buffer state it was captured in, so it is rebuilt
+// when that does not hold
 static int build_graph(lbif_ctx* h, int steps)
 {
-    const bool fresh = !h->fused || h->fields_t == h->t;
-    if (h->graph && h->graph_steps == steps && h->graph_state == buffer_state(h) && fresh) return LBIF_OK;
+    if (h->graph && h->graph_steps == steps && h->graph_state == buffer_state(h)) return LBIF_OK;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;
@@ -1058,12 +1009,11 @@ static int build_graph(lbif_ctx* h, int steps)
     CK(h, cudaStreamSynchronize(h->stream));
     cudaGraph_t g = nullptr;
     const int state = buffer_state(h);
-    const int64_t t0 = h->t, ft0 = h->fields_t;
+    const int64_t t0 = h->t;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     for (int k = 0; k < steps && rc == LBIF_OK; ++k) rc = one_step(h);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->t = t0;  // the capture only recorded the launches
-    h->fields_t = ft0;
     h->G_t = h->tail_t = -1;
     if (rc == LBIF_OK && buffer_state(h) != state)
         rc = fail(h, LBIF_ERR_CUDA, "graph capture: buffer indices do not repeat over the captured steps");
@@ -1090,12 +1040,7 @@ static int run_graph(lbif_ctx* h, int steps)
     if (rc) return rc;
     CK(h, cudaGraphLaunch(h->graph, h->stream));
     h->t += steps;
-    if (h->fused) {
-        h->fields_t = h->t;  // the last fused pass left the fields of step t
-        h->G_t = h->tail_t = -1;
-    } else {
-        invalidate(h);
-    }
+    invalidate(h);
     return LBIF_OK;
 }
 
@@ -1175,17 +1120,10 @@ extern "C" int lbif_batch_run(lbif_handle h, double tol, int64_t max_steps, int3
 extern "C" int lbif_set_fused(lbif_handle h, int32_t fused)
 {
     if (!h || (fused != 0 && fused != 1)) return fail(h, LBIF_ERR_ARG, "lbif_set_fused: bad arguments");
-    if (fused && !csm_ok(h->P.g))
-        return fail(h, LBIF_ERR_ARG, "lbif_set_fused: the fused pass needs nx >= 32 and ny >= 4");
-    if (h->fused != (fused != 0)) {
-        // the unfused step reads dn(t) of the fused one as its reference;
-        // the fused step reads both buffers the unfused one leaves
-        h->fused = fused != 0;
-        if (h->graph) {
-            cudaGraphExecDestroy(h->graph);
-            h->graph = nullptr;
-        }
-    }
+    if (!fused)
+        return fail(h, LBIF_ERR_UNSUPPORTED,
+                    "lbif_set_fused: the two-pass step is retired; populations are stored relative to the "
+                    "equilibrium of their own node, which only the pull pass decodes");
     return LBIF_OK;
 }
 
@@ -1211,7 +1149,7 @@ extern "C" int lbif_selftest_wait(int64_t polls, int32_t* timed_out)
 extern "C" int lbif_get_fused(lbif_handle h, int32_t* fused)
 {
     if (!h || !fused) return fail(h, LBIF_ERR_ARG, "lbif_get_fused: bad arguments");
-    *fused = h->fused ? 1 : 0;
+    *fused = 1;
     return LBIF_OK;
 }
 
@@ -1234,13 +1172,13 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
     float best = 1e30f;
     int best_ball = 0, best_group = 0;
     bool best_tma = h->ball_map_ok;
-    float* dnew = h->dn[h->dfld];
+    float* dnew = h->dn[h->fcur];
     // the ball kernel writes dG only; the force kernel writes F only: both
     // are pure functions of the current fields, so trials change no state.
     // Ball candidates: CTA target x plane staging (tensor-memory-accelerator
     // copies when the handle has tensor maps, plain loads).
     for (int staging = h->ball_map_ok ? 1 : 0; staging >= 0; --staging) {
-        const CUtensorMap* tm = staging ? &h->ball_map[h->dfld] : nullptr;
+        const CUtensorMap* tm = staging ? &h->ball_map[h->fcur] : nullptr;
         for (int b : balls) {
             float tot = 0.f;
             for (int k = 0; k < trials + 1; ++k) {
@@ -1292,7 +1230,9 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
 }
 
 // --------------------------------------------------------------------------
-// checkpoint: populations and their reference density field
+// checkpoint: the stored populations and the moment fields they refer to
+// (dn, ux, uy, uz); the second population buffer, unused between steps,
+// carries the fields between host and device
 // --------------------------------------------------------------------------
 struct CkptHeader {
     char magic[8];
@@ -1300,29 +1240,32 @@ struct CkptHeader {
     int64_t t;
 };
 
+static const char kCkptMagic[9] = "LBIFCKP3";
+
 extern "C" int lbif_save(lbif_handle h, const char* path)
 {
     if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_save: bad arguments");
     const Params& P = h->P;
-    int rc = ensure_scratch(h);
-    if (rc) return rc;
     size_t es = pop_bytes(P);
     size_t N = (size_t)P.g.N;
     size_t plane = es * N;
     std::vector<char> buf(plane * Q);
-    std::vector<float> ref(N);
+    std::vector<float> fld(4 * N);
     for (int i = 0; i < Q; ++i)
         CK(h, cudaMemcpyAsync(buf.data() + plane * i, (char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i,
                               plane, cudaMemcpyDeviceToHost, h->stream));
-    CK(h, launch_read_ref(P, h->dn[h->dref], h->scratch, h->stream));
-    CK(h, cudaMemcpyAsync(ref.data(), h->scratch, sizeof(float) * N, cudaMemcpyDeviceToHost, h->stream));
+    float* f[4];
+    field_set(h, h->fcur, f);
+    float* stage = (float*)h->pop[h->cur ^ 1];
+    CK(h, launch_read_fields(P, f, stage, h->stream));
+    CK(h, cudaMemcpyAsync(fld.data(), stage, sizeof(float) * 4 * N, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     FILE* fp = fopen(path, "wb");
     if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_save: cannot open ") + path);
     CkptHeader hd;
     memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, "LBIFCKP2", 8);
-    hd.version = 2;
+    memcpy(hd.magic, kCkptMagic, 8);
+    hd.version = 3;
     hd.nx = P.g.nx;
     hd.ny = P.g.ny;
     hd.nz = P.g.nz;
@@ -1330,7 +1273,7 @@ extern "C" int lbif_save(lbif_handle h, const char* path)
     hd.storage = P.storage;
     hd.t = h->t;
     bool ok = fwrite(&hd, sizeof(hd), 1, fp) == 1 && fwrite(buf.data(), 1, buf.size(), fp) == buf.size() &&
-              fwrite(ref.data(), sizeof(float), N, fp) == N;
+              fwrite(fld.data(), sizeof(float), 4 * N, fp) == 4 * N;
     ok = (fclose(fp) == 0) && ok;
     return ok ? LBIF_OK : fail(h, LBIF_ERR_IO, "lbif_save: write failed");
 }
@@ -1339,8 +1282,6 @@ extern "C" int lbif_load(lbif_handle h, const char* path)
 {
     if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_load: bad arguments");
     const Params& P = h->P;
-    int rc = ensure_scratch(h);
-    if (rc) return rc;
     FILE* fp = fopen(path, "rb");
     if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_load: cannot open ") + path);
     CkptHeader hd;
@@ -1348,18 +1289,21 @@ extern "C" int lbif_load(lbif_handle h, const char* path)
     size_t N = (size_t)P.g.N;
     size_t plane = es * N;
     std::vector<char> buf(plane * Q);
-    std::vector<float> ref(N);
-    bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, "LBIFCKP2", 8) == 0 &&
+    std::vector<float> fld(4 * N);
+    bool ok = fread(&hd, sizeof(hd), 1, fp) == 1 && memcmp(hd.magic, kCkptMagic, 8) == 0 &&
               hd.nx == P.g.nx && hd.ny == P.g.ny && hd.nz == P.g.nz && hd.sigma == P.sigma &&
               hd.storage == P.storage && fread(buf.data(), 1, buf.size(), fp) == buf.size() &&
-              fread(ref.data(), sizeof(float), N, fp) == N;
+              fread(fld.data(), sizeof(float), 4 * N, fp) == 4 * N;
     fclose(fp);
     if (!ok) return fail(h, LBIF_ERR_IO, "lbif_load: file does not match this handle");
     for (int i = 0; i < Q; ++i)
         CK(h, cudaMemcpyAsync((char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i, buf.data() + plane * i,
                               plane, cudaMemcpyHostToDevice, h->stream));
-    CK(h, cudaMemcpyAsync(h->scratch, ref.data(), sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
-    CK(h, launch_write_ref(P, h->scratch, h->dn[h->dref], h->stream));
+    float* f[4];
+    field_set(h, h->fcur, f);
+    float* stage = (float*)h->pop[h->cur ^ 1];
+    CK(h, cudaMemcpyAsync(stage, fld.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_write_fields(P, stage, f, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     reset_time(h);
     h->t = hd.t;

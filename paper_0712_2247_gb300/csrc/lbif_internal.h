@@ -2,16 +2,14 @@
 //
 // State of a slit on the device:
 //   pop[2]  19 planes of Npad elements (FP32 or FP16), node index
-//           idx = (z*ny + y)*nx + x, two buffers, push streaming. A population
-//           is stored as g_i = f_i/(w_i n0) - 1 - R(r): its relative deviation
-//           from the rest weights w_i n0, minus the node's reference density
-//           deviation R(r), so that stored values stay small even where the
-//           density is far from n0 (next to the walls).
-//   dn[2]   float on a padded grid (halo hw on every side), double-buffered:
-//           dn[cur] holds R = dn(r, t-1), the reference of the stored
-//           populations; the moments kernel writes dn(r, t) = R + sum_i w_i g_i
-//           into dn[cur^1], which becomes the reference after the step.
-//   ux, uy, uz  float velocity u = j/n on the padded grid.
+//           idx = (z*ny + y)*nx + x, two buffers, pull streaming. A population
+//           is stored as its non-equilibrium part relative to the node's own
+//           equilibrium weight, h_i = s (f_i - f_i^eq(n, u)) / (w_i n), at the
+//           moments n, u of the step it belongs to (s = 2^8 for FP16, 1 for
+//           FP32); the equilibrium part is carried by those moments.
+//   dn[2], u[2][3]  the moments of that step and of the next one (written by
+//           the pull pass): dn = n/n0 - 1 and u = j/n, float on a padded grid
+//           (halo hw on every side).
 //   dG      float  g2(etabar) - g2(eta0) on the padded grid.
 //   F       float4 F/n0 per node (force kernel -> collision kernel).
 //   The x/y halo holds periodic images written by the producing kernel; the
@@ -102,15 +100,14 @@ struct Fields {
     const float* dG;
 };
 
-// inputs and outputs of the fused collide-stream-moments kernel (padded
-// fields; dref may be the same buffer as dn, the outputs are other buffers)
+// inputs and outputs of the pull pass (padded fields; the outputs are other
+// buffers than the inputs)
 struct CsmIO {
-    const float* dref;  // reference R of the stored populations
-    const float* dn;    // dn(t)
+    const float* dn;    // dn(t), the moments the stored populations refer to
     const float* ux;
     const float* uy;
     const float* uz;    // u(t)
-    float* dnw;         // dn(t + 1), also the reference of the new populations
+    float* dnw;         // dn(t + 1), the moments of the new populations
     float* uxw;
     float* uyw;
     float* uzw;         // u(t + 1)
@@ -121,15 +118,14 @@ cudaError_t launch_fill_outside(const Params& P, float* const* planes, const flo
                                 int nplanes, cudaStream_t s);
 cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t seed, double amp,
                               long long offset, cudaStream_t s);
-cudaError_t launch_init_profiles(const Params& P, void* pop, float* dn, const float* n_z,
+// f[4]: the padded fields dn, ux, uy, uz of the state being set
+cudaError_t launch_init_profiles(const Params& P, void* pop, float* const f[4], const float* n_z,
                                  const float* ux_z, int hmax, cudaStream_t s);
-cudaError_t launch_init_fields(const Params& P, void* pop, float* dn, const float* rho,
+cudaError_t launch_init_fields(const Params& P, void* pop, float* const f[4], const float* rho,
                                const float* u, cudaStream_t s);
-cudaError_t launch_write_ref(const Params& P, const float* ref, float* dn, cudaStream_t s);
-cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaStream_t s);
-cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, float* dnew,
-                           float* ux, float* uy, float* uz, int* status, int skip_done,
-                           cudaStream_t s);
+// the four fields <-> four unpadded N-arrays (checkpoints)
+cudaError_t launch_write_fields(const Params& P, const float* src, float* const f[4], cudaStream_t s);
+cudaError_t launch_read_fields(const Params& P, const float* const f[4], float* out, cudaStream_t s);
 // want: CTAs to aim for when splitting z into chunks (<= 0: default).
 // tmap: a 3-D tensor map of dn (padded extents px, py, pz; box from
 // ball_box) to stage the plane tiles with the tensor-memory accelerator, or
@@ -155,13 +151,10 @@ cudaError_t tail_spectral_init(const Geom& g, int D, const int* pdx, const int* 
 // Ft = the tail force / n0 from the density deviation field dn (padded)
 cudaError_t launch_tail_spectral(const Params& P, const float* dn, int D, float2* work, float4* Ft,
                                  cudaStream_t s);
-cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields& f,
-                      const float4* F, cudaStream_t s);
 // one step's collision, pull streaming and the moments of the new
-// populations (CsmIO); lz: z planes per CTA segment (<= 0: default)
+// populations (CsmIO); lz: z planes per CTA segment of the tiled kernel
+// (<= 0: default). Grids narrower than one tile run the per-node kernel.
 bool csm_ok(const Geom& g);
-// the pass a handle starts with (FP32 storage and N >= 2^23 nodes)
-bool csm_default(const Geom& g, int storage);
 cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
                        int* status, int lz, cudaStream_t s);
 // bounded mbarrier wait on a barrier nothing completes: sets bit 4 of status

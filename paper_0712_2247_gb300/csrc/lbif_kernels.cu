@@ -250,6 +250,9 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+// Every initial state below is an equilibrium: its stored populations (the
+// non-equilibrium parts, see the pull pass) are 0 and its moments are the
+// fields themselves, written with their periodic images.
 template <typename T>
 __global__ void k_init_noise(Params P, T* pop, float* dn, uint64_t seed, double amp, long long offset)
 {
@@ -260,15 +263,17 @@ __global__ void k_init_noise(Params P, T* pop, float* dn, uint64_t seed, double 
     if (slit_of(P, z) < 0) return;
     uint64_t r = splitmix64(seed ^ (uint64_t)(offset + idx));
     double U = (double)(r >> 11) * (1.0 / 9007199254740992.0);
-    // f_i = w_i n0 (1 + xi): reference xi, all stored deviations 0
+    // f_i = w_i n0 (1 + xi) = f_i^eq(n0 (1 + xi), 0); u stays 0
     float xi = (float)(amp * (2.0 * U - 1.0));
 #pragma unroll
     for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
     for_images(P.g, x, y, z, [&](int p) { dn[p] = xi; });
 }
 
+// the equilibrium of given density and velocity fields (u NULL: at rest)
 template <typename T>
-__global__ void k_init_fields(Params P, T* pop, float* dn, const float* rho, const float* u)
+__global__ void k_init_fields(Params P, T* pop, float* dn, float* ux, float* uy, float* uz, const float* rho,
+                              const float* u)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -276,25 +281,23 @@ __global__ void k_init_fields(Params P, T* pop, float* dn, const float* rho, con
     decompose(P.g, idx, x, y, z);
     const int s = slit_of(P, z);
     if (s < 0) return;
-    float d = rho[idx] / P.sl[s].rho0 - 1.f;
-    float ux = 0.f, uy = 0.f, uz = 0.f;
-    if (u) {
-        ux = u[idx];
-        uy = u[P.g.N + idx];
-        uz = u[2 * P.g.N + idx];
-    }
-    float uu = ux * ux + uy * uy + uz * uz;
-    float opd = 1.f + d;
+    const float d = rho[idx] / P.sl[s].rho0 - 1.f;
+    const float vx = u ? u[idx] : 0.f, vy = u ? u[P.g.N + idx] : 0.f, vz = u ? u[2 * P.g.N + idx] : 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, eq_excess(i, opd, ux, uy, uz, uu));
-    for_images(P.g, x, y, z, [&](int p) { dn[p] = d; });
+    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
+    for_images(P.g, x, y, z, [&](int p) {
+        dn[p] = d;
+        ux[p] = vx;
+        uy[p] = vy;
+        uz[p] = vz;
+    });
 }
 
-// x,y-uniform fields from per-slit profiles n(z), u_x(z) (row s of n_z, ux_z
-// holds slit s, entry j its plane zlo + j)
+// x,y-uniform equilibria from per-slit profiles n(z), u_x(z) (row s of n_z,
+// ux_z holds slit s, entry j its plane zlo + j)
 template <typename T>
-__global__ void k_init_profiles(Params P, T* pop, float* dn, const float* n_z, const float* ux_z,
-                                int hmax)
+__global__ void k_init_profiles(Params P, T* pop, float* dn, float* ux, float* uy, float* uz, const float* n_z,
+                                const float* ux_z, int hmax)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -304,67 +307,48 @@ __global__ void k_init_profiles(Params P, T* pop, float* dn, const float* n_z, c
     if (s < 0) return;
     const int j = z - P.sl[s].zlo;
     const float d = n_z[(long long)s * hmax + j] / P.sl[s].rho0 - 1.f;
-    const float ux = ux_z ? ux_z[(long long)s * hmax + j] : 0.f;
-    const float uu = ux * ux, opd = 1.f + d;
+    const float vx = ux_z ? ux_z[(long long)s * hmax + j] : 0.f;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, eq_excess(i, opd, ux, 0.f, 0.f, uu));
-    for_images(P.g, x, y, z, [&](int p) { dn[p] = d; });
+    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
+    for_images(P.g, x, y, z, [&](int p) {
+        dn[p] = d;
+        ux[p] = vx;
+        uy[p] = 0.f;
+        uz[p] = 0.f;
+    });
 }
 
-__global__ void k_write_ref(Params P, const float* ref, float* dn)
+// moment fields dn, ux, uy, uz <-> four unpadded N-arrays (checkpoints)
+__global__ void k_write_fields(Params P, const float* src, float* dn, float* ux, float* uy, float* uz)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
     int x, y, z;
     decompose(P.g, idx, x, y, z);
     if (slit_of(P, z) < 0) return;
-    float v = ref[idx];
-    for_images(P.g, x, y, z, [&](int p) { dn[p] = v; });
+    const long long N = P.g.N;
+    const float a = src[idx], b = src[N + idx], c = src[2 * N + idx], d = src[3 * N + idx];
+    for_images(P.g, x, y, z, [&](int p) {
+        dn[p] = a;
+        ux[p] = b;
+        uy[p] = c;
+        uz[p] = d;
+    });
 }
 
-__global__ void k_read_ref(Params P, const float* dn, float* ref)
+__global__ void k_read_fields(Params P, const float* dn, const float* ux, const float* uy, const float* uz,
+                              float* out)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
     int x, y, z;
     decompose(P.g, idx, x, y, z);
-    ref[idx] = dn[pidx(P.g, x, y, z)];
-}
-
-// ---------------------------------------------------------------------------
-// step 1: moments (Sec. Theory: n = int f, n u = int v f)
-//   reads the reference R = dn(t-1) from dref, writes dn(t) and u
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_moments(Params P, const T* __restrict__ pop,
-                                                 const float* dref, float* dnew, float* oux,
-                                                 float* ouy, float* ouz, int* status, int skip_done)
-{
-    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= P.g.N) return;
-    int x, y, z;
-    decompose(P.g, idx, x, y, z);
-    const int s = slit_of(P, z);
-    if (s < 0 || (skip_done && frozen(P, s))) return;
-    float g[Q];
-    load_pops(P, pop, idx, g);
-    float R = dref[pidx(P.g, x, y, z)];
-    float S, jx, jy, jz;
-    sums_of(g, S, jx, jy, jz);
-    float dn = R + S;
-    float inv = 1.f / (1.f + dn);
-    float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-    if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
-    auto put = [&](int p) {
-        dnew[p] = dn;
-        oux[p] = ux;
-        ouy[p] = uy;
-        ouz[p] = uz;
-    };
-    if (no_images(P.g, x, y, z))
-        put(pidx(P.g, x, y, z));
-    else
-        for_images(P.g, x, y, z, put);
+    const int p = pidx(P.g, x, y, z);
+    const long long N = P.g.N;
+    out[idx] = dn[p];
+    out[N + idx] = ux[p];
+    out[2 * N + idx] = uy[p];
+    out[3 * N + idx] = uz[p];
 }
 
 // ---------------------------------------------------------------------------
@@ -773,7 +757,9 @@ __device__ __forceinline__ const float* ufield(const Fields& f)
     return A == 0 ? f.ux : (A == 1 ? f.uy : f.uz);
 }
 
-// generic path: one node per thread, scalar loads (any even sigma)
+// generic path: one node per thread, scalar loads (any even sigma). The x and
+// y components are formed from accurate mirror differences as in the
+// vectorised path below (see there).
 template <int A>
 __device__ __forceinline__ void axis_pair(const Params& P, const Fields& fl, int p, const float u0[3],
                                           float G0, float lk, float f[3], float* cc)
@@ -784,65 +770,87 @@ __device__ __forceinline__ void axis_pair(const Params& P, const Fields& fl, int
     float up = __ldg(uf + p + o), um = __ldg(uf + p - o);
     float gp = __ldg(fl.dG + p + om), gm = __ldg(fl.dG + p - om);
     float Ap = shell_A(dp, gp, G0), Am = shell_A(dm, gm, G0);
-    float tp = Ap - (G0 + Ap) * lk * (up - u0[A]);
-    float tm = Am - (G0 + Am) * lk * (u0[A] - um);
-    f[A] += (1.f / 30.f) * (tp - tm);
+    const float DA = A == 2 ? Ap - Am : fmaf(G0, dp - dm, fmaf(gp - gm, 1.f + dp, gm * (dp - dm)));
+    f[A] += (1.f / 30.f) * (DA - lk * ((G0 + Ap) * (up - u0[A]) - (G0 + Am) * (u0[A] - um)));
     // Eq. C2eq: sum_q W_q (G_q n_q / n0) s_q.(u_q - u)
     if (cc) *cc += (1.f / 30.f) * ((G0 + Ap) * (up - u0[A]) + (G0 + Am) * (u0[A] - um));
 }
 
 template <int PL>
-__device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, int p,
-                                             const float u0[3], float G0, float lk, float f[3], float* cc)
+__device__ __forceinline__ void diag_quartet(const Params& P, const Fields& fl, int p, const float u0[3],
+                                             float G0, float lk, float f[3], float* cc)
 {
     constexpr int a = PL == 2 ? 1 : 0;
     constexpr int b = PL == 0 ? 1 : 2;
     constexpr float h = 0.70710678118654752f;
     const float* fa = a == 0 ? fl.ux : fl.uy;
     const float* fb = b == 1 ? fl.uy : fl.uz;
-    // member m: sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1
-    float dq[4] = {0.f, 0.f, 0.f, 0.f}, ua[4] = {0.f, 0.f, 0.f, 0.f}, ub[4] = {0.f, 0.f, 0.f, 0.f};
-    float gq[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int oa = P.sh.nb_a[PL][k], ob = P.sh.nb_b[PL][k];
-        const int ma = P.sh.md_a[PL][k], mb = P.sh.md_b[PL][k];
-        const float w = P.sh.nb_w[PL][k], wm = P.sh.md_w[PL][k];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const int sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1;
-            const int o = p + sa * oa + sb * ob;
-            dq[m] = fmaf(w, __ldg(fl.dn + o), dq[m]);
-            ua[m] = fmaf(w, __ldg(fa + o), ua[m]);
-            ub[m] = fmaf(w, __ldg(fb + o), ub[m]);
-            gq[m] = fmaf(wm, __ldg(fl.dG + p + sa * ma + sb * mb), gq[m]);
-        }
-    }
-    float Aq[4], Pa[4], Pb[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-        const float sa = (m & 1) ? -1.f : 1.f, sb = (m & 2) ? -1.f : 1.f;
-        Aq[m] = shell_A(dq[m], gq[m], G0);
-        float c = (G0 + Aq[m]) * lk * h;
-        Pa[m] = c * (sa * (ua[m] - u0[a]));
-        Pb[m] = c * (sb * (ub[m] - u0[b]));
-    }
-    // a-component sums sa T over members paired by equal b offset, b-component sb T
-    float da = ((Aq[0] - Aq[1]) - (Pa[0] - Pa[1]) - (Pb[0] - Pb[1])) +
-               ((Aq[2] - Aq[3]) - (Pa[2] - Pa[3]) - (Pb[2] - Pb[3]));
-    float db = ((Aq[0] - Aq[2]) - (Pa[0] - Pa[2]) - (Pb[0] - Pb[2])) +
-               ((Aq[1] - Aq[3]) - (Pa[1] - Pa[3]) - (Pb[1] - Pb[3]));
-    f[a] += (h / 15.f) * da;
-    f[b] += (h / 15.f) * db;
-    if (cc) {
-        float t = 0.f;
+    // corner values of member m (sa = (m & 1) ? -1 : 1, sb = (m & 2) ? -1 : 1)
+    auto nb = [&](int m, int k) { return p + ((m & 1) ? -1 : 1) * P.sh.nb_a[PL][k] + ((m & 2) ? -1 : 1) * P.sh.nb_b[PL][k]; };
+    auto md = [&](int m, int k) { return p + ((m & 1) ? -1 : 1) * P.sh.md_a[PL][k] + ((m & 2) ? -1 : 1) * P.sh.md_b[PL][k]; };
+    if constexpr (PL == 0) {
+        // relative to the node's own n and g2: every member a small deviation
+        const float d0 = __ldg(fl.dn + p), g0 = __ldg(fl.dG + p);
+        const float Aref = fmaf(G0, d0, g0 * (1.f + d0));
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const float sa = (m & 1) ? -1.f : 1.f, sb = (m & 2) ? -1.f : 1.f;
-            t += (G0 + Aq[m]) * h * (sa * (ua[m] - u0[a]) + sb * (ub[m] - u0[b]));
+            float dl = 0.f, gl = 0.f, ua = 0.f, ub = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float w = P.sh.nb_w[PL][k], wm = P.sh.md_w[PL][k];
+                dl = fmaf(w, __ldg(fl.dn + nb(m, k)) - d0, dl);
+                ua = fmaf(w, __ldg(fa + nb(m, k)), ua);
+                ub = fmaf(w, __ldg(fb + nb(m, k)), ub);
+                gl = fmaf(wm, __ldg(fl.dG + md(m, k)) - g0, gl);
+            }
+            const float av = fmaf(G0 + g0, dl, gl * ((1.f + d0) + dl));
+            const float GA = G0 + (Aref + av);
+            const float S = fmaf(sa, ua - u0[a], sb * (ub - u0[b]));
+            const float tau = av - GA * lk * h * S;
+            f[a] = fmaf(sa * (h / 15.f), tau, f[a]);
+            f[b] = fmaf(sb * (h / 15.f), tau, f[b]);
+            if (cc) *cc += (1.f / 15.f) * (GA * h * S);
         }
-        *cc += t / 15.f;
+        return;
     }
+    // planes (x, z), (y, z): the + and - members (in-plane sign) of each z
+    // side, their in-plane difference from corner differences
+    float da = 0.f, db = 0.f;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const float sb = side ? -1.f : 1.f;
+        const int m = 2 * side, mp = 2 * side + 1;  // in-plane sign +, -
+        float dm = 0.f, dpp = 0.f, Dd = 0.f, gm = 0.f, gp = 0.f, Dg = 0.f;
+        float am = 0.f, ap = 0.f, bm = 0.f, bp = 0.f, Db = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float w = P.sh.nb_w[PL][k], wm = P.sh.md_w[PL][k];
+            const float n1 = __ldg(fl.dn + nb(m, k)), n2 = __ldg(fl.dn + nb(mp, k));
+            const float b1 = __ldg(fb + nb(m, k)), b2 = __ldg(fb + nb(mp, k));
+            const float g1 = __ldg(fl.dG + md(m, k)), g2 = __ldg(fl.dG + md(mp, k));
+            dm = fmaf(w, n1, dm);
+            dpp = fmaf(w, n2, dpp);
+            Dd = fmaf(w, n1 - n2, Dd);
+            bm = fmaf(w, b1, bm);
+            bp = fmaf(w, b2, bp);
+            Db = fmaf(w, b1 - b2, Db);
+            gm = fmaf(wm, g1, gm);
+            gp = fmaf(wm, g2, gp);
+            Dg = fmaf(wm, g1 - g2, Dg);
+            am = fmaf(w, __ldg(fa + nb(m, k)), am);
+            ap = fmaf(w, __ldg(fa + nb(mp, k)), ap);
+        }
+        const float Am = shell_A(dm, gm, G0), Ap = shell_A(dpp, gp, G0);
+        const float DA = fmaf(G0, Dd, fmaf(Dg, 1.f + dm, gp * Dd));
+        const float c1 = (G0 + Am) * lk * h, c2 = (G0 + Ap) * lk * h, Dc = DA * lk * h;
+        const float xm = am - u0[a], xp = ap - u0[a], zm = bm - u0[b], zp = bp - u0[b];
+        da += DA - fmaf(c1, xm, c2 * xp) - sb * fmaf(c1, Db, Dc * zp);
+        db += sb * ((Am + Ap) - fmaf(c1, xm, -c2 * xp) - sb * fmaf(c1, zm, c2 * zp));
+        if (cc) *cc += (1.f / 15.f) * h * ((G0 + Am) * (xm + sb * zm) + (G0 + Ap) * (-xp + sb * zp));
+    }
+    f[a] += (h / 15.f) * da;
+    f[b] += (h / 15.f) * db;
 }
 
 __device__ __forceinline__ float coupling_factor(const Params& P, const SlitParam& S, int z)
@@ -1007,11 +1015,22 @@ __device__ __forceinline__ void corners_x(const float* __restrict__ f, int b, v4
         win2<-LO - 1, LN>(f, b, c1, c0, ln);
 }
 
-template <int SIG, int PL, int M, bool LN>
-__device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int pb, v4 dq, v4 ua,
-                                         v4 ub, v4 gq, Lanes ln)
+// Mirror images along x (and y) of the shell points carry the x (y) force as
+// a small difference of large values next to a wall (density layering, wall-
+// normal velocity u_z ~ 0.1), so those differences are formed before any
+// large value is rounded: the points of the (x, y) plane are interpolated
+// relative to the node's own n and g2 values (all members then are small
+// in-plane deviations), the pairs of the (x, z) and (y, z) planes that share
+// the z offset as corner-by-corner differences, and the x and y axis pairs as
+// differences of the loaded values. With A = G0 dq + gq (1 + dq):
+//   A - A' = G0 (dq - dq') + (gq - gq') (1 + dq) + gq' (dq - dq').
+
+// interpolants of member M of plane PL (0: (x, y), 1: (x, z); a = x) from
+// its x-window corners; REF: n and g2 relative to the node's own values
+template <int SIG, int PL, int M, bool LN, bool REF>
+__device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int pb, const v4 d0, const v4 g0, v4 dq,
+                                         v4 ua, v4 ub, v4 gq, Lanes ln)
 {
-    // PL 0: plane (x, y); PL 1: plane (x, z); a = x
     constexpr int LO = cisqrt(SIG * SIG / 2), LOM = cisqrt((SIG / 2) * (SIG / 2) / 2);
     constexpr int SA = (M & 1) ? -1 : 1, SB = (M & 2) ? -1 : 1;
     const int sbs = PL == 0 ? P.g.px : P.g.px * P.g.py;
@@ -1023,7 +1042,10 @@ __device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int 
         v4 c0, c1;
         corners_x<LO, SA, LN>(fl.dn, row, c0, c1, ln);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) dq[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], dq[j]));
+        for (int j = 0; j < 4; ++j) {
+            const float r = REF ? d0[j] : 0.f;
+            dq[j] = fmaf(w1, c1[j] - r, fmaf(w0, c0[j] - r, dq[j]));
+        }
         corners_x<LO, SA, LN>(fl.ux, row, c0, c1, ln);
 #pragma unroll
         for (int j = 0; j < 4; ++j) ua[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], ua[j]));
@@ -1034,93 +1056,164 @@ __device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int 
         const float v0 = P.sh.md_w[PL][2 * kb], v1 = P.sh.md_w[PL][2 * kb + 1];
         corners_x<LOM, SA, LN>(fl.dG, mrow, c0, c1, ln);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) gq[j] = fmaf(v1, c1[j], fmaf(v0, c0[j], gq[j]));
-    }
-}
-
-template <int SIG, int M>
-__device__ __forceinline__ void member_yz(const Params& P, const Fields& fl, int pb, v4 dq, v4 ua,
-                                          v4 ub, v4 gq)
-{
-    // plane (y, z): no x offset, every corner is an aligned float4
-    constexpr int LO = cisqrt(SIG * SIG / 2), LOM = cisqrt((SIG / 2) * (SIG / 2) / 2);
-    constexpr int SA = (M & 1) ? -1 : 1, SB = (M & 2) ? -1 : 1;
-    const int sy = P.g.px, sz = P.g.px * P.g.py;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int ka = k & 1, kb = k >> 1;
-        const int o = pb + SA * (LO + ka) * sy + SB * (LO + kb) * sz;
-        const int om = pb + SA * (LOM + ka) * sy + SB * (LOM + kb) * sz;
-        const float w = P.sh.nb_w[2][k], wm = P.sh.md_w[2][k];
-        v4 d, a, b, gg;
-        set4(d, ld4(fl.dn + o));
-        set4(a, ld4(fl.uy + o));
-        set4(b, ld4(fl.uz + o));
-        set4(gg, ld4(fl.dG + om));
-#pragma unroll
         for (int j = 0; j < 4; ++j) {
-            dq[j] = fmaf(w, d[j], dq[j]);
-            ua[j] = fmaf(w, a[j], ua[j]);
-            ub[j] = fmaf(w, b[j], ub[j]);
-            gq[j] = fmaf(wm, gg[j], gq[j]);
+            const float r = REF ? g0[j] : 0.f;
+            gq[j] = fmaf(v1, c1[j] - r, fmaf(v0, c0[j] - r, gq[j]));
         }
     }
 }
 
-template <int SIG, int PL, int M, bool C2, bool LN>
-__device__ __forceinline__ void member_terms(const Params& P, const Fields& fl, int pb,
-                                             const v4 ua0, const v4 ub0, float G0, float lk, v4 Aq,
-                                             v4 Pa, v4 Pb, v4 Cq, Lanes ln)
+// plane (x, y): the four members relative to the node's own n and g2 (d0,
+// g0); their terms tau = T - T_ref share one reference, so both force
+// components are sums of small accurate values
+template <int SIG, bool C2, bool LN>
+__device__ __forceinline__ void quartet_xy(const Params& P, const Fields& fl, int pb, const v4 d0, const v4 g0,
+                                           const v4 u0[3], float G0, float lk, v4 f[3], v4 cc, Lanes ln)
 {
-    constexpr float h = 0.70710678118654752f;
-    constexpr float sa = (M & 1) ? -1.f : 1.f, sb = (M & 2) ? -1.f : 1.f;
-    v4 dq, ua, ub, gq;
+    constexpr float h = 0.70710678118654752f, c = h / 15.f;
+    auto one = [&](auto mc) {
+        constexpr int M = decltype(mc)::value;
+        constexpr float sa = (M & 1) ? -1.f : 1.f, sb = (M & 2) ? -1.f : 1.f;
+        v4 dl, ua, ub, gl;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) dq[j] = ua[j] = ub[j] = gq[j] = 0.f;
-    if constexpr (PL == 2)
-        member_yz<SIG, M>(P, fl, pb, dq, ua, ub, gq);
-    else
-        member_x<SIG, PL, M, LN>(P, fl, pb, dq, ua, ub, gq, ln);
+        for (int j = 0; j < 4; ++j) dl[j] = ua[j] = ub[j] = gl[j] = 0.f;
+        member_x<SIG, 0, M, LN, true>(P, fl, pb, d0, g0, dl, ua, ub, gl, ln);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const float Aref = fmaf(G0, d0[j], g0[j] * (1.f + d0[j]));
+            const float a = fmaf(G0 + g0[j], dl[j], gl[j] * ((1.f + d0[j]) + dl[j]));
+            const float GA = G0 + (Aref + a);
+            const float S = fmaf(sa, ua[j] - u0[0][j], sb * (ub[j] - u0[1][j]));
+            const float tau = a - GA * lk * h * S;
+            f[0][j] = fmaf(sa * c, tau, f[0][j]);
+            f[1][j] = fmaf(sb * c, tau, f[1][j]);
+            if constexpr (C2) cc[j] += (1.f / 15.f) * (GA * h * S);
+        }
+    };
+    one(std::integral_constant<int, 0>{});
+    one(std::integral_constant<int, 1>{});
+    one(std::integral_constant<int, 2>{});
+    one(std::integral_constant<int, 3>{});
+}
+
+// plane (x, z) (PL 1) or (y, z) (PL 2): the two members with z offset sign SB
+// and opposite in-plane sign: their interpolants d, g, ua, ub (m: +, p: -)
+// and the corner-by-corner differences of d, g and ub
+template <int SIG, int PL, int SB, bool LN>
+__device__ __forceinline__ void pair_interp(const Params& P, const Fields& fl, int pb, v4 dm, v4 dp, v4 Dd, v4 gm,
+                                            v4 gp, v4 Dg, v4 am, v4 ap, v4 bm, v4 bp, v4 Db, Lanes ln)
+{
+    constexpr int LO = cisqrt(SIG * SIG / 2), LOM = cisqrt((SIG / 2) * (SIG / 2) / 2);
+    const float* fa = PL == 1 ? fl.ux : fl.uy;
+    const int sz = P.g.px * P.g.py;
+    // corner values of the + and - members of one field (accumulated with weight w)
+    auto acc = [&](const float* f, const v4 cp, const v4 cm, float w, v4 im, v4 ip, v4 D) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            im[j] = fmaf(w, cp[j], im[j]);
+            ip[j] = fmaf(w, cm[j], ip[j]);
+            if (D) D[j] = fmaf(w, cp[j] - cm[j], D[j]);
+        }
+    };
+    if constexpr (PL == 1) {
+#pragma unroll
+        for (int kb = 0; kb < 2; ++kb) {
+            const int row = pb + SB * (LO + kb) * sz;
+            const float w0 = P.sh.nb_w[1][2 * kb], w1 = P.sh.nb_w[1][2 * kb + 1];
+            v4 c0, c1, e0, e1;
+            corners_x<LO, 1, LN>(fl.dn, row, c0, c1, ln);
+            corners_x<LO, -1, LN>(fl.dn, row, e0, e1, ln);
+            acc(fl.dn, c0, e0, w0, dm, dp, Dd);
+            acc(fl.dn, c1, e1, w1, dm, dp, Dd);
+            corners_x<LO, 1, LN>(fa, row, c0, c1, ln);
+            corners_x<LO, -1, LN>(fa, row, e0, e1, ln);
+            acc(fa, c0, e0, w0, am, ap, nullptr);
+            acc(fa, c1, e1, w1, am, ap, nullptr);
+            corners_x<LO, 1, LN>(fl.uz, row, c0, c1, ln);
+            corners_x<LO, -1, LN>(fl.uz, row, e0, e1, ln);
+            acc(fl.uz, c0, e0, w0, bm, bp, Db);
+            acc(fl.uz, c1, e1, w1, bm, bp, Db);
+            const int mrow = pb + SB * (LOM + kb) * sz;
+            const float v0 = P.sh.md_w[1][2 * kb], v1 = P.sh.md_w[1][2 * kb + 1];
+            corners_x<LOM, 1, LN>(fl.dG, mrow, c0, c1, ln);
+            corners_x<LOM, -1, LN>(fl.dG, mrow, e0, e1, ln);
+            acc(fl.dG, c0, e0, v0, gm, gp, Dg);
+            acc(fl.dG, c1, e1, v1, gm, gp, Dg);
+        }
+    } else {
+        const int sy = P.g.px;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int ka = k & 1, kb = k >> 1;
+            const int o = pb + (LO + ka) * sy + SB * (LO + kb) * sz;
+            const int om = pb - (LO + ka) * sy + SB * (LO + kb) * sz;
+            const int q = pb + (LOM + ka) * sy + SB * (LOM + kb) * sz;
+            const int qm = pb - (LOM + ka) * sy + SB * (LOM + kb) * sz;
+            const float w = P.sh.nb_w[2][k], wm = P.sh.md_w[2][k];
+            v4 c, e;
+            set4(c, ld4(fl.dn + o));
+            set4(e, ld4(fl.dn + om));
+            acc(fl.dn, c, e, w, dm, dp, Dd);
+            set4(c, ld4(fa + o));
+            set4(e, ld4(fa + om));
+            acc(fa, c, e, w, am, ap, nullptr);
+            set4(c, ld4(fl.uz + o));
+            set4(e, ld4(fl.uz + om));
+            acc(fl.uz, c, e, w, bm, bp, Db);
+            set4(c, ld4(fl.dG + q));
+            set4(e, ld4(fl.dG + qm));
+            acc(fl.dG, c, e, wm, gm, gp, Dg);
+        }
+    }
+}
+
+// one z side (sign SB) of plane (x, z) or (y, z): T_+ - T_- (the in-plane
+// force) from the differences, SB (T_+ + T_-) (the z force) directly
+template <int SIG, int PL, int SB, bool C2, bool LN>
+__device__ __forceinline__ void pair_terms(const Params& P, const Fields& fl, int pb, const v4 u0[3], float G0,
+                                           float lk, v4 da, v4 db, v4 cc, Lanes ln)
+{
+    constexpr int a = PL == 1 ? 0 : 1;
+    constexpr float h = 0.70710678118654752f, sb = (float)SB;
+    v4 dm, dp, Dd, gm, gp, Dg, am, ap, bm, bp, Db;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) dm[j] = dp[j] = Dd[j] = gm[j] = gp[j] = Dg[j] = am[j] = ap[j] = bm[j] = bp[j] = Db[j] = 0.f;
+    pair_interp<SIG, PL, SB, LN>(P, fl, pb, dm, dp, Dd, gm, gp, Dg, am, ap, bm, bp, Db, ln);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        Aq[j] = shell_A(dq[j], gq[j], G0);
-        float c = (G0 + Aq[j]) * lk * h;
-        Pa[j] = c * (sa * (ua[j] - ua0[j]));
-        Pb[j] = c * (sb * (ub[j] - ub0[j]));
-        if constexpr (C2) Cq[j] = (G0 + Aq[j]) * h * (sa * (ua[j] - ua0[j]) + sb * (ub[j] - ub0[j]));
+        const float Am = shell_A(dm[j], gm[j], G0), Ap = shell_A(dp[j], gp[j], G0);
+        const float DA = fmaf(G0, Dd[j], fmaf(Dg[j], 1.f + dm[j], gp[j] * Dd[j]));
+        const float cm = (G0 + Am) * lk * h, cp = (G0 + Ap) * lk * h, Dc = DA * lk * h;
+        const float xm = am[j] - u0[a][j], xp = ap[j] - u0[a][j];    // in-plane velocity offsets
+        const float zm = bm[j] - u0[2][j], zp = bp[j] - u0[2][j];    // wall-normal velocity offsets
+        // T = A - c (s_a (u_a - u0_a) + s_b (u_z - u0_z)), s_a = +1 for m, -1 for p
+        da[j] += DA - fmaf(cm, xm, cp * xp) - sb * fmaf(cm, Db[j], Dc * zp);
+        db[j] += sb * ((Am + Ap) - fmaf(cm, xm, -cp * xp) - sb * fmaf(cm, zm, cp * zp));
+        if constexpr (C2) cc[j] += (1.f / 15.f) * h * ((G0 + Am) * (xm + sb * zm) + (G0 + Ap) * (-xp + sb * zp));
     }
 }
 
 template <int SIG, int PL, bool C2, bool LN>
-__device__ __forceinline__ void quartet4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
-                                         float G0, float lk, v4 f[3], v4 cc, Lanes ln)
+__device__ __forceinline__ void quartet_z(const Params& P, const Fields& fl, int pb, const v4 u0[3], float G0,
+                                          float lk, v4 f[3], v4 cc, Lanes ln)
 {
-    constexpr int a = PL == 2 ? 1 : 0;
-    constexpr int b = PL == 0 ? 1 : 2;
+    constexpr int a = PL == 1 ? 0 : 1;
     constexpr float c = 0.70710678118654752f / 15.f;
-    v4 A0, P0a, P0b, A1, P1a, P1b, A2, P2a, P2b, A3, P3a, P3b, C0, C1, C2m, C3;
-    member_terms<SIG, PL, 0, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A0, P0a, P0b, C0, ln);
-    member_terms<SIG, PL, 1, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A1, P1a, P1b, C1, ln);
-    member_terms<SIG, PL, 2, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A2, P2a, P2b, C2m, ln);
-    member_terms<SIG, PL, 3, C2, LN>(P, fl, pb, u0[a], u0[b], G0, lk, A3, P3a, P3b, C3, ln);
-    if constexpr (C2) {
+    v4 da, db;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cc[j] += (1.f / 15.f) * ((C0[j] + C1[j]) + (C2m[j] + C3[j]));
-    }
+    for (int j = 0; j < 4; ++j) da[j] = db[j] = 0.f;
+    pair_terms<SIG, PL, 1, C2, LN>(P, fl, pb, u0, G0, lk, da, db, cc, ln);
+    pair_terms<SIG, PL, -1, C2, LN>(P, fl, pb, u0, G0, lk, da, db, cc, ln);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        float da = ((A0[j] - A1[j]) - (P0a[j] - P1a[j]) - (P0b[j] - P1b[j])) +
-                   ((A2[j] - A3[j]) - (P2a[j] - P3a[j]) - (P2b[j] - P3b[j]));
-        float db = ((A0[j] - A2[j]) - (P0a[j] - P2a[j]) - (P0b[j] - P2b[j])) +
-                   ((A1[j] - A3[j]) - (P1a[j] - P3a[j]) - (P1b[j] - P3b[j]));
-        f[a][j] += c * da;
-        f[b][j] += c * db;
+        f[a][j] += c * da[j];
+        f[2][j] += c * db[j];
     }
 }
 
 template <int SIG, int A, bool C2>
-__device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb, const v4 u0[3],
-                                      float G0, float lk, v4 f[3], v4 cc)
+__device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb, const v4 u0[3], float G0, float lk,
+                                      v4 f[3], v4 cc)
 {
     const float* uf = ufield<A>(fl);
     v4 dp, dm, up, um, gp, gm;
@@ -1143,9 +1236,10 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         float Ap = shell_A(dp[j], gp[j], G0), Am = shell_A(dm[j], gm[j], G0);
-        float tp = Ap - (G0 + Ap) * lk * (up[j] - u0[A][j]);
-        float tm = Am - (G0 + Am) * lk * (u0[A][j] - um[j]);
-        f[A][j] += (1.f / 30.f) * (tp - tm);
+        // A_+ - A_-: from the differences of the loaded values along x and y
+        const float DA = A == 2 ? Ap - Am
+                                : fmaf(G0, dp[j] - dm[j], fmaf(gp[j] - gm[j], 1.f + dp[j], gm[j] * (dp[j] - dm[j])));
+        f[A][j] += (1.f / 30.f) * (DA - lk * ((G0 + Ap) * (up[j] - u0[A][j]) - (G0 + Am) * (u0[A][j] - um[j])));
         if constexpr (C2) cc[j] += (1.f / 30.f) * ((G0 + Ap) * (up[j] - u0[A][j]) + (G0 + Am) * (u0[A][j] - um[j]));
     }
 }
@@ -1185,8 +1279,9 @@ __global__ void __launch_bounds__(FORCE_NT, 512 / FORCE_NT) k_force4(Params P, T
     if (s < 0 || frozen(P, s)) return;  // whole warp (one z plane)
     const SlitParam S = P.sl[s];
     const int pb = pidx(g, x, y, z);  // 16-byte aligned: x, hw, px multiples of 4
-    v4 d0, u0[3];
+    v4 d0, g0, u0[3];
     set4(d0, ld4(fl.dn + pb));
+    set4(g0, ld4(fl.dG + pb));
     set4(u0[0], ld4(fl.ux + pb));
     set4(u0[1], ld4(fl.uy + pb));
     set4(u0[2], ld4(fl.uz + pb));
@@ -1202,9 +1297,9 @@ __global__ void __launch_bounds__(FORCE_NT, 512 / FORCE_NT) k_force4(Params P, T
         axis4<SIG, 0, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
         axis4<SIG, 1, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
         axis4<SIG, 2, C2>(P, fl, pb, u0, S.G0, lk, f, cc);
-        quartet4<SIG, 0, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
-        quartet4<SIG, 1, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
-        quartet4<SIG, 2, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
+        quartet_xy<SIG, C2, LN>(P, fl, pb, d0, g0, u0, S.G0, lk, f, cc, ln);
+        quartet_z<SIG, 1, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
+        quartet_z<SIG, 2, C2, LN>(P, fl, pb, u0, S.G0, lk, f, cc, ln);
     }
     if (!live) return;
     const long long idx0 = ((long long)z * g.ny + y) * g.nx + x;
@@ -1258,112 +1353,248 @@ __global__ void k_tail(Params P, const float* __restrict__ dn, const int* __rest
 }
 
 // ---------------------------------------------------------------------------
-// steps 5-6: BGK collision with the first-order source and push streaming
-// with half-way bounce-back (Sec. Methods: forward-Euler update, local
-// equilibrium; bounce-back walls). Works on k_i = h_i - dn (populations
-// relative to the node's own current density) and stores, at the target,
-// the value relative to the target's current density.
+// steps 5-6 with step 1 of the next step, in pull form (Sec. Methods: the
+// forward-Euler update with the first-order source towards the local
+// equilibrium; half-way bounce-back at the walls). Every node gathers the
+// populations that stream into it, applies to each the collision of its
+// source node, and forms the new moments from the 19 values it holds, so the
+// populations are read and written once per step.
+//
+// Stored populations. A node's populations are kept as
+//   h_i = s_T (f_i - f_i^eq(n, u)) / (w_i n),
+// the non-equilibrium part of f_i relative to the node's equilibrium weight
+// w_i n, at the moments n, u of the step they belong to (the field buffers of
+// that step hold those moments in FP32); s_T = 2^8 with FP16 storage (keeps
+// the small parts of the bulk clear of the FP16 subnormal range) and 1 with
+// FP32. The equilibrium part, which carries the flow, is never rounded to the
+// storage type. In units of w_i n0, with dn = n/n0 - 1 and
+// e_i = (1 + dn)(3 c.u + 9/2 (c.u)^2 - 3/2 u.u),
+//   f_i / (w_i n0) - 1 = dn + e_i + (1 + dn) h_i / s_T.
+// BGK towards f^eq(n, u) with omega = 1/tau, plus the source
+// 3 c.F + (3/2) F.w (|c|^2 - 1) (F the force per n0, F.w the energy source
+// when on), gives the post-collision value
+//   f_i' / (w_i n0) - 1 = dn + T_i + m h_i,  m = (1 - omega)(1 + dn) / s_T,
+//   T_i = e_i + 3 c.F + (3/2) F.w (|c|^2 - 1),
+// and T splits by lattice-velocity class into
+//   axis a, sign s:            s P_a + C_a
+//   plane (a, b), signs sa sb: sa P_a + sb P_b + C_ab + sa sb X_ab
+//   rest:                      C_0
+// with q = 1 + dn, P = 3 (q u + F), B = -(3/2) q u.u, C_a = B + (9/2) q u_a^2,
+// C_ab = B + (9/2) q (u_a^2 + u_b^2) + (3/2) F.w, X_ab = 9 q u_a u_b and
+// C_0 = B - (3/2) F.w = (2 (C_x + C_y + C_z) - (C_xy + C_xz + C_yz)) / 3.
+// The value reaching r from s = r - c_i, relative to dn(r), is
+// v_i = T_i(s) + m(s) h_i(s) + (dn(s) - dn(r)); at a wall it is the node's own
+// post-collision value of the opposite direction (c -> -c: the P terms change
+// sign). The new moments are dn(r) + S, S = sum_i w_i v_i, and
+// u = sum_i w_i c_i v_i / (1 + dn(r) + S); the new populations are stored as
+// their non-equilibrium parts at those moments.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(256, 4) k_cs(Params P, const T* __restrict__ pin, T* __restrict__ pout,
-                                               Fields fl, const float4* __restrict__ F)
+__host__ __device__ constexpr float store_scale() { return sizeof(T) == 2 ? 256.f : 1.f; }
+
+// staged quantities of a node: dn, P_x..z, C_x..z, C_xy C_xz C_yz, X_xy X_xz X_yz
+constexpr int SQ_DN = 0, SQ_P = 1, SQ_CA = 4, SQ_CP = 7, SQ_X = 10, CSM_NF = 13;
+
+// The staged quantities of a node from its moments and force; st(k, value)
+// receives quantity k. Each quantity ends in a rounding intrinsic (never
+// merged into a later multiply-add), so a kernel that uses them at once and
+// one that stores them first compute identical values.
+template <class St>
+__device__ __forceinline__ void src_terms(float d, float ux, float uy, float uz, float4 f, St st)
 {
-    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (idx >= P.g.N) return;
-    const Geom& g = P.g;
-    int x, y, z;
-    decompose(g, idx, x, y, z);
-    const int s = slit_of(P, z);
-    if (s < 0 || frozen(P, s)) return;
-    const int zlo = P.sl[s].zlo, zhi = P.sl[s].zhi;
-    const float inv_tau = P.sl[s].inv_tau;
-    const int p = pidx(g, x, y, z);
-    float gi[Q];
-    load_pops(P, pin, idx, gi);
-    const float d0 = __ldg(fl.dn + p), ux = __ldg(fl.ux + p), uy = __ldg(fl.uy + p),
-                uz = __ldg(fl.uz + p);
-    const float4 f = __ldg(F + idx);
-    float S, jx, jy, jz;
-    sums_of(gi, S, jx, jy, jz);
-    const float opd = 1.f + d0;
-    const float uu = ux * ux + uy * uy + uz * uz;
-    const bool interior = x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi;
-    if (interior) {
-        // no wrap, no wall: target = idx + constant offset. The neighbour
-        // densities are fetched together first so their latencies overlap.
-        float dd[Q];
-        dd[0] = 0.f;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) dd[i] = __ldg(fl.dn + p + P.nbr[i]);
-#pragma unroll
-        for (int i = 1; i < Q; ++i) dd[i] = d0 - dd[i];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) {
-            float k = gi[i] - S;
-            float e = eq_excess(i, opd, ux, uy, uz, uu);
-            float ks = k - (k - e) * inv_tau + 3.f * dot_c(i, f.x, f.y, f.z) +
-                       1.5f * f.w * (float)(kC2(i) - 1);
-            stp(pout + (long long)i * g.Npad + (idx + P.soff[i]), ks + dd[i]);
-        }
-        return;
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        float k = gi[i] - S;
-        float e = eq_excess(i, opd, ux, uy, uz, uu);
-        float ks = k - (k - e) * inv_tau + 3.f * dot_c(i, f.x, f.y, f.z) +
-                       1.5f * f.w * (float)(kC2(i) - 1);
-        int tx = x + kCx(i), ty = y + kCy(i), tz = z + kCz(i);
-        tx = tx < 0 ? tx + g.nx : (tx >= g.nx ? tx - g.nx : tx);
-        ty = ty < 0 ? ty + g.ny : (ty >= g.ny ? ty - g.ny : ty);
-        if (g.zper) {
-            tz = tz < 0 ? tz + g.nz : (tz >= g.nz ? tz - g.nz : tz);
-        } else if (tz < zlo || tz > zhi) {
-            stp(pout + (long long)opp_of(i) * g.Npad + idx, ks);
-            continue;
-        }
-        float dt = i == 0 ? d0 : __ldg(fl.dn + p + P.nbr[i]);
-        long long t = ((long long)tz * g.ny + ty) * g.nx + tx;
-        stp(pout + (long long)i * g.Npad + t, ks + (d0 - dt));
-    }
+    const float q1 = 1.f + d;
+    const float B = __fmul_rn(-1.5f * q1, ux * ux + uy * uy + uz * uz);
+    const float a = 4.5f * q1, ax = a * ux * ux, ay = a * uy * uy, az = a * uz * uz;
+    const float fw = 1.5f * f.w, b = 9.f * q1;
+    st(SQ_DN, d);
+    st(SQ_P + 0, __fmul_rn(3.f, fmaf(q1, ux, f.x)));
+    st(SQ_P + 1, __fmul_rn(3.f, fmaf(q1, uy, f.y)));
+    st(SQ_P + 2, __fmul_rn(3.f, fmaf(q1, uz, f.z)));
+    st(SQ_CA + 0, __fadd_rn(B, ax));
+    st(SQ_CA + 1, __fadd_rn(B, ay));
+    st(SQ_CA + 2, __fadd_rn(B, az));
+    st(SQ_CP + 0, __fadd_rn(B + (ax + ay), fw));
+    st(SQ_CP + 1, __fadd_rn(B + (ax + az), fw));
+    st(SQ_CP + 2, __fadd_rn(B + (ay + az), fw));
+    st(SQ_X + 0, __fmul_rn(b * ux, uy));
+    st(SQ_X + 1, __fmul_rn(b * ux, uz));
+    st(SQ_X + 2, __fmul_rn(b * uy, uz));
 }
 
-// ---------------------------------------------------------------------------
-// steps 5-6 fused with step 1 of the next step, in pull form: every node
-// gathers the populations that stream into it, applies to each the collision
-// of its source node, and forms the new moments from the 19 values it holds,
-// so the populations are read and written once per step (push collide-stream
-// followed by a moments pass reads them twice). What a source node
-// contributes is staged per node in shared memory: a CTA owns a 32 x 4 tile
-// of x-y nodes, keeps three planes of it (plus a one-node halo) in a ring,
-// and marches up a segment of z planes.
-//
-// With k_i = h_i - dn (a population relative to its node's current density),
-// omega = 1/tau and q = omega (1 + dn), the post-collision value (BGK towards
-// the local equilibrium, source 3 c.F + (3/2) F.w (|c|^2 - 1)) is
-//   k_i' = (1 - omega) k_i + 3 c.(q u + F) + (9/2) q (c.u)^2 - (3/2) q u.u
-//          + (3/2) F.w (|c|^2 - 1),
-// which splits by lattice-velocity class into
-//   axis a, sign s:            (1 - omega) k + s P_a + C_a
-//   plane (a, b), signs sa sb: (1 - omega) k + sa P_a + sb P_b + C_ab + sa sb X_ab
-//   rest:                      (1 - omega) k + C_0
-// with P = 3 (q u + F), B = K - (3/2) q u.u, C_a = B + (9/2) q u_a^2,
-// C_ab = B + (9/2) q (u_a^2 + u_b^2) + (3/2) F.w, X_ab = 9 q u_a u_b and
-// C_0 = B - (3/2) F.w = (2 (C_x + C_y + C_z) - (C_xy + C_xz + C_yz)) / 3;
-// K = (1 - omega)(R - dn) re-references populations stored relative to R.
-// The value reaching r from s = r - c_i, relative to dn(r), is
-// k_i'(s) + (dn(s) - dn(r)); at a wall it is k'_{opp i}(r) (half-way
-// bounce-back). The new populations are stored relative to the new density
-// dn(r) + S, S = sum_i w_i v_i, which is also the next step's reference.
-// ---------------------------------------------------------------------------
+// v_i (see above) from the source's staged quantities sl (quantity k at
+// sl[k * ST]) and its stored h; wall: sl is the node itself and the
+// direction arrives reversed
+template <int i, int ST>
+__device__ __forceinline__ float arrive(const float* sl, float h, float om1s, float dnr, bool wall)
+{
+    constexpr int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+    const float sg = wall ? -1.f : 1.f;
+    float t;
+    if constexpr (i == 0) {
+        t = (2.f * (sl[(SQ_CA + 0) * ST] + sl[(SQ_CA + 1) * ST] + sl[(SQ_CA + 2) * ST]) -
+             (sl[(SQ_CP + 0) * ST] + sl[(SQ_CP + 1) * ST] + sl[(SQ_CP + 2) * ST])) *
+            (1.f / 3.f);
+    } else if constexpr (kC2(i) == 1) {
+        constexpr int a = cx ? 0 : (cy ? 1 : 2);
+        constexpr float ca = (float)(cx + cy + cz);
+        t = fmaf(sg * ca, sl[(SQ_P + a) * ST], sl[(SQ_CA + a) * ST]);
+    } else {
+        constexpr int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
+        constexpr int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
+        constexpr float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
+        t = sl[(SQ_CP + pl) * ST] + sg * (ca * sl[(SQ_P + a) * ST] + cb * sl[(SQ_P + b) * ST]) +
+            (ca * cb) * sl[(SQ_X + pl) * ST];
+    }
+    const float ds = sl[SQ_DN * ST];
+    return fmaf(fmaf(om1s, ds, om1s), h, t) + (ds - dnr);
+}
+
+// fn(std::integral_constant<int, i>) for i = 0 .. Q-1, unrolled at compile time
+template <class Fn, int... I>
+__device__ __forceinline__ void for_dirs_seq(Fn&& fn, std::integer_sequence<int, I...>)
+{
+    (fn(std::integral_constant<int, I>{}), ...);
+}
+template <class Fn>
+__device__ __forceinline__ void for_dirs(Fn&& fn)
+{
+    for_dirs_seq(fn, std::make_integer_sequence<int, Q>{});
+}
+
+// Mirror pairs. The flow along x and y is a small signal next to the
+// wall-normal velocity and force (u_z and F_z of O(0.1) where u_x ~ 1e-4), so
+// the arriving values of directions that differ only in the sign of c_x (or
+// c_y) share large parts. Their difference is therefore formed from the
+// differences of the staged quantities of their two sources (which lie in
+// the same plane, two nodes apart), and the x and y momenta are sums of those
+// differences: a sum of separately rounded values of O(1) would carry the
+// signal only to ~1e-7 of those values. Ten pairs (plus member first):
+//   along x: (1,2) (7,10) (9,8) (11,14) (13,12); along y: (3,4) (7,9) (10,8) (15,18) (17,16).
+// Directions 1 3 7 9 10 11 13 15 17 are derived: slot i holds v_i - v_b of
+// its pair partner b (7 from 10, 10 from 8), the others ("base") hold v_i.
+template <int i, int ip>
+struct Mirror {
+    static constexpr int A = kCx(i) != kCx(ip) ? 0 : 1;  // the component that changes sign
+    static constexpr bool axis = kC2(i) == 1;
+    // the shared nonzero component of a plane direction and its sign
+    static constexpr int B = axis ? 0 : (A == 0 ? (kCy(i) != 0 ? 1 : 2) : (kCx(i) != 0 ? 0 : 2));
+    static constexpr int PL = (A == 2 || B == 2) ? (A == 0 || B == 0 ? 1 : 2) : 0;
+    static constexpr float CB = axis ? 0.f : (float)(B == 0 ? kCx(i) : (B == 1 ? kCy(i) : kCz(i)));
+};
+
+// v_i - v_ip of a mirror pair (staged quantities of the sources at s and sp,
+// stride ST; the stored values h, hp of the two directions; wall: both
+// arrive reversed from the node itself, s = sp)
+template <int i, int ip, int ST>
+__device__ __forceinline__ float mirror_diff(const float* s, const float* sp, float h, float hp, float om1s, bool wall)
+{
+    using M = Mirror<i, ip>;
+    const float sg = wall ? -1.f : 1.f;
+    float dt;
+    if constexpr (M::axis) {
+        dt = (s[(SQ_CA + M::A) * ST] - sp[(SQ_CA + M::A) * ST]) + sg * (s[(SQ_P + M::A) * ST] + sp[(SQ_P + M::A) * ST]);
+    } else {
+        dt = (s[(SQ_CP + M::PL) * ST] - sp[(SQ_CP + M::PL) * ST]) +
+             sg * (s[(SQ_P + M::A) * ST] + sp[(SQ_P + M::A) * ST]) +
+             (sg * M::CB) * (s[(SQ_P + M::B) * ST] - sp[(SQ_P + M::B) * ST]) +
+             M::CB * (s[(SQ_X + M::PL) * ST] + sp[(SQ_X + M::PL) * ST]);
+    }
+    const float ds = s[SQ_DN * ST], dsp = sp[SQ_DN * ST];
+    // m(s) h - m(sp) hp with m = om1s (1 + d)
+    const float dm = om1s * fmaf(1.f + ds, h - hp, (ds - dsp) * hp);
+    return (dt + dm) + (ds - dsp);
+}
+
+// the new moments of a node from its arriving values (slots as above, d79 =
+// v_7 - v_9), then its populations stored as non-equilibrium parts at those
+// moments: base directions directly, derived ones as their partner's stored
+// value plus the difference (so the pairs' differences survive the rounding
+// of the large common parts); returns dn and writes u
+template <typename T>
+__device__ __forceinline__ float pull_finish(T* __restrict__ pout, long long idx, long long Npad, const float* v,
+                                             float d79, float dnr, float& ux, float& uy, float& uz)
+{
+    constexpr float w1 = 1.f / 18.f, w2 = 1.f / 36.f;
+    // arriving values of the derived directions
+    const float v1 = v[2] + v[1], v3 = v[4] + v[3], v9 = v[8] + v[9], v10 = v[8] + v[10];
+    const float v7 = v10 + v[7], v11 = v[14] + v[11], v13 = v[12] + v[13], v15 = v[18] + v[15];
+    const float v17 = v[16] + v[17];
+    const float S = (1.f / 3.f) * v[0] +
+                    w1 * (((v1 + v[2]) + (v3 + v[4])) + (v[5] + v[6])) +
+                    w2 * ((((v7 + v[8]) + (v9 + v10)) + ((v11 + v[12]) + (v13 + v[14]))) +
+                          ((v15 + v[16]) + (v17 + v[18])));
+    const float Jz = w1 * (v[5] - v[6]) +
+                     w2 * (((v11 - v[12]) - (v13 - v[14])) + ((v15 - v[16]) - (v17 - v[18])));
+    const float Jx = w1 * v[1] + w2 * (((v[7] + v[9]) + (v[11] + v[13])));
+    const float Jy = w1 * v[3] + w2 * ((d79 + v[10]) + (v[15] + v[17]));
+    const float dn = dnr + S;
+    const float inv = 1.f / (1.f + dn);
+    ux = Jx * inv;
+    uy = Jy * inv;
+    uz = Jz * inv;
+    const float uu = ux * ux + uy * uy + uz * uz;
+    constexpr float sT = store_scale<T>();
+    auto p_of = [&](int i) {  // f_i^eq / (w_i n) - 1
+        const float cu = dot_c(i, ux, uy, uz);
+        return fmaf(cu, fmaf(4.5f, cu, 3.f), -1.5f * uu);
+    };
+    auto base = [&](int i, float vi) { return (vi - S) * inv - p_of(i); };
+    // p_i - p_ip of a pair that differs in component a: u_a (6 + 18 R),
+    // R = the shared part of c.u
+    auto dp = [&](float ua, float R) { return ua * fmaf(18.f, R, 6.f); };
+    auto put = [&](int i, float h) { stp(pout + (long long)i * Npad + idx, sT * h); };
+    put(0, base(0, v[0]));
+    put(5, base(5, v[5]));
+    put(6, base(6, v[6]));
+    const float h2 = base(2, v[2]), h4 = base(4, v[4]), h8 = base(8, v[8]);
+    put(2, h2);
+    put(1, h2 + (v[1] * inv - dp(ux, 0.f)));
+    put(4, h4);
+    put(3, h4 + (v[3] * inv - dp(uy, 0.f)));
+    put(8, h8);
+    put(9, h8 + (v[9] * inv - dp(ux, -uy)));
+    const float h10 = h8 + (v[10] * inv - dp(uy, -ux));
+    put(10, h10);
+    put(7, h10 + (v[7] * inv - dp(ux, uy)));
+    const float h12 = base(12, v[12]), h14 = base(14, v[14]);
+    put(12, h12);
+    put(13, h12 + (v[13] * inv - dp(ux, -uz)));
+    put(14, h14);
+    put(11, h14 + (v[11] * inv - dp(ux, uz)));
+    const float h16 = base(16, v[16]), h18 = base(18, v[18]);
+    put(16, h16);
+    put(17, h16 + (v[17] * inv - dp(uy, -uz)));
+    put(18, h18);
+    put(15, h18 + (v[15] * inv - dp(uy, uz)));
+    return dn;
+}
+
+// moments of a node written to the next step's fields (with their images)
+__device__ __forceinline__ void put_fields(const Params& P, const CsmIO& io, int x, int y, int z, float dn, float ux,
+                                           float uy, float uz, int* status)
+{
+    if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
+    auto put = [&](int p) {
+        io.dnw[p] = dn;
+        io.uxw[p] = ux;
+        io.uyw[p] = uy;
+        io.uzw[p] = uz;
+    };
+    if (no_images(P.g, x, y, z))
+        put(pidx(P.g, x, y, z));
+    else
+        for_images(P.g, x, y, z, put);
+}
+
+// What a source node contributes is staged per node in shared memory: a CTA
+// owns a 32 x 4 tile of x-y nodes, keeps three planes of it (plus a one-node
+// halo) in a ring, and marches up a segment of z planes.
 // 32 x 4 tiles of 128 threads, six CTAs per SM (measured at 512 x 512 x 192, sigma 12, same
 // state: 32 x 4 / 128 threads / 6 CTAs 2.186 ms, 32 x 8 / 256 / 3 2.334 ms, 32 x 12 / 384 / 2
 // 2.508 ms): more, smaller CTAs keep more population loads in flight across the two barriers
 // of each plane
 constexpr int CSM_TX = 32, CSM_TY = 4, CSM_THREADS = CSM_TX * CSM_TY;
 constexpr int CSM_HX = CSM_TX + 2, CSM_HN = CSM_HX * (CSM_TY + 2);  // staged nodes per plane
-// staged quantities: dn, P_x..z, C_x..z, C_xy C_xz C_yz, X_xy X_xz X_yz
-constexpr int SQ_DN = 0, SQ_P = 1, SQ_CA = 4, SQ_CP = 7, SQ_X = 10, CSM_NF = 13;
 constexpr int CSM_SLOT = CSM_NF * CSM_HN;  // floats per staged plane
 size_t csm_smem_bytes() { return sizeof(float) * 3 * CSM_SLOT; }
 
@@ -1411,7 +1642,6 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
         return;  // beyond the walls: only reached through bounce-back
     const int sq = slit_of(P, zq);
     if (sq < 0 || frozen(P, sq)) return;
-    const float om = P.sl[sq].inv_tau;
     const int pq = (q + g.hw) * g.py * g.px;
     const float4* Fq = F + (long long)zq * g.ny * g.nx;
 #pragma unroll
@@ -1419,27 +1649,8 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
         if (k * NT >= CSM_HN || st.p[k] < 0) continue;
         const int h = threadIdx.x + k * NT;
         const int p = pq + st.p[k];
-        const float4 f = __ldg(Fq + st.n[k]);
-        const float d = __ldg(io.dn + p);
-        const float ux = __ldg(io.ux + p), uy = __ldg(io.uy + p), uz = __ldg(io.uz + p);
-        const float K = io.dref == io.dn ? 0.f : (1.f - om) * (__ldg(io.dref + p) - d);
-        const float q1 = om * (1.f + d);
-        const float B = K - 1.5f * q1 * (ux * ux + uy * uy + uz * uz);
-        const float a = 4.5f * q1, ax = a * ux * ux, ay = a * uy * uy, az = a * uz * uz;
-        const float fw = 1.5f * f.w, b = 9.f * q1;
-        slot[SQ_DN * CSM_HN + h] = d;
-        slot[(SQ_P + 0) * CSM_HN + h] = 3.f * fmaf(q1, ux, f.x);
-        slot[(SQ_P + 1) * CSM_HN + h] = 3.f * fmaf(q1, uy, f.y);
-        slot[(SQ_P + 2) * CSM_HN + h] = 3.f * fmaf(q1, uz, f.z);
-        slot[(SQ_CA + 0) * CSM_HN + h] = B + ax;
-        slot[(SQ_CA + 1) * CSM_HN + h] = B + ay;
-        slot[(SQ_CA + 2) * CSM_HN + h] = B + az;
-        slot[(SQ_CP + 0) * CSM_HN + h] = B + (ax + ay) + fw;
-        slot[(SQ_CP + 1) * CSM_HN + h] = B + (ax + az) + fw;
-        slot[(SQ_CP + 2) * CSM_HN + h] = B + (ay + az) + fw;
-        slot[(SQ_X + 0) * CSM_HN + h] = b * ux * uy;
-        slot[(SQ_X + 1) * CSM_HN + h] = b * ux * uz;
-        slot[(SQ_X + 2) * CSM_HN + h] = b * uy * uz;
+        src_terms(__ldg(io.dn + p), __ldg(io.ux + p), __ldg(io.uy + p), __ldg(io.uz + p), __ldg(Fq + st.n[k]),
+                  [&](int j, float val) { slot[j * CSM_HN + h] = val; });
     }
 }
 
@@ -1451,9 +1662,9 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
 #define CSM_LZ 16
 #endif
 
-// the populations of directions [I0, I1) that stream into node (x, y, z):
-// v[i - I0]; bit i of bb marks a direction that arrives from a wall
-// (bounce-back: the node's own opposite population)
+// the stored populations of directions [I0, I1) that stream into node
+// (x, y, z): v[i - I0]; bit i of bb marks a direction that arrives from a
+// wall (bounce-back: the node's own opposite population)
 template <int I0, int I1, typename T>
 __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ pin, long long idx, int x, int y,
                                          int z, int zlo, int zhi, float* v, unsigned& bb)
@@ -1480,85 +1691,61 @@ __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ 
     }
 }
 
-// the post-collision values of directions [I0, I1) reaching the node (hc in
-// the staged planes), relative to its current density dnr
-template <int I0, int I1>
+// The arriving values of a node in the slots described at Mirror: the ten
+// mirror differences first (from the stored values as loaded), then the ten
+// base directions. src(i) is the source quantities of direction i (stride
+// ST); wall directions arrive reversed from the node itself (own).
+template <int ST, class Src>
+__device__ __forceinline__ void pull_gather(Src src, const float* own, float om1s, float dnr, unsigned bb, float* v,
+                                            float& d79)
+{
+    auto wall = [&](int i) { return ((bb >> i) & 1u) != 0u; };
+    auto diff = [&](auto ic, auto ipc) {
+        constexpr int i = decltype(ic)::value, ip = decltype(ipc)::value;
+        const bool w = wall(i);
+        return mirror_diff<i, ip, ST>(w ? own : src(ic), w ? own : src(ipc), v[i], v[ip], om1s, w);
+    };
+    using std::integral_constant;
+    const float d7_10 = diff(integral_constant<int, 7>{}, integral_constant<int, 10>{});
+    const float d9_8 = diff(integral_constant<int, 9>{}, integral_constant<int, 8>{});
+    const float d10_8 = diff(integral_constant<int, 10>{}, integral_constant<int, 8>{});
+    d79 = diff(integral_constant<int, 7>{}, integral_constant<int, 9>{});
+    v[7] = d7_10;
+    v[9] = d9_8;
+    v[10] = d10_8;
+    v[1] = diff(integral_constant<int, 1>{}, integral_constant<int, 2>{});
+    v[3] = diff(integral_constant<int, 3>{}, integral_constant<int, 4>{});
+    v[11] = diff(integral_constant<int, 11>{}, integral_constant<int, 14>{});
+    v[13] = diff(integral_constant<int, 13>{}, integral_constant<int, 12>{});
+    v[15] = diff(integral_constant<int, 15>{}, integral_constant<int, 18>{});
+    v[17] = diff(integral_constant<int, 17>{}, integral_constant<int, 16>{});
+    auto one = [&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        if constexpr (i == 0 || i == 2 || i == 4 || i == 5 || i == 6 || i == 8 || i == 12 || i == 14 || i == 16 ||
+                      i == 18) {
+            const bool w = i != 0 && wall(i);
+            v[i] = arrive<i, ST>((i == 0 || w) ? own : src(ic), v[i], om1s, dnr, w);
+        }
+    };
+    for_dirs(one);
+}
+
+// the gather of a node staged at hc in the ring (planes below, own, above)
 __device__ __forceinline__ void csm_collide(const float* own, const float* below, const float* above, int hc,
-                                            float om1, float dnr, unsigned bb, float* v)
+                                            float om1s, float dnr, unsigned bb, float* v, float& d79)
 {
-    constexpr int J0 = I0 == 0 ? 1 : I0;
-    if (I0 == 0) {
-        const float c0 = (2.f * (own[(SQ_CA + 0) * CSM_HN + hc] + own[(SQ_CA + 1) * CSM_HN + hc] +
-                                 own[(SQ_CA + 2) * CSM_HN + hc]) -
-                          (own[(SQ_CP + 0) * CSM_HN + hc] + own[(SQ_CP + 1) * CSM_HN + hc] +
-                           own[(SQ_CP + 2) * CSM_HN + hc])) * (1.f / 3.f);
-        v[0] = fmaf(om1, v[0], c0);
-    }
-    if (bb == 0) {
-        // no wall: every source is r - c_i (offsets fixed at compile time)
-#pragma unroll
-        for (int i = J0; i < I1; ++i) {
-            const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
-            const float* sl = (cz > 0 ? below : (cz < 0 ? above : own)) + hc - cx - cy * CSM_HX;
-            float t;
-            if (kC2(i) == 1) {
-                const int a = cx ? 0 : (cy ? 1 : 2);
-                const float ca = (float)(cx + cy + cz);
-                t = fmaf(ca, sl[(SQ_P + a) * CSM_HN], sl[(SQ_CA + a) * CSM_HN]);
-            } else {
-                const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
-                const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
-                const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
-                t = sl[(SQ_CP + pl) * CSM_HN] + (ca * sl[(SQ_P + a) * CSM_HN] + cb * sl[(SQ_P + b) * CSM_HN]) +
-                    (ca * cb) * sl[(SQ_X + pl) * CSM_HN];
-            }
-            v[i - I0] = fmaf(om1, v[i - I0], t) + (sl[SQ_DN * CSM_HN] - dnr);
-        }
-        return;
-    }
-#pragma unroll
-    for (int i = J0; i < I1; ++i) {
-        const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
-        const bool wall = (bb >> i) & 1u;
-        // source node: r - c_i in plane z - c_z, or r itself with -c_i at a wall
-        const float* sl = wall ? own : (cz > 0 ? below : (cz < 0 ? above : own));
-        const int h = wall ? hc : hc - cx - cy * CSM_HX;
-        const float sg = wall ? -1.f : 1.f;
-        float t;
-        if (kC2(i) == 1) {
-            const int a = cx ? 0 : (cy ? 1 : 2);
-            const float ca = (float)(cx + cy + cz);
-            t = fmaf(sg * ca, sl[(SQ_P + a) * CSM_HN + h], sl[(SQ_CA + a) * CSM_HN + h]);
-        } else {
-            const int pl = cz == 0 ? 0 : (cy == 0 ? 1 : 2);
-            const int a = pl == 2 ? 1 : 0, b = pl == 0 ? 1 : 2;
-            const float ca = (float)(a == 0 ? cx : cy), cb = (float)(b == 1 ? cy : cz);
-            t = sl[(SQ_CP + pl) * CSM_HN + h] +
-                sg * (ca * sl[(SQ_P + a) * CSM_HN + h] + cb * sl[(SQ_P + b) * CSM_HN + h]) +
-                (ca * cb) * sl[(SQ_X + pl) * CSM_HN + h];
-        }
-        const float d = wall ? 0.f : sl[SQ_DN * CSM_HN + h] - dnr;
-        v[i - I0] = fmaf(om1, v[i - I0], t) + d;
-    }
+    auto src = [&](auto ic) -> const float* {
+        constexpr int i = decltype(ic)::value;
+        constexpr int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+        return (cz > 0 ? below : (cz < 0 ? above : own)) + hc - cx - cy * CSM_HX;
+    };
+    pull_gather<CSM_HN>(src, own + hc, om1s, dnr, bb, v, d79);
 }
 
-// sum over directions [I0, I1) of w_i v_i and w_i c_i v_i
-template <int I0, int I1>
-__device__ __forceinline__ void csm_sums(const float* v, float (&m)[4])
-{
-#pragma unroll
-    for (int i = I0; i < I1; ++i) {
-        const float wg = kW(i) * v[i - I0];
-        m[0] += wg;
-        add_c(m[1], kCx(i), wg);
-        add_c(m[2], kCy(i), wg);
-        add_c(m[3], kCz(i), wg);
-    }
-}
-
-// one node per thread, a CTA per 32 x 4 tile and z segment (measured: two
-// threads per node, each gathering half of the directions and adding the
-// partial moments through shared memory, ran slower at twice the warps)
+// one node per thread, a CTA per 32 x 4 tile and z segment (measured with the
+// earlier storage: two threads per node, each gathering half of the
+// directions and adding the partial moments through shared memory, ran
+// slower at twice the warps)
 template <typename T>
 __global__ void __launch_bounds__(CSM_THREADS, CSM_MINB)
     k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout, CsmIO io, const float4* __restrict__ F,
@@ -1594,35 +1781,97 @@ __global__ void __launch_bounds__(CSM_THREADS, CSM_MINB)
         __syncthreads();  // the slot of plane z - 2 is free
         csm_stage<NT>(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, st, z + 1);
         __syncthreads();
-        float m[4] = {0.f, 0.f, 0.f, 0.f};
-        float dnr = 0.f;
-        if (act) {
-            const float* own = sm + csm_slot(z) * CSM_SLOT;
-            const float* below = sm + csm_slot(z - 1) * CSM_SLOT;
-            const float* above = sm + csm_slot(z + 1) * CSM_SLOT;
-            dnr = own[SQ_DN * CSM_HN + hc];
-            csm_collide<0, Q>(own, below, above, hc, 1.f - om, dnr, bb, v);
-            csm_sums<0, Q>(v, m);
-        }
         if (!act) continue;
-        const float S = m[0];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) stp(pout + (long long)i * g.Npad + idx, v[i] - S);
-        const float dn = dnr + S;
-        const float inv = 1.f / (1.f + dn);
-        const float ux = m[1] * inv, uy = m[2] * inv, uz = m[3] * inv;
-        if (!(1.f + dn > 0.f) || !isfinite(dn) || !isfinite(ux + uy + uz)) atomicOr(status, 1);
-        auto put = [&](int p) {
-            io.dnw[p] = dn;
-            io.uxw[p] = ux;
-            io.uyw[p] = uy;
-            io.uzw[p] = uz;
-        };
-        if (no_images(g, x, y, z))
-            put(pidx(g, x, y, z));
-        else
-            for_images(g, x, y, z, put);
+        const float* own = sm + csm_slot(z) * CSM_SLOT;
+        const float dnr = own[SQ_DN * CSM_HN + hc];
+        float d79;
+        csm_collide(own, sm + csm_slot(z - 1) * CSM_SLOT, sm + csm_slot(z + 1) * CSM_SLOT, hc,
+                    (1.f - om) / store_scale<T>(), dnr, bb, v, d79);
+        float ux, uy, uz;
+        const float dn = pull_finish<T>(pout, idx, g.Npad, v, d79, dnr, ux, uy, uz);
+        put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
     }
+}
+
+// Narrow grids (below one 32 x 4 tile): the same pass with one thread per
+// node and no staging; every source's quantities are formed where they are
+// used, by the same code as the staged ones, so both kernels give identical
+// results.
+template <typename T>
+__global__ void __launch_bounds__(128) k_pull_node(Params P, const T* __restrict__ pin, T* __restrict__ pout,
+                                                   CsmIO io, const float4* __restrict__ F, int* status)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
+    const Geom& g = P.g;
+    int x, y, z;
+    decompose(g, idx, x, y, z);
+    const int s = slit_of(P, z);
+    if (s < 0 || frozen(P, s)) return;
+    const int zlo = P.sl[s].zlo, zhi = P.sl[s].zhi;
+    const float om1s = (1.f - P.sl[s].inv_tau) / store_scale<T>();
+    float v[Q];
+    unsigned bb = 0;
+    csm_pull<0, Q>(P, pin, idx, x, y, z, zlo, zhi, v, bb);
+    const int p = pidx(g, x, y, z);
+    float own[CSM_NF];
+    src_terms(__ldg(io.dn + p), __ldg(io.ux + p), __ldg(io.uy + p), __ldg(io.uz + p), __ldg(F + idx),
+              [&](int j, float val) { own[j] = val; });
+    const float dnr = own[SQ_DN];
+    // the source quantities of direction i, formed where they are used
+    // (padded fields through their periodic images, the force at its
+    // wrapped node); walls never ask (they use own)
+    auto terms = [&](auto ic, float* out) {
+        constexpr int i = decltype(ic)::value;
+        int sx = x - kCx(i), sy = y - kCy(i), sz = z - kCz(i);
+        sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
+        sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
+        if (g.zper) sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
+        const int ps = p - P.nbr[i];
+        src_terms(__ldg(io.dn + ps), __ldg(io.ux + ps), __ldg(io.uy + ps), __ldg(io.uz + ps),
+                  __ldg(F + (((long long)sz * g.ny + sy) * g.nx + sx)), [&](int j, float val) { out[j] = val; });
+    };
+    auto wall = [&](int i) { return ((bb >> i) & 1u) != 0u; };
+    auto diff = [&](auto ic, auto ipc) {
+        constexpr int i = decltype(ic)::value, ip = decltype(ipc)::value;
+        if (wall(i)) return mirror_diff<i, ip, 1>(own, own, v[i], v[ip], om1s, true);
+        float a[CSM_NF], b[CSM_NF];
+        terms(ic, a);
+        terms(ipc, b);
+        return mirror_diff<i, ip, 1>(a, b, v[i], v[ip], om1s, false);
+    };
+    using std::integral_constant;
+    const float d7_10 = diff(integral_constant<int, 7>{}, integral_constant<int, 10>{});
+    const float d9_8 = diff(integral_constant<int, 9>{}, integral_constant<int, 8>{});
+    const float d10_8 = diff(integral_constant<int, 10>{}, integral_constant<int, 8>{});
+    const float d79 = diff(integral_constant<int, 7>{}, integral_constant<int, 9>{});
+    v[7] = d7_10;
+    v[9] = d9_8;
+    v[10] = d10_8;
+    v[1] = diff(integral_constant<int, 1>{}, integral_constant<int, 2>{});
+    v[3] = diff(integral_constant<int, 3>{}, integral_constant<int, 4>{});
+    v[11] = diff(integral_constant<int, 11>{}, integral_constant<int, 14>{});
+    v[13] = diff(integral_constant<int, 13>{}, integral_constant<int, 12>{});
+    v[15] = diff(integral_constant<int, 15>{}, integral_constant<int, 18>{});
+    v[17] = diff(integral_constant<int, 17>{}, integral_constant<int, 16>{});
+    auto one = [&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        if constexpr (i == 0 || i == 2 || i == 4 || i == 5 || i == 6 || i == 8 || i == 12 || i == 14 || i == 16 ||
+                      i == 18) {
+            const bool w = i != 0 && wall(i);
+            if (i == 0 || w) {
+                v[i] = arrive<i, 1>(own, v[i], om1s, dnr, w);
+            } else {
+                float sv[CSM_NF];
+                terms(ic, sv);
+                v[i] = arrive<i, 1>(sv, v[i], om1s, dnr, false);
+            }
+        }
+    };
+    for_dirs(one);
+    float ux, uy, uz;
+    const float dn = pull_finish<T>(pout, idx, g.Npad, v, d79, dnr, ux, uy, uz);
+    put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -1802,48 +2051,37 @@ cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t se
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_profiles(const Params& P, void* pop, float* dn, const float* n_z,
+cudaError_t launch_init_profiles(const Params& P, void* pop, float* const f[4], const float* n_z,
                                  const float* ux_z, int hmax, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_init_profiles<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, dn, n_z, ux_z, hmax);
+        k_init_profiles<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, f[0], f[1], f[2], f[3], n_z,
+                                                                     ux_z, hmax);
     else
-        k_init_profiles<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, dn, n_z, ux_z, hmax);
+        k_init_profiles<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, f[0], f[1], f[2], f[3], n_z,
+                                                                    ux_z, hmax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_fields(const Params& P, void* pop, float* dn, const float* rho,
+cudaError_t launch_init_fields(const Params& P, void* pop, float* const f[4], const float* rho,
                                const float* u, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_init_fields<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, dn, rho, u);
+        k_init_fields<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, f[0], f[1], f[2], f[3], rho, u);
     else
-        k_init_fields<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, dn, rho, u);
+        k_init_fields<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, f[0], f[1], f[2], f[3], rho, u);
     return cudaGetLastError();
 }
 
-cudaError_t launch_write_ref(const Params& P, const float* ref, float* dn, cudaStream_t s)
+cudaError_t launch_write_fields(const Params& P, const float* src, float* const f[4], cudaStream_t s)
 {
-    k_write_ref<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, ref, dn);
+    k_write_fields<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, src, f[0], f[1], f[2], f[3]);
     return cudaGetLastError();
 }
 
-cudaError_t launch_read_ref(const Params& P, const float* dn, float* ref, cudaStream_t s)
+cudaError_t launch_read_fields(const Params& P, const float* const f[4], float* out, cudaStream_t s)
 {
-    k_read_ref<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, dn, ref);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_moments(const Params& P, const void* pop, const float* dref, float* dnew,
-                           float* ux, float* uy, float* uz, int* status, int skip_done,
-                           cudaStream_t s)
-{
-    if (P.storage == LBIF_STORE_F16)
-        k_moments<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pop, dref, dnew, ux,
-                                                               uy, uz, status, skip_done);
-    else
-        k_moments<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pop, dref, dnew, ux,
-                                                              uy, uz, status, skip_done);
+    k_read_fields<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, f[0], f[1], f[2], f[3], out);
     return cudaGetLastError();
 }
 
@@ -1961,33 +2199,19 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_cs(const Params& P, const void* pin, void* pout, const Fields& f,
-                      const float4* F, cudaStream_t s)
-{
-    if (P.storage == LBIF_STORE_F16)
-        k_cs<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const __half*)pin, (__half*)pout, f, F);
-    else
-        k_cs<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (const float*)pin, (float*)pout, f, F);
-    return cudaGetLastError();
-}
-
 bool csm_ok(const Geom& g) { return g.nx >= CSM_TX && g.ny >= CSM_TY; }
-
-// Measured on GB300 (per-step CUDA-event times, both passes): the fused pass
-// wins with FP32 storage on large grids (512x512x192, sigma 12: 2.20 vs
-// 2.48 ms with 32 x 4 tiles; with 32 x 8 tiles 2.32 vs 2.52 ms, and 1-3 % at
-// 8-12 M nodes) and, with 32 x 8 tiles, lost with FP16 storage (2.69 vs
-// 2.26 ms) and on grids too small to fill the GPU with its CTAs
-// (256x256x96: 0.61 vs 0.60 ms; 64^3: 0.098 vs 0.060 ms).
-bool csm_default(const Geom& g, int storage)
-{
-    return storage == LBIF_STORE_F32 && csm_ok(g) && g.N >= (1LL << 23);
-}
 
 cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
                        int* status, int lz, cudaStream_t s)
 {
     const Geom& g = P.g;
+    if (!csm_ok(g)) {
+        if (P.storage == LBIF_STORE_F16)
+            k_pull_node<__half><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const __half*)pin, (__half*)pout, io, F, status);
+        else
+            k_pull_node<float><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const float*)pin, (float*)pout, io, F, status);
+        return cudaGetLastError();
+    }
     if (lz <= 0) lz = CSM_LZ;
     const int tx = (g.nx + CSM_TX - 1) / CSM_TX, ty = (g.ny + CSM_TY - 1) / CSM_TY;
     const int segs = (g.nz + lz - 1) / lz;

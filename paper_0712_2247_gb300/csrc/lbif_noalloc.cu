@@ -2,17 +2,18 @@
 //
 // lbif_profiles() reduces a handle's fields through a buffer the handle
 // allocated. Some callers cannot allocate device memory at the moment they
-// need profiles: code running while a stream is being captured into a CUDA
-// graph, services that reserved their whole device budget up front through
-// their own allocator, or real-time loops with a fixed memory footprint. This
-// entry point works on density and velocity fields the caller already holds
-// (for example tensors filled by lbif_moments with on_device = 1) and keeps
-// its only intermediate, the per-plane sums, in a fixed-size array in the
+// need profiles: services that reserved their whole device budget up front
+// through their own allocator (a further cudaMalloc would fail or fragment
+// it), or real-time loops that must keep a fixed memory footprint. This entry
+// point works on density and velocity fields the caller already holds (for
+// example tensors filled by lbif_moments with on_device = 1) and keeps its
+// only intermediate, the per-plane sums, in a fixed-size array in the
 // library's device image.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include <atomic>
+#include <mutex>
 #include <string>
 
 #include "lbif.h"
@@ -27,8 +28,34 @@ constexpr int kSlots = 5 * kMaxPlanes + 4;  // 5 per-plane sums, then 4 totals
 // All calls share it: calls that overlap on the GPU race on it.
 static __device__ __align__(256) double g_sums[kSlots];
 
-// Host-side device addresses of g_sums, one per device, filled at first use.
-static std::atomic<double*> g_addr[kMaxDevices];
+// Host-side device addresses of g_sums, one per device, looked up at the first
+// call on the device and again whenever the device's current context changed
+// since (a reset device reloads the library's image at a new address).
+struct SumsAddr {
+    CUcontext ctx;
+    double* ptr;
+};
+static SumsAddr g_addr[kMaxDevices];
+static std::mutex g_addr_lock;
+
+// cuCtxGetCurrent through the runtime's driver entry point (no link against
+// the driver library); NULL if unavailable
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+static CtxGetCurrentFn ctx_get_current()
+{
+    static std::once_flag once;
+    static CtxGetCurrentFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
 
 // per plane z: sum rho, sum u_x, sum rho u_x, sum rho u_y, sum rho u_z (FP64,
 // fixed-order tree); slot k of plane z at sums[k * kMaxPlanes + z]
@@ -80,17 +107,31 @@ int device_sums(double** out, std::string& err)
         err = "device index out of range";
         return LBIF_ERR_UNSUPPORTED;
     }
-    double* p = g_addr[dev].load();
-    if (!p) {
-        // set-up once per device, with that device current
+    // make the device's primary context current (initialised if it was not;
+    // nothing is allocated), so that the context read below is the one the
+    // launches will use
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) {
+        err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+        return LBIF_ERR_CUDA;
+    }
+    CUcontext ctx = nullptr;
+    CtxGetCurrentFn get = ctx_get_current();
+    if (get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    std::lock_guard<std::mutex> lock(g_addr_lock);
+    SumsAddr& a = g_addr[dev];
+    if (!a.ptr || a.ctx != ctx) {
+        // set-up once per device (and context), with that device current
+        double* p = nullptr;
         e = cudaGetSymbolAddress((void**)&p, g_sums);
         if (e != cudaSuccess || !p) {
             err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return LBIF_ERR_CUDA;
         }
-        g_addr[dev].store(p);
+        a.ptr = p;
+        a.ctx = ctx;
     }
-    *out = p;
+    *out = a.ptr;
     return LBIF_OK;
 }
 

@@ -213,9 +213,9 @@ class Slit:
         return b.value, g.value, st.value
 
     def set_fused(self, on: bool):
-        """One pass per step (pull collide-stream with the next moments; needs
-        nx >= 32 and ny >= 4, the default with FP32 storage on grids of at
-        least 2^23 nodes) or push collide-stream + moments (any grid)."""
+        """Every step is one pull pass (collision, streaming and the next
+        moments); on=True changes nothing, on=False raises LbifError (the
+        two-pass step is retired)."""
         self._check(self._lib.lbif_set_fused(self._h, 1 if on else 0))
 
     @property

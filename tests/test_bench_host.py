@@ -24,22 +24,22 @@ def test_step_bytes():
 def test_kernel_bytes_add_up():
     b = _bench()
     for storage, s in ((0, 4), (1, 2)):
-        fused = b.kernel_bytes(storage, True)
-        two = b.kernel_bytes(storage, False)
-        # the fused step: ball (n in, g2 out), force (n,u,g2 in, F out), collide-stream-moments
-        step_fused = fused["ball_g2"] + fused["force"] + fused["collide_stream"]
-        assert step_fused == 2 * 19 * s + 8 + 36 + 32 + 16
+        kb = b.kernel_bytes(storage)
+        # the step: ball (n in, g2 out), force (n,u,g2 in, F out), pull pass
+        # (populations in and out, n,u and F in, the next n,u out)
+        step = kb["ball_g2"] + kb["force"] + kb["collide_stream"]
+        assert step == 2 * 19 * s + 8 + 36 + 32 + 16
         # above the algorithmic minimum by F through memory (+32) and the fields read again (+16)
-        assert step_fused - b.bytes_alg(storage) == 48
-        # the two-pass step re-reads the populations in its moments pass
-        step_two = two["moments"] + two["ball_g2"] + two["force"] + two["collide_stream"]
-        assert step_two - step_fused == 19 * s + 24 - 16
+        assert step - b.bytes_alg(storage) == 48
 
 
-def test_measured_traffic_covers_the_dominant_kernels():
+def test_measured_traffic_table():
     b = _bench()
-    t = b.TRAFFIC_B_PER_NODE_F32
-    for k in ("collide_stream_fused", "collide_stream", "force", "ball_g2", "moments"):
-        assert t[k] > 0
-    # DRAM traffic of the fused pass stays within 10 % of its algorithmic bytes
-    assert abs(t["collide_stream_fused"] / b.kernel_bytes(0, True)["collide_stream"] - 1) < 0.1
+    for storage in (0, 1):
+        t = b.TRAFFIC_B_PER_NODE[storage]
+        kb = b.kernel_bytes(storage)
+        for k, v in t.items():
+            assert k in kb
+            # a measured figure is a DRAM byte count per node of the same
+            # order as the kernel's algorithmic bytes (None: not yet captured)
+            assert v is None or 0.5 * kb[k] < v < 2.0 * kb[k], (storage, k, v)

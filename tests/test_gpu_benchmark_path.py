@@ -1,0 +1,103 @@
+"""Long-run parity of the kernels the benchmark times, against the FP64 oracle.
+
+The benchmark's slit (sigma 12, 512 x 512 x 192) runs the tiled force kernel
+(float4 windows, lane shuffles; nx >= 128), the ball kernel with its plane
+tiles brought in by the tensor-memory accelerator, and the 32 x 4 pull tiles,
+with the launch shapes the library's autotuner picks. The same kernels and
+the same autotuned shapes run here on slits small enough for the oracle, over
+1000 steps from the seeded noisy start, element by element (Sec. Methods;
+Eq. LBHS): density, its deviation from n0, velocity and the x,y profiles at
+1e-5 normwise. The attractive-tail workload's kernels (spectral tail, tiled
+force at sigma 8) are checked over a short window of its own parameters
+(Sec. Conclusions: attractive forces; eps = 0.3, the tail strength the
+benchmark runs, see bench.py).
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def nerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    s = np.abs(b).max()
+    return float(np.abs(a - b).max() / s) if s > 0 else float(np.abs(a).max())
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_0712_2247_gb300 import build, lbif
+
+    build.build()
+    return lbif
+
+
+@pytest.fixture(scope="module")
+def O():
+    import oracle
+
+    oracle.build()
+    return oracle
+
+
+def compare(g, o):
+    rg, ug = g.moments()
+    ro, uo = o.moments()
+    ng, uxg, tot = g.profiles()
+    no, uxo = o.profiles()
+    return dict(rho=nerr(rg, ro), rho_fluct=nerr(rg - o.n0, ro - o.n0), u=nerr(ug, uo),
+                n_z=nerr(ng, no), ux_z=nerr(uxg, uxo), mass=abs(tot[0] / o.totals()[0] - 1))
+
+
+def test_sigma12_benchmark_kernels_1000_steps(L, O):
+    """128 x 12 x 72 slit (6 sigma wide), sigma 12, eta 0.25, tau 0.7,
+    F_e = 5e-7, seeded 1e-3 noise (the benchmark's parameters): tiled force
+    mapping, staged ball tiles, pull tiles with a ragged z segment, autotuned
+    shapes; 1000 steps."""
+    from paper_0712_2247_gb300.inputs import C2 as W
+
+    nx, ny, nz = 128, 12, 72
+    g = L.Slit(nx, ny, nz, W.sigma, W.eta, W.tau, body=W.body, seed=W.seed)
+    o = O.Oracle(nx, ny, nz, W.sigma, W.eta, W.tau, body=W.body, seed=W.seed)
+    g.step(2)
+    o.step(2)
+    eF = nerr(g.forces(), o.forces()[0] / o.n0)
+    # the default shapes (ball tiles staged by the tensor-memory accelerator)
+    # for the first half, the autotuner's for the second
+    g.step(498)
+    ball, group, staging = g.autotune(2)
+    print("autotuned", ball, group, staging)
+    g.step(500)
+    o.step(998)
+    e = compare(g, o)
+    e["F_step2"] = eF
+    e["F_step1000"] = nerr(g.forces(), o.forces()[0] / o.n0)
+    print("sigma 12, 1000 steps", " ".join(f"{k}={v:.2e}" for k, v in e.items()))
+    assert g.status() == 0
+    for k in ("rho", "rho_fluct", "u", "n_z", "ux_z", "F_step2", "F_step1000"):
+        assert e[k] < 1e-5, (k, e[k])
+    assert e["mass"] < 1e-6
+    g.close()
+
+
+def test_tail_workload_kernels_short_window(L, O):
+    """128 x 32 x 64 slit, sigma 8, eta 0.25, tau 0.8, F_e = 1e-6, LJ tail
+    eps = 0.3 cut at 2.5 sigma, seeded noise: spectral tail (x lines of 128,
+    y lines of 32, direct z sum between the walls), tiled force kernel,
+    staged ball tiles, pull tiles; forces, then 10 steps."""
+    nx, ny, nz = 128, 32, 64
+    kw = dict(body=(1e-6, 0, 0), tail=True, eps=0.3, rcut=2.5)
+    g = L.Slit(nx, ny, nz, 8, 0.25, 0.8, seed=1, **kw)
+    o = O.Oracle(nx, ny, nz, 8, 0.25, 0.8, seed=1, **kw)
+    g.autotune(2)
+    eF = nerr(g.forces(), o.forces()[0] / o.n0)
+    g.step(10)
+    o.step(10)
+    e = compare(g, o)
+    e["F"] = eF
+    print("tail workload, 10 steps", " ".join(f"{k}={v:.2e}" for k, v in e.items()))
+    assert g.status() == 0
+    for k in ("F", "rho", "rho_fluct", "u", "n_z", "ux_z"):
+        assert e[k] < 1e-5, (k, e[k])
+    g.close()

@@ -1,12 +1,9 @@
-"""The fused pass (collision, pull streaming and the next step's moments in one
-kernel) against the FP64 oracle, and against the two-pass step.
-
-Both passes compute the same forward-Euler BGK update with the first-order
-source, streaming and half-way bounce-back (Sec. Methods); they differ only in
-the order of FP32 roundings, so each is held to the oracle at the tolerances
-of the two-pass tests (1e-5 normwise, FP32) and to the other at a few FP32
-ulps of the state. Shapes span several 32 x 4 tiles with ragged tails in x and
-y, z segments of the marching CTAs, walls and periodic z.
+"""The pull pass (collision, pull streaming and the next step's moments in one
+kernel) against the FP64 oracle: the forward-Euler BGK update with the
+first-order source, streaming and half-way bounce-back (Sec. Methods), held to
+1e-5 normwise (FP32). Shapes span several 32 x 4 tiles with ragged tails in x
+and y, z segments of the marching CTAs, walls and periodic z; grids narrower
+than one tile run the per-node form of the same arithmetic.
 """
 import numpy as np
 import pytest
@@ -61,7 +58,6 @@ CASES = [
 @pytest.mark.parametrize("shape,sigma,zper", CASES)
 def test_fused_parity(L, O, shape, sigma, zper):
     g, o = pair(L, O, shape, sigma, zper, body=(2e-5, -1e-5, 0.0))
-    g.set_fused(True)
     for n in (1, 40):
         g.step(n)
         o.step(n)
@@ -77,7 +73,6 @@ def test_fused_long_run_1000_steps(L, O):
     """1000 steps of a flowing sigma = 4 slit (one tile column, ragged y)."""
     g = L.Slit(32, 12, 32, 4, 0.25, 1.0, body=(1e-6, 0, 0), seed=5)
     o = O.Oracle(32, 12, 32, 4, 0.25, 1.0, body=(1e-6, 0, 0), seed=5)
-    g.set_fused(True)
     g.step(1000)
     o.step(1000)
     rg, ug = g.moments()
@@ -86,34 +81,25 @@ def test_fused_long_run_1000_steps(L, O):
     no, uxo = o.profiles()
     e = dict(rho=nerr(rg, ro), u=nerr(ug, uo), n_z=nerr(ng, no), ux_z=nerr(uxg, uxo),
              mass=abs(tot[0] / o.totals()[0] - 1))
+    e["rho_fluct"] = nerr(rg - o.n0, ro - o.n0)
     print("fused 1000 steps", e)
-    assert e["rho"] < 1e-5 and e["u"] < 1e-5 and e["n_z"] < 1e-5 and e["ux_z"] < 1e-4
+    assert e["rho"] < 1e-5 and e["u"] < 1e-5 and e["n_z"] < 1e-5 and e["ux_z"] < 1e-5
+    assert e["rho_fluct"] < 1e-5
     assert e["mass"] < 1e-6
 
 
-def test_fused_and_two_pass_agree(L):
-    """The same 200 steps through either pass: equal to FP32 rounding."""
-    kw = dict(body=(1e-5, 0, 0), seed=3)
-    a = L.Slit(48, 16, 28, 4, 0.25, 0.9, **kw)
-    b = L.Slit(48, 16, 28, 4, 0.25, 0.9, **kw)
-    a.set_fused(True)
-    b.set_fused(False)
-    a.step(200)
-    b.step(200)
-    ra, ua = a.moments()
-    rb, ub = b.moments()
-    assert nerr(ra, rb) < 2e-6 and nerr(ua, ub) < 2e-6
-    a.close()
-    b.close()
-
-
-def test_switch_between_passes(L, O):
-    """Fused -> two-pass -> fused across steps, against 90 oracle steps."""
+def test_two_pass_step_is_retired(L, O):
+    """lbif_set_fused(0) is refused (the stored non-equilibrium parts are
+    decoded by the pull pass only); the handle keeps stepping correctly."""
     g, o = pair(L, O, (40, 10, 22), 4, body=(1e-5, 0, 0))
-    for on in (True, False, True):
-        g.set_fused(on)
-        g.step(30)
-    o.step(90)
+    g.step(30)
+    with pytest.raises(L.LbifError) as ex:
+        g.set_fused(False)
+    assert ex.value.code == -6
+    g.set_fused(True)
+    assert g.fused
+    g.step(30)
+    o.step(60)
     rg, ug = g.moments()
     ro, uo = o.moments()
     assert nerr(rg, ro) < 1e-5 and nerr(ug, uo) < 1e-5
@@ -121,7 +107,6 @@ def test_switch_between_passes(L, O):
 
 def test_fused_fp16_storage(L, O):
     g, o = pair(L, O, (40, 12, 30), 4, storage=1, body=(1e-5, 0, 0))
-    g.set_fused(True)
     g.step(40)
     o.step(40)
     rg, ug = g.moments()
@@ -144,7 +129,6 @@ def test_fused_with_options(L, O, extra):
     rho, u = inputs.random_fields((nz, ny, nx), o.n0, 4)
     g.set_fields(rho, u)
     o.init_fields(rho.astype(np.float64), u.astype(np.float64))
-    g.set_fused(True)
     g.step(30)
     o.step(30)
     rg, ug = g.moments()
@@ -153,15 +137,15 @@ def test_fused_with_options(L, O, extra):
 
 
 def test_fused_ensemble_matches_oracle_and_freezes(L, O):
-    """Stacked slits on 32 x 8 rows (two tile rows) through the fused pass: parity per slit,
-    and run-to-steady-state with frozen slits gives the same profiles as the
-    two-pass ensemble to FP32 rounding."""
+    """Stacked slits on 32 x 8 rows (two tile rows): parity per slit; a slit in
+    the stack evolves bit-identically to the same slit alone; and a run to
+    steady state freezes each slit at the step its residual met the
+    tolerance, leaving exactly the state of a lone slit stepped that far."""
     H = np.array([9, 16, 12], np.int32)
     eta = np.array([0.15, 0.25, 0.2])
     F = np.array([2e-6, 1e-6, 5e-6])
     tau = np.array([0.8, 1.0, 0.7])
     e = L.Ensemble(H, eta, F, tau, sigma=4, nx=32, ny=8, storage=0, noise=0.0)
-    e.set_fused(True)
     hmax = int(H.max())
     nz = np.zeros((len(H), hmax), np.float32)
     for s, h in enumerate(H):
@@ -177,27 +161,30 @@ def test_fused_ensemble_matches_oracle_and_freezes(L, O):
         z0 = int(e.zlo[s])
         assert nerr(rho[z0:z0 + h], n_o) < 1e-5, s
         assert nerr(u[:, z0:z0 + h], u_o) < 1e-5, s
-    # a slit in the stack evolves bit-identically to the same slit alone
-    n_g, ux_g = e.slit_profiles(hmax)
-    for s in (0, 2):
+
+    def lone(s, steps):
         h = int(H[s])
         g = L.Slit(32, 8, h, 4, eta[s], tau[s], body=(F[s], 0, 0), noise=0.0)
-        g.set_fused(True)
         g.set_fields(np.repeat(nz[s, :h], 256).reshape(h, 8, 32).astype(np.float32))
-        g.step(50)
+        g.step(steps)
         n1, u1, _ = g.profiles()
-        assert np.array_equal(n1, n_g[s, :h]) and np.array_equal(u1, ux_g[s, :h]), s
         g.close()
+        return n1, u1
+
+    n_g, ux_g = e.slit_profiles(hmax)
+    for s in (0, 2):
+        n1, u1 = lone(s, 50)
+        assert np.array_equal(n1, n_g[s, :int(H[s])]), s
+        assert np.array_equal(u1, ux_g[s, :int(H[s])]), s
     e.close()
 
-    prof = []
-    for fused in (True, False):
-        e = L.Ensemble(H, eta, F, tau, sigma=4, nx=32, ny=8, storage=0, noise=0.0)
-        e.set_fused(fused)
-        e.seed(nz)
-        steps = e.run(tol=1e-7, max_steps=6000, check_every=50, patience=20)
-        assert np.all(steps != -2)
-        prof.append(e.slit_profiles())
-        e.close()
-    (na, ua), (nb, ub) = prof
-    assert nerr(na, nb) < 1e-5
+    e = L.Ensemble(H, eta, F, tau, sigma=4, nx=32, ny=8, storage=0, noise=0.0)
+    e.seed(nz)
+    taken = e.run(tol=1e-7, max_steps=6000, check_every=50, patience=20)
+    print("steps to 1e-7", taken)
+    assert np.all(taken > 0), taken
+    n_e, u_e = e.slit_profiles(hmax)
+    e.close()
+    for s in range(len(H)):
+        n1, u1 = lone(s, int(taken[s]))
+        assert np.array_equal(n1, n_e[s, :int(H[s])]) and np.array_equal(u1, u_e[s, :int(H[s])]), s
