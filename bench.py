@@ -409,11 +409,11 @@ def storage_f16_leg(args, stream, peak):
     W = c2(args.eta, 1)
     g = _slit(W, 1, W.seed, stream.cuda_stream)
     g.step(args.warmup)
-    tuned = g.autotune(3)
+    g.autotune(3)
     g.step(1)
     r, _, _, _ = time_steps(g, args.steps, stream, 1, W.nodes, peak)
     r["status"] = g.status()
-    r["autotuned"] = {"ball_ctas": tuned[0], "force_group": tuned[1], "ball_staging": "tma" if tuned[2] else "loads"}
+    r["autotuned"] = g.shapes()
     r["pass"] = "pull"
     g.close()
     dom = max(r["kernels"], key=lambda k: r["kernels"][k]["ms"])
@@ -475,7 +475,8 @@ def run_ours(args, world, rank, local):
     # warm-up, then the launch shapes the library's autotuner picks on this
     # state (ball CTAs and staging, force tile group; results bit-identical)
     g.step(args.warmup)
-    tuned = g.autotune(3)
+    g.autotune(3)
+    shapes = g.shapes()
     g.step(1)
     torch.cuda.synchronize()
     if world > 1:
@@ -548,8 +549,7 @@ def run_ours(args, world, rank, local):
         "config": {"workload": f"slit {W.nx}x{W.ny}x{W.nz} sigma={W.sigma} eta={W.eta} tau={W.tau} "
                                f"F_e={W.body[0]} bounce-back z, periodic x,y, seeded 1e-3 noise",
                    "storage": args.storage, "nodes": N, "pass": "pull",
-                   "autotuned": {"ball_ctas": tuned[0], "force_group": tuned[1],
-                                 "ball_staging": "tma" if tuned[2] else "loads"}, "parallelism": f"replicas x{world}",
+                   "autotuned": shapes, "parallelism": f"replicas x{world}",
                    "l2": "populations (>= 1.9 GB) exceed L2; no flush",
                    "bytes_alg_per_node": bytes_alg(storage),
                    "step_gbs_alg": step_gbs, "step_roofline_frac": step_gbs / peak,

@@ -226,14 +226,23 @@ int lbif_get_fused(lbif_handle h, int32_t* fused);
  * stays usable afterwards. */
 int lbif_selftest_wait(int64_t polls, int32_t* timed_out);
 
-/* Time the candidate launch shapes of the ball and force kernels on this
- * handle's current state (trials launches each) and keep the fastest: the
- * ball kernel's CTA target and its plane staging (1 = tensor-memory-
- * accelerator copies, 0 = plain loads), the force kernel's tile-group edge.
- * The state is unchanged. Chosen values (each may be NULL): ball CTA target,
- * force tile-group edge in nodes, ball staging. */
+/* Time the candidate launch shapes of the step's kernels on this handle's
+ * current state (trials launches each) and keep the fastest: the ball
+ * kernel's CTA target and its plane staging (1 = tensor-memory-accelerator
+ * copies, 0 = plain loads), the force kernel's tile-group edge, and the pull
+ * pass's z planes per CTA segment (8, 16, 32) and gather prefetch (the next
+ * plane's populations loaded while the current one is collided). Trials
+ * write only buffers the step overwrites, so the state is unchanged, and no
+ * choice changes the arithmetic (results are bit-identical). Chosen values
+ * (each may be NULL): ball CTA target, force tile-group edge in nodes, ball
+ * staging; lbif_get_shapes gives all of them. */
 int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* force_group,
                   int32_t* ball_staging);
+/* The launch shapes in use: shapes[0] ball CTA target (0 = default),
+ * [1] force tile-group edge (0 = default), [2] ball staging (1 = tensor-
+ * memory accelerator), [3] pull-pass z planes per segment (0 = default 16),
+ * [4] pull-pass gather prefetch (0 or 1). */
+int lbif_get_shapes(lbif_handle h, int32_t shapes[5]);
 
 /* ---- warm-start network -------------------------------------------------
  * A multilayer perceptron nin -> nhidden layers of width `hidden` (GELU, erf

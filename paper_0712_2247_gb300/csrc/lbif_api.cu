@@ -34,6 +34,7 @@ struct lbif_ctx {
     float* u[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int fcur = 0;                     // dn[fcur], u[fcur]: the moments of step t (pop[cur] refers to them)
     int csm_lz = 0;                   // z planes per CTA of the pull pass (0 = default)
+    int csm_pf = 0;                   // pull pass with the next plane's gathers prefetched (autotuner)
     float* dG = nullptr;
     float4* Ft = nullptr;
     float4* F = nullptr;              // F / n0 per node (force kernel -> collision kernel)
@@ -615,7 +616,8 @@ static int collide_stream(lbif_ctx* h)
     float* const* u = h->u[h->fcur];
     float* const* w = h->u[h->fcur ^ 1];
     CsmIO io{h->dn[h->fcur], u[0], u[1], u[2], h->dn[h->fcur ^ 1], w[0], w[1], w[2]};
-    CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->stream));
+    CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->csm_pf,
+                     h->stream));
     h->cur ^= 1;
     h->fcur ^= 1;
     h->t += 1;
@@ -1146,6 +1148,17 @@ extern "C" int lbif_selftest_wait(int64_t polls, int32_t* timed_out)
                       : LBIF_OK;
 }
 
+extern "C" int lbif_get_shapes(lbif_handle h, int32_t shapes[5])
+{
+    if (!h || !shapes) return fail(h, LBIF_ERR_ARG, "lbif_get_shapes: bad arguments");
+    shapes[0] = h->ball_want;
+    shapes[1] = h->force_group;
+    shapes[2] = h->ball_map_ok && h->ball_tma ? 1 : 0;
+    shapes[3] = h->csm_lz;
+    shapes[4] = h->csm_pf;
+    return LBIF_OK;
+}
+
 extern "C" int lbif_get_fused(lbif_handle h, int32_t* fused)
 {
     if (!h || !fused) return fail(h, LBIF_ERR_ARG, "lbif_get_fused: bad arguments");
@@ -1214,11 +1227,44 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
             best_group = gsz;
         }
     }
+    // Pull pass: z planes per CTA segment x gather prefetch. A trial reads the
+    // current populations and fields and writes only the next step's buffers
+    // (not adopted), so trials change no state either.
+    int best_lz = h->csm_lz, best_pf = h->csm_pf;
+    if (csm_ok(P.g)) {
+        const float4* Fp = h->F;
+        CK(h, launch_force(P, fields_of(h), h->Ft, h->F, best_group, h->stream));
+        float* const* u = h->u[h->fcur];
+        float* const* w = h->u[h->fcur ^ 1];
+        CsmIO io{h->dn[h->fcur], u[0], u[1], u[2], h->dn[h->fcur ^ 1], w[0], w[1], w[2]};
+        const int lzs[] = {8, 16, 32};
+        best = 1e30f;
+        for (int pf = 0; pf <= 1; ++pf)
+            for (int lz : lzs) {
+                float tot = 0.f;
+                for (int k = 0; k < trials + 1; ++k) {
+                    CK(h, cudaEventRecord(e0, h->stream));
+                    CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, Fp, h->status_d, lz, pf, h->stream));
+                    CK(h, cudaEventRecord(e1, h->stream));
+                    CK(h, cudaEventSynchronize(e1));
+                    float ms;
+                    CK(h, cudaEventElapsedTime(&ms, e0, e1));
+                    if (k) tot += ms;
+                }
+                if (tot < best) {
+                    best = tot;
+                    best_lz = lz;
+                    best_pf = pf;
+                }
+            }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     h->ball_want = best_ball;
     h->force_group = best_group;
     h->ball_tma = best_tma;
+    h->csm_lz = best_lz;
+    h->csm_pf = best_pf;
     if (h->graph) {
         cudaGraphExecDestroy(h->graph);
         h->graph = nullptr;

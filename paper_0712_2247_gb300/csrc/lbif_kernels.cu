@@ -1695,11 +1695,11 @@ __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ 
 // mirror differences first (from the stored values as loaded), then the ten
 // base directions. src(i) is the source quantities of direction i (stride
 // ST); wall directions arrive reversed from the node itself (own).
-template <int ST, class Src>
-__device__ __forceinline__ void pull_gather(Src src, const float* own, float om1s, float dnr, unsigned bb, float* v,
-                                            float& d79)
+template <int ST, bool WALLS, class Src>
+__device__ __forceinline__ void pull_gather_impl(Src src, const float* own, float om1s, float dnr, unsigned bb,
+                                                 float* v, float& d79)
 {
-    auto wall = [&](int i) { return ((bb >> i) & 1u) != 0u; };
+    auto wall = [&](int i) { return WALLS && ((bb >> i) & 1u) != 0u; };
     auto diff = [&](auto ic, auto ipc) {
         constexpr int i = decltype(ic)::value, ip = decltype(ipc)::value;
         const bool w = wall(i);
@@ -1730,6 +1730,22 @@ __device__ __forceinline__ void pull_gather(Src src, const float* own, float om1
     for_dirs(one);
 }
 
+// The arriving values of a node in the slots described at Mirror: the ten
+// mirror differences first (from the stored values as loaded), then the ten
+// base directions. src(i) is the source quantities of direction i (stride
+// ST); wall directions arrive reversed from the node itself (own). Nodes
+// with no wall direction (bb = 0, almost all) take a path without the wall
+// selections.
+template <int ST, class Src>
+__device__ __forceinline__ void pull_gather(Src src, const float* own, float om1s, float dnr, unsigned bb, float* v,
+                                            float& d79)
+{
+    if (bb == 0u)
+        pull_gather_impl<ST, false>(src, own, om1s, dnr, bb, v, d79);
+    else
+        pull_gather_impl<ST, true>(src, own, om1s, dnr, bb, v, d79);
+}
+
 // the gather of a node staged at hc in the ring (planes below, own, above)
 __device__ __forceinline__ void csm_collide(const float* own, const float* below, const float* above, int hc,
                                             float om1s, float dnr, unsigned bb, float* v, float& d79)
@@ -1745,9 +1761,11 @@ __device__ __forceinline__ void csm_collide(const float* own, const float* below
 // one node per thread, a CTA per 32 x 4 tile and z segment (measured with the
 // earlier storage: two threads per node, each gathering half of the
 // directions and adding the partial moments through shared memory, ran
-// slower at twice the warps)
-template <typename T>
-__global__ void __launch_bounds__(CSM_THREADS, CSM_MINB)
+// slower at twice the warps). PF: the population gathers of the next plane
+// are issued before the current plane is staged and collided, so they are in
+// flight across both barriers (19 more live registers: five CTAs per SM).
+template <typename T, bool PF>
+__global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
     k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout, CsmIO io, const float4* __restrict__ F,
           int lz, int tiles_x, int tiles_y, int* status)
 {
@@ -1763,25 +1781,45 @@ __global__ void __launch_bounds__(CSM_THREADS, CSM_MINB)
     const bool in_xy = x < g.nx && y < g.ny;
     const int zb = seg * lz, ze = min(zb + lz, g.nz);
     const CsmStaged st = csm_staged<NT>(g, x0, y0);
+    // the population gathers of plane z (act: the node steps; om its 1/tau)
+    auto gather = [&](int z, float* v, unsigned& bb, bool& act, float& om) {
+        const int s = slit_of(P, z);
+        act = in_xy && s >= 0 && !frozen(P, s);
+        bb = 0;
+        om = 0.f;
+        if (act) {
+            om = P.sl[s].inv_tau;
+            csm_pull<0, Q>(P, pin, ((long long)z * g.ny + y) * g.nx + x, x, y, z, P.sl[s].zlo, P.sl[s].zhi, v, bb);
+        }
+    };
+    float vn[Q];
+    unsigned bbn = 0;
+    bool actn = false;
+    float omn = 0.f;
+    if constexpr (PF) gather(zb, vn, bbn, actn, omn);
     csm_stage<NT>(P, io, F, sm + csm_slot(zb - 1) * CSM_SLOT, st, zb - 1);
     csm_stage<NT>(P, io, F, sm + csm_slot(zb) * CSM_SLOT, st, zb);
     for (int z = zb; z < ze; ++z) {
         // issue the population loads first: they do not depend on the ring
-        const int s = slit_of(P, z);
-        const bool act = in_xy && s >= 0 && !frozen(P, s);
         float v[Q];
-        unsigned bb = 0;
-        const long long idx = ((long long)z * g.ny + y) * g.nx + x;
-        float om = 0.f;
-        if (act) {
-            const int zlo = P.sl[s].zlo, zhi = P.sl[s].zhi;
-            om = P.sl[s].inv_tau;
-            csm_pull<0, Q>(P, pin, idx, x, y, z, zlo, zhi, v, bb);
+        unsigned bb;
+        bool act;
+        float om;
+        if constexpr (PF) {
+#pragma unroll
+            for (int i = 0; i < Q; ++i) v[i] = vn[i];
+            bb = bbn;
+            act = actn;
+            om = omn;
+            if (z + 1 < ze) gather(z + 1, vn, bbn, actn, omn);
+        } else {
+            gather(z, v, bb, act, om);
         }
         __syncthreads();  // the slot of plane z - 2 is free
         csm_stage<NT>(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, st, z + 1);
         __syncthreads();
         if (!act) continue;
+        const long long idx = ((long long)z * g.ny + y) * g.nx + x;
         const float* own = sm + csm_slot(z) * CSM_SLOT;
         const float dnr = own[SQ_DN * CSM_HN + hc];
         float d79;
@@ -2201,18 +2239,11 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
 
 bool csm_ok(const Geom& g) { return g.nx >= CSM_TX && g.ny >= CSM_TY; }
 
-cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
-                       int* status, int lz, cudaStream_t s)
+template <typename T, bool PF>
+static cudaError_t csm_tiled(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
+                             int* status, int lz, cudaStream_t s)
 {
     const Geom& g = P.g;
-    if (!csm_ok(g)) {
-        if (P.storage == LBIF_STORE_F16)
-            k_pull_node<__half><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const __half*)pin, (__half*)pout, io, F, status);
-        else
-            k_pull_node<float><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const float*)pin, (float*)pout, io, F, status);
-        return cudaGetLastError();
-    }
-    if (lz <= 0) lz = CSM_LZ;
     const int tx = (g.nx + CSM_TX - 1) / CSM_TX, ty = (g.ny + CSM_TY - 1) / CSM_TY;
     const int segs = (g.nz + lz - 1) / lz;
     const long long blocks = (long long)tx * ty * segs;
@@ -2225,19 +2256,31 @@ cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO
     if (e != cudaSuccess) return e;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(configured.load() & bit)) {
-        e = cudaFuncSetAttribute(k_csm<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_csm<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_csm<T, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
-    if (P.storage == LBIF_STORE_F16)
-        k_csm<__half><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const __half*)pin, (__half*)pout, io, F, lz,
-                                                                 tx, ty, status);
-    else
-        k_csm<float><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const float*)pin, (float*)pout, io, F, lz,
-                                                                tx, ty, status);
+    k_csm<T, PF><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const T*)pin, (T*)pout, io, F, lz, tx, ty, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
+                       int* status, int lz, int prefetch, cudaStream_t s)
+{
+    const Geom& g = P.g;
+    if (!csm_ok(g)) {
+        if (P.storage == LBIF_STORE_F16)
+            k_pull_node<__half><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const __half*)pin, (__half*)pout, io, F, status);
+        else
+            k_pull_node<float><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const float*)pin, (float*)pout, io, F, status);
+        return cudaGetLastError();
+    }
+    if (lz <= 0) lz = CSM_LZ;
+    if (P.storage == LBIF_STORE_F16)
+        return prefetch ? csm_tiled<__half, true>(P, pin, pout, io, F, status, lz, s)
+                        : csm_tiled<__half, false>(P, pin, pout, io, F, status, lz, s);
+    return prefetch ? csm_tiled<float, true>(P, pin, pout, io, F, status, lz, s)
+                    : csm_tiled<float, false>(P, pin, pout, io, F, status, lz, s);
 }
 
 cudaError_t launch_wait_selftest(long long polls, int* status, cudaStream_t s)

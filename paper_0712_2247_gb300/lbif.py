@@ -68,6 +68,7 @@ SIGNATURES = {
     "lbif_batch_profiles": (_i32, [_vp, _pd, _pd, _i32]),
     "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "lbif_set_fused": (_i32, [_vp, _i32]),
+    "lbif_get_shapes": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "lbif_get_fused": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "lbif_selftest_wait": (_i32, [_i64, ctypes.POINTER(_i32)]),
     "lbif_field_profiles_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _pd, _pd, _pd, _vp]),
@@ -211,6 +212,13 @@ class Slit:
         self._check(self._lib.lbif_autotune(self._h, int(trials), ctypes.byref(b), ctypes.byref(g),
                                             ctypes.byref(st)))
         return b.value, g.value, st.value
+
+    def shapes(self) -> dict:
+        """The launch shapes in use (see lbif_get_shapes)."""
+        v = (_i32 * 5)()
+        self._check(self._lib.lbif_get_shapes(self._h, v))
+        return {"ball_ctas": v[0], "force_group": v[1], "ball_staging": "tma" if v[2] else "loads",
+                "pull_lz": v[3], "pull_prefetch": v[4]}
 
     def set_fused(self, on: bool):
         """Every step is one pull pass (collision, streaming and the next

@@ -204,6 +204,24 @@ def test_fp16_storage_velocity_profile(L, O):
     assert e < 1e-3
 
 
+@pytest.mark.parametrize("tau", [0.6, 0.8, 1.2])
+def test_fp16_storage_profiles_tau_not_one(L, O, tau):
+    """FP16 storage where the stored non-equilibrium parts enter the update
+    (their factor 1 - 1/tau vanishes at tau = 1): an 8 x 8 x 16 slit, sigma 4,
+    eta 0.25, F_e = 1e-6, seeded noise, 12000 steps (several viscous times of
+    the 16-plane slit), profiles against the FP64 oracle at 1e-3; the same
+    rounding emulated on the oracle moves them by ~1e-4
+    (tests/test_storage_emulation.py)."""
+    g, o = make_pair(L, O, 8, 8, 16, 4, 0.25, tau, seed=0, body=(1e-6, 0, 0), storage=1)
+    g.step(12000)
+    o.step(12000)
+    ng, uxg, _ = g.profiles()
+    no, uxo = o.profiles()
+    e = dict(n_z=nerr(ng, no), ux_z=nerr(uxg, uxo))
+    report(f"fp16 tau={tau} 12000 steps", **e)
+    assert e["n_z"] < 1e-3 and e["ux_z"] < 1e-3
+
+
 @pytest.mark.parametrize("shape,sigma,zper", [
     ((26, 22, 28), 4, False),   # direct pair sum (lateral extents not powers of two)
     ((32, 16, 28), 4, False),   # spectral in x, y, direct in z between walls
