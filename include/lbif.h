@@ -67,6 +67,14 @@ typedef struct {
                           w_i C2 (|c_i|^2 - 3 kT) / (6 kT^2) (no mass, no
                           momentum; C2 from the same shell quadrature and
                           interpolants as the force, not regularised)       */
+    int32_t shifted;   /* 1: velocity-shifted second-order forcing instead of
+                          the first-order source of Sec. Methods: the force
+                          F from the moments n, u = j/n as before (explicit),
+                          BGK towards f^eq(n, u + F/(2n)), source
+                          (1 - 1/(2 tau)) w_i [(c_i - u').F/c_s^2 +
+                          (c_i.u')(c_i.F)/c_s^4]. lbif_moments still reports
+                          u = j/n (the physical velocity is u + F/(2n), F
+                          from lbif_forces). Not with c2. */
 } lbif_force;
 
 /* Population storage. Each population is stored as its non-equilibrium part
@@ -83,6 +91,11 @@ typedef struct {
     uint64_t seed;     /* initial density noise: n = n0 (1 + noise (2U - 1)),  */
     double   noise;    /*   U from SplitMix64(seed ^ node index)                */
     void*    stream;   /* cudaStream_t to enqueue on; NULL = default stream    */
+    int32_t  inplace;  /* 1: the populations live in one buffer (half the
+                          memory): direction i of every node moves by c_i
+                          slots each step, so each step reads and writes the
+                          same slots; 0: two buffers (read one, write the
+                          other). Same arithmetic, same results.              */
 } lbif_opts;
 
 /* Create a slit (or periodic box) of packing fraction eta = pi sigma^3 n0/6

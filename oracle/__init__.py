@@ -260,10 +260,11 @@ class Oracle:
     def step(self, nsteps: int = 1, lagged: bool = False, shifted: bool = False):
         """Plain steps, steps of the lagged-force variant (the force of the
         previous step's moments drives the collision), or steps with the
-        velocity-shifted second-order forcing (body force only)."""
+        velocity-shifted second-order forcing (the force from the unshifted
+        moments; the equilibrium at (j + F/2)/n)."""
         if shifted:
             if self._lib.or_step_shifted(self._h, int(nsteps)) != 0:
-                raise ValueError("oracle: the shifted forcing needs a force independent of u")
+                raise ValueError("oracle: the shifted forcing does not add the energy source")
             return
         (self._lib.or_step_lagged if lagged else self._lib.or_step)(self._h, int(nsteps))
 

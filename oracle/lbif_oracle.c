@@ -548,8 +548,8 @@ static void collide_stream(or_state* s)
 /* Collision and streaming with velocity-shifted (second-order) forcing, for
  * comparison with the paper's first-order source: the equilibrium takes
  * u = (j + F/2)/n and the source is
- *   (1 - 1/(2 tau)) w_i [ (c_i - u).F / c_s^2 + (c_i.u)(c_i.F) / c_s^4 ].
- * Explicit only when F does not depend on u (body force alone).           */
+ *   (1 - 1/(2 tau)) w_i [ (c_i - u).F / c_s^2 + (c_i.u)(c_i.F) / c_s^4 ],
+ * with F the force of the step (from the unshifted moments).              */
 static void collide_stream_shifted(or_state* s)
 {
     long N = s->N;
@@ -582,12 +582,16 @@ static void collide_stream_shifted(or_state* s)
     double* tmp = s->f; s->f = s->fn; s->fn = tmp;
 }
 
-/* steps with the velocity-shifted forcing; -1 (nothing done) when the force
- * depends on u (hard-sphere or tail force on)                               */
+/* steps with the velocity-shifted forcing. Reading: the force is evaluated
+ * from the moments n, u = j/n of the pre-collision populations (as in the
+ * paper's scheme), which keeps the step explicit when the force depends on
+ * u (the density-current term of Eq. LBHS); only the equilibrium velocity
+ * (j + F/2)/n and the source are shifted. -1 (nothing done) with the energy
+ * source of Eq. C2eq on, which this variant does not add.                  */
 int or_step_shifted(void* h, long nsteps)
 {
     or_state* s = (or_state*)h;
-    if (s->hs || s->tail) return -1;
+    if (s->c2) return -1;
     for (long k = 0; k < nsteps; ++k) {
         compute_moments(s);
         compute_forces(s, 0);

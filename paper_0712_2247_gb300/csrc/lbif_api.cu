@@ -45,6 +45,7 @@ struct lbif_ctx {
     int tail_D = 0;                   // z reach of the tail kernel (planes)
     bool tail_fft = false;
     int* status_d = nullptr;
+    int4* clk_d = nullptr;            // in place: per slit clock (t mod nx, ny, R)
     double* prof_d = nullptr;
     float* scratch = nullptr;         // 3 N floats, for host-side outputs
     SlitParam* d_sl = nullptr;
@@ -170,7 +171,7 @@ static void free_ctx(lbif_ctx* h)
     if (!h) return;
     if (h->graph) cudaGraphExecDestroy(h->graph);
     void* bufs[] = {h->pop[0], h->pop[1], h->Ft, h->F, h->tail_off, h->tail_K, h->tail_work, h->status_d,
-                    h->prof_d, h->scratch, h->d_sl, h->d_zslit, h->d_done};
+                    h->prof_d, h->scratch, h->d_sl, h->d_zslit, h->d_done, h->clk_d};
     for (void* b : bufs)
         if (b) cudaFree(b);
     float* pads[] = {h->dn[0], h->dn[1], h->u[0][0], h->u[0][1], h->u[0][2],
@@ -302,6 +303,9 @@ static int check_common(double sigma, const lbif_force& F, const lbif_opts& O, c
         return fail(nullptr, LBIF_ERR_ARG, w + ": tail needs rcut in [1,4] and eps >= 0");
     if ((F.g2_form != 0 && F.g2_form != 1)) return fail(nullptr, LBIF_ERR_ARG, w + ": g2_form must be 0 or 1");
     if (F.c2 != 0 && F.c2 != 1) return fail(nullptr, LBIF_ERR_ARG, w + ": c2 must be 0 or 1");
+    if (F.shifted != 0 && F.shifted != 1) return fail(nullptr, LBIF_ERR_ARG, w + ": shifted must be 0 or 1");
+    if (F.shifted && F.c2)
+        return fail(nullptr, LBIF_ERR_UNSUPPORTED, w + ": the shifted forcing does not add the energy source");
     for (int a = 0; a < 3; ++a)
         if (!isfinite(F.body[a])) return fail(nullptr, LBIF_ERR_ARG, w + ": body force not finite");
     return LBIF_OK;
@@ -327,8 +331,15 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     g.pz = g.nz + 2 * g.hw;
     g.N = (long long)g.nx * g.ny * g.nz;
     g.Npad = (g.N + 63) / 64 * 64;
+    long long ring_planes = 0;  // in place: every slit's ring of storage planes
+    std::vector<int> ring_base;
+    for (const SlitDesc& d : slits) {
+        ring_base.push_back((int)ring_planes);
+        ring_planes += (d.zhi - d.zlo + 1) + (zper ? 0 : 1);
+    }
+    if (O.inplace) g.Npad = ((long long)g.nx * g.ny * ring_planes + 63) / 64 * 64;
     g.P = (long long)g.px * g.py * g.pz;
-    if (g.P >= (1LL << 31)) {
+    if (g.P >= (1LL << 31) || g.Npad >= (1LL << 31)) {
         delete h;
         return fail(nullptr, LBIF_ERR_UNSUPPORTED, "create: padded grid exceeds 2^31 nodes");
     }
@@ -343,7 +354,9 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     P.g2form = F.g2_form;
     P.tail = F.tail ? 1 : 0;
     P.c2 = F.c2 ? 1 : 0;
+    P.shifted = F.shifted ? 1 : 0;
     P.storage = O.storage;
+    P.inplace = O.inplace ? 1 : 0;
     P.nslits = (int)slits.size();
     {
         const int cx[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -359,7 +372,12 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
         return fail(nullptr, LBIF_ERR_UNSUPPORTED, "create: quadrature tables do not fit");
     }
     h->batch = batch;
-    for (const SlitDesc& d : slits) h->sl.push_back(slit_param(d, sigma, F.g2_form));
+    for (size_t k = 0; k < slits.size(); ++k) {
+        SlitParam sp = slit_param(slits[k], sigma, F.g2_form);
+        sp.zb = ring_base[k];
+        sp.R = (slits[k].zhi - slits[k].zlo + 1) + (zper ? 0 : 1);
+        h->sl.push_back(sp);
+    }
     h->zslit = zslit;
     h->done.assign(slits.size(), 0);
     if (O.stream) {
@@ -410,7 +428,8 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
         }                                                                                   \
     } while (0)
     ALLOC(h->pop[0], pb);
-    ALLOC(h->pop[1], pb);
+    if (!P.inplace) ALLOC(h->pop[1], pb);
+    ALLOC(h->clk_d, sizeof(int4) * h->sl.size());
     ALLOC(h->F, sizeof(float4) * (size_t)g.N);
     ALLOC(h->status_d, sizeof(int));
     ALLOC(h->prof_d, sizeof(double) * profile_doubles(g));
@@ -439,6 +458,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     P.sl = h->d_sl;
     P.zslit = h->d_zslit;
     P.done = h->d_done;
+    P.clk = h->clk_d;
     lbif_ctx* hc = h;
 #define CKC(call)                                                                           \
     do {                                                                                    \
@@ -455,7 +475,8 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
                         cudaMemcpyHostToDevice, h->stream));
     CKC(cudaMemsetAsync(h->d_done, 0, sizeof(int) * h->sl.size(), h->stream));
     CKC(cudaMemsetAsync(h->pop[0], 0, pb, h->stream));
-    CKC(cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
+    if (h->pop[1]) CKC(cudaMemsetAsync(h->pop[1], 0, pb, h->stream));
+    CKC(cudaMemsetAsync(h->clk_d, 0, sizeof(int4) * h->sl.size(), h->stream));
     {
         float* pads[] = {h->dn[0], h->dn[1], h->u[0][0], h->u[0][1], h->u[0][2],
                          h->u[1][0], h->u[1][1], h->u[1][2], h->dG};
@@ -495,7 +516,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
         CKC(cudaMemcpyAsync(h->tail_K, tK.data(), sizeof(float4) * tK.size(),
                             cudaMemcpyHostToDevice, h->stream));
     }
-    CKC(launch_init_noise(P, h->pop[0], h->dn[0], O.seed, O.noise, 0, h->stream));
+    CKC(launch_init_noise(P, h->dn[0], O.seed, O.noise, 0, h->stream));
     CKC(cudaStreamSynchronize(h->stream));
 #undef CKC
     *out = h;
@@ -616,9 +637,14 @@ static int collide_stream(lbif_ctx* h)
     float* const* u = h->u[h->fcur];
     float* const* w = h->u[h->fcur ^ 1];
     CsmIO io{h->dn[h->fcur], u[0], u[1], u[2], h->dn[h->fcur ^ 1], w[0], w[1], w[2]};
-    CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->csm_pf,
-                     h->stream));
-    h->cur ^= 1;
+    if (P.inplace) {
+        CK(h, launch_csm(P, h->pop[0], h->pop[0], io, h->F, h->status_d, h->csm_lz, h->csm_pf, h->stream));
+        CK(h, launch_tick(P, h->clk_d, h->stream));
+    } else {
+        CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->csm_pf,
+                         h->stream));
+        h->cur ^= 1;
+    }
     h->fcur ^= 1;
     h->t += 1;
     return LBIF_OK;
@@ -714,10 +740,12 @@ static int check_status(lbif_ctx* h)
     return LBIF_OK;
 }
 
+// 4 N floats: host-side outputs and inputs (a density and a velocity field,
+// the four moment fields of a checkpoint)
 static int ensure_scratch(lbif_ctx* h)
 {
     if (h->scratch) return LBIF_OK;
-    if (cudaMalloc((void**)&h->scratch, sizeof(float) * 3 * (size_t)h->P.g.N) != cudaSuccess) {
+    if (cudaMalloc((void**)&h->scratch, sizeof(float) * 4 * (size_t)h->P.g.N) != cudaSuccess) {
         cudaGetLastError();
         h->scratch = nullptr;
         return fail(h, LBIF_ERR_NOMEM, "scratch allocation failed");
@@ -781,6 +809,16 @@ static void reset_time(lbif_ctx* h)
     invalidate(h);
 }
 
+// every stored population of the current state 0 (an equilibrium; in place,
+// the slits' clocks restart)
+static int zero_populations(lbif_ctx* h)
+{
+    const size_t pb = pop_bytes(h->P) * (size_t)Q * (size_t)h->P.g.Npad;
+    CK(h, cudaMemsetAsync(h->pop[h->cur], 0, pb, h->stream));
+    CK(h, cudaMemsetAsync(h->clk_d, 0, sizeof(int4) * h->sl.size(), h->stream));
+    return LBIF_OK;
+}
+
 extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, int32_t on_device)
 {
     if (!h || !rho) return fail(h, LBIF_ERR_ARG, "lbif_set_fields: bad arguments");
@@ -791,21 +829,21 @@ extern "C" int lbif_set_fields(lbif_handle h, const float* rho, const float* u, 
     if (!on_device) {
         int rc = ensure_scratch(h);
         if (rc) return rc;
-        // rho goes to the (not yet used) second population buffer, u to the scratch
-        float* d = (float*)h->pop[h->cur ^ 1];
+        float* d = h->scratch;
         CK(h, cudaMemcpyAsync(d, rho, sizeof(float) * N, cudaMemcpyHostToDevice, h->stream));
         drho = d;
         if (u) {
-            CK(h, cudaMemcpyAsync(h->scratch, u, sizeof(float) * 3 * N, cudaMemcpyHostToDevice,
-                                  h->stream));
-            du = h->scratch;
+            CK(h, cudaMemcpyAsync(d + N, u, sizeof(float) * 3 * N, cudaMemcpyHostToDevice, h->stream));
+            du = d + N;
         }
     }
     // the equilibrium of the given fields: stored non-equilibrium parts 0,
     // the fields themselves are its moments (no moments pass)
+    int rc = zero_populations(h);
+    if (rc) return rc;
     float* f[4];
     field_set(h, h->fcur, f);
-    CK(h, launch_init_fields(P, h->pop[h->cur], f, drho, du, h->stream));
+    CK(h, launch_init_fields(P, f, drho, du, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     reset_time(h);
     return LBIF_OK;
@@ -960,8 +998,10 @@ extern "C" int lbif_batch_seed(lbif_handle h, const float* n_z, const float* ux_
     if (e == cudaSuccess && ux_z)
         e = cudaMemcpyAsync(d + cnt, ux_z, sizeof(float) * cnt, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = launch_init_profiles(h->P, h->pop[h->cur], fs, d, ux_z ? d + cnt : nullptr, hmax,
-                                 h->stream);
+        e = cudaMemsetAsync(h->pop[h->cur], 0, pop_bytes(h->P) * (size_t)Q * (size_t)h->P.g.Npad, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->clk_d, 0, sizeof(int4) * h->sl.size(), h->stream);
+    if (e == cudaSuccess)
+        e = launch_init_profiles(h->P, fs, d, ux_z ? d + cnt : nullptr, hmax, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return fail(h, LBIF_ERR_CUDA, std::string("lbif_batch_seed: ") + cudaGetErrorString(e));
@@ -1231,7 +1271,9 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
     // current populations and fields and writes only the next step's buffers
     // (not adopted), so trials change no state either.
     int best_lz = h->csm_lz, best_pf = h->csm_pf;
-    if (csm_ok(P.g)) {
+    // (in place a trial would overwrite the state it reads: the pull pass
+    // keeps its defaults there)
+    if (csm_ok(P.g) && !P.inplace) {
         const float4* Fp = h->F;
         CK(h, launch_force(P, fields_of(h), h->Ft, h->F, best_group, h->stream));
         float* const* u = h->u[h->fcur];
@@ -1292,19 +1334,23 @@ extern "C" int lbif_save(lbif_handle h, const char* path)
 {
     if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_save: bad arguments");
     const Params& P = h->P;
+    int rc = ensure_scratch(h);
+    if (rc) return rc;
     size_t es = pop_bytes(P);
     size_t N = (size_t)P.g.N;
     size_t plane = es * N;
     std::vector<char> buf(plane * Q);
     std::vector<float> fld(4 * N);
-    for (int i = 0; i < Q; ++i)
-        CK(h, cudaMemcpyAsync(buf.data() + plane * i, (char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i,
-                              plane, cudaMemcpyDeviceToHost, h->stream));
+    // each direction in node order (the layout of the buffer is the
+    // library's), then the moment fields
+    for (int i = 0; i < Q; ++i) {
+        CK(h, launch_pop_canon(P, h->pop[h->cur], i, h->scratch, 0, h->stream));
+        CK(h, cudaMemcpyAsync(buf.data() + plane * i, h->scratch, plane, cudaMemcpyDeviceToHost, h->stream));
+    }
     float* f[4];
     field_set(h, h->fcur, f);
-    float* stage = (float*)h->pop[h->cur ^ 1];
-    CK(h, launch_read_fields(P, f, stage, h->stream));
-    CK(h, cudaMemcpyAsync(fld.data(), stage, sizeof(float) * 4 * N, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, launch_read_fields(P, f, h->scratch, h->stream));
+    CK(h, cudaMemcpyAsync(fld.data(), h->scratch, sizeof(float) * 4 * N, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     FILE* fp = fopen(path, "wb");
     if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_save: cannot open ") + path);
@@ -1328,6 +1374,8 @@ extern "C" int lbif_load(lbif_handle h, const char* path)
 {
     if (!h || !path) return fail(h, LBIF_ERR_ARG, "lbif_load: bad arguments");
     const Params& P = h->P;
+    int rc = ensure_scratch(h);
+    if (rc) return rc;
     FILE* fp = fopen(path, "rb");
     if (!fp) return fail(h, LBIF_ERR_IO, std::string("lbif_load: cannot open ") + path);
     CkptHeader hd;
@@ -1342,14 +1390,15 @@ extern "C" int lbif_load(lbif_handle h, const char* path)
               fread(fld.data(), sizeof(float), 4 * N, fp) == 4 * N;
     fclose(fp);
     if (!ok) return fail(h, LBIF_ERR_IO, "lbif_load: file does not match this handle");
-    for (int i = 0; i < Q; ++i)
-        CK(h, cudaMemcpyAsync((char*)h->pop[h->cur] + es * (size_t)P.g.Npad * i, buf.data() + plane * i,
-                              plane, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = zero_populations(h))) return rc;  // the clocks restart: node-order slots
+    for (int i = 0; i < Q; ++i) {
+        CK(h, cudaMemcpyAsync(h->scratch, buf.data() + plane * i, plane, cudaMemcpyHostToDevice, h->stream));
+        CK(h, launch_pop_canon(P, h->pop[h->cur], i, h->scratch, 1, h->stream));
+    }
     float* f[4];
     field_set(h, h->fcur, f);
-    float* stage = (float*)h->pop[h->cur ^ 1];
-    CK(h, cudaMemcpyAsync(stage, fld.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice, h->stream));
-    CK(h, launch_write_fields(P, stage, f, h->stream));
+    CK(h, cudaMemcpyAsync(h->scratch, fld.data(), sizeof(float) * 4 * N, cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_write_fields(P, h->scratch, f, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     reset_time(h);
     h->t = hd.t;

@@ -2,7 +2,9 @@
 //
 // State of a slit on the device:
 //   pop[2]  19 planes of Npad elements (FP32 or FP16), node index
-//           idx = (z*ny + y)*nx + x, two buffers, pull streaming. A population
+//           idx = (z*ny + y)*nx + x, two buffers, pull streaming; or, in
+//           place, one buffer in which direction i of a node moves by c_i
+//           slots every step (see the pull pass). A population
 //           is stored as its non-equilibrium part relative to the node's own
 //           equilibrium weight, h_i = s (f_i - f_i^eq(n, u)) / (w_i n), at the
 //           moments n, u of the step it belongs to (s = 2^8 for FP16, 1 for
@@ -71,7 +73,7 @@ struct SlitParam {
     float p_pref;    // kT sigma^3/6 4 pi n0^2
     float body[3];   // F_e per particle
     int zlo, zhi;    // first and last fluid plane
-    int pad;
+    int zb, R;       // in place: the slit's ring of R storage planes starts at plane zb
 };
 
 struct Params {
@@ -82,10 +84,13 @@ struct Params {
     int sigma;
     int hs, coupling, regularize, g2form, tail, storage;
     int c2;               // energy source of Eq. C2eq on (F.w carries C2 / n0)
+    int shifted;          // velocity-shifted second-order forcing (equilibrium at u + F/(2n))
     int nslits;
     const SlitParam* sl;  // device table, nslits entries
     const int* zslit;     // device table, nz entries
     const int* done;      // device flags, nslits entries (1 = frozen)
+    int inplace;          // populations in one buffer (shifting slots)
+    const int4* clk;      // in place: per slit (t mod nx, t mod ny, t mod R) of its step t
     int nbr[Q];           // padded offsets of the 19 lattice neighbours
     long long soff[Q];    // node-index offsets of the 19 neighbours (no wrap)
     Shell sh;
@@ -116,13 +121,19 @@ struct CsmIO {
 // ---- launchers (lbif_kernels.cu) -------------------------------------------
 cudaError_t launch_fill_outside(const Params& P, float* const* planes, const float* values,
                                 int nplanes, cudaStream_t s);
-cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t seed, double amp,
-                              long long offset, cudaStream_t s);
+// the initial states are equilibria: the caller zeroes the stored populations
+cudaError_t launch_init_noise(const Params& P, float* dn, uint64_t seed, double amp, long long offset,
+                              cudaStream_t s);
 // f[4]: the padded fields dn, ux, uy, uz of the state being set
-cudaError_t launch_init_profiles(const Params& P, void* pop, float* const f[4], const float* n_z,
-                                 const float* ux_z, int hmax, cudaStream_t s);
-cudaError_t launch_init_fields(const Params& P, void* pop, float* const f[4], const float* rho,
-                               const float* u, cudaStream_t s);
+cudaError_t launch_init_profiles(const Params& P, float* const f[4], const float* n_z, const float* ux_z,
+                                 int hmax, cudaStream_t s);
+cudaError_t launch_init_fields(const Params& P, float* const f[4], const float* rho, const float* u,
+                               cudaStream_t s);
+// in place: advance the clocks of the slits not frozen (after every pull pass)
+cudaError_t launch_tick(const Params& P, int4* clk, cudaStream_t s);
+// the populations of direction i of the current state in node order (N
+// elements; gap planes skipped) <-> the buffer (to_pop: scatter into it)
+cudaError_t launch_pop_canon(const Params& P, void* pop, int i, void* canon, int to_pop, cudaStream_t s);
 // the four fields <-> four unpadded N-arrays (checkpoints)
 cudaError_t launch_write_fields(const Params& P, const float* src, float* const f[4], cudaStream_t s);
 cudaError_t launch_read_fields(const Params& P, const float* const f[4], float* out, cudaStream_t s);

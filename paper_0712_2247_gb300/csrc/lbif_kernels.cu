@@ -251,10 +251,10 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x)
 }
 
 // Every initial state below is an equilibrium: its stored populations (the
-// non-equilibrium parts, see the pull pass) are 0 and its moments are the
-// fields themselves, written with their periodic images.
-template <typename T>
-__global__ void k_init_noise(Params P, T* pop, float* dn, uint64_t seed, double amp, long long offset)
+// non-equilibrium parts, see the pull pass) are 0 (the host zeroes the
+// population buffer) and its moments are the fields themselves, written with
+// their periodic images.
+__global__ void k_init_noise(Params P, float* dn, uint64_t seed, double amp, long long offset)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -265,15 +265,11 @@ __global__ void k_init_noise(Params P, T* pop, float* dn, uint64_t seed, double 
     double U = (double)(r >> 11) * (1.0 / 9007199254740992.0);
     // f_i = w_i n0 (1 + xi) = f_i^eq(n0 (1 + xi), 0); u stays 0
     float xi = (float)(amp * (2.0 * U - 1.0));
-#pragma unroll
-    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
     for_images(P.g, x, y, z, [&](int p) { dn[p] = xi; });
 }
 
 // the equilibrium of given density and velocity fields (u NULL: at rest)
-template <typename T>
-__global__ void k_init_fields(Params P, T* pop, float* dn, float* ux, float* uy, float* uz, const float* rho,
-                              const float* u)
+__global__ void k_init_fields(Params P, float* dn, float* ux, float* uy, float* uz, const float* rho, const float* u)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -283,8 +279,6 @@ __global__ void k_init_fields(Params P, T* pop, float* dn, float* ux, float* uy,
     if (s < 0) return;
     const float d = rho[idx] / P.sl[s].rho0 - 1.f;
     const float vx = u ? u[idx] : 0.f, vy = u ? u[P.g.N + idx] : 0.f, vz = u ? u[2 * P.g.N + idx] : 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
     for_images(P.g, x, y, z, [&](int p) {
         dn[p] = d;
         ux[p] = vx;
@@ -295,8 +289,7 @@ __global__ void k_init_fields(Params P, T* pop, float* dn, float* ux, float* uy,
 
 // x,y-uniform equilibria from per-slit profiles n(z), u_x(z) (row s of n_z,
 // ux_z holds slit s, entry j its plane zlo + j)
-template <typename T>
-__global__ void k_init_profiles(Params P, T* pop, float* dn, float* ux, float* uy, float* uz, const float* n_z,
+__global__ void k_init_profiles(Params P, float* dn, float* ux, float* uy, float* uz, const float* n_z,
                                 const float* ux_z, int hmax)
 {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -308,14 +301,116 @@ __global__ void k_init_profiles(Params P, T* pop, float* dn, float* ux, float* u
     const int j = z - P.sl[s].zlo;
     const float d = n_z[(long long)s * hmax + j] / P.sl[s].rho0 - 1.f;
     const float vx = ux_z ? ux_z[(long long)s * hmax + j] : 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) stp(pop + (long long)i * P.g.Npad + idx, 0.f);
     for_images(P.g, x, y, z, [&](int p) {
         dn[p] = d;
         ux[p] = vx;
         uy[p] = 0.f;
         uz[p] = 0.f;
     });
+}
+
+// ---- populations in place ---------------------------------------------
+// One buffer. Direction i of node (x, y, z) of slit s, in the slit's step t,
+// sits at storage node
+//   ((zb + (z - zlo - t c_iz) mod R) ny + (y - t c_iy) mod ny) nx + (x - t c_ix) mod nx,
+// R = the slit's planes plus one ghost plane beyond its walls (none with
+// periodic z). The slot a node's pull reads for direction i (its source
+// r - c_i at step t) is then the slot it writes (itself at step t + 1); a
+// bounce-back reads the node's own slot of the opposite direction at step t,
+// which no other node reads or writes in that step, and writes a slot that
+// belongs to a ghost-plane node at step t (read by nobody). Every slot is
+// therefore read and written by one thread per step. The slit's clock holds
+// t mod (nx, ny, R) and advances after every pull pass (not while the slit
+// is frozen, so a frozen slit's slots stay where they are).
+__device__ __forceinline__ int wrap_lo(int a, int n) { return a < 0 ? a + n : a; }   // a in [-n, n)
+__device__ __forceinline__ int wrap_hi(int a, int n) { return a >= n ? a - n : a; }  // a in [0, 2n)
+
+struct IpSlots {
+    int x, xm, xp, y, ym, yp, zr, zm, zp;  // the node's coordinates and c_a = +1 (m) / -1 (p) shifted by t + 1
+    int tx, ty, tz;                        // t mod (nx, ny, R)
+    int zb, R, nx, ny;
+    // the slot of direction i of the node at step t + 1 (= of its source at step t)
+    __device__ __forceinline__ int slot(int i) const
+    {
+        const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+        const int xx = cx > 0 ? xm : (cx < 0 ? xp : x);
+        const int yy = cy > 0 ? ym : (cy < 0 ? yp : y);
+        const int zz = cz > 0 ? zm : (cz < 0 ? zp : zr);
+        return ((zb + zz) * ny + yy) * nx + xx;
+    }
+    // the slot of the node's own direction opp(i) at step t (bounce-back of i)
+    __device__ __forceinline__ int wall_slot(int i) const
+    {
+        const int cx = kCx(i), cy = kCy(i), cz = kCz(i);
+        const int xx = cx > 0 ? wrap_hi(x + tx, nx) : (cx < 0 ? wrap_lo(x - tx, nx) : x);
+        const int yy = cy > 0 ? wrap_hi(y + ty, ny) : (cy < 0 ? wrap_lo(y - ty, ny) : y);
+        const int zz = cz > 0 ? wrap_hi(zr + tz, R) : (cz < 0 ? wrap_lo(zr - tz, R) : zr);
+        return ((zb + zz) * ny + yy) * nx + xx;
+    }
+};
+
+__device__ __forceinline__ IpSlots ip_slots(const Params& P, const SlitParam& S, int s, int x, int y, int z)
+{
+    const int4 c = __ldg(P.clk + s);
+    IpSlots q;
+    q.nx = P.g.nx;
+    q.ny = P.g.ny;
+    q.zb = S.zb;
+    q.R = S.R;
+    q.tx = c.x;
+    q.ty = c.y;
+    q.tz = c.z;
+    const int sx = wrap_hi(c.x + 1, q.nx), sy = wrap_hi(c.y + 1, q.ny), sz = wrap_hi(c.z + 1, q.R);
+    q.x = x;
+    q.xm = wrap_lo(x - sx, q.nx);
+    q.xp = wrap_hi(x + sx, q.nx);
+    q.y = y;
+    q.ym = wrap_lo(y - sy, q.ny);
+    q.yp = wrap_hi(y + sy, q.ny);
+    q.zr = z - S.zlo;
+    q.zm = wrap_lo(q.zr - sz, q.R);
+    q.zp = wrap_hi(q.zr + sz, q.R);
+    return q;
+}
+
+__global__ void k_tick(Params P, int4* clk)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= P.nslits || frozen(P, s)) return;
+    int4 c = clk[s];
+    c.x = c.x + 1 == P.g.nx ? 0 : c.x + 1;
+    c.y = c.y + 1 == P.g.ny ? 0 : c.y + 1;
+    c.z = c.z + 1 == P.sl[s].R ? 0 : c.z + 1;
+    clk[s] = c;
+}
+
+// direction i of the current state in node order (gap planes skipped):
+// to_pop = 0 gathers it from the buffer into canon, 1 scatters canon into it
+template <typename T>
+__global__ void k_pop_canon(Params P, T* pop, int i, T* canon, int to_pop)
+{
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= P.g.N) return;
+    int x, y, z;
+    decompose(P.g, idx, x, y, z);
+    const int s = slit_of(P, z);
+    if (s < 0) return;
+    long long at = idx;
+    if (P.inplace) {
+        // f_i(r, t) sits at the slot of coordinates r - t c_i
+        const SlitParam S = P.sl[s];
+        const int4 c = P.clk[s];
+        const int xx = kCx(i) > 0 ? wrap_lo(x - c.x, P.g.nx) : (kCx(i) < 0 ? wrap_hi(x + c.x, P.g.nx) : x);
+        const int yy = kCy(i) > 0 ? wrap_lo(y - c.y, P.g.ny) : (kCy(i) < 0 ? wrap_hi(y + c.y, P.g.ny) : y);
+        const int zr = z - S.zlo;
+        const int zz = kCz(i) > 0 ? wrap_lo(zr - c.z, S.R) : (kCz(i) < 0 ? wrap_hi(zr + c.z, S.R) : zr);
+        at = ((long long)(S.zb + zz) * P.g.ny + yy) * P.g.nx + xx;
+    }
+    T* q = pop + (long long)i * P.g.Npad + at;
+    if (to_pop)
+        *q = canon[idx];
+    else
+        canon[idx] = *q;
 }
 
 // moment fields dn, ux, uy, uz <-> four unpadded N-arrays (checkpoints)
@@ -1399,14 +1494,51 @@ constexpr int SQ_DN = 0, SQ_P = 1, SQ_CA = 4, SQ_CP = 7, SQ_X = 10, CSM_NF = 13;
 // receives quantity k. Each quantity ends in a rounding intrinsic (never
 // merged into a later multiply-add), so a kernel that uses them at once and
 // one that stores them first compute identical values.
+//
+// shifted (velocity-shifted second-order forcing, the force F from the
+// unshifted moments): BGK towards f^eq(n, u') with u' = u + F/(2 q), and the
+// source k [3 (c - u').F + 9 (c.u')(c.F)], k = 1 - omega/2. T_i is then
+// (1 - omega) e_i(u) + omega e_i(u') + that source, whose class split, with
+// T = alpha + beta.c + c.gamma.c, is P_a = beta_a, C_a = alpha + gamma_aa,
+// C_ab = alpha + gamma_aa + gamma_bb, X_ab = 2 gamma_ab:
+//   alpha   = -(3/2) q ((1 - omega) u.u + omega u'.u') - 3 k u'.F
+//   beta_a  = 3 q ((1 - omega) u_a + omega u'_a) + 3 k F_a
+//   gamma_ab = (9/2) q ((1 - omega) u_a u_b + omega u'_a u'_b) + (9/2) k (u'_a F_b + u'_b F_a).
 template <class St>
-__device__ __forceinline__ void src_terms(float d, float ux, float uy, float uz, float4 f, St st)
+__device__ __forceinline__ void src_terms(float d, float ux, float uy, float uz, float4 f, float om, bool shifted,
+                                          St st)
 {
     const float q1 = 1.f + d;
+    st(SQ_DN, d);
+    if (shifted) {
+        const float hq = 0.5f / q1;
+        const float vx = fmaf(hq, f.x, ux), vy = fmaf(hq, f.y, uy), vz = fmaf(hq, f.z, uz);  // u'
+        const float k = fmaf(-0.5f, om, 1.f), a1 = 1.f - om;
+        const float uu = ux * ux + uy * uy + uz * uz, vv = vx * vx + vy * vy + vz * vz;
+        const float vF = vx * f.x + vy * f.y + vz * f.z;
+        const float alpha = fmaf(-1.5f * q1, fmaf(a1, uu, om * vv), -3.f * k * vF);
+        const float u[3] = {ux, uy, uz}, v[3] = {vx, vy, vz}, F[3] = {f.x, f.y, f.z};
+        auto gam = [&](int a, int b) {
+            return fmaf(4.5f * q1, fmaf(a1, u[a] * u[b], om * (v[a] * v[b])), 4.5f * k * fmaf(v[a], F[b], v[b] * F[a]));
+        };
+        const float gxx = gam(0, 0), gyy = gam(1, 1), gzz = gam(2, 2);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            st(SQ_P + a, __fmul_rn(3.f, fmaf(q1, fmaf(a1, u[a], om * v[a]), k * F[a])));
+        st(SQ_CA + 0, __fadd_rn(alpha, gxx));
+        st(SQ_CA + 1, __fadd_rn(alpha, gyy));
+        st(SQ_CA + 2, __fadd_rn(alpha, gzz));
+        st(SQ_CP + 0, __fadd_rn(alpha, gxx + gyy));
+        st(SQ_CP + 1, __fadd_rn(alpha, gxx + gzz));
+        st(SQ_CP + 2, __fadd_rn(alpha, gyy + gzz));
+        st(SQ_X + 0, __fmul_rn(2.f, gam(0, 1)));
+        st(SQ_X + 1, __fmul_rn(2.f, gam(0, 2)));
+        st(SQ_X + 2, __fmul_rn(2.f, gam(1, 2)));
+        return;
+    }
     const float B = __fmul_rn(-1.5f * q1, ux * ux + uy * uy + uz * uz);
     const float a = 4.5f * q1, ax = a * ux * ux, ay = a * uy * uy, az = a * uz * uz;
     const float fw = 1.5f * f.w, b = 9.f * q1;
-    st(SQ_DN, d);
     st(SQ_P + 0, __fmul_rn(3.f, fmaf(q1, ux, f.x)));
     st(SQ_P + 1, __fmul_rn(3.f, fmaf(q1, uy, f.y)));
     st(SQ_P + 2, __fmul_rn(3.f, fmaf(q1, uz, f.z)));
@@ -1510,8 +1642,8 @@ __device__ __forceinline__ float mirror_diff(const float* s, const float* sp, fl
 // moments: base directions directly, derived ones as their partner's stored
 // value plus the difference (so the pairs' differences survive the rounding
 // of the large common parts); returns dn and writes u
-template <typename T>
-__device__ __forceinline__ float pull_finish(T* __restrict__ pout, long long idx, long long Npad, const float* v,
+template <typename T, class Addr>
+__device__ __forceinline__ float pull_finish(T* __restrict__ pout, Addr at, long long Npad, const float* v,
                                              float d79, float dnr, float& ux, float& uy, float& uz)
 {
     constexpr float w1 = 1.f / 18.f, w2 = 1.f / 36.f;
@@ -1542,7 +1674,7 @@ __device__ __forceinline__ float pull_finish(T* __restrict__ pout, long long idx
     // p_i - p_ip of a pair that differs in component a: u_a (6 + 18 R),
     // R = the shared part of c.u
     auto dp = [&](float ua, float R) { return ua * fmaf(18.f, R, 6.f); };
-    auto put = [&](int i, float h) { stp(pout + (long long)i * Npad + idx, sT * h); };
+    auto put = [&](int i, float h) { stp(pout + (long long)i * Npad + at(i), sT * h); };
     put(0, base(0, v[0]));
     put(5, base(5, v[5]));
     put(6, base(6, v[6]));
@@ -1644,13 +1776,15 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
     if (sq < 0 || frozen(P, sq)) return;
     const int pq = (q + g.hw) * g.py * g.px;
     const float4* Fq = F + (long long)zq * g.ny * g.nx;
+    const float om = P.sl[sq].inv_tau;
+    const bool shifted = P.shifted != 0;
 #pragma unroll
     for (int k = 0; k < CSM_KS; ++k) {
         if (k * NT >= CSM_HN || st.p[k] < 0) continue;
         const int h = threadIdx.x + k * NT;
         const int p = pq + st.p[k];
-        src_terms(__ldg(io.dn + p), __ldg(io.ux + p), __ldg(io.uy + p), __ldg(io.uz + p), __ldg(Fq + st.n[k]),
-                  [&](int j, float val) { slot[j * CSM_HN + h] = val; });
+        src_terms(__ldg(io.dn + p), __ldg(io.ux + p), __ldg(io.uy + p), __ldg(io.uz + p), __ldg(Fq + st.n[k]), om,
+                  shifted, [&](int j, float val) { slot[j * CSM_HN + h] = val; });
     }
 }
 
@@ -1664,12 +1798,26 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
 
 // the stored populations of directions [I0, I1) that stream into node
 // (x, y, z): v[i - I0]; bit i of bb marks a direction that arrives from a
-// wall (bounce-back: the node's own opposite population)
-template <int I0, int I1, typename T>
+// wall (bounce-back: the node's own opposite population). IP: in place
+// (slots from q, see above).
+template <int I0, int I1, bool IP, typename T>
 __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ pin, long long idx, int x, int y,
-                                         int z, int zlo, int zhi, float* v, unsigned& bb)
+                                         int z, int zlo, int zhi, float* v, unsigned& bb, const IpSlots& q)
 {
     const Geom& g = P.g;
+    if constexpr (IP) {
+#pragma unroll
+        for (int i = I0; i < I1; ++i) {
+            const int sz = z - kCz(i);
+            if (!g.zper && (sz < zlo || sz > zhi)) {
+                bb |= 1u << i;
+                v[i - I0] = ldp(pin + (long long)opp_of(i) * g.Npad + q.wall_slot(i));
+            } else {
+                v[i - I0] = ldp(pin + (long long)i * g.Npad + q.slot(i));
+            }
+        }
+        return;
+    }
     if (x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi) {
 #pragma unroll
         for (int i = I0; i < I1; ++i) v[i - I0] = ldp(pin + (long long)i * g.Npad + (idx - P.soff[i]));
@@ -1764,10 +1912,10 @@ __device__ __forceinline__ void csm_collide(const float* own, const float* below
 // slower at twice the warps). PF: the population gathers of the next plane
 // are issued before the current plane is staged and collided, so they are in
 // flight across both barriers (19 more live registers: five CTAs per SM).
-template <typename T, bool PF>
+template <typename T, bool PF, bool IP>
 __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
-    k_csm(Params P, const T* __restrict__ pin, T* __restrict__ pout, CsmIO io, const float4* __restrict__ F,
-          int lz, int tiles_x, int tiles_y, int* status)
+    k_csm(Params P, const T* pin, T* pout, CsmIO io, const float4* __restrict__ F, int lz, int tiles_x, int tiles_y,
+          int* status)
 {
     constexpr int NT = CSM_THREADS;
     extern __shared__ float sm[];
@@ -1789,7 +1937,10 @@ __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
         om = 0.f;
         if (act) {
             om = P.sl[s].inv_tau;
-            csm_pull<0, Q>(P, pin, ((long long)z * g.ny + y) * g.nx + x, x, y, z, P.sl[s].zlo, P.sl[s].zhi, v, bb);
+            IpSlots q;
+            if constexpr (IP) q = ip_slots(P, P.sl[s], s, x, y, z);
+            csm_pull<0, Q, IP>(P, pin, ((long long)z * g.ny + y) * g.nx + x, x, y, z, P.sl[s].zlo, P.sl[s].zhi, v,
+                               bb, q);
         }
     };
     float vn[Q];
@@ -1826,7 +1977,14 @@ __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
         csm_collide(own, sm + csm_slot(z - 1) * CSM_SLOT, sm + csm_slot(z + 1) * CSM_SLOT, hc,
                     (1.f - om) / store_scale<T>(), dnr, bb, v, d79);
         float ux, uy, uz;
-        const float dn = pull_finish<T>(pout, idx, g.Npad, v, d79, dnr, ux, uy, uz);
+        float dn;
+        if constexpr (IP) {
+            const int s = slit_of(P, z);
+            const IpSlots q = ip_slots(P, P.sl[s], s, x, y, z);
+            dn = pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, g.Npad, v, d79, dnr, ux, uy, uz);
+        } else {
+            dn = pull_finish<T>(pout, [&](int) { return idx; }, g.Npad, v, d79, dnr, ux, uy, uz);
+        }
         put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
     }
 }
@@ -1835,9 +1993,9 @@ __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
 // node and no staging; every source's quantities are formed where they are
 // used, by the same code as the staged ones, so both kernels give identical
 // results.
-template <typename T>
-__global__ void __launch_bounds__(128) k_pull_node(Params P, const T* __restrict__ pin, T* __restrict__ pout,
-                                                   CsmIO io, const float4* __restrict__ F, int* status)
+template <typename T, bool IP>
+__global__ void __launch_bounds__(128) k_pull_node(Params P, const T* pin, T* pout, CsmIO io,
+                                                   const float4* __restrict__ F, int* status)
 {
     const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (idx >= P.g.N) return;
@@ -1847,13 +2005,16 @@ __global__ void __launch_bounds__(128) k_pull_node(Params P, const T* __restrict
     const int s = slit_of(P, z);
     if (s < 0 || frozen(P, s)) return;
     const int zlo = P.sl[s].zlo, zhi = P.sl[s].zhi;
-    const float om1s = (1.f - P.sl[s].inv_tau) / store_scale<T>();
+    const float om = P.sl[s].inv_tau, om1s = (1.f - om) / store_scale<T>();
+    const bool shifted = P.shifted != 0;
     float v[Q];
     unsigned bb = 0;
-    csm_pull<0, Q>(P, pin, idx, x, y, z, zlo, zhi, v, bb);
+    IpSlots q;
+    if constexpr (IP) q = ip_slots(P, P.sl[s], s, x, y, z);
+    csm_pull<0, Q, IP>(P, pin, idx, x, y, z, zlo, zhi, v, bb, q);
     const int p = pidx(g, x, y, z);
     float own[CSM_NF];
-    src_terms(__ldg(io.dn + p), __ldg(io.ux + p), __ldg(io.uy + p), __ldg(io.uz + p), __ldg(F + idx),
+    src_terms(__ldg(io.dn + p), __ldg(io.ux + p), __ldg(io.uy + p), __ldg(io.uz + p), __ldg(F + idx), om, shifted,
               [&](int j, float val) { own[j] = val; });
     const float dnr = own[SQ_DN];
     // the source quantities of direction i, formed where they are used
@@ -1867,7 +2028,8 @@ __global__ void __launch_bounds__(128) k_pull_node(Params P, const T* __restrict
         if (g.zper) sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
         const int ps = p - P.nbr[i];
         src_terms(__ldg(io.dn + ps), __ldg(io.ux + ps), __ldg(io.uy + ps), __ldg(io.uz + ps),
-                  __ldg(F + (((long long)sz * g.ny + sy) * g.nx + sx)), [&](int j, float val) { out[j] = val; });
+                  __ldg(F + (((long long)sz * g.ny + sy) * g.nx + sx)), om, shifted,
+                  [&](int j, float val) { out[j] = val; });
     };
     auto wall = [&](int i) { return ((bb >> i) & 1u) != 0u; };
     auto diff = [&](auto ic, auto ipc) {
@@ -1908,7 +2070,9 @@ __global__ void __launch_bounds__(128) k_pull_node(Params P, const T* __restrict
     };
     for_dirs(one);
     float ux, uy, uz;
-    const float dn = pull_finish<T>(pout, idx, g.Npad, v, d79, dnr, ux, uy, uz);
+    const float dn = IP ? pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, g.Npad, v, d79, dnr, ux,
+                                         uy, uz)
+                        : pull_finish<T>(pout, [&](int) { return idx; }, g.Npad, v, d79, dnr, ux, uy, uz);
     put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
 }
 
@@ -2079,35 +2243,39 @@ cudaError_t launch_fill_outside(const Params& P, float* const* planes, const flo
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_noise(const Params& P, void* pop, float* dn, uint64_t seed, double amp,
-                              long long offset, cudaStream_t s)
+cudaError_t launch_init_noise(const Params& P, float* dn, uint64_t seed, double amp, long long offset,
+                              cudaStream_t s)
 {
-    if (P.storage == LBIF_STORE_F16)
-        k_init_noise<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, dn, seed, amp, offset);
-    else
-        k_init_noise<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, dn, seed, amp, offset);
+    k_init_noise<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, dn, seed, amp, offset);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_profiles(const Params& P, void* pop, float* const f[4], const float* n_z,
-                                 const float* ux_z, int hmax, cudaStream_t s)
+cudaError_t launch_init_profiles(const Params& P, float* const f[4], const float* n_z, const float* ux_z,
+                                 int hmax, cudaStream_t s)
 {
-    if (P.storage == LBIF_STORE_F16)
-        k_init_profiles<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, f[0], f[1], f[2], f[3], n_z,
-                                                                     ux_z, hmax);
-    else
-        k_init_profiles<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, f[0], f[1], f[2], f[3], n_z,
-                                                                    ux_z, hmax);
+    k_init_profiles<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, f[0], f[1], f[2], f[3], n_z, ux_z, hmax);
     return cudaGetLastError();
 }
 
-cudaError_t launch_init_fields(const Params& P, void* pop, float* const f[4], const float* rho,
-                               const float* u, cudaStream_t s)
+cudaError_t launch_init_fields(const Params& P, float* const f[4], const float* rho, const float* u,
+                               cudaStream_t s)
+{
+    k_init_fields<<<nblocks(P.g.N, 256), 256, 0, s>>>(P, f[0], f[1], f[2], f[3], rho, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tick(const Params& P, int4* clk, cudaStream_t s)
+{
+    k_tick<<<nblocks(P.nslits, 128), 128, 0, s>>>(P, clk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pop_canon(const Params& P, void* pop, int i, void* canon, int to_pop, cudaStream_t s)
 {
     if (P.storage == LBIF_STORE_F16)
-        k_init_fields<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, f[0], f[1], f[2], f[3], rho, u);
+        k_pop_canon<__half><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (__half*)pop, i, (__half*)canon, to_pop);
     else
-        k_init_fields<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, f[0], f[1], f[2], f[3], rho, u);
+        k_pop_canon<float><<<nblocks(P.g.N, 256), 256, 0, s>>>(P, (float*)pop, i, (float*)canon, to_pop);
     return cudaGetLastError();
 }
 
@@ -2239,7 +2407,7 @@ cudaError_t launch_force(const Params& P, const Fields& f, const float4* Ft, flo
 
 bool csm_ok(const Geom& g) { return g.nx >= CSM_TX && g.ny >= CSM_TY; }
 
-template <typename T, bool PF>
+template <typename T, bool PF, bool IP>
 static cudaError_t csm_tiled(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
                              int* status, int lz, cudaStream_t s)
 {
@@ -2256,11 +2424,11 @@ static cudaError_t csm_tiled(const Params& P, const void* pin, void* pout, const
     if (e != cudaSuccess) return e;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(configured.load() & bit)) {
-        e = cudaFuncSetAttribute(k_csm<T, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_csm<T, PF, IP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured.fetch_or(bit);
     }
-    k_csm<T, PF><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const T*)pin, (T*)pout, io, F, lz, tx, ty, status);
+    k_csm<T, PF, IP><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, (const T*)pin, (T*)pout, io, F, lz, tx, ty, status);
     return cudaGetLastError();
 }
 
@@ -2268,19 +2436,28 @@ cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO
                        int* status, int lz, int prefetch, cudaStream_t s)
 {
     const Geom& g = P.g;
+    const bool ip = P.inplace != 0, h16 = P.storage == LBIF_STORE_F16;
     if (!csm_ok(g)) {
-        if (P.storage == LBIF_STORE_F16)
-            k_pull_node<__half><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const __half*)pin, (__half*)pout, io, F, status);
-        else
-            k_pull_node<float><<<nblocks(g.N, 128), 128, 0, s>>>(P, (const float*)pin, (float*)pout, io, F, status);
+        const unsigned nb = nblocks(g.N, 128);
+        if (h16 && ip) k_pull_node<__half, true><<<nb, 128, 0, s>>>(P, (const __half*)pin, (__half*)pout, io, F, status);
+        if (h16 && !ip) k_pull_node<__half, false><<<nb, 128, 0, s>>>(P, (const __half*)pin, (__half*)pout, io, F, status);
+        if (!h16 && ip) k_pull_node<float, true><<<nb, 128, 0, s>>>(P, (const float*)pin, (float*)pout, io, F, status);
+        if (!h16 && !ip) k_pull_node<float, false><<<nb, 128, 0, s>>>(P, (const float*)pin, (float*)pout, io, F, status);
         return cudaGetLastError();
     }
     if (lz <= 0) lz = CSM_LZ;
-    if (P.storage == LBIF_STORE_F16)
-        return prefetch ? csm_tiled<__half, true>(P, pin, pout, io, F, status, lz, s)
-                        : csm_tiled<__half, false>(P, pin, pout, io, F, status, lz, s);
-    return prefetch ? csm_tiled<float, true>(P, pin, pout, io, F, status, lz, s)
-                    : csm_tiled<float, false>(P, pin, pout, io, F, status, lz, s);
+    if (h16) {
+        if (ip)
+            return prefetch ? csm_tiled<__half, true, true>(P, pin, pout, io, F, status, lz, s)
+                            : csm_tiled<__half, false, true>(P, pin, pout, io, F, status, lz, s);
+        return prefetch ? csm_tiled<__half, true, false>(P, pin, pout, io, F, status, lz, s)
+                        : csm_tiled<__half, false, false>(P, pin, pout, io, F, status, lz, s);
+    }
+    if (ip)
+        return prefetch ? csm_tiled<float, true, true>(P, pin, pout, io, F, status, lz, s)
+                        : csm_tiled<float, false, true>(P, pin, pout, io, F, status, lz, s);
+    return prefetch ? csm_tiled<float, true, false>(P, pin, pout, io, F, status, lz, s)
+                    : csm_tiled<float, false, false>(P, pin, pout, io, F, status, lz, s);
 }
 
 cudaError_t launch_wait_selftest(long long polls, int* status, cudaStream_t s)

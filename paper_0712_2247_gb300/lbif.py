@@ -38,12 +38,13 @@ class Walls(ctypes.Structure):
 class Force(ctypes.Structure):
     _fields_ = [("body", ctypes.c_double * 3), ("hs", ctypes.c_int32), ("coupling", ctypes.c_int32),
                 ("regularize", ctypes.c_int32), ("g2_form", ctypes.c_int32), ("tail", ctypes.c_int32),
-                ("eps", ctypes.c_double), ("rcut", ctypes.c_double), ("c2", ctypes.c_int32)]
+                ("eps", ctypes.c_double), ("rcut", ctypes.c_double), ("c2", ctypes.c_int32),
+                ("shifted", ctypes.c_int32)]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int32), ("seed", ctypes.c_uint64), ("noise", ctypes.c_double),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("inplace", ctypes.c_int32)]
 
 
 SIGNATURES = {
@@ -151,11 +152,12 @@ class Slit:
                  periodic_z: bool = False, body: Sequence[float] = (0.0, 0.0, 0.0), hs: bool = True,
                  coupling: bool = True, regularize: bool = True, g2_form: int = 0,
                  tail: bool = False, eps: float = 1.0, rcut: float = 2.5, storage: int = STORE_F32,
-                 seed: int = 0, noise: float = 1e-3, stream: Optional[int] = None, c2: bool = False):
+                 seed: int = 0, noise: float = 1e-3, stream: Optional[int] = None, c2: bool = False,
+                 inplace: bool = False, shifted: bool = False):
         self._lib = load_library()
         f = Force((ctypes.c_double * 3)(*[float(b) for b in body]), int(hs), int(coupling),
-                  int(regularize), int(g2_form), int(tail), float(eps), float(rcut), int(c2))
-        o = Opts(int(storage), int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), stream)
+                  int(regularize), int(g2_form), int(tail), float(eps), float(rcut), int(c2), int(shifted))
+        o = Opts(int(storage), int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), stream, int(inplace))
         h = _vp()
         rc = self._lib.lbif_create(ctypes.byref(h), Grid(nx, ny, nz), float(sigma), float(eta),
                                    float(tau), Walls(1 if periodic_z else 0), ctypes.byref(f),
@@ -307,7 +309,7 @@ class Ensemble(Slit):
     def __init__(self, H, eta, F, tau, sigma: float, nx: int = 32, ny: int = 32, *,
                  hs: bool = True, coupling: bool = True, regularize: bool = True,
                  g2_form: int = 0, storage: int = STORE_F16, seed: int = 0, noise: float = 1e-3,
-                 stream: Optional[int] = None):
+                 stream: Optional[int] = None, inplace: bool = False):
         self._lib = load_library()
         H = np.ascontiguousarray(H, dtype=np.int32)
         eta = np.ascontiguousarray(eta, dtype=np.float64)
@@ -317,7 +319,7 @@ class Ensemble(Slit):
         assert len(eta) == len(F) == len(tau) == n
         f = Force((ctypes.c_double * 3)(0.0, 0.0, 0.0), int(hs), int(coupling), int(regularize),
                   int(g2_form), 0, 1.0, 2.5)
-        o = Opts(int(storage), int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), stream)
+        o = Opts(int(storage), int(seed) & 0xFFFFFFFFFFFFFFFF, float(noise), stream, int(inplace))
         h = _vp()
         pd = lambda a: a.ctypes.data_as(_pd)
         rc = self._lib.lbif_batch_create(ctypes.byref(h), n, H.ctypes.data_as(ctypes.POINTER(_i32)),
