@@ -371,11 +371,11 @@ def run_reference(args, world, rank):
     return 0
 
 
-def _slit(W, storage, seed, stream):
+def _slit(W, storage, seed, stream, inplace=False):
     from paper_0712_2247_gb300 import lbif
 
     return lbif.Slit(W.nx, W.ny, W.nz, W.sigma, W.eta, W.tau, body=W.body, storage=storage,
-                     seed=seed, stream=stream)
+                     seed=seed, stream=stream, inplace=inplace)
 
 
 def time_steps(g, steps, stream, storage, N, peak):
@@ -401,20 +401,28 @@ def time_steps(g, steps, stream, storage, N, peak):
             "step_roofline_frac": bytes_alg(storage) * N / (mps * 1e-3) / 1e9 / peak}, kms, nl, ms
 
 
-def storage_f16_leg(args, stream, peak):
-    """The benchmark slit with FP16 population storage (2^8 times the
-    non-equilibrium parts): its own step time, kernels and roofline."""
+def storage_leg(args, stream, peak, storage=1, inplace=False):
+    """The benchmark slit with another population storage: FP16 (2^8 times
+    the non-equilibrium parts) or one buffer in place: its own step time,
+    kernels, roofline and device memory."""
+    import torch
+
     from paper_0712_2247_gb300.inputs import c2
 
-    W = c2(args.eta, 1)
-    g = _slit(W, 1, W.seed, stream.cuda_stream)
+    W = c2(args.eta, storage)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    g = _slit(W, storage, W.seed, stream.cuda_stream, inplace=inplace)
+    torch.cuda.synchronize()
+    dev_bytes = free0 - torch.cuda.mem_get_info()[0]
     g.step(args.warmup)
     g.autotune(3)
     g.step(1)
-    r, _, _, _ = time_steps(g, args.steps, stream, 1, W.nodes, peak)
+    r, _, _, _ = time_steps(g, args.steps, stream, storage, W.nodes, peak)
     r["status"] = g.status()
     r["autotuned"] = g.shapes()
-    r["pass"] = "pull"
+    r["pass"] = "pull, in place" if inplace else "pull"
+    r["device_bytes"] = dev_bytes
     g.close()
     dom = max(r["kernels"], key=lambda k: r["kernels"][k]["ms"])
     r["roofline"] = {"kernel": dom, "achieved": r["kernels"][dom]["gbs_alg"], "peak": peak,
@@ -535,7 +543,8 @@ def run_ours(args, world, rank, local):
         except Exception as e:  # reported, never hides the throughput line
             return {"error": f"{type(e).__name__}: {e}"}
 
-    f16 = leg(not args.no_sweep and storage == 0, storage_f16_leg, args, stream, peak)
+    f16 = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 1, False)
+    inpl = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 0, True)
     sweep = leg(not args.no_sweep and storage == 0 and args.eta == 0.25, eta_sweep_leg, args, stream, peak)
     tail = leg(not args.no_tail, tail_leg, args)
     mlp = leg(not args.no_mlp, mlp_leg, args)
@@ -562,6 +571,7 @@ def run_ours(args, world, rank, local):
                      "bytes_alg_per_launch": dom_bytes},
         "cpu_baseline": cpu,
         "storage_f16": f16,
+        "storage_inplace": inpl,
         "eta_sweep": sweep,
         "ensemble": ens,
         "tail_workload": tail,
