@@ -278,12 +278,21 @@ def ensemble_leg(args):
     e.run(tol=1e-300, max_steps=steps, check_every=100)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    # the same kernels launched one by one, each timed with CUDA events: what
+    # a single persistent launch could save at most is the graph's time per
+    # step beyond the kernels' own (launch gaps and the residual checks)
+    kms, nl = e.step_profiled(200)
+    per = {k: kms[k] / nl[k] for k in kms if nl[k]}
+    kern = sum(per.values())
     fluid = int(np.sum(p.H)) * p.nx * p.ny
     e.close()
+    graph_ms = dt / steps * 1e3
     return {"workload": "256 slits 32x32xH, sigma=4, FP16 storage, graph-captured steps",
             "fluid_nodes": fluid, "stacked_nodes": e.N, "steps": steps, "seconds": dt,
             "mlups_fluid": fluid * steps / dt / 1e6, "autotuned": {"ball_ctas": ball, "force_group": group,
-                                                        "ball_staging": "tma" if staging else "loads"}}
+                                                        "ball_staging": "tma" if staging else "loads"},
+            "graph_ms_per_step": graph_ms, "kernel_ms_per_step": kern, "kernels_ms": per,
+            "beyond_kernels_frac": (graph_ms - kern) / graph_ms}
 
 
 def mlp_leg(args):

@@ -365,6 +365,8 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
         for (int i = 0; i < Q; ++i) {
             P.nbr[i] = padded_offset(g, cx[i], cy[i], cz[i]);
             P.soff[i] = cx[i] + (long long)cy[i] * g.nx + (long long)cz[i] * g.nx * g.ny;
+            P.dbase[i] = (long long)i * g.Npad;
+            P.doff[i] = P.dbase[i] - P.soff[i];
         }
     }
     if (build_shell(P)) {

@@ -93,6 +93,8 @@ struct Params {
     const int4* clk;      // in place: per slit (t mod nx, t mod ny, t mod R) of its step t
     int nbr[Q];           // padded offsets of the 19 lattice neighbours
     long long soff[Q];    // node-index offsets of the 19 neighbours (no wrap)
+    long long dbase[Q];   // i Npad: start of direction i in a population buffer
+    long long doff[Q];    // i Npad - soff[i]: where node idx pulls direction i from (no wrap)
     Shell sh;
 };
 

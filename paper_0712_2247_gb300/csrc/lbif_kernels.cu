@@ -1643,7 +1643,7 @@ __device__ __forceinline__ float mirror_diff(const float* s, const float* sp, fl
 // value plus the difference (so the pairs' differences survive the rounding
 // of the large common parts); returns dn and writes u
 template <typename T, class Addr>
-__device__ __forceinline__ float pull_finish(T* __restrict__ pout, Addr at, long long Npad, const float* v,
+__device__ __forceinline__ float pull_finish(T* __restrict__ pout, Addr at, const long long* dbase, const float* v,
                                              float d79, float dnr, float& ux, float& uy, float& uz)
 {
     constexpr float w1 = 1.f / 18.f, w2 = 1.f / 36.f;
@@ -1674,7 +1674,7 @@ __device__ __forceinline__ float pull_finish(T* __restrict__ pout, Addr at, long
     // p_i - p_ip of a pair that differs in component a: u_a (6 + 18 R),
     // R = the shared part of c.u
     auto dp = [&](float ua, float R) { return ua * fmaf(18.f, R, 6.f); };
-    auto put = [&](int i, float h) { stp(pout + (long long)i * Npad + at(i), sT * h); };
+    auto put = [&](int i, float h) { stp(pout + (dbase[i] + at(i)), sT * h); };
     put(0, base(0, v[0]));
     put(5, base(5, v[5]));
     put(6, base(6, v[6]));
@@ -1811,16 +1811,16 @@ __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ 
             const int sz = z - kCz(i);
             if (!g.zper && (sz < zlo || sz > zhi)) {
                 bb |= 1u << i;
-                v[i - I0] = ldp(pin + (long long)opp_of(i) * g.Npad + q.wall_slot(i));
+                v[i - I0] = ldp(pin + (P.dbase[opp_of(i)] + q.wall_slot(i)));
             } else {
-                v[i - I0] = ldp(pin + (long long)i * g.Npad + q.slot(i));
+                v[i - I0] = ldp(pin + (P.dbase[i] + q.slot(i)));
             }
         }
         return;
     }
     if (x > 0 && x < g.nx - 1 && y > 0 && y < g.ny - 1 && z > zlo && z < zhi) {
 #pragma unroll
-        for (int i = I0; i < I1; ++i) v[i - I0] = ldp(pin + (long long)i * g.Npad + (idx - P.soff[i]));
+        for (int i = I0; i < I1; ++i) v[i - I0] = ldp(pin + (idx + P.doff[i]));
         return;
     }
 #pragma unroll
@@ -1832,10 +1832,10 @@ __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ 
             sz = sz < 0 ? sz + g.nz : (sz >= g.nz ? sz - g.nz : sz);
         } else if (sz < zlo || sz > zhi) {
             bb |= 1u << i;
-            v[i - I0] = ldp(pin + (long long)opp_of(i) * g.Npad + idx);
+            v[i - I0] = ldp(pin + (P.dbase[opp_of(i)] + idx));
             continue;
         }
-        v[i - I0] = ldp(pin + (long long)i * g.Npad + (((long long)sz * g.ny + sy) * g.nx + sx));
+        v[i - I0] = ldp(pin + (P.dbase[i] + (((long long)sz * g.ny + sy) * g.nx + sx)));
     }
 }
 
@@ -1981,9 +1981,9 @@ __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
         if constexpr (IP) {
             const int s = slit_of(P, z);
             const IpSlots q = ip_slots(P, P.sl[s], s, x, y, z);
-            dn = pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, g.Npad, v, d79, dnr, ux, uy, uz);
+            dn = pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, P.dbase, v, d79, dnr, ux, uy, uz);
         } else {
-            dn = pull_finish<T>(pout, [&](int) { return idx; }, g.Npad, v, d79, dnr, ux, uy, uz);
+            dn = pull_finish<T>(pout, [&](int) { return idx; }, P.dbase, v, d79, dnr, ux, uy, uz);
         }
         put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
     }
@@ -2070,9 +2070,9 @@ __global__ void __launch_bounds__(128) k_pull_node(Params P, const T* pin, T* po
     };
     for_dirs(one);
     float ux, uy, uz;
-    const float dn = IP ? pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, g.Npad, v, d79, dnr, ux,
+    const float dn = IP ? pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, P.dbase, v, d79, dnr, ux,
                                          uy, uz)
-                        : pull_finish<T>(pout, [&](int) { return idx; }, g.Npad, v, d79, dnr, ux, uy, uz);
+                        : pull_finish<T>(pout, [&](int) { return idx; }, P.dbase, v, d79, dnr, ux, uy, uz);
     put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
 }
 

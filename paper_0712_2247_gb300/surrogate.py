@@ -232,6 +232,7 @@ def warm_vs_cold(net: MLP, scaling: Scaling, p: inputs.Ensemble, nx: int = 32, n
         "warm": {"wall_s": ww + t_pred, "predict_s": t_pred, "steps_mean": float(ws[ws > 0].mean()),
                  "steps_max": int(ws.max()), "not_converged": int((ws <= 0).sum())},
         "wall_speedup": cw / (ww + t_pred),
+        "both_converged": int(both.sum()),
         "steps_ratio_mean": float((cs[ok] / ws[ok]).mean()) if ok.any() else None,
         "final_profile_diff": {"n_max": float(en.max()), "ux_max": float(eu.max()),
                                "n_max_both_below_tol": float(en[both].max()) if both.any() else None,
