@@ -243,8 +243,11 @@ int lbif_selftest_wait(int64_t polls, int32_t* timed_out);
  * current state (trials launches each) and keep the fastest: the ball
  * kernel's CTA target and its plane staging (1 = tensor-memory-accelerator
  * copies, 0 = plain loads), the force kernel's tile-group edge, and the pull
- * pass's z planes per CTA segment (8, 16, 32) and gather prefetch (the next
- * plane's populations loaded while the current one is collided). Trials
+ * pass's z planes per CTA segment (8, 16, 32) and its gathers (plain; the
+ * next plane's populations loaded while the current one is collided; or the
+ * per-direction source boxes of each tile copied into shared memory one plane
+ * ahead by the tensor-memory accelerator, two-buffer handles whose x rows
+ * are a multiple of 16 bytes). Trials
  * write only buffers the step overwrites, so the state is unchanged, and no
  * choice changes the arithmetic (results are bit-identical). Chosen values
  * (each may be NULL): ball CTA target, force tile-group edge in nodes, ball
@@ -254,8 +257,14 @@ int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, int32_t* fo
 /* The launch shapes in use: shapes[0] ball CTA target (0 = default),
  * [1] force tile-group edge (0 = default), [2] ball staging (1 = tensor-
  * memory accelerator), [3] pull-pass z planes per segment (0 = default 16),
- * [4] pull-pass gather prefetch (0 or 1). */
+ * [4] pull-pass gathers (0 plain, 1 prefetched, 2 tensor-memory accelerator). */
 int lbif_get_shapes(lbif_handle h, int32_t shapes[5]);
+/* Set the launch shapes (same order and meaning as lbif_get_shapes) instead of
+ * timing them; no shape changes the arithmetic. Accepted: [0] 0 or 1..2^20,
+ * [1] 0 or 1..2^20, [2] 0/1, [3] 0 or 1..2^20, [4] 0/1/2. LBIF_ERR_ARG for a value
+ * out of range; LBIF_ERR_UNSUPPORTED for [2] = 1 or [4] = 2 on a handle
+ * without the tensor maps they read (none is changed then). */
+int lbif_set_shapes(lbif_handle h, const int32_t shapes[5]);
 
 /* ---- warm-start network -------------------------------------------------
  * A multilayer perceptron nin -> nhidden layers of width `hidden` (GELU, erf

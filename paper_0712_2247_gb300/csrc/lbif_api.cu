@@ -34,7 +34,7 @@ struct lbif_ctx {
     float* u[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     int fcur = 0;                     // dn[fcur], u[fcur]: the moments of step t (pop[cur] refers to them)
     int csm_lz = 0;                   // z planes per CTA of the pull pass (0 = default)
-    int csm_pf = 0;                   // pull pass with the next plane's gathers prefetched (autotuner)
+    int csm_pf = 0;                   // pull-pass gathers: 0 plain, 1 prefetched, 2 TMA boxes (autotuner)
     float* dG = nullptr;
     float4* Ft = nullptr;
     float4* F = nullptr;              // F / n0 per node (force kernel -> collision kernel)
@@ -58,6 +58,8 @@ struct lbif_ctx {
     int ball_want = 0, force_group = 0;  // launch shapes (0 = defaults; set by the autotuner)
     CUtensorMap ball_map[2];             // tensor maps of dn[0..1] for the ball kernel's tiles
     bool ball_map_ok = false;
+    CUtensorMap pop_map[2];              // tensor maps of pop[0..1] for the pull pass's source boxes
+    bool pop_map_ok = false;
     bool ball_tma = true;                // stage the ball tiles with the maps (autotuner's choice)
     cudaGraphExec_t graph = nullptr;
     int graph_steps = 0;
@@ -123,6 +125,33 @@ static bool make_ball_map(const Geom& g, int sigma, float* base, CUtensorMap* ou
     return enc(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 4-D map (x, y, z, direction) of a two-buffer population array, with the
+// pull pass's per-direction source box; false where the layout does not
+// allow one (rows not a multiple of 16 bytes, grids narrower than a box).
+static bool make_pop_map(const Params& P, void* base, CUtensorMap* out)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    const Geom& g = P.g;
+    if (!enc || P.inplace || !csm_ok(g)) return false;
+    const int es = P.storage == LBIF_STORE_F16 ? 2 : 4;
+    int W, H;
+    pop_box(P.storage, &W, &H);
+    if (((long long)g.nx * es) % 16 || ((long long)g.Npad * es) % 16 || g.nx < W || g.ny < H + 2) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, (cuuint64_t)Q};
+    cuuint64_t strides[3] = {(cuuint64_t)g.nx * es, (cuuint64_t)g.nx * g.ny * es, (cuuint64_t)g.Npad * es};
+    cuuint32_t box[4] = {(cuuint32_t)W, (cuuint32_t)H, 1, 1};
+    cuuint32_t ests[4] = {1, 1, 1, 1};
+    return enc(out, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims,
+               strides, box, ests, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// the map of the population buffer the pull pass reads (pop[i]), or NULL
+static const CUtensorMap* pop_map(const lbif_ctx* h, int i)
+{
+    return h->pop_map_ok ? &h->pop_map[i] : nullptr;
 }
 
 // the map of the buffer the ball kernel reads (dn[i]), or NULL
@@ -431,6 +460,8 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
     } while (0)
     ALLOC(h->pop[0], pb);
     if (!P.inplace) ALLOC(h->pop[1], pb);
+    h->pop_map_ok = !P.inplace && make_pop_map(P, h->pop[0], &h->pop_map[0]) &&
+                    make_pop_map(P, h->pop[1], &h->pop_map[1]);
     ALLOC(h->clk_d, sizeof(int4) * h->sl.size());
     ALLOC(h->F, sizeof(float4) * (size_t)g.N);
     ALLOC(h->status_d, sizeof(int));
@@ -644,7 +675,7 @@ static int collide_stream(lbif_ctx* h)
         CK(h, launch_tick(P, h->clk_d, h->stream));
     } else {
         CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, h->F, h->status_d, h->csm_lz, h->csm_pf,
-                         h->stream));
+                         h->stream, pop_map(h, h->cur)));
         h->cur ^= 1;
     }
     h->fcur ^= 1;
@@ -1201,6 +1232,27 @@ extern "C" int lbif_get_shapes(lbif_handle h, int32_t shapes[5])
     return LBIF_OK;
 }
 
+extern "C" int lbif_set_shapes(lbif_handle h, const int32_t shapes[5])
+{
+    if (!h || !shapes) return fail(h, LBIF_ERR_ARG, "lbif_set_shapes: bad arguments");
+    const int32_t* v = shapes;
+    if (v[0] < 0 || v[0] > (1 << 20) || v[1] < 0 || v[1] > (1 << 20) || v[2] < 0 || v[2] > 1 || v[3] < 0 ||
+        v[3] > (1 << 20) || v[4] < 0 || v[4] > 2)
+        return fail(h, LBIF_ERR_ARG, "lbif_set_shapes: value out of range");
+    if ((v[2] == 1 && !h->ball_map_ok) || (v[4] == 2 && !h->pop_map_ok))
+        return fail(h, LBIF_ERR_UNSUPPORTED, "lbif_set_shapes: this handle has no tensor map for that staging");
+    h->ball_want = v[0];
+    h->force_group = v[1];
+    h->ball_tma = v[2] == 1;
+    h->csm_lz = v[3];
+    h->csm_pf = v[4];
+    if (h->graph) {
+        cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+    }
+    return LBIF_OK;
+}
+
 extern "C" int lbif_get_fused(lbif_handle h, int32_t* fused)
 {
     if (!h || !fused) return fail(h, LBIF_ERR_ARG, "lbif_get_fused: bad arguments");
@@ -1269,7 +1321,9 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
             best_group = gsz;
         }
     }
-    // Pull pass: z planes per CTA segment x gather prefetch. A trial reads the
+    // Pull pass: z planes per CTA segment x gathers (plain, prefetched one
+    // plane ahead, tensor-memory-accelerator boxes when the handle has
+    // population maps). A trial reads the
     // current populations and fields and writes only the next step's buffers
     // (not adopted), so trials change no state either.
     int best_lz = h->csm_lz, best_pf = h->csm_pf;
@@ -1283,12 +1337,13 @@ extern "C" int lbif_autotune(lbif_handle h, int32_t trials, int32_t* ball_want, 
         CsmIO io{h->dn[h->fcur], u[0], u[1], u[2], h->dn[h->fcur ^ 1], w[0], w[1], w[2]};
         const int lzs[] = {8, 16, 32};
         best = 1e30f;
-        for (int pf = 0; pf <= 1; ++pf)
+        for (int pf = 0; pf <= (h->pop_map_ok ? 2 : 1); ++pf)
             for (int lz : lzs) {
                 float tot = 0.f;
                 for (int k = 0; k < trials + 1; ++k) {
                     CK(h, cudaEventRecord(e0, h->stream));
-                    CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, Fp, h->status_d, lz, pf, h->stream));
+                    CK(h, launch_csm(P, h->pop[h->cur], h->pop[h->cur ^ 1], io, Fp, h->status_d, lz, pf, h->stream,
+                                     pop_map(h, h->cur)));
                     CK(h, cudaEventRecord(e1, h->stream));
                     CK(h, cudaEventSynchronize(e1));
                     float ms;

@@ -166,12 +166,17 @@ cudaError_t launch_tail_spectral(const Params& P, const float* dn, int D, float2
                                  cudaStream_t s);
 // one step's collision, pull streaming and the moments of the new
 // populations (CsmIO); lz: z planes per CTA segment of the tiled kernel
-// (<= 0: default); prefetch: issue the next plane's population gathers
-// before the current plane is collided. Grids narrower than one tile run
-// the per-node kernel (lz, prefetch unused).
+// (<= 0: default); prefetch: 0 plain, 1 the next plane's population gathers
+// issued before the current plane is collided, 2 the gathers brought in by
+// the tensor-memory accelerator from pmap (a 4-D map of pin: x, y, z,
+// direction, box from pop_box; two-buffer layout only; bit 4 of status
+// records a bounded wait that ran out). Grids narrower than one tile run the
+// per-node kernel (lz, prefetch unused).
 bool csm_ok(const Geom& g);
 cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
-                       int* status, int lz, int prefetch, cudaStream_t s);
+                       int* status, int lz, int prefetch, cudaStream_t s, const CUtensorMap* pmap = nullptr);
+// box (x extent W, y extent H) of the tensor-memory-accelerator pull pass
+void pop_box(int storage, int* W, int* H);
 // bounded mbarrier wait on a barrier nothing completes: sets bit 4 of status
 cudaError_t launch_wait_selftest(long long polls, int* status, cudaStream_t s);
 cudaError_t launch_force_soa(const Params& P, const float4* F, float* out, cudaStream_t s);

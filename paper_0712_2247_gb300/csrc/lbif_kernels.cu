@@ -1348,8 +1348,11 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
 // x test is taken by whole warps; lanes past the grid's edge stay, on the
 // row's first block, until the stores)
 constexpr int FORCE_NT = 64;
+#ifndef FORCE_MINB
+#define FORCE_MINB (512 / FORCE_NT)
+#endif
 template <int SIG, bool C2, bool LN>
-__global__ void __launch_bounds__(FORCE_NT, 512 / FORCE_NT) k_force4(Params P, TileMap tm, Fields fl,
+__global__ void __launch_bounds__(FORCE_NT, FORCE_MINB) k_force4(Params P, TileMap tm, Fields fl,
                                                 const float4* __restrict__ Ft, float4* __restrict__ F)
 {
     const Geom& g = P.g;
@@ -1989,6 +1992,156 @@ __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
     }
 }
 
+// The pull pass with its population gathers brought in by the tensor-memory
+// accelerator (two-buffer layout). For every plane whose 19 sources lie
+// inside the grid - interior tiles, no wall direction, away from the ends of
+// a periodic z - one thread issues, one plane ahead, one copy per direction
+// i of the tile's source box (the tile shifted by -c_i, widened in x to
+// 16-byte boundaries: BW nodes from x0 - XM when c_ix = 1, else from x0;
+// a 4-D tensor map: x, y, z, direction) into one of two shared-memory
+// stages, completion counted in bytes on an mbarrier; the threads then read
+// their 19 values from there. Other planes gather directly. The arithmetic
+// is k_csm's (identical results).
+template <typename T>
+__host__ __device__ constexpr int tma_xm() { return sizeof(T) == 2 ? 8 : 4; }
+template <typename T>
+__host__ __device__ constexpr int tma_bw() { return CSM_TX + tma_xm<T>(); }
+template <typename T>
+__host__ __device__ constexpr int tma_box_bytes() { return tma_bw<T>() * CSM_TY * (int)sizeof(T); }
+template <typename T>
+__host__ __device__ constexpr int tma_box_pitch() { return (tma_box_bytes<T>() + 127) / 128 * 128; }
+__host__ __device__ constexpr int csm_ring_bytes() { return (3 * CSM_SLOT * 4 + 127) / 128 * 128; }
+template <typename T>
+__host__ __device__ constexpr int csm_tma_smem_bytes() { return csm_ring_bytes() + 2 * Q * tma_box_pitch<T>() + 16; }
+
+void pop_box(int storage, int* W, int* H)
+{
+    *W = storage == LBIF_STORE_F16 ? tma_bw<__half>() : tma_bw<float>();
+    *H = CSM_TY;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CSM_THREADS, 4)
+    k_csm_tma(Params P, const __grid_constant__ CUtensorMap pmap, const T* pin, T* pout, CsmIO io,
+              const float4* __restrict__ F, int lz, int tiles_x, int tiles_y, int* status)
+{
+    constexpr int NT = CSM_THREADS, XM = tma_xm<T>(), BW = tma_bw<T>(), BOX = tma_box_bytes<T>();
+    constexpr int PB = tma_box_pitch<T>(), SB = Q * PB;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    float* sm = reinterpret_cast<float*>(smraw);
+    unsigned char* stg = smraw + csm_ring_bytes();
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(stg + 2 * SB);
+    const Geom& g = P.g;
+    const int tiles = tiles_x * tiles_y;
+    const int tile = blockIdx.x % tiles, seg = blockIdx.x / tiles;
+    const int x0 = (tile % tiles_x) * CSM_TX, y0 = (tile / tiles_x) * CSM_TY;
+    const int t = threadIdx.x;
+    const int tx = t % CSM_TX, ty = t / CSM_TX;
+    const int x = x0 + tx, y = y0 + ty;
+    const int hc = (ty + 1) * CSM_HX + tx + 1;
+    const bool in_xy = x < g.nx && y < g.ny;
+    const int zb = seg * lz, ze = min(zb + lz, g.nz);
+    const bool interior = x0 >= 1 && x0 + CSM_TX <= g.nx - 1 && y0 >= 1 && y0 + CSM_TY <= g.ny - 1;
+    // every source of plane z inside the grid and no wall direction (CTA-uniform)
+    auto plane_tma = [&](int z) -> bool {
+        if (!interior || z < 1 || z > g.nz - 2) return false;
+        const int s = slit_of(P, z);
+        if (s < 0 || frozen(P, s)) return false;
+        return z > P.sl[s].zlo && z < P.sl[s].zhi;
+    };
+    if (t == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&pmap)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar)) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(mbar + 1)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int z) {  // one thread: the 19 boxes of plane z into stage z & 1
+        const int b = z & 1;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar + b)),
+                     "r"((uint32_t)(Q * BOX))
+                     : "memory");
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+                "%5}], [%6];" ::"r"(smem_addr(stg + b * SB + i * PB)),
+                "l"(reinterpret_cast<uint64_t>(&pmap)), "r"(kCx(i) > 0 ? x0 - XM : x0), "r"(y0 - kCy(i)),
+                "r"(z - kCz(i)), "r"(i), "r"(smem_addr(mbar + b))
+                : "memory");
+    };
+    uint32_t pbits = 0u;  // bit b: the parity expected next on stage b
+    uint32_t pend = 0u;  // bit b: stage b has copies in flight
+    // bounded wait for stage b's copies; false if it ran out
+    auto wait_stage = [&](int b) -> bool {
+        long long spins = 0;
+        bool ok;
+        while (!(ok = mbar_wait_parity(mbar + b, (pbits >> b) & 1u)) && ++spins < BALL_WAIT_LIMIT) {
+        }
+        return ok;
+    };
+    const CsmStaged st = csm_staged<NT>(g, x0, y0);
+    if (zb < ze && plane_tma(zb)) {
+        if (t == 0) issue(zb);
+        pend = 1u << (zb & 1);
+    }
+    csm_stage<NT>(P, io, F, sm + csm_slot(zb - 1) * CSM_SLOT, st, zb - 1);
+    csm_stage<NT>(P, io, F, sm + csm_slot(zb) * CSM_SLOT, st, zb);
+    for (int z = zb; z < ze; ++z) {
+        const int s = slit_of(P, z);
+        const bool act = in_xy && s >= 0 && !frozen(P, s);
+        const bool tz = (pend >> (z & 1)) & 1u;
+        float v[Q];
+        unsigned bb = 0;
+        const long long idx = ((long long)z * g.ny + y) * g.nx + x;
+        const float om = act ? P.sl[s].inv_tau : 0.f;
+        if (act && !tz) {
+            IpSlots q;
+            csm_pull<0, Q, false>(P, pin, idx, x, y, z, P.sl[s].zlo, P.sl[s].zhi, v, bb, q);
+        }
+        __syncthreads();  // ring slot of plane z - 2 and stage (z + 1) & 1 are free
+        const bool tn = z + 1 < ze && plane_tma(z + 1);
+        if (tn) {
+            if (t == 0) issue(z + 1);
+            pend |= 1u << ((z + 1) & 1);
+        }
+        csm_stage<NT>(P, io, F, sm + csm_slot(z + 1) * CSM_SLOT, st, z + 1);
+        __syncthreads();
+        if (tz) {
+            const int b = z & 1;
+            if (!__syncthreads_and(wait_stage(b))) {
+                // record the timeout and wait (bounded) for the copies in flight
+                if (t == 0) atomicOr(status, 4);
+                if (tn) wait_stage((z + 1) & 1);
+                return;
+            }
+            pbits ^= 1u << b;
+            pend &= ~(1u << b);
+            if (act) {
+#pragma unroll
+                for (int i = 0; i < Q; ++i) {
+                    const T* p = reinterpret_cast<const T*>(stg + b * SB + i * PB) + ty * BW +
+                                 (tx - kCx(i) + (kCx(i) > 0 ? XM : 0));
+                    if constexpr (sizeof(T) == 2)
+                        v[i] = __half2float(*reinterpret_cast<const __half*>(p));
+                    else
+                        v[i] = *reinterpret_cast<const float*>(p);
+                }
+            }
+        }
+        if (!act) continue;
+        const float* own = sm + csm_slot(z) * CSM_SLOT;
+        const float dnr = own[SQ_DN * CSM_HN + hc];
+        float d79;
+        csm_collide(own, sm + csm_slot(z - 1) * CSM_SLOT, sm + csm_slot(z + 1) * CSM_SLOT, hc,
+                    (1.f - om) / store_scale<T>(), dnr, bb, v, d79);
+        float ux, uy, uz;
+        const float dn = pull_finish<T>(pout, [&](int) { return idx; }, P.dbase, v, d79, dnr, ux, uy, uz);
+        put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
+    }
+}
+
 // Narrow grids (below one 32 x 4 tile): the same pass with one thread per
 // node and no staging; every source's quantities are formed where they are
 // used, by the same code as the staged ones, so both kernels give identical
@@ -2432,11 +2585,41 @@ static cudaError_t csm_tiled(const Params& P, const void* pin, void* pout, const
     return cudaGetLastError();
 }
 
+template <typename T>
+static cudaError_t csm_tma(const Params& P, const CUtensorMap* pmap, const void* pin, void* pout, const CsmIO& io,
+                           const float4* F, int* status, int lz, cudaStream_t s)
+{
+    const Geom& g = P.g;
+    const int tx = (g.nx + CSM_TX - 1) / CSM_TX, ty = (g.ny + CSM_TY - 1) / CSM_TY;
+    const int segs = (g.nz + lz - 1) / lz;
+    const long long blocks = (long long)tx * ty * segs;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const size_t smem = csm_tma_smem_bytes<T>();
+    static std::atomic<uint64_t> configured{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(configured.load() & bit)) {
+        e = cudaFuncSetAttribute(k_csm_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured.fetch_or(bit);
+    }
+    k_csm_tma<T><<<(unsigned)blocks, CSM_THREADS, smem, s>>>(P, *pmap, (const T*)pin, (T*)pout, io, F, lz, tx, ty,
+                                                            status);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_csm(const Params& P, const void* pin, void* pout, const CsmIO& io, const float4* F,
-                       int* status, int lz, int prefetch, cudaStream_t s)
+                       int* status, int lz, int prefetch, cudaStream_t s, const CUtensorMap* pmap)
 {
     const Geom& g = P.g;
     const bool ip = P.inplace != 0, h16 = P.storage == LBIF_STORE_F16;
+    if (prefetch == 2 && pmap && !ip && csm_ok(g)) {
+        if (lz <= 0) lz = CSM_LZ;
+        return h16 ? csm_tma<__half>(P, pmap, pin, pout, io, F, status, lz, s)
+                   : csm_tma<float>(P, pmap, pin, pout, io, F, status, lz, s);
+    }
     if (!csm_ok(g)) {
         const unsigned nb = nblocks(g.N, 128);
         if (h16 && ip) k_pull_node<__half, true><<<nb, 128, 0, s>>>(P, (const __half*)pin, (__half*)pout, io, F, status);

@@ -70,6 +70,7 @@ SIGNATURES = {
     "lbif_autotune": (_i32, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     "lbif_set_fused": (_i32, [_vp, _i32]),
     "lbif_get_shapes": (_i32, [_vp, ctypes.POINTER(_i32)]),
+    "lbif_set_shapes": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "lbif_get_fused": (_i32, [_vp, ctypes.POINTER(_i32)]),
     "lbif_selftest_wait": (_i32, [_i64, ctypes.POINTER(_i32)]),
     "lbif_field_profiles_noalloc": (_i32, [_vp, _vp, _i32, _i32, _i32, _pd, _pd, _pd, _vp]),
@@ -220,7 +221,16 @@ class Slit:
         v = (_i32 * 5)()
         self._check(self._lib.lbif_get_shapes(self._h, v))
         return {"ball_ctas": v[0], "force_group": v[1], "ball_staging": "tma" if v[2] else "loads",
-                "pull_lz": v[3], "pull_prefetch": v[4]}
+                "pull_lz": v[3], "pull_gathers": self.PULL_GATHERS[v[4]]}
+
+    PULL_GATHERS = ("loads", "prefetch", "tma")
+
+    def set_shapes(self, ball_ctas=0, force_group=0, ball_staging="loads", pull_lz=0, pull_gathers="loads"):
+        """Set the launch shapes (see lbif_set_shapes); no shape changes the
+        arithmetic."""
+        v = (_i32 * 5)(int(ball_ctas), int(force_group), 1 if ball_staging == "tma" else 0, int(pull_lz),
+                       self.PULL_GATHERS.index(pull_gathers))
+        self._check(self._lib.lbif_set_shapes(self._h, v))
 
     def set_fused(self, on: bool):
         """Every step is one pull pass (collision, streaming and the next
