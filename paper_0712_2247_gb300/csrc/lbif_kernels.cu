@@ -1037,6 +1037,27 @@ __device__ __forceinline__ void set4(v4 r, float4 a)
     r[3] = a.w;
 }
 
+// Paired FP32 arithmetic on nodes (j, j + 1) of a v4: one instruction does
+// both nodes (fma / add / mul .f32x2, sm_100 and later); each component
+// rounds as the scalar operation does.
+__device__ __forceinline__ float2 p2(const v4 r, int j) { return make_float2(r[j], r[j + 1]); }
+__device__ __forceinline__ void put2(v4 r, int j, float2 v)
+{
+    r[j] = v.x;
+    r[j + 1] = v.y;
+}
+__device__ __forceinline__ float2 bc2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+// a - b, rounded once (b (-1) is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
+// shell_A of a pair: G0 dq + gq (1 + dq)
+__device__ __forceinline__ float2 shell_A2(float2 dq, float2 gq, float G0)
+{
+    return fma2(bc2(G0), dq, mul2(gq, add2(bc2(1.f), dq)));
+}
+
 // values at x offsets D..D+3 of a float4-aligned base
 template <int D>
 __device__ __forceinline__ void win(const float* __restrict__ f, int b, v4 r)
@@ -1135,26 +1156,28 @@ __device__ __forceinline__ void member_x(const Params& P, const Fields& fl, int 
         const int row = pb + SB * (LO + kb) * sbs;
         const float w0 = P.sh.nb_w[PL][2 * kb], w1 = P.sh.nb_w[PL][2 * kb + 1];
         v4 c0, c1;
+        // acc += w0 (c0 - r) + w1 (c1 - r), r the reference (REF) or 0
+        auto interp = [&](float a0, float a1, const v4 r, v4 acc) {
+#pragma unroll
+            for (int j = 0; j < 4; j += 2) {
+                float2 e0 = p2(c0, j), e1 = p2(c1, j);
+                if (REF && r) {
+                    e0 = sub2(e0, p2(r, j));
+                    e1 = sub2(e1, p2(r, j));
+                }
+                put2(acc, j, fma2(bc2(a1), e1, fma2(bc2(a0), e0, p2(acc, j))));
+            }
+        };
         corners_x<LO, SA, LN>(fl.dn, row, c0, c1, ln);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float r = REF ? d0[j] : 0.f;
-            dq[j] = fmaf(w1, c1[j] - r, fmaf(w0, c0[j] - r, dq[j]));
-        }
+        interp(w0, w1, d0, dq);
         corners_x<LO, SA, LN>(fl.ux, row, c0, c1, ln);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) ua[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], ua[j]));
+        interp(w0, w1, nullptr, ua);
         corners_x<LO, SA, LN>(fb, row, c0, c1, ln);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) ub[j] = fmaf(w1, c1[j], fmaf(w0, c0[j], ub[j]));
+        interp(w0, w1, nullptr, ub);
         const int mrow = pb + SB * (LOM + kb) * sbs;
         const float v0 = P.sh.md_w[PL][2 * kb], v1 = P.sh.md_w[PL][2 * kb + 1];
         corners_x<LOM, SA, LN>(fl.dG, mrow, c0, c1, ln);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float r = REF ? g0[j] : 0.f;
-            gq[j] = fmaf(v1, c1[j] - r, fmaf(v0, c0[j] - r, gq[j]));
-        }
+        interp(v0, v1, g0, gq);
     }
 }
 
@@ -1174,15 +1197,16 @@ __device__ __forceinline__ void quartet_xy(const Params& P, const Fields& fl, in
         for (int j = 0; j < 4; ++j) dl[j] = ua[j] = ub[j] = gl[j] = 0.f;
         member_x<SIG, 0, M, LN, true>(P, fl, pb, d0, g0, dl, ua, ub, gl, ln);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float Aref = fmaf(G0, d0[j], g0[j] * (1.f + d0[j]));
-            const float a = fmaf(G0 + g0[j], dl[j], gl[j] * ((1.f + d0[j]) + dl[j]));
-            const float GA = G0 + (Aref + a);
-            const float S = fmaf(sa, ua[j] - u0[0][j], sb * (ub[j] - u0[1][j]));
-            const float tau = a - GA * lk * h * S;
-            f[0][j] = fmaf(sa * c, tau, f[0][j]);
-            f[1][j] = fmaf(sb * c, tau, f[1][j]);
-            if constexpr (C2) cc[j] += (1.f / 15.f) * (GA * h * S);
+        for (int j = 0; j < 4; j += 2) {
+            const float2 d = p2(d0, j), gg = p2(g0, j), dlj = p2(dl, j), opd = add2(bc2(1.f), d);
+            const float2 Aref = fma2(bc2(G0), d, mul2(gg, opd));
+            const float2 a = fma2(add2(bc2(G0), gg), dlj, mul2(p2(gl, j), add2(opd, dlj)));
+            const float2 GA = add2(bc2(G0), add2(Aref, a));
+            const float2 S = fma2(bc2(sa), sub2(p2(ua, j), p2(u0[0], j)), mul2(bc2(sb), sub2(p2(ub, j), p2(u0[1], j))));
+            const float2 tau = fma2(mul2(GA, bc2(-lk * h)), S, a);
+            put2(f[0], j, fma2(bc2(sa * c), tau, p2(f[0], j)));
+            put2(f[1], j, fma2(bc2(sb * c), tau, p2(f[1], j)));
+            if constexpr (C2) put2(cc, j, fma2(bc2(h / 15.f), mul2(GA, S), p2(cc, j)));
         }
     };
     one(std::integral_constant<int, 0>{});
@@ -1204,10 +1228,11 @@ __device__ __forceinline__ void pair_interp(const Params& P, const Fields& fl, i
     // corner values of the + and - members of one field (accumulated with weight w)
     auto acc = [&](const float* f, const v4 cp, const v4 cm, float w, v4 im, v4 ip, v4 D) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            im[j] = fmaf(w, cp[j], im[j]);
-            ip[j] = fmaf(w, cm[j], ip[j]);
-            if (D) D[j] = fmaf(w, cp[j] - cm[j], D[j]);
+        for (int j = 0; j < 4; j += 2) {
+            const float2 a = p2(cp, j), b = p2(cm, j), W = bc2(w);
+            put2(im, j, fma2(W, a, p2(im, j)));
+            put2(ip, j, fma2(W, b, p2(ip, j)));
+            if (D) put2(D, j, fma2(W, sub2(a, b), p2(D, j)));
         }
     };
     if constexpr (PL == 1) {
@@ -1274,17 +1299,25 @@ __device__ __forceinline__ void pair_terms(const Params& P, const Fields& fl, in
 #pragma unroll
     for (int j = 0; j < 4; ++j) dm[j] = dp[j] = Dd[j] = gm[j] = gp[j] = Dg[j] = am[j] = ap[j] = bm[j] = bp[j] = Db[j] = 0.f;
     pair_interp<SIG, PL, SB, LN>(P, fl, pb, dm, dp, Dd, gm, gp, Dg, am, ap, bm, bp, Db, ln);
+    const float2 one = bc2(1.f), g0 = bc2(G0), lkh = bc2(lk * h), SB2 = bc2(sb);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float Am = shell_A(dm[j], gm[j], G0), Ap = shell_A(dp[j], gp[j], G0);
-        const float DA = fmaf(G0, Dd[j], fmaf(Dg[j], 1.f + dm[j], gp[j] * Dd[j]));
-        const float cm = (G0 + Am) * lk * h, cp = (G0 + Ap) * lk * h, Dc = DA * lk * h;
-        const float xm = am[j] - u0[a][j], xp = ap[j] - u0[a][j];    // in-plane velocity offsets
-        const float zm = bm[j] - u0[2][j], zp = bp[j] - u0[2][j];    // wall-normal velocity offsets
+    for (int j = 0; j < 4; j += 2) {
+        const float2 dmj = p2(dm, j), dpj = p2(dp, j), Ddj = p2(Dd, j);
+        const float2 Am = shell_A2(dmj, p2(gm, j), G0), Ap = shell_A2(dpj, p2(gp, j), G0);
+        const float2 DA = fma2(g0, Ddj, fma2(p2(Dg, j), add2(one, dmj), mul2(p2(gp, j), Ddj)));
+        const float2 Gm = add2(g0, Am), Gp = add2(g0, Ap);
+        const float2 cm = mul2(Gm, lkh), cp = mul2(Gp, lkh), Dc = mul2(DA, lkh);
+        const float2 xm = sub2(p2(am, j), p2(u0[a], j)), xp = sub2(p2(ap, j), p2(u0[a], j));  // in-plane offsets
+        const float2 zm = sub2(p2(bm, j), p2(u0[2], j)), zp = sub2(p2(bp, j), p2(u0[2], j));  // wall-normal offsets
         // T = A - c (s_a (u_a - u0_a) + s_b (u_z - u0_z)), s_a = +1 for m, -1 for p
-        da[j] += DA - fmaf(cm, xm, cp * xp) - sb * fmaf(cm, Db[j], Dc * zp);
-        db[j] += sb * ((Am + Ap) - fmaf(cm, xm, -cp * xp) - sb * fmaf(cm, zm, cp * zp));
-        if constexpr (C2) cc[j] += (1.f / 15.f) * h * ((G0 + Am) * (xm + sb * zm) + (G0 + Ap) * (-xp + sb * zp));
+        const float2 ta = sub2(sub2(DA, fma2(cm, xm, mul2(cp, xp))), mul2(SB2, fma2(cm, p2(Db, j), mul2(Dc, zp))));
+        put2(da, j, add2(p2(da, j), ta));
+        const float2 tb = sub2(sub2(add2(Am, Ap), sub2(mul2(cm, xm), mul2(cp, xp))),
+                               mul2(SB2, fma2(cm, zm, mul2(cp, zp))));
+        put2(db, j, fma2(SB2, tb, p2(db, j)));
+        if constexpr (C2)
+            put2(cc, j, fma2(bc2(h / 15.f), fma2(Gm, fma2(SB2, zm, xm), mul2(Gp, fma2(SB2, zp, mul2(bc2(-1.f), xp)))),
+                             p2(cc, j)));
     }
 }
 
@@ -1300,9 +1333,9 @@ __device__ __forceinline__ void quartet_z(const Params& P, const Fields& fl, int
     pair_terms<SIG, PL, 1, C2, LN>(P, fl, pb, u0, G0, lk, da, db, cc, ln);
     pair_terms<SIG, PL, -1, C2, LN>(P, fl, pb, u0, G0, lk, da, db, cc, ln);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        f[a][j] += c * da[j];
-        f[2][j] += c * db[j];
+    for (int j = 0; j < 4; j += 2) {
+        put2(f[a], j, fma2(bc2(c), p2(da, j), p2(f[a], j)));
+        put2(f[2], j, fma2(bc2(c), p2(db, j), p2(f[2], j)));
     }
 }
 
@@ -1329,13 +1362,21 @@ __device__ __forceinline__ void axis4(const Params& P, const Fields& fl, int pb,
         set4(gm, ld4(fl.dG + pb - (SIG / 2) * st));
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        float Ap = shell_A(dp[j], gp[j], G0), Am = shell_A(dm[j], gm[j], G0);
+    for (int j = 0; j < 4; j += 2) {
+        const float2 dpj = p2(dp, j), dmj = p2(dm, j), gpj = p2(gp, j), gmj = p2(gm, j), u0j = p2(u0[A], j);
+        const float2 Ap = shell_A2(dpj, gpj, G0), Am = shell_A2(dmj, gmj, G0);
         // A_+ - A_-: from the differences of the loaded values along x and y
-        const float DA = A == 2 ? Ap - Am
-                                : fmaf(G0, dp[j] - dm[j], fmaf(gp[j] - gm[j], 1.f + dp[j], gm[j] * (dp[j] - dm[j])));
-        f[A][j] += (1.f / 30.f) * (DA - lk * ((G0 + Ap) * (up[j] - u0[A][j]) - (G0 + Am) * (u0[A][j] - um[j])));
-        if constexpr (C2) cc[j] += (1.f / 30.f) * ((G0 + Ap) * (up[j] - u0[A][j]) + (G0 + Am) * (u0[A][j] - um[j]));
+        float2 DA;
+        if constexpr (A == 2) {
+            DA = sub2(Ap, Am);
+        } else {
+            const float2 dd = sub2(dpj, dmj);
+            DA = fma2(bc2(G0), dd, fma2(sub2(gpj, gmj), add2(bc2(1.f), dpj), mul2(gmj, dd)));
+        }
+        const float2 wp = mul2(add2(bc2(G0), Ap), sub2(p2(up, j), u0j));
+        const float2 wm = mul2(add2(bc2(G0), Am), sub2(u0j, p2(um, j)));
+        put2(f[A], j, fma2(bc2(1.f / 30.f), fma2(bc2(-lk), sub2(wp, wm), DA), p2(f[A], j)));
+        if constexpr (C2) put2(cc, j, fma2(bc2(1.f / 30.f), add2(wp, wm), p2(cc, j)));
     }
 }
 
@@ -1640,14 +1681,22 @@ __device__ __forceinline__ float mirror_diff(const float* s, const float* sp, fl
     return (dt + dm) + (ds - dsp);
 }
 
+// element off of direction i's part of a population buffer
+template <typename T>
+__device__ __forceinline__ T* pop_at(T* p, const Params& P, int i, long long off)
+{
+    return p + (P.dbase[i] + off);
+}
+
 // the new moments of a node from its arriving values (slots as above, d79 =
 // v_7 - v_9), then its populations stored as non-equilibrium parts at those
-// moments: base directions directly, derived ones as their partner's stored
-// value plus the difference (so the pairs' differences survive the rounding
-// of the large common parts); returns dn and writes u
+// moments (at(i): where direction i goes): base directions directly, derived
+// ones as their partner's stored value plus the difference (so the pairs'
+// differences survive the rounding of the large common parts); returns dn
+// and writes u
 template <typename T, class Addr>
-__device__ __forceinline__ float pull_finish(T* __restrict__ pout, Addr at, const long long* dbase, const float* v,
-                                             float d79, float dnr, float& ux, float& uy, float& uz)
+__device__ __forceinline__ float pull_finish(Addr at, const float* v, float d79, float dnr, float& ux, float& uy,
+                                             float& uz)
 {
     constexpr float w1 = 1.f / 18.f, w2 = 1.f / 36.f;
     // arriving values of the derived directions
@@ -1677,7 +1726,7 @@ __device__ __forceinline__ float pull_finish(T* __restrict__ pout, Addr at, cons
     // p_i - p_ip of a pair that differs in component a: u_a (6 + 18 R),
     // R = the shared part of c.u
     auto dp = [&](float ua, float R) { return ua * fmaf(18.f, R, 6.f); };
-    auto put = [&](int i, float h) { stp(pout + (dbase[i] + at(i)), sT * h); };
+    auto put = [&](int i, float h) { stp(at(i), sT * h); };
     put(0, base(0, v[0]));
     put(5, base(5, v[5]));
     put(6, base(6, v[6]));
@@ -1814,9 +1863,9 @@ __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ 
             const int sz = z - kCz(i);
             if (!g.zper && (sz < zlo || sz > zhi)) {
                 bb |= 1u << i;
-                v[i - I0] = ldp(pin + (P.dbase[opp_of(i)] + q.wall_slot(i)));
+                v[i - I0] = ldp(pop_at(pin, P, opp_of(i), q.wall_slot(i)));
             } else {
-                v[i - I0] = ldp(pin + (P.dbase[i] + q.slot(i)));
+                v[i - I0] = ldp(pop_at(pin, P, i, q.slot(i)));
             }
         }
         return;
@@ -1984,9 +2033,9 @@ __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
         if constexpr (IP) {
             const int s = slit_of(P, z);
             const IpSlots q = ip_slots(P, P.sl[s], s, x, y, z);
-            dn = pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, P.dbase, v, d79, dnr, ux, uy, uz);
+            dn = pull_finish<T>([&](int i) { return pop_at(pout, P, i, q.slot(i)); }, v, d79, dnr, ux, uy, uz);
         } else {
-            dn = pull_finish<T>(pout, [&](int) { return idx; }, P.dbase, v, d79, dnr, ux, uy, uz);
+            dn = pull_finish<T>([&](int i) { return pop_at(pout, P, i, idx); }, v, d79, dnr, ux, uy, uz);
         }
         put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
     }
@@ -2137,7 +2186,7 @@ __global__ void __launch_bounds__(CSM_THREADS, 4)
         csm_collide(own, sm + csm_slot(z - 1) * CSM_SLOT, sm + csm_slot(z + 1) * CSM_SLOT, hc,
                     (1.f - om) / store_scale<T>(), dnr, bb, v, d79);
         float ux, uy, uz;
-        const float dn = pull_finish<T>(pout, [&](int) { return idx; }, P.dbase, v, d79, dnr, ux, uy, uz);
+        const float dn = pull_finish<T>([&](int i) { return pop_at(pout, P, i, idx); }, v, d79, dnr, ux, uy, uz);
         put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
     }
 }
@@ -2223,9 +2272,9 @@ __global__ void __launch_bounds__(128) k_pull_node(Params P, const T* pin, T* po
     };
     for_dirs(one);
     float ux, uy, uz;
-    const float dn = IP ? pull_finish<T>(pout, [&](int i) { return (long long)q.slot(i); }, P.dbase, v, d79, dnr, ux,
+    const float dn = IP ? pull_finish<T>([&](int i) { return pop_at(pout, P, i, q.slot(i)); }, v, d79, dnr, ux,
                                          uy, uz)
-                        : pull_finish<T>(pout, [&](int) { return idx; }, P.dbase, v, d79, dnr, ux, uy, uz);
+                        : pull_finish<T>([&](int i) { return pop_at(pout, P, i, idx); }, v, d79, dnr, ux, uy, uz);
     put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
 }
 
