@@ -111,13 +111,12 @@ def kernel_bytes(storage: int):
     return {"ball_g2": 8, "tail": 20, "force": 36, "collide_stream": 2 * 19 * s + 32 + 16}
 
 
-# DRAM bytes per node (dram__bytes_read.sum + dram__bytes_write.sum) of each
-# step kernel, from ncu captures of the 256x256x192 sigma = 12 slit of the
-# current kernels; a full-size launch moves these bytes times its node count
-# (traffic grows with the nodes). None where the kernel changed after its
-# last capture (re-measured with every kernel change).
-TRAFFIC_B_PER_NODE = {0: {"ball_g2": 6.0, "force": 45.7, "collide_stream": None},
-                      1: {"ball_g2": 6.0, "force": 45.7, "collide_stream": None}}
+# DRAM bytes per node of each step kernel (dram__bytes_read.sum + dram__bytes_write.sum of one
+# ncu capture on the 128x128x192 sigma = 12 slit, default launch shapes, divided by its nodes;
+# the same per-node traffic as the 256x256x192 capture of the pull pass, so it scales with the
+# nodes of a launch). The ball kernel's dG writes stay in L2 at that size: read bytes only.
+TRAFFIC_B_PER_NODE = {0: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 209.7},
+                      1: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 155.6}}
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
@@ -490,9 +489,12 @@ def run_ours(args, world, rank, local):
     N = W.nodes
     peak, peak_kind = _peaks()
     # warm-up, then the launch shapes the library's autotuner picks on this
-    # state (ball CTAs and staging, force tile group; results bit-identical)
+    # state (ball CTAs and staging, force tile group, pull segments and
+    # gathers; results bit-identical), or its defaults (profiler captures,
+    # whose timings would mislead the autotuner)
     g.step(args.warmup)
-    g.autotune(3)
+    if args.shapes == "auto":
+        g.autotune(3)
     shapes = g.shapes()
     g.step(1)
     torch.cuda.synchronize()
@@ -615,6 +617,8 @@ def main():
     ap.add_argument("--ws-heldout", type=int, default=128, help="held-out slits of the warm-start leg")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the FP16-storage record and the packing-fraction sweep")
+    ap.add_argument("--shapes", choices=["auto", "default"], default="auto",
+                    help="launch shapes: the autotuner's (auto) or the library defaults (profiler captures)")
     ap.add_argument("--grid", default=None,
                     help="override the slit extents NXxNYxNZ (profiling captures on a smaller case)")
     args = ap.parse_args()
