@@ -201,8 +201,16 @@ __device__ __forceinline__ bool cta_wait(uint64_t* mbar, uint32_t parity)
 
 // One CTA: a 128-row block (blockIdx.x) x an ntile-column block (blockIdx.y)
 // of C, accumulated in TMEM over K in rounds of 64; the copies of round k+1
-// are in flight while the tensor core works on round k.
-__global__ void __launch_bounds__(128) k_gemm_tc(Gemm g, int ntile)
+// are in flight while the tensor core works on round k. GEMM_THREADS threads:
+// the epilogue (bias, GELU, the FP32 and BF16 copies) dominates at K <= 256,
+// and TMEM (ntile columns per CTA) caps the CTAs per SM, so the CTA is wide:
+// warp w reads TMEM lanes 32 (w % 4) .. + 31 and every (GEMM_THREADS / 128)-th
+// 16-column chunk, starting at chunk w / 4.
+#ifndef LBIF_GEMM_THREADS
+#define LBIF_GEMM_THREADS 256
+#endif
+constexpr int GEMM_THREADS = LBIF_GEMM_THREADS;
+__global__ void __launch_bounds__(GEMM_THREADS, 2) k_gemm_tc(Gemm g, int ntile)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int SB = gemm_stage_bytes(ntile);
@@ -272,10 +280,11 @@ __global__ void __launch_bounds__(128) k_gemm_tc(Gemm g, int ntile)
     if (ok) {
         // each thread owns one row (its TMEM lane) and 16 consecutive columns
         // per chunk: a full chunk is written with 16-byte vector stores
-        const int row = m0 + 32 * warp + lane;
-        for (int c = 0; c < NT; c += 16) {
+        const int lg = warp % 4, cg = warp / 4, ncg = GEMM_THREADS / 128;
+        const int row = m0 + 32 * lg + lane;
+        for (int c = 16 * cg; c < NT; c += 16 * ncg) {
             float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            tmem_ld16(tmem + ((uint32_t)(32 * lg) << 16) + (uint32_t)c, v);
             if (row >= g.M) continue;
             const int nb = n0 + c;
             const bool full = nb + 16 <= g.N && (g.ldz % 4) == 0 && (g.ldh % 8) == 0;
@@ -293,10 +302,21 @@ __global__ void __launch_bounds__(128) k_gemm_tc(Gemm g, int ntile)
                     for (int j = 0; j < 16; ++j) zp[j] = nb + j < g.N ? g.zprev[(size_t)row * g.ldz + nb + j] : 0.f;
                 }
             }
+            // the chunk's 16 biases: four 16-byte loads when aligned
+            float bz[16];
+            if (g.bias && nb + 16 <= g.N && ((uintptr_t)(g.bias + nb) & 15) == 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(g.bias + nb) + q);
+                    bz[4 * q] = t.x, bz[4 * q + 1] = t.y, bz[4 * q + 2] = t.z, bz[4 * q + 3] = t.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) bz[j] = (g.bias && nb + j < g.N) ? g.bias[nb + j] : 0.f;
+            }
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                const int n = nb + j;
-                float zz = v[j] + ((g.bias && n < g.N) ? g.bias[n] : 0.f);
+                float zz = v[j] + bz[j];
                 float hh = zz;
                 if (g.epi == EPI_GELU) {
                     hh = gelu(zz);
@@ -656,7 +676,7 @@ static int gemm(lbif_mlp_ctx* m, const Gemm& g)
     // columns (32..256 each) always fit in the SM's 512 together
     int smem = gemm_smem_bytes(ntile);
     if (tmem_cols(ntile) == 256 && smem < 80 * 1024) smem = 80 * 1024;
-    k_gemm_tc<<<grid, 128, smem, m->stream>>>(g, ntile);
+    k_gemm_tc<<<grid, GEMM_THREADS, smem, m->stream>>>(g, ntile);
     MCK(m, cudaGetLastError());
     return LBIF_OK;
 }
@@ -669,8 +689,12 @@ static Gemm blank(lbif_mlp_ctx* m)
     return g;
 }
 
-// forward of `batch` rows already packed in H[0] / HT[0]
-static int forward(lbif_mlp_ctx* m, int batch)
+// forward of `batch` rows already packed in H[0] / HT[0]. train: keep what
+// back-propagation reads (every layer's FP32 pre-activation Z and the
+// transposed BF16 activations HT); otherwise each hidden layer writes only
+// the next layer's BF16 input, and the output goes to Yout (batch x nout,
+// device memory) when given, else to Z of the last layer.
+static int forward(lbif_mlp_ctx* m, int batch, bool train, float* Yout = nullptr)
 {
     const int bp = up16(batch);
     for (int l = 0; l < m->L; ++l) {
@@ -685,13 +709,21 @@ static int forward(lbif_mlp_ctx* m, int batch)
         g.K = m->kpad[l];
         g.bias = m->p + m->boff[l];
         g.epi = last ? EPI_NONE : EPI_GELU;
-        g.Z = m->Z[l];
-        g.ldz = m->dout[l];
+        if (train || last) {
+            g.Z = m->Z[l];
+            g.ldz = m->dout[l];
+        }
+        if (last && !train && Yout) {
+            g.Z = Yout;
+            g.M = batch;  // the rows Yout holds
+        }
         if (!last) {
             g.H = m->H[l + 1];
             g.ldh = m->kpad[l + 1];
-            g.HT = m->HT[l + 1];
-            g.ldht = bp;
+            if (train) {
+                g.HT = m->HT[l + 1];
+                g.ldht = bp;
+            }
         }
         int rc = gemm(m, g);
         if (rc) return rc;
@@ -728,10 +760,11 @@ extern "C" int lbif_mlp_forward(lbif_mlp m, const float* X, int32_t batch, float
         return mfail(m, LBIF_ERR_ARG, "lbif_mlp_forward: bad arguments");
     int rc = pack_input(m, X, batch, on_device);
     if (rc) return rc;
-    if ((rc = forward(m, batch))) return rc;
-    const float* Zl = m->Z[m->L - 1];
-    MCK(m, cudaMemcpyAsync(Y, Zl, sizeof(float) * (size_t)batch * m->nout,
-                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, m->stream));
+    // device output: the last product writes Y itself
+    if ((rc = forward(m, batch, false, on_device ? Y : nullptr))) return rc;
+    if (!on_device)
+        MCK(m, cudaMemcpyAsync(Y, m->Z[m->L - 1], sizeof(float) * (size_t)batch * m->nout, cudaMemcpyDeviceToHost,
+                               m->stream));
     return check_err(m);
 }
 
@@ -811,7 +844,7 @@ extern "C" int lbif_mlp_gradients(lbif_mlp m, const float* X, const float* T, co
         return mfail(m, LBIF_ERR_ARG, "lbif_mlp_gradients: bad arguments");
     int rc = pack_input(m, X, batch, on_device);
     if (rc) return rc;
-    if ((rc = forward(m, batch))) return rc;
+    if ((rc = forward(m, batch, true))) return rc;
     if ((rc = backward(m, T, mask, batch, on_device, loss))) return rc;
     if (grads) {
         MCK(m, cudaMemcpyAsync(grads, m->g, sizeof(float) * m->nparams,
@@ -828,7 +861,7 @@ extern "C" int lbif_mlp_train_step(lbif_mlp m, const float* X, const float* T, c
         return mfail(m, LBIF_ERR_ARG, "lbif_mlp_train_step: bad arguments");
     int rc = pack_input(m, X, batch, on_device);
     if (rc) return rc;
-    if ((rc = forward(m, batch))) return rc;
+    if ((rc = forward(m, batch, true))) return rc;
     if ((rc = backward(m, T, mask, batch, on_device, loss))) return rc;
     m->adam_t += 1;
     const float c1 = (float)(1.0 - pow((double)beta1, (double)m->adam_t));
