@@ -480,8 +480,12 @@ __host__ __device__ constexpr int cisqrt(int n)
 // tile of the z-marching ball kernel: 32 x 16 nodes, 256 threads, each
 // thread a column of BALL_YT = 2 nodes in y (measured at sigma = 12 on a
 // 512 x 512 x 192 slit: 1 node per thread 0.86 ms, 2 nodes 0.72 ms, 4 nodes
-// 0.90 ms, each with its best CTA count)
-constexpr int BALL_TX = 32, BALL_YT = 2, BALL_TY = 8 * BALL_YT, BALL_THREADS = 256;
+// 0.90 ms, each with its best CTA count; with tensor-memory-accelerator
+// staging, CTAs of 4 / 8 / 16 warps 0.567 / 0.552 / 0.573 ms)
+#ifndef BALL_WARPS
+#define BALL_WARPS 8
+#endif
+constexpr int BALL_TX = 32, BALL_YT = 2, BALL_TY = BALL_WARPS * BALL_YT, BALL_THREADS = 32 * BALL_WARPS;
 
 
 // x halo of the staged plane tile: R rounded up to 4, so that tile rows and

@@ -59,6 +59,31 @@ def test_forward_matches_oracle(mlp_mod, nin, hidden, nhidden, nout, batch):
 
 
 @pytest.mark.parametrize("nin,hidden,nhidden,nout,batch", CASES)
+def test_device_forward_equals_host_forward(mlp_mod, nin, hidden, nhidden, nout, batch):
+    """Device arrays: the last product writes the caller's (batch x nout)
+    array itself, rows past the batch untouched; the same products as the
+    host path, so the same bits. A forward after a training step (which keeps
+    the back-propagation copies) gives the same bits as one before."""
+    torch = pytest.importorskip("torch")
+    net = mlp_mod.MLP(nin, hidden, nhidden, nout, max_batch=512, seed=6)
+    X, T, M = _data(nin, nout, batch, 7)
+    Yh = net.forward(X)
+    Xd = torch.from_numpy(X).cuda()
+    guard = torch.full((batch + 3, nout), 7.0, dtype=torch.float32, device="cuda")
+    Yd = net.forward(Xd)
+    assert np.array_equal(Yd.cpu().numpy(), Yh)
+    # the device entry writes exactly batch rows into a caller's view
+    lib = net._lib
+    rc = lib.lbif_mlp_forward(net._h, Xd.data_ptr(), batch, guard.data_ptr(), 1)
+    assert rc == 0
+    g = guard.cpu().numpy()
+    assert np.array_equal(g[:batch], Yh) and np.all(g[batch:] == 7.0)
+    net.gradients(X, T, M)
+    assert np.array_equal(net.forward(X), Yh)
+    net.close()
+
+
+@pytest.mark.parametrize("nin,hidden,nhidden,nout,batch", CASES)
 def test_gradients_match_oracle(mlp_mod, nin, hidden, nhidden, nout, batch):
     net = mlp_mod.MLP(nin, hidden, nhidden, nout, max_batch=512, seed=3)
     p = net.get_params()
