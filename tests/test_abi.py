@@ -93,6 +93,10 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.lbif_selftest_wait(10, None) == -1
     v = ctypes.c_int32(7)
     assert lib.lbif_get_fused(None, ctypes.byref(v)) == -1 and v.value == 7
+    shapes = (ctypes.c_int32 * 5)(0, 0, 0, 0, 0)
+    assert lib.lbif_get_shapes(None, shapes) == -1
+    assert lib.lbif_set_shapes(None, shapes) == -1
+    assert lib.lbif_autotune(None, 1, None, None, None) == -1
     assert lib.lbif_last_error(None)
 
 
