@@ -286,12 +286,23 @@ def ensemble_leg(args):
     fluid = int(np.sum(p.H)) * p.nx * p.ny
     e.close()
     graph_ms = dt / steps * 1e3
+    # the same ensemble with FP32 storage, for comparison (same steps, graph)
+    e32 = lbif.Ensemble(p.H, p.eta, p.F, p.tau, p.sigma, p.nx, p.ny, storage=lbif.STORE_F32, seed=3)
+    e32.autotune(trials=3)
+    e32.run(tol=1e-300, max_steps=200, check_every=100)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e32.run(tol=1e-300, max_steps=steps, check_every=100)
+    torch.cuda.synchronize()
+    dt32 = time.perf_counter() - t0
+    e32.close()
     return {"workload": "256 slits 32x32xH, sigma=4, FP16 storage, graph-captured steps",
             "fluid_nodes": fluid, "stacked_nodes": e.N, "steps": steps, "seconds": dt,
             "mlups_fluid": fluid * steps / dt / 1e6, "autotuned": {"ball_ctas": ball, "force_group": group,
                                                         "ball_staging": "tma" if staging else "loads"},
             "graph_ms_per_step": graph_ms, "kernel_ms_per_step": kern, "kernels_ms": per,
-            "beyond_kernels_frac": (graph_ms - kern) / graph_ms}
+            "beyond_kernels_frac": (graph_ms - kern) / graph_ms,
+            "mlups_fluid_fp32_storage": fluid * steps / dt32 / 1e6}
 
 
 def mlp_leg(args):
