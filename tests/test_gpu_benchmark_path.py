@@ -101,3 +101,63 @@ def test_tail_workload_kernels_short_window(L, O):
     for k in ("F", "rho", "rho_fluct", "u", "n_z", "ux_z"):
         assert e[k] < 1e-5, (k, e[k])
     g.close()
+
+
+def _read_tail_golden(path):
+    """The fixture written by tests/golden/make_tail_window_1000.py (FP64
+    oracle only): {time: {"n_z", "ux_z", "totals", (x, y): {field: column}}}."""
+    out, cur, n0 = {}, None, None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *rest = line.split()
+            if key == "n0":
+                n0 = float(rest[0])
+            elif key == "time":
+                cur = out.setdefault(int(rest[0]), {})
+            elif key in ("n_z", "ux_z", "totals"):
+                cur[key] = np.array(rest, dtype=np.float64)
+            elif key == "col":
+                x, y = (int(v) for v in rest[0].split(","))
+                cur.setdefault((x, y), {})[rest[1]] = np.array(rest[2:], dtype=np.float64)
+    return n0, out
+
+
+def test_tail_workload_1000_steps_against_cached_oracle(L):
+    """The attractive-tail workload (sigma 8, eta 0.25, tau 0.8, F_e = 1e-6,
+    LJ tail eps = 0.3 cut at 2.5 sigma, seeded noise) on a 32 x 32 x 128 slit
+    against the FP64 oracle's state after 100 and 1000 steps, stored by
+    tests/golden/make_tail_window_1000.py (the oracle's direct tail sum takes
+    about 80 minutes on 8 cores): plane profiles n(z), u_x(z), the totals, and
+    n, u on four columns, at 1e-5. The device runs the spectral tail (x and y
+    lines of 32 points, the kernel wrapped over the periodic extent as the
+    oracle's direct sum is) and the tiled pull pass."""
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "tail_window_32x32x128_sigma8.txt")
+    if not os.path.exists(path):
+        pytest.skip("fixture not generated")
+    n0, gold = _read_tail_golden(path)
+    g = L.Slit(32, 32, 128, 8, 0.25, 0.8, body=(1e-6, 0, 0), tail=True, eps=0.3, rcut=2.5, seed=1)
+    assert abs(g.n0 / n0 - 1) < 1e-12
+    t = 0
+    for T in sorted(gold):
+        g.step(T - t)
+        t = T
+        ref = gold[T]
+        n_z, ux_z, tot = g.profiles()
+        rho, u = g.moments()
+        e = dict(n_z=nerr(n_z, ref["n_z"]), ux_z=nerr(ux_z, ref["ux_z"]),
+                 mass=abs(tot[0] / ref["totals"][0] - 1), momx=nerr(tot[1:2], ref["totals"][1:2]))
+        for (x, y), cols in ((k, v) for k, v in ref.items() if isinstance(k, tuple)):
+            e[f"n@{x},{y}"] = nerr(rho[:, y, x], cols["n"])
+            e[f"n-n0@{x},{y}"] = nerr(rho[:, y, x] - n0, cols["n"] - n0)
+            uc = np.stack([cols["ux"], cols["uy"], cols["uz"]])
+            e[f"u@{x},{y}"] = nerr(u[:, :, y, x], uc)
+        print(f"tail workload vs cached oracle, step {T}:", " ".join(f"{k}={v:.2e}" for k, v in e.items()))
+        assert g.status() == 0
+        assert e["mass"] < 1e-6
+        for k, v in e.items():
+            assert v < 1e-5, (T, k, v)
+    g.close()
