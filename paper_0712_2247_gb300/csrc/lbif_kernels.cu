@@ -1858,7 +1858,9 @@ __device__ __forceinline__ void csm_stage(const Params& P, const CsmIO& io, cons
     }
 }
 
-// CTAs per SM the register budget is sized for, and z planes per CTA segment
+// CTAs per SM the register budget is sized for (5 / 6 / 7 at 96 / 80 / 72
+// registers: 2.57 / 2.39 / 2.55 ms at 512 x 512 x 192, sigma 12, FP32), and
+// z planes per CTA segment
 #ifndef CSM_MINB
 #define CSM_MINB 6
 #endif
