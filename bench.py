@@ -116,7 +116,7 @@ def kernel_bytes(storage: int):
 # the same per-node traffic as the 256x256x192 capture of the pull pass, so it scales with the
 # nodes of a launch). The ball kernel's dG writes stay in L2 at that size: read bytes only.
 TRAFFIC_B_PER_NODE = {0: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 209.7},
-                      1: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 155.6}}
+                      1: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 157.5}}
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
