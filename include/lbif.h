@@ -95,7 +95,10 @@ typedef struct {
                           memory): direction i of every node moves by c_i
                           slots each step, so each step reads and writes the
                           same slots; 0: two buffers (read one, write the
-                          other). Same arithmetic, same results.              */
+                          other). Same arithmetic, same results. In place,
+                          19 x (nodes of the slits' storage rings, padded)
+                          must stay below 2^32 (about 226 M nodes), else
+                          LBIF_ERR_UNSUPPORTED.                               */
 } lbif_opts;
 
 /* Create a slit (or periodic box) of packing fraction eta = pi sigma^3 n0/6

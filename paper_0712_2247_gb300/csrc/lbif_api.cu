@@ -372,6 +372,11 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
         delete h;
         return fail(nullptr, LBIF_ERR_UNSUPPORTED, "create: padded grid exceeds 2^31 nodes");
     }
+    if (O.inplace && (long long)Q * g.Npad >= (1LL << 32)) {
+        delete h;
+        return fail(nullptr, LBIF_ERR_UNSUPPORTED,
+                    "create: the in-place layout holds at most 2^32 population elements (use two buffers)");
+    }
     const double kT = 1.0 / 3.0;
     P.sigma = sigma;
     P.kappa = (float)(2.0 / (sqrt(kT) * sqrt(M_PI)));
@@ -396,6 +401,7 @@ static int create_impl(lbif_handle* out, int nx, int ny, int nz, int sigma, int 
             P.soff[i] = cx[i] + (long long)cy[i] * g.nx + (long long)cz[i] * g.nx * g.ny;
             P.dbase[i] = (long long)i * g.Npad;
             P.doff[i] = P.dbase[i] - P.soff[i];
+            P.dbase32[i] = O.inplace ? (unsigned)P.dbase[i] : 0u;
         }
     }
     if (build_shell(P)) {

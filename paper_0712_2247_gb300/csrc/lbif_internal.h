@@ -95,6 +95,7 @@ struct Params {
     long long soff[Q];    // node-index offsets of the 19 neighbours (no wrap)
     long long dbase[Q];   // i Npad: start of direction i in a population buffer
     long long doff[Q];    // i Npad - soff[i]: where node idx pulls direction i from (no wrap)
+    unsigned dbase32[Q];  // in place: i Npad (the layout keeps Q Npad below 2^32)
     Shell sh;
 };
 

@@ -1705,6 +1705,13 @@ __device__ __forceinline__ T* pop_at(T* p, const Params& P, int i, long long off
 {
     return p + (P.dbase[i] + off);
 }
+// the same in place, where every element offset fits 32 bits: one 32-bit add
+// and one widening multiply-add per address
+template <typename T>
+__device__ __forceinline__ T* pop_at_ip(T* p, const Params& P, int i, int slot)
+{
+    return p + (P.dbase32[i] + (unsigned)slot);
+}
 
 // the new moments of a node from its arriving values (slots as above, d79 =
 // v_7 - v_9), then its populations stored as non-equilibrium parts at those
@@ -1883,9 +1890,9 @@ __device__ __forceinline__ void csm_pull(const Params& P, const T* __restrict__ 
             const int sz = z - kCz(i);
             if (!g.zper && (sz < zlo || sz > zhi)) {
                 bb |= 1u << i;
-                v[i - I0] = ldq<RAW>(pop_at(pin, P, opp_of(i), q.wall_slot(i)));
+                v[i - I0] = ldq<RAW>(pop_at_ip(pin, P, opp_of(i), q.wall_slot(i)));
             } else {
-                v[i - I0] = ldq<RAW>(pop_at(pin, P, i, q.slot(i)));
+                v[i - I0] = ldq<RAW>(pop_at_ip(pin, P, i, q.slot(i)));
             }
         }
         return;
@@ -2063,7 +2070,7 @@ __global__ void __launch_bounds__(CSM_THREADS, PF ? CSM_MINB - 1 : CSM_MINB)
         if constexpr (IP) {
             const int s = slit_of(P, z);
             const IpSlots q = ip_slots(P, P.sl[s], s, x, y, z);
-            dn = pull_finish<T>([&](int i) { return pop_at(pout, P, i, q.slot(i)); }, v, d79, dnr, ux, uy, uz);
+            dn = pull_finish<T>([&](int i) { return pop_at_ip(pout, P, i, q.slot(i)); }, v, d79, dnr, ux, uy, uz);
         } else {
             dn = pull_finish<T>([&](int i) { return pop_at(pout, P, i, idx); }, v, d79, dnr, ux, uy, uz);
         }
@@ -2302,7 +2309,7 @@ __global__ void __launch_bounds__(128) k_pull_node(Params P, const T* pin, T* po
     };
     for_dirs(one);
     float ux, uy, uz;
-    const float dn = IP ? pull_finish<T>([&](int i) { return pop_at(pout, P, i, q.slot(i)); }, v, d79, dnr, ux,
+    const float dn = IP ? pull_finish<T>([&](int i) { return pop_at_ip(pout, P, i, q.slot(i)); }, v, d79, dnr, ux,
                                          uy, uz)
                         : pull_finish<T>([&](int i) { return pop_at(pout, P, i, idx); }, v, d79, dnr, ux, uy, uz);
     put_fields(P, io, x, y, z, dn, ux, uy, uz, status);
