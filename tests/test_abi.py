@@ -56,12 +56,12 @@ def test_binding_covers_every_declared_symbol():
     assert declared <= bound, sorted(declared - bound)
 
 
-def _create(lib, nx=8, ny=8, nz=8, sigma=4.0, eta=0.3, tau=1.0, zbc=0, storage=0, noise=1e-3):
+def _create(lib, nx=8, ny=8, nz=8, sigma=4.0, eta=0.3, tau=1.0, zbc=0, storage=0, noise=1e-3, inplace=0):
     from paper_0712_2247_gb300 import lbif
 
     h = ctypes.c_void_p()
     f = lbif.Force((ctypes.c_double * 3)(0, 0, 0), 1, 1, 1, 0, 0, 1.0, 2.5)
-    o = lbif.Opts(storage, 0, noise, None)
+    o = lbif.Opts(storage, 0, noise, None, inplace)
     rc = lib.lbif_create(ctypes.byref(h), lbif.Grid(nx, ny, nz), sigma, eta, tau, lbif.Walls(zbc),
                          ctypes.byref(f), ctypes.byref(o))
     return rc, h
@@ -74,6 +74,8 @@ def _create(lib, nx=8, ny=8, nz=8, sigma=4.0, eta=0.3, tau=1.0, zbc=0, storage=0
     (dict(ny=-3), -1), (dict(nz=0), -1),
     # padded grid beyond 32-bit node indices: refused before any allocation
     (dict(nx=2048, ny=2048, nz=1024), -6),
+    # in place: 19 x 253 M ring nodes exceed 32-bit element offsets
+    (dict(nx=1024, ny=1024, nz=240, inplace=1), -6),
 ])
 def test_create_rejects_bad_arguments(lib, kw, code):
     rc, h = _create(lib, **kw)
