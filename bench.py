@@ -258,17 +258,19 @@ def warm_start_leg(args):
 def ensemble_leg(args):
     """Throughput of the batched ensemble: 256 slits of 32x32xH (H in
     [8, 80], eta in [0.10, 0.25], F log-uniform in [1e-7, 1e-5], tau in
-    [0.6, 1.2], SplitMix64 seed 3), FP16 population storage, advanced by the
-    CUDA-graph runner (graphs of 100 steps, FP64 residual check after each)
-    after the autotuner has picked the launch shapes. The tolerance is set
-    below reach, so every slit runs all steps."""
+    [0.6, 1.2], SplitMix64 seed 3), FP16 population storage in place,
+    advanced by the CUDA-graph runner (graphs of 100 steps, FP64 residual
+    check after each) after the autotuner has picked the launch shapes. The
+    tolerance is set below reach, so every slit runs all steps. The same
+    ensemble with FP32 storage and with two population buffers is timed for
+    comparison."""
     import numpy as np
     import torch
 
     from paper_0712_2247_gb300 import inputs, lbif
 
     p = inputs.ensemble(256, seed=3)
-    e = lbif.Ensemble(p.H, p.eta, p.F, p.tau, p.sigma, p.nx, p.ny, storage=lbif.STORE_F16, seed=3)
+    e = lbif.Ensemble(p.H, p.eta, p.F, p.tau, p.sigma, p.nx, p.ny, storage=lbif.STORE_F16, seed=3, inplace=True)
     ball, group, staging = e.autotune(trials=3)
     e.run(tol=1e-300, max_steps=200, check_every=100)  # builds the graph
     steps = args.ens_steps
@@ -286,23 +288,29 @@ def ensemble_leg(args):
     fluid = int(np.sum(p.H)) * p.nx * p.ny
     e.close()
     graph_ms = dt / steps * 1e3
-    # the same ensemble with FP32 storage, for comparison (same steps, graph)
-    e32 = lbif.Ensemble(p.H, p.eta, p.F, p.tau, p.sigma, p.nx, p.ny, storage=lbif.STORE_F32, seed=3)
-    e32.autotune(trials=3)
-    e32.run(tol=1e-300, max_steps=200, check_every=100)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e32.run(tol=1e-300, max_steps=steps, check_every=100)
-    torch.cuda.synchronize()
-    dt32 = time.perf_counter() - t0
-    e32.close()
-    return {"workload": "256 slits 32x32xH, sigma=4, FP16 storage, graph-captured steps",
+    # the same ensemble with FP32 storage, and with two population buffers,
+    # for comparison (same steps, graph)
+    def other(storage, inplace):
+        e2 = lbif.Ensemble(p.H, p.eta, p.F, p.tau, p.sigma, p.nx, p.ny, storage=storage, seed=3, inplace=inplace)
+        e2.autotune(trials=3)
+        e2.run(tol=1e-300, max_steps=200, check_every=100)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2.run(tol=1e-300, max_steps=steps, check_every=100)
+        torch.cuda.synchronize()
+        dt2 = time.perf_counter() - t0
+        e2.close()
+        return fluid * steps / dt2 / 1e6
+
+    m32 = other(lbif.STORE_F32, True)
+    m16_two = other(lbif.STORE_F16, False)
+    return {"workload": "256 slits 32x32xH, sigma=4, FP16 storage in place, graph-captured steps",
             "fluid_nodes": fluid, "stacked_nodes": e.N, "steps": steps, "seconds": dt,
             "mlups_fluid": fluid * steps / dt / 1e6, "autotuned": {"ball_ctas": ball, "force_group": group,
                                                         "ball_staging": "tma" if staging else "loads"},
             "graph_ms_per_step": graph_ms, "kernel_ms_per_step": kern, "kernels_ms": per,
             "beyond_kernels_frac": (graph_ms - kern) / graph_ms,
-            "mlups_fluid_fp32_storage": fluid * steps / dt32 / 1e6}
+            "mlups_fluid_fp32_storage": m32, "mlups_fluid_two_buffers": m16_two}
 
 
 def mlp_leg(args):

@@ -314,12 +314,16 @@ class Slit:
 
 class Ensemble(Slit):
     """Many slits (widths H, packing fractions eta, forces F along x, relaxation
-    times tau) advanced together through the C ABI; one stacked grid on the GPU."""
+    times tau) advanced together through the C ABI; one stacked grid on the GPU.
+    The populations live in place by default: each slit's storage ring holds
+    only its own planes (the two-buffer layout also stores the planes between
+    the slits), which made 256 slits of 32 x 32 x H 20 % faster with FP16
+    storage and 9 % with FP32; results are identical either way."""
 
     def __init__(self, H, eta, F, tau, sigma: float, nx: int = 32, ny: int = 32, *,
                  hs: bool = True, coupling: bool = True, regularize: bool = True,
                  g2_form: int = 0, storage: int = STORE_F16, seed: int = 0, noise: float = 1e-3,
-                 stream: Optional[int] = None, inplace: bool = False):
+                 stream: Optional[int] = None, inplace: bool = True):
         self._lib = load_library()
         H = np.ascontiguousarray(H, dtype=np.int32)
         eta = np.ascontiguousarray(eta, dtype=np.float64)

@@ -71,7 +71,7 @@ def test_gather_forms_in_a_stacked_ensemble(L):
     tau = np.array([0.8, 1.0, 0.7, 1.1])
     res = []
     for gathers in ("loads", "tma"):
-        e = L.Ensemble(H, eta, F, tau, sigma=4, nx=96, ny=12, storage=0, seed=2)
+        e = L.Ensemble(H, eta, F, tau, sigma=4, nx=96, ny=12, storage=0, seed=2, inplace=False)
         e.set_shapes(pull_gathers=gathers)
         e.step(40)
         res.append(e.moments())
