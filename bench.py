@@ -581,6 +581,7 @@ def run_ours(args, world, rank, local):
 
     f16 = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 1, False)
     inpl = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 0, True)
+    f16_inpl = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 1, True)
     sweep = leg(not args.no_sweep and storage == 0 and args.eta == 0.25, eta_sweep_leg, args, stream, peak)
     tail = leg(not args.no_tail, tail_leg, args)
     mlp = leg(not args.no_mlp, mlp_leg, args)
@@ -608,6 +609,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "storage_f16": f16,
         "storage_inplace": inpl,
+        "storage_f16_inplace": f16_inpl,
         "eta_sweep": sweep,
         "ensemble": ens,
         "tail_workload": tail,
