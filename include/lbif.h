@@ -182,7 +182,10 @@ int lbif_load(lbif_handle h, const char* path);
  * f gives the force model (its body[] is ignored); o as for lbif_create, but
  * with o->stream NULL the handle creates and owns a non-blocking stream
  * (needed for graph capture). lbif_step / lbif_moments / lbif_profiles /
- * lbif_save / lbif_load work on the stacked grid (gap planes read as 0). */
+ * lbif_save / lbif_load work on the stacked grid (gap planes read as 0).
+ * With o->inplace = 1 each slit's populations occupy only its own ring of
+ * H + 1 planes (the gap planes hold fields but no populations), which is
+ * both half the memory and the faster layout for ensembles. */
 int lbif_batch_create(lbif_handle* out, int32_t nslits, const int32_t* H, const double* eta,
                       const double* F, const double* tau, double sigma, int32_t nx, int32_t ny,
                       const lbif_force* f, const lbif_opts* o);
