@@ -117,6 +117,9 @@ def kernel_bytes(storage: int):
 # nodes of a launch). The ball kernel's dG writes stay in L2 at that size: read bytes only.
 TRAFFIC_B_PER_NODE = {0: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 209.7},
                       1: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 157.5}}
+# the in-place pull pass (FP32; the FP16 in-place populations of that capture,
+# 120 MB, nearly fit in L2, so its DRAM figure does not scale and is left out)
+TRAFFIC_INPLACE = {0: {"ball_g2": 5.8, "force": 40.9, "collide_stream": 197.1}}
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
@@ -510,7 +513,7 @@ def run_ours(args, world, rank, local):
         nx, ny, nz = (int(v) for v in args.grid.lower().split("x"))
         W = W.with_(nx=nx, ny=ny, nz=nz)
     stream = torch.cuda.current_stream()
-    g = _slit(W, storage, W.seed + rank, stream.cuda_stream)
+    g = _slit(W, storage, W.seed + rank, stream.cuda_stream, inplace=args.inplace)
     N = W.nodes
     peak, peak_kind = _peaks()
     # warm-up, then the launch shapes the library's autotuner picks on this
@@ -540,7 +543,7 @@ def run_ours(args, world, rank, local):
     dom_ms = kms[dom] / max(nl[dom], 1)
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
     step_gbs = bytes_alg(storage) * N / (ms_per_step * 1e-3) / 1e9
-    tb = TRAFFIC_B_PER_NODE.get(storage, {}).get(dom)
+    tb = (TRAFFIC_INPLACE if args.inplace else TRAFFIC_B_PER_NODE).get(storage, {}).get(dom)
 
     # end to end through the C ABI's host-pointer path: per iteration the
     # density field goes from pinned host memory through lbif_set_fields
@@ -579,9 +582,9 @@ def run_ours(args, world, rank, local):
         except Exception as e:  # reported, never hides the throughput line
             return {"error": f"{type(e).__name__}: {e}"}
 
-    f16 = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 1, False)
-    inpl = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 0, True)
-    f16_inpl = leg(not args.no_sweep and storage == 0, storage_leg, args, stream, peak, 1, True)
+    f16 = leg(not args.no_sweep and storage == 0 and not args.inplace, storage_leg, args, stream, peak, 1, False)
+    inpl = leg(not args.no_sweep and storage == 0 and not args.inplace, storage_leg, args, stream, peak, 0, True)
+    f16_inpl = leg(not args.no_sweep and storage == 0 and not args.inplace, storage_leg, args, stream, peak, 1, True)
     sweep = leg(not args.no_sweep and storage == 0 and args.eta == 0.25, eta_sweep_leg, args, stream, peak)
     tail = leg(not args.no_tail, tail_leg, args)
     mlp = leg(not args.no_mlp, mlp_leg, args)
@@ -594,7 +597,8 @@ def run_ours(args, world, rank, local):
         "data": "synthetic",
         "config": {"workload": f"slit {W.nx}x{W.ny}x{W.nz} sigma={W.sigma} eta={W.eta} tau={W.tau} "
                                f"F_e={W.body[0]} bounce-back z, periodic x,y, seeded 1e-3 noise",
-                   "storage": args.storage, "nodes": N, "pass": "pull",
+                   "storage": args.storage, "nodes": N,
+                   "pass": "pull, in place" if args.inplace else "pull",
                    "autotuned": shapes, "parallelism": f"replicas x{world}",
                    "l2": "populations (>= 1.9 GB) exceed L2; no flush",
                    "bytes_alg_per_node": bytes_alg(storage),
@@ -644,6 +648,8 @@ def main():
     ap.add_argument("--ws-heldout", type=int, default=128, help="held-out slits of the warm-start leg")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the FP16-storage record and the packing-fraction sweep")
+    ap.add_argument("--inplace", action="store_true",
+                    help="populations in one buffer (the main line's layout; default two buffers)")
     ap.add_argument("--shapes", choices=["auto", "default"], default="auto",
                     help="launch shapes: the autotuner's (auto) or the library defaults (profiler captures)")
     ap.add_argument("--grid", default=None,
